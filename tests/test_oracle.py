@@ -1,0 +1,329 @@
+"""Pins of the CPU oracle against things other than itself: the paper's worked
+examples (tests/golden), brute-force path enumeration on tiny CFGs, closed
+forms of Eq. 1/2/4/5, Theorem 1, and invariants. No GPU."""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from bruteforce import Fn, reaching as bf_reaching, sources as bf_sources, tiny_program
+from progbuild import I, counts, program, res, sample
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+ARCH = synth.default_arch()
+LAT = dict(zip(synth.OPS, ARCH[0]))
+C_EXEC, C_MEM, C_SYNC, C_CONST = 2, 3, 5, 6
+
+
+def gold(name):
+    with open(os.path.join(GOLD, name)) as f:
+        return json.load(f)
+
+
+def one_block(ins):
+    return program([([ins], [[]], [])])
+
+
+# ---------------------------------------------------------------- Sec. 2.1, Fig. 1
+def test_fig1_sampling_ratios():
+    g = gold("fig1_sampling.json")
+    prog = one_block([I("IADD", ["R1"], ["R2", "R3"]), I("EXIT")])
+    ss = []
+    for s in g["samples"]:
+        # stall samples carry a stall reason; the one sample without one is SELECTED
+        cls = (C_MEM if s["latency"] else 9) if s["stall"] else 0
+        ss.append(sample(0, 0, cls, s["latency"]))
+    cnt, bad = oracle.histogram(prog, np.array(ss, dtype=np.uint64))
+    assert bad == 0
+    R = oracle.analyze(prog, ARCH, cnt)
+    T, A, L, issued = (int(x) for x in R["totals"][0])
+    e = g["expect"]
+    assert (T, A, L) == (e["total"], e["active"], e["latency"])
+    assert T - issued == e["stall_samples"]
+    assert L / T == e["stall_ratio"] and A / T == e["active_ratio"]
+
+
+def test_histogram_exact_and_invalid():
+    prog = program([([[I("IADD", ["R1"], ["R2"]), I("IADD", ["R3"], ["R1"])]], [[]], []),
+                    ([[I("MOV", ["R1"], ["R2"])]], [[]], [])])
+    ss = [sample(0, 0, 0, 0)] * 3 + [sample(0, 1, 2, 1)] * 2 + [sample(1, 0, 11, 0)]
+    bad = [sample(2, 0, 0, 0),            # unknown kernel
+           sample(1, 1, 0, 0),            # pc past the function
+           sample(0, 0, 12, 0),           # class out of range
+           sample(0, 0, 0, 1),            # SELECTED with the latency flag
+           sample(0, 0, 3, 0) | np.uint64(5)]  # reserved bits set
+    cnt, nbad = oracle.histogram(prog, np.array(ss + bad, dtype=np.uint64))
+    assert nbad == len(bad)
+    assert cnt[0, 0, 0] == 3 and cnt[1, 2, 1] == 2 and cnt[2, 11, 0] == 1
+    assert int(cnt.sum()) == len(ss)
+
+
+def test_histogram_generated_conserves():
+    ps, _, kz = synth.workload("rodinia")
+    P = synth.make_program(ps, kz)
+    s = P.samples(200_000, invalid_ppm=20_000)
+    cnt, bad = oracle.histogram(P, s)
+    assert int(cnt.sum()) + bad == s.size
+    assert 0 < bad < s.size // 10
+    k = (s >> np.uint64(48)).astype(np.int64)
+    ok = k < P.n_functions
+    # per-kernel totals equal the number of valid samples of that kernel
+    tot = np.add.reduceat(cnt.reshape(P.n_instr, -1).sum(1), P.func_instr_off[:-1])
+    assert int(tot.sum()) <= int(ok.sum())
+
+
+# ---------------------------------------------------------------- Sec. 4, Fig. 3
+def test_fig3_barrier_dependency():
+    gold("fig3_barrier.json")
+    prog = one_block([I("LDG", ["R0"], ["R2", "R3"], wb=0), I("IADD", ["R5"], ["R6", "R7"]),
+                      I("BRA", [], [], wait=[0])])
+    cnt = counts(3, {(0, 0, 0): 5, (2, C_MEM, 0): 40, (2, C_MEM, 1): 60})
+    R = oracle.analyze(prog, ARCH, cnt)
+    b = R["blame"]
+    assert b[0, C_MEM, 0] == 40 and b[0, C_MEM, 1] == 60
+    assert b[2, C_MEM].sum() == 0
+    e = R["edges"]
+    assert list(e["i"]) == [0] and list(e["j"]) == [2]
+    assert e["flags"][0] & 2 and not e["flags"][0] & 4      # through a barrier, not a register
+
+
+# ---------------------------------------------------------------- Sec. 4, Fig. 4
+def fig4(use_guard=None, mov_between=False):
+    ins = [I("ISETP", ["P0"], ["R10", "R11"]), I("ISETP", ["P1"], ["R10", "R12"]),
+           I("MOV", ["R20"], ["R21"]), I("MOV", ["R22"], ["R21"]),
+           I("LDC", ["R0"], [], guard="!P0"),
+           I("IMAD", ["R0"], ["R4", "R5", "R6"], guard="P1"),
+           I("MOV", ["R0"] if mov_between else ["R23"], ["R21"]),
+           I("LDG", ["R0"], ["R2", "R3"], guard="P0"),
+           I("MOV", ["R24"], ["R21"]), I("MOV", ["R25"], ["R21"]),
+           I("IADD", ["R1"], ["R0", "R7"], guard=use_guard)]
+    return one_block(ins)
+
+
+def test_fig4a_predicate_coverage():
+    g = gold("fig4_blamer.json")
+    src = {s["i"]: s for s in oracle.search(fig4(), 10, res("R0"))}
+    assert sorted(src) == [4, 5, 7]                           # LDC, IMAD, LDG
+    assert {4: "LDC", 7: "LDG"}.keys() <= src.keys()
+    assert set(g["expect"]["sources_unpredicated_use"]) == {"LDG", "LDC"}
+    assert [src[i]["dmin"] for i in (7, 5, 4)] == [3, 5, 6]
+    # an unguarded def between them ends the search there
+    src = {s["i"] for s in oracle.search(fig4(mov_between=True), 10, res("R0"))}
+    assert src == {6, 7}
+    # a use guarded by P0 is covered by the @P0 def alone
+    src = {s["i"] for s in oracle.search(fig4(use_guard="P0"), 10, res("R0"))}
+    assert src == {7}
+
+
+def test_fig4cd_opcode_pruning_and_equal_shares():
+    prog = fig4()
+    cnt = counts(11, {(7, 0, 0): 10, (4, 0, 0): 20, (5, 0, 0): 7, (10, C_MEM, 0): 100, (10, C_EXEC, 1): 9})
+    R = oracle.analyze(prog, ARCH, cnt)
+    b = R["blame"]
+    # memory stalls: IMAD pruned by opcode; LDC (2x issue, 2x path) and LDG get equal shares
+    assert b[5, C_MEM].sum() == 0
+    assert b[7, C_MEM, 0] == 50 and b[4, C_MEM, 0] == 50
+    assert gold("fig4_blamer.json")["expect"]["ldc_over_ldg_share"] == b[4, C_MEM, 0] / b[7, C_MEM, 0]
+    # execution stalls: no opcode rule, all three sources share them
+    assert int(b[[4, 5, 7], C_EXEC, 1].sum()) == 9 and b[5, C_EXEC, 1] > 0
+
+
+# ---------------------------------------------------------------- pruning rules
+def test_dominator_pruning_straight_line():
+    prog = one_block([I("LDG", ["R0"], ["R2", "R3"], wb=0), I("IADD", ["R1"], ["R0", "R5"], wait=[0]),
+                      I("FFMA", ["R3"], ["R0", "R6", "R7"])])
+    s = oracle.search(prog, 2, res("R0"))
+    assert len(s) == 1 and s[0]["i"] == 0 and s[0]["dom"]       # IADD reads R0 on the only path
+    cnt = counts(3, {(2, C_MEM, 0): 30, (1, C_MEM, 1): 12, (0, 0, 0): 1})
+    R = oracle.analyze(prog, ARCH, cnt)
+    assert R["blame"][2, C_MEM, 0] == 30                         # no surviving source: stays
+    assert R["blame"][0, C_MEM, 1] == 12                         # IADD's stalls go to the LDG
+
+
+def diamond(extra_use_in_entry):
+    b0 = [I("LDG", ["R0"], ["R2", "R3"])]
+    if extra_use_in_entry:
+        b0.append(I("IADD", ["R9"], ["R0", "R5"]))
+    b0 += [I("ISETP", ["P0"], ["R5", "R6"]), I("BRA", [], [], guard="P0")]
+    b1 = [I("IADD", ["R1"], ["R0", "R5"])]
+    b2 = [I("FFMA", ["R3"], ["R0", "R6", "R7"]), I("EXIT")]
+    return program([([b0, b1, b2], [[1, 2], [2], []], [])])
+
+
+def test_dominator_pruning_needs_every_path():
+    p = diamond(False)
+    j = int(p["block_instr_off"][2])
+    s = oracle.search(p, j, res("R0"))
+    assert [(x["i"], x["dom"]) for x in s] == [(0, False)]      # the B0->B2 path avoids the IADD
+    assert s[0]["dmin"] == 3 and s[0]["dlong"] == 4
+    p = diamond(True)
+    j = int(p["block_instr_off"][2])
+    s = oracle.search(p, j, res("R0"))
+    assert [(x["i"], x["dom"]) for x in s] == [(0, True)]       # now an unguarded reader is on both
+
+
+@pytest.mark.parametrize("pad,blamed", [(3, True), (4, True), (5, False)])
+def test_latency_pruning(pad, blamed):
+    ins = [I("IMAD", ["R0"], ["R1", "R2", "R3"])] + [I("MOV", ["R9"], ["R8"])] * pad + \
+          [I("IADD", ["R4"], ["R0", "R5"])]
+    prog = one_block(ins)
+    j = len(ins) - 1
+    cnt = counts(len(ins), {(j, C_EXEC, 0): 10, (0, 0, 0): 3})
+    R = oracle.analyze(prog, ARCH, cnt)
+    assert pad + 1 <= LAT["IMAD"] or not blamed
+    assert (R["blame"][0, C_EXEC, 0] == 10) == blamed
+    assert (R["blame"][j, C_EXEC, 0] == 10) == (not blamed)
+
+
+def test_loop_carried_longest_path():
+    # B0 entry; B1 loop (body: use of R0, then later def of R0); B2 exit.
+    b0 = [I("MOV", ["R0"], ["R1"])]
+    b1 = [I("IADD", ["R2"], ["R0", "R3"]), I("MOV", ["R7"], ["R8"]), I("MOV", ["R0"], ["R2"]),
+          I("ISETP", ["P0"], ["R2", "R3"]), I("BRA", [], [], guard="P0")]
+    b2 = [I("EXIT")]
+    p = program([([b0, b1, b2], [[1], [2, 1], []], [(1, [1], -1)])])
+    s = {x["i"]: x for x in oracle.search(p, 1, res("R0"))}
+    assert sorted(s) == [0, 3]
+    assert (s[0]["dmin"], s[0]["K"], s[0]["dlong"]) == (1, 0, 1)
+    assert (s[3]["dmin"], s[3]["K"], s[3]["dlong"]) == (3, 1, 3)   # def -> ISETP -> BRA -> back edge -> use
+
+
+# ---------------------------------------------------------------- brute force
+@pytest.mark.parametrize("seed", range(40))
+def test_sources_match_bruteforce(seed):
+    P = tiny_program(seed, n_instr=22 + seed % 15, n_loops=seed % 3, guard_pct=20 + 5 * (seed % 6))
+    assert oracle.check_loops(P, 0) == 0
+    F = Fn(P, 0)
+    n = 0
+    for j in range(P.n_instr):
+        for r in sorted(set(F.uses(j))):
+            want = bf_sources(F, j, r)
+            got = {s["i"]: dict(dmin=s["dmin"], K=s["K"], dlong=s["dlong"], dom=s["dom"])
+                   for s in oracle.search(P, j, r)}
+            assert got == want, (seed, j, r)
+            n += len(want)
+    assert n > 0
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_reaching_match_bruteforce(seed):
+    P = tiny_program(100 + seed, n_instr=40, n_loops=1 + seed % 2, guard_pct=30)
+    rin, rout = oracle.reaching(P)
+    bin_, bout = bf_reaching(Fn(P, 0))
+    assert (rin == bin_).all() and (rout == bout).all()
+
+
+def test_generated_loops_are_natural_loops():
+    for name in ("plain", "rodinia"):
+        ps, _, kz = synth.workload(name)
+        P = synth.make_program(ps, kz)
+        assert all(oracle.check_loops(P, f) == 0 for f in range(P.n_functions))
+    ps = synth.batched_params(40, np.random.default_rng(1), 1)
+    P = synth.make_program(ps)
+    assert all(oracle.check_loops(P, f) == 0 for f in range(P.n_functions))
+
+
+# ---------------------------------------------------------------- Eq. 1
+def _apportion_prog(dists, issues, S):
+    """One use with len(dists) unguarded-reader-free sources at the given distances."""
+    n = max(dists) + 1
+    ins = [I("MOV", ["R30"], ["R31"]) for _ in range(n)]
+    srcs = []
+    for t, d in enumerate(dists):
+        ins[n - 1 - d] = I("LDG", [f"R{t}"], ["R20", "R21"])
+        srcs.append(n - 1 - d)
+    ins[n - 1] = I("FFMA", ["R29"], [f"R{t}" for t in range(len(dists))])
+    ent = {(x, 0, 0): v for x, v in zip(srcs, issues) if v}
+    ent[(n - 1, C_MEM, 0)] = S
+    return one_block(ins), counts(n, ent), srcs
+
+
+def test_eq1_largest_remainder_rule():
+    # equal weights: floor(7/3) = 2 each, the leftover unit goes to the lowest def index
+    prog, cnt, srcs = _apportion_prog([1, 2, 3], [4, 8, 12], 7)   # issue/dist = 4 for all three
+    R = oracle.analyze(prog, ARCH, cnt)
+    sh = {x: int(R["blame"][x, C_MEM, 0]) for x in srcs}
+    assert sorted(sh.values()) == [2, 2, 3] and sh[min(srcs)] == 3
+    # proportional case: weights 10/2 : 60/4 = 1:3 split 100 as 25:75
+    prog, cnt, srcs = _apportion_prog([2, 4], [10, 60], 100)
+    R = oracle.analyze(prog, ARCH, cnt)
+    assert [int(R["blame"][x, C_MEM, 0]) for x in srcs] == [25, 75]
+    # no issued samples anywhere: weight by 1 / longest path (2:1)
+    prog, cnt, srcs = _apportion_prog([1, 2], [0, 0], 30)
+    R = oracle.analyze(prog, ARCH, cnt)
+    assert [int(R["blame"][x, C_MEM, 0]) for x in srcs] == [20, 10]
+
+
+# ---------------------------------------------------------------- Sec. 5
+def test_eq2_eq4_closed_forms():
+    ins = [I("LDG", ["R0"], ["R2", "R3"]), I("MOV", ["R9"], ["R8"]), I("FFMA", ["R1"], ["R0", "R5", "R6"])]
+    prog = one_block(ins)
+    cnt = counts(3, {(0, 0, 0): 20, (1, 1, 0): 15, (1, 1, 1): 10, (2, C_MEM, 1): 40, (2, 9, 0): 15})
+    R = oracle.analyze(prog, ARCH, cnt)
+    T, A, L, _ = (int(x) for x in R["totals"][0])
+    assert (T, A, L) == (100, 50, 50)
+    sp = R["speedup"][0]
+    assert sp[2] == 100 / (100 - 25)                         # Function Split, Eq. 2: INST_FETCH
+    assert sp[7] == 100 / (100 - min(50, 40))                # Code Reordering, Eq. 4
+    assert R["M"][0][7] == 40
+    assert list(R["rank"][0][:2]) == [7, 2]
+    hot = R["hot"][0][7][0]
+    assert list(hot[[0, 1, 4, 5]]) == [0, 2, 2, 40]          # def pc, use pc, distance, samples
+
+
+def test_theorem1_latency_hiding_bound():
+    ps, _, kz = synth.workload("rodinia")
+    P = synth.make_program(ps[:8], kz)
+    for seed in range(3):
+        cnt, _ = oracle.histogram(P, P.samples(300_000, seed=seed))
+        R = oracle.analyze(P, ARCH, cnt)
+        assert (R["speedup"][:, 6] <= 2.0).all() and (R["speedup"][:, 7] <= 2.0).all()
+        assert (R["loop_S"] <= 2.0).all()
+        T = R["totals"][:, 0].astype(float)
+        A = R["totals"][:, 1].astype(float)
+        M = R["M"][:, 7].astype(float)
+        ok = T > 0
+        assert np.array_equal(R["speedup"][ok, 7], T[ok] / (T[ok] - np.minimum(A[ok], M[ok])))
+
+
+def test_eq5_scope_nesting():
+    # loop scopes: A of an outer loop includes the inner loop's active samples
+    ps, _, kz = synth.workload("rodinia")
+    P = synth.make_program(ps[:6], kz)
+    cnt, _ = oracle.histogram(P, P.samples(300_000, seed=4))
+    R = oracle.analyze(P, ARCH, cnt)
+    par = P.loop_parent
+    for l in range(P.n_loops):
+        if par[l] >= 0:
+            assert R["loop_A"][par[l]] >= R["loop_A"][l]
+            assert R["loop_ML"][par[l]] >= R["loop_ML"][l]
+
+
+# ---------------------------------------------------------------- invariants
+@pytest.mark.parametrize("name,nfun,ns", [("plain", 1, 100_000), ("rodinia", 20, 400_000)])
+def test_blame_invariants(name, nfun, ns):
+    ps, _, kz = synth.workload(name)
+    P = synth.make_program(ps[:nfun], kz)
+    cnt, _ = oracle.histogram(P, P.samples(ns))
+    R = oracle.analyze(P, ARCH, cnt)
+    # conservation per (class, latency flag)
+    assert np.array_equal(R["blame"].sum(0), cnt.sum(0))
+    e = R["edges"]
+    assert len(e["j"]) > 0
+    for t in range(len(e["j"])):
+        i, j = int(e["i"][t]), int(e["j"][t])
+        di = {int(x) & 0x1FF for x in P.def_res[P.def_off[i]:P.def_off[i + 1]]}
+        uj = {int(x) & 0x1FF for x in P.use_res[P.use_off[j]:P.use_off[j + 1]]}
+        assert di & uj                                        # the blamed def writes what j reads
+        assert e["dmin"][t] <= ARCH[0][P.opclass[i]]          # latency rule holds on survivors
+        assert 1 <= e["dmin"][t] <= e["dlong"][t]
+    # edge shares add up to the blame moved off each use
+    sh = e["share"].sum(0)
+    assert int(sh.sum()) <= int(cnt[:, [2, 3, 5, 6], :].sum())
+    # sorted by (use, def)
+    key = e["j"].astype(np.int64) * (1 << 32) + e["i"]
+    assert (np.diff(key) > 0).all()
