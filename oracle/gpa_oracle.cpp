@@ -215,7 +215,11 @@ struct SrcRes {
 // immediate source; the path stops once S contains it. Then distances, back
 // edge counts, longest paths and the single-k dominator rule are computed over
 // the set of source paths.
-std::vector<SrcRes> search(const Fn& F, int j, int r) {
+//
+// With `latency` given, the dominator rule is only evaluated for sources whose
+// shortest path passes the latency rule (the others are dropped by rule 3
+// whatever rule 2 says); without it, for every source.
+std::vector<SrcRes> search(const Fn& F, int j, int r, const int32_t* latency = nullptr) {
   const OProg& P = *F.P;
   const int gj = P.guard[F.i0 + j];
   std::map<std::pair<int, uint16_t>, int> id;
@@ -316,12 +320,18 @@ std::vector<SrcRes> search(const Fn& F, int j, int r) {
   // Dominator-based pruning: remove i -> j if an unguarded instruction k
   // (k not i, not j) that uses r lies on every source path from i to j, i.e.
   // removing k's states disconnects j from every source state of i.
+  auto needs_dom = [&](const SrcRes& R) {
+    return !R.dom && (!latency || R.dmin <= latency[P.opclass[F.i0 + R.i]]);
+  };
   std::set<int> cand;
   for (int s = 0; s < ns; ++s) {
     int k = sx[s];
     if (k != j && P.guard[F.i0 + k] == 0 && uses(P, F.i0 + k, r)) cand.insert(k);
   }
   for (int k : cand) {
+    bool any = false;
+    for (auto& kv : src) any = any || needs_dom(kv.second);
+    if (!any) break;
     std::vector<char> seen(ns, 0);
     std::deque<int> q;
     for (auto [s, bk] : roots) if (sx[s] != k && !seen[s]) { seen[s] = 1; q.push_back(s); }
@@ -331,7 +341,8 @@ std::vector<SrcRes> search(const Fn& F, int j, int r) {
     }
     std::set<int> still;
     for (int s = 0; s < ns; ++s) if (seen[s] && is_occ(s)) still.insert(sx[s]);
-    for (auto& kv : src) if (kv.first != k && !still.count(kv.first)) kv.second.dom = true;
+    for (auto& kv : src)
+      if (needs_dom(kv.second) && kv.first != k && !still.count(kv.first)) kv.second.dom = true;
   }
   std::vector<SrcRes> out;
   for (auto& kv : src) out.push_back(kv.second);
@@ -446,7 +457,7 @@ void analyze_function(const OProg& P, const OArch& arch, const uint64_t* cnt, in
     std::map<int, Edge> m;
     for (int e = P.use_off[i0 + j]; e < P.use_off[i0 + j + 1]; ++e) {
       int r = P.use_res[e] & 0x1FF;
-      for (const SrcRes& s : search(F, j, r)) {
+      for (const SrcRes& s : search(F, j, r, arch.latency)) {
         int op = P.opclass[i0 + s.i];
         bool survive = !s.dom && s.dmin <= arch.latency[op];  // dominator and latency pruning
         if (!survive) continue;
@@ -660,22 +671,37 @@ int oracle_reaching(const OProg* P, int32_t f_lo, int32_t f_hi, uint32_t* rin, u
   const int bb0 = P->func_block_off[f_lo];
   for (int f = f_lo; f < f_hi; ++f) {
     const int b0 = P->func_block_off[f], b1 = P->func_block_off[f + 1];
+    const int i0 = P->func_instr_off[f], i1 = P->func_instr_off[f + 1];
     const int nbf = b1 - b0;
-    using DefSet = std::map<int, std::set<int>>;  // resource -> def sites (global instruction)
-    std::vector<DefSet> IN(nbf), OUT(nbf);
+    // Def sites of the function: (instruction, resource), numbered in order.
+    std::vector<int> site_res;
+    std::vector<int> site_first(i1 - i0 + 1, 0);
+    for (int x = i0; x < i1; ++x) {
+      site_first[x - i0] = (int)site_res.size();
+      for (int e = P->def_off[x]; e < P->def_off[x + 1]; ++e) site_res.push_back(P->def_res[e] & 0x1FF);
+    }
+    site_first[i1 - i0] = (int)site_res.size();
+    const int ns = (int)site_res.size();
+    const int nw = (ns + 63) / 64;
+    std::vector<std::vector<uint64_t>> of_res(kNumRes, std::vector<uint64_t>(nw, 0));  // all sites of r
+    for (int t = 0; t < ns; ++t) of_res[site_res[t]][t >> 6] |= 1ULL << (t & 63);
+    using Bits = std::vector<uint64_t>;
+    std::vector<Bits> IN(nbf, Bits(nw, 0)), OUT(nbf, Bits(nw, 0));
     std::vector<std::vector<int>> pred(nbf), succ(nbf);
     for (int b = 0; b < nbf; ++b)
       for (int e = P->succ_off[b0 + b]; e < P->succ_off[b0 + b + 1]; ++e) {
         succ[b].push_back(P->succ[e] - b0);
         pred[P->succ[e] - b0].push_back(b);
       }
-    auto transfer = [&](int b, const DefSet& in) {
-      DefSet cur = in;
+    // Transfer through a block, instruction by instruction: an unguarded def
+    // kills every other def site of its resource; every def generates its site.
+    auto transfer = [&](int b, const Bits& in) {
+      Bits cur = in;
       for (int x = P->block_instr_off[b0 + b]; x < P->block_instr_off[b0 + b + 1]; ++x)
-        for (int e = P->def_off[x]; e < P->def_off[x + 1]; ++e) {
-          int r = P->def_res[e] & 0x1FF;
-          if (P->guard[x] == 0) cur[r].clear();
-          cur[r].insert(x);
+        for (int t = site_first[x - i0]; t < site_first[x - i0 + 1]; ++t) {
+          if (P->guard[x] == 0)
+            for (int w = 0; w < nw; ++w) cur[w] &= ~of_res[site_res[t]][w];
+          cur[t >> 6] |= 1ULL << (t & 63);
         }
       return cur;
     };
@@ -684,22 +710,26 @@ int oracle_reaching(const OProg* P, int32_t f_lo, int32_t f_hi, uint32_t* rin, u
     for (int b = 0; b < nbf; ++b) wl.push_back(b);
     while (!wl.empty()) {
       int b = wl.front(); wl.pop_front(); inwl[b] = 0;
-      DefSet in;
+      Bits in(nw, 0);
       for (int p : pred[b])
-        for (auto& kv : OUT[p]) in[kv.first].insert(kv.second.begin(), kv.second.end());
+        for (int w = 0; w < nw; ++w) in[w] |= OUT[p][w];
       IN[b] = in;
-      DefSet out = transfer(b, in);
+      Bits out = transfer(b, in);
       if (out != OUT[b]) {
         OUT[b] = out;
-        for (int s : succ[b]) if (!inwl[s]) { inwl[s] = 1; wl.push_back(s); }
+        for (int s2 : succ[b]) if (!inwl[s2]) { inwl[s2] = 1; wl.push_back(s2); }
       }
     }
+    // Resource projection: r is set iff some def site of r is in the set.
     for (int b = 0; b < nbf; ++b) {
       uint32_t* wi = rin + (size_t)(b0 + b - bb0) * 9;
       uint32_t* wo = rout + (size_t)(b0 + b - bb0) * 9;
       std::memset(wi, 0, 36); std::memset(wo, 0, 36);
-      for (auto& kv : IN[b]) if (!kv.second.empty()) wi[kv.first >> 5] |= 1u << (kv.first & 31);
-      for (auto& kv : OUT[b]) if (!kv.second.empty()) wo[kv.first >> 5] |= 1u << (kv.first & 31);
+      for (int t = 0; t < ns; ++t) {
+        const int r = site_res[t];
+        if (IN[b][t >> 6] >> (t & 63) & 1) wi[r >> 5] |= 1u << (r & 31);
+        if (OUT[b][t >> 6] >> (t & 63) & 1) wo[r >> 5] |= 1u << (r & 31);
+      }
     }
   }
   return 0;
