@@ -1,0 +1,330 @@
+#!/usr/bin/env python3
+"""Throughput of the GPA stall-blame path on GB300.
+
+A step is one pass of the whole path over one batch: zero the counters,
+aggregate the batch's packed PC samples (Sec. 2.1), reaching definitions and
+backward slicing, pruning and Eq. 1 apportioning (Sec. 4), roll-up,
+optimizer matching and estimators (Sec. 5). The default workload is the
+batched uneven one: 2,000 synthetic SASS-like functions of 50-20,000
+instructions (log-uniform) and 5e8 packed samples (4 GB, larger than L2, so
+no L2 flush is needed between steps).
+
+  value  blamed PC samples/s with samples and program resident in HBM
+  e2e    the same through the C ABI from pinned host memory: host->device copy
+         of the samples inside the timed region, advice copied back to the host
+Prints one JSON line on rank 0. Under torchrun every rank processes its own
+batch (seeded by rank) on its own GPU with no data-path collective (weak scaling).
+`--impl reference` times the CPU oracle on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "blamed PC samples/s & analysed instrs/s (batched vs plain); p99 advise latency"
+UNIT = "samples/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gpa", choices=["gpa", "reference"])
+    ap.add_argument("--workload", default="batched", choices=["plain", "rodinia", "batched", "large"])
+    ap.add_argument("--samples", type=int, default=0, help="override the workload's sample count")
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-functions", type=int, default=40, help="functions in the CPU-baseline sample")
+    return ap.parse_args()
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def traffic_record(kernel: str):
+    """Per-launch DRAM bytes of `kernel` from profiles/traffic.json, or None if the
+    kernel source changed since the counters were taken."""
+    import hashlib
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            rec = json.load(f)[kernel]
+        with open(os.path.join(ROOT, rec["source"]), "rb") as f:
+            h = hashlib.sha256(f.read()).hexdigest()[:16]
+        return rec if h == rec["source_sha"] else None
+    except Exception:
+        return None
+
+
+class Clocks:
+    """nvidia-smi sampled every 200 ms while the timed region runs."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index, self.proc, self.path = index, None, None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        try:
+            with open(self.path) as f:
+                for line in f:
+                    v = [x.strip() for x in line.split(",")]
+                    if len(v) >= 8 and v[0].replace(".", "").isdigit():
+                        rows.append(v)
+        except Exception:
+            pass
+        finally:
+            if self.path:
+                os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        sm = [float(r[0]) for r in rows]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[4 + k].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": float(rows[0][1]), "reasons": reasons,
+                "power_w_max": max(float(r[2]) for r in rows if r[2].replace(".", "").isdigit()),
+                "samples": len(rows)}
+
+
+def make_workload(name: str, seed: int, n_override: int = 0):
+    ps, ns, kz = synth.workload(name, seed=seed)
+    P = synth.make_program(ps, kz, kseed=seed)
+    return P, (n_override or ns)
+
+
+def cpu_sample(P, n_total: int, k_funcs: int, seed: int):
+    """The oracle's bounded sample: the first k_funcs functions with all their samples
+    from the first min(n_total, 5e7) samples of the stream."""
+    m = min(n_total, 50_000_000)
+    s = P.samples(m, seed=seed)
+    k = (s >> np.uint64(48)).astype(np.int64)
+    sub = np.ascontiguousarray(s[k < k_funcs])
+    return sub, m
+
+
+def run_oracle_once(P, sub, k_funcs):
+    import oracle
+    arch = synth.default_arch()
+    t0 = time.perf_counter()
+    cnt, _ = oracle.histogram(P, sub)
+    oracle.analyze(P, arch, cnt, 0, k_funcs)
+    return time.perf_counter() - t0
+
+
+def reference_arm(a):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    P, n = make_workload(a.workload, a.seed, a.samples)
+    k_funcs = min(P.n_functions, max(1, a.cpu_functions // 4))
+    sub, m = cpu_sample(P, n, k_funcs, a.seed)
+    for _ in range(a.warmup):
+        run_oracle_once(P, sub, k_funcs)
+    ts = [run_oracle_once(P, sub, k_funcs) for _ in range(a.steps)]
+    t = statistics.mean(ts)
+    v = sub.size / t
+    instr = int(P.func_instr_off[k_funcs])
+    sample = (f"functions 0..{k_funcs - 1} of the {a.workload} workload ({instr} instructions) with their "
+              f"{sub.size} samples from the first {m} of the stream")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": a.gpus, "steps": a.steps,
+        "warmup": a.warmup, "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": {"workload": a.workload, "sample": sample},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    a = parse()
+    if a.impl == "reference":
+        return reference_arm(a)
+    import torch
+    import torch.distributed as dist
+
+    import paper_2009_04061_gb300 as gpa
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    P, n = make_workload(a.workload, a.seed + rank, a.samples)
+    host = torch.empty(n, dtype=torch.int64).pin_memory()
+    P.samples(n, seed=a.seed + rank, out=host.numpy().view(np.uint64))
+    d = host.to(dev, non_blocking=False)
+    ctx = gpa.Context(synth.default_arch())
+    prog = ctx.load_program(P)
+    stream = torch.cuda.current_stream(dev)
+
+    def step(ev=None):
+        if ev:
+            ev[0].record(stream)
+        prog.reset(stream)
+        prog.ingest(d, stream=stream)
+        if ev:
+            ev[1].record(stream)
+        prog.blame(stream)
+        if ev:
+            ev[2].record(stream)
+        prog.advise(fetch=False, stream=stream)
+        if ev:
+            ev[3].record(stream)
+
+    for _ in range(a.warmup):
+        step()
+    st, info = prog.status(stream)
+    if st != 0:
+        raise SystemExit(f"device status {st} after warm-up: {info}")
+    cnt, bad = prog.counts(stream)
+    assert int(cnt.sum()) + bad == n, "counts do not add up to the samples ingested"
+
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(a.steps)]
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    l0 = ctx.launches()
+    with Clocks(local) as clk:
+        start.record(stream)
+        for k in range(a.steps):
+            step(evs[k])
+        end.record(stream)
+        torch.cuda.synchronize(dev)
+    launches = ctx.launches() - l0
+    ms = start.elapsed_time(end) / a.steps
+    phase = {
+        "ingest_ms": statistics.mean(e[0].elapsed_time(e[1]) for e in evs),
+        "blame_ms": statistics.mean(e[1].elapsed_time(e[2]) for e in evs),
+        "advise_ms": statistics.mean(e[2].elapsed_time(e[3]) for e in evs),
+    }
+    if world > 1:
+        t = torch.tensor([ms], dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        dist.barrier()
+    clocks = clk.summary()
+    value = world * n / (ms / 1e3)
+    instr_per_s = world * P.n_instr / (ms / 1e3)
+
+    # Roofline of the dominant kernel. The aggregation reads 8 algorithmic bytes per
+    # sample; the reset memset that shares its phase is timed apart here.
+    hbm_peak, peak_kind = load_peaks()
+    e_a, e_b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    hist_ms = []
+    for _ in range(3):
+        prog.reset(stream)
+        e_a.record(stream)
+        prog.ingest(d, stream=stream)
+        e_b.record(stream)
+        torch.cuda.synchronize(dev)
+        hist_ms.append(e_a.elapsed_time(e_b))
+    t_hist = statistics.median(hist_ms) / 1e3
+    achieved = 8.0 * n / t_hist / 1e9
+    tr = traffic_record("k_histogram")
+    roofline = {"kernel": "k_histogram", "bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                "frac": achieved / hbm_peak, "peak_kind": f"{peak_kind} (copy bandwidth)",
+                "traffic": (tr["dram_bytes_per_sample"] * n) if tr else None,
+                "algorithmic_bytes": 8 * n, "launch_ms": t_hist * 1e3}
+
+    # End to end through the C ABI from pinned host memory.
+    e2e = None
+    if not a.no_e2e:
+        for _ in range(2):
+            prog.reset(stream)
+            prog.ingest_host(host, stream=stream)
+            prog.blame(stream)
+            adv = prog.advise(fetch=True, stream=stream)
+        d2h = sum(v.nbytes for v in adv.values())
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        reps = max(1, min(a.steps, 5))
+        for _ in range(reps):
+            prog.reset(stream)
+            prog.ingest_host(host, stream=stream)
+            prog.blame(stream)
+            adv = prog.advise(fetch=True, stream=stream)  # synchronizes the stream
+        te = (time.perf_counter() - t0) / reps
+        if world > 1:
+            t = torch.tensor([te], dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            te = float(t.item())
+        e2e = {"value": world * n / te, "unit": UNIT, "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": d2h,
+               "ms_per_step": te * 1e3}
+
+    cpu = None
+    if rank == 0 and world == 1 and not a.no_cpu_baseline:
+        k_funcs = min(P.n_functions, a.cpu_functions)
+        sub, m = cpu_sample(P, n, k_funcs, a.seed)
+        t = run_oracle_once(P, sub, k_funcs)
+        cpu = {"value": sub.size / t, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"functions 0..{k_funcs - 1} ({int(P.func_instr_off[k_funcs])} instructions) with their "
+                         f"{sub.size} samples from the first {m} of the stream; {t:.1f} s single-threaded"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
+            "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "int64", "data": "synthetic",
+            "config": {"workload": a.workload, "functions": P.n_functions, "instructions": P.n_instr,
+                       "blocks": P.n_blocks, "loops": P.n_loops, "samples_per_gpu": n,
+                       "sample_bytes_per_gpu": 8 * n, "l2": "inputs (samples) larger than L2, no flush",
+                       "parallelism": f"replicas x{world}, no collective on the data path"},
+            "analysed_instrs_per_s": instr_per_s, "phases_ms": phase,
+            "general_searches": info["general_searches"], "gpu_launches": launches,
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    prog.unload()
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,261 @@
+/*
+ * gpa.h — C ABI of the GB300-native GPA stall-blame library (libgpa.so).
+ *
+ * The library turns packed PC samples into attributed stall blame and
+ * speedup advice, following Zhou et al., "GPA: A GPU Performance Advisor
+ * Based on Instruction Sampling": sample aggregation (Sec. 2.1), backward
+ * slicing over registers, predicates and virtual barrier registers with
+ * predicate coverage (Sec. 4), opcode/dominator/latency pruning and the
+ * apportioning of Eq. 1 (Sec. 4), the detailed dependency classes (Sec. 4,
+ * Fig. 6), the code optimizers of Table 2 and the estimators of Eq. 2, 4 and 5
+ * (Sec. 5). Every step runs in CUDA kernels on the current device; there is
+ * no CPU fallback.
+ *
+ * Conventions for every entry point:
+ *  - Return value: GPA_OK (0) or a negative gpa_status. Argument and program
+ *    validation errors are returned synchronously and leave all state
+ *    unchanged. CUDA runtime failures return GPA_ERR_CUDA.
+ *  - Device-side anomalies (invalid samples, iteration or capacity limits
+ *    reached inside a kernel) never trap: kernels record them in a per-program
+ *    status word that gpa_sync_status() reads.
+ *  - "host" pointers are ordinary CPU memory; "device" pointers are CUDA
+ *    device memory of the current device. Pinned host memory makes the host
+ *    copies asynchronous.
+ *  - gpa_stream is a cudaStream_t (NULL = legacy default stream). Work is
+ *    enqueued on it and completes asynchronously unless stated otherwise.
+ *  - A context and its programs are not thread safe: serialize calls on one
+ *    gpa_ctx from the host.
+ */
+#ifndef GPA_H_
+#define GPA_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct gpa_ctx gpa_ctx;
+typedef int32_t gpa_status;
+typedef uint32_t gpa_pid;
+typedef void* gpa_stream;
+
+enum {
+  GPA_OK = 0,
+  GPA_ERR_INVALID_ARG = -1,      /* bad pointer, size or handle */
+  GPA_ERR_INVALID_PROGRAM = -2,  /* program arrays violate the format below */
+  GPA_ERR_CUDA = -3,             /* a CUDA runtime call failed */
+  GPA_ERR_NOT_CONVERGED = -4,    /* reaching-definitions sweeps hit their limit */
+  GPA_ERR_CAPACITY = -5,         /* a per-search or per-use capacity was exceeded */
+  GPA_ERR_TIMEOUT = -6,          /* a bounded device-side wait gave up */
+  GPA_ERR_NO_PROGRAM = -7,       /* pid is not loaded */
+  GPA_ERR_OOM = -8               /* device allocation failed or budget exceeded */
+};
+
+#define GPA_NUM_RES 268      /* R0..R254 = 0..254, P0..P6 = 255..261, B0..B5 = 262..267 */
+#define GPA_NUM_CLASSES 12   /* stall reasons, see below */
+#define GPA_NUM_OPT 8        /* optimizers, see below */
+#define GPA_MAX_OPCLASSES 64
+
+/* Stall reasons (class field of a sample). Sec. 4 names memory dependency,
+ * execution dependency and synchronization as the reasons caused by other
+ * instructions; the list follows the public CUPTI PC-sampling reasons. */
+enum {
+  GPA_SELECTED = 0, GPA_INST_FETCH = 1, GPA_EXEC_DEPENDENCY = 2, GPA_MEMORY_DEPENDENCY = 3,
+  GPA_TEXTURE = 4, GPA_SYNC = 5, GPA_CONSTANT_MEMORY_DEPENDENCY = 6, GPA_PIPE_BUSY = 7,
+  GPA_MEMORY_THROTTLE = 8, GPA_NOT_SELECTED = 9, GPA_OTHER = 10, GPA_SLEEPING = 11
+};
+
+/* Optimizers of Table 2 (code optimizers), in result order. */
+enum {
+  GPA_OPT_REGISTER_REUSE = 0, GPA_OPT_STRENGTH_REDUCTION = 1, GPA_OPT_FUNCTION_SPLIT = 2,
+  GPA_OPT_FAST_MATH = 3, GPA_OPT_WARP_BALANCE = 4, GPA_OPT_MEMORY_TRANSACTION_REDUCTION = 5,
+  GPA_OPT_LOOP_UNROLLING = 6, GPA_OPT_CODE_REORDERING = 7
+};
+
+/* Opcode-class property bits of gpa_arch_desc.flags. */
+enum {
+  GPA_F_MEM = 1,         /* memory instruction: may take memory-dependency blame (Sec. 4 rule 1) */
+  GPA_F_SYNC = 2,        /* synchronization instruction: may take sync blame (Sec. 4 rule 1) */
+  GPA_F_GLOBAL = 4,      /* global memory (detailed class, Memory Transaction Reduction) */
+  GPA_F_LOCAL = 8,       /* local memory (detailed class, Register Reuse) */
+  GPA_F_CONST = 16,      /* constant memory (detailed class) */
+  GPA_F_SHARED = 32,     /* shared memory (detailed execution-dependency class) */
+  GPA_F_LONG_ARITH = 64, /* long-latency arithmetic (Strength Reduction) */
+  GPA_F_VARLAT = 128     /* variable latency (write-after-read detection) */
+};
+
+/* Architecture table (Sec. 3 "Architectural features"; Sec. 4 latency rule).
+ * latency[op]: instructions a def of opcode class op needs before its result
+ * is ready; an edge whose shortest path is longer is pruned. Both arrays are
+ * host memory of n_opclasses entries, copied by gpa_create. */
+typedef struct {
+  int32_t n_opclasses;       /* 1..GPA_MAX_OPCLASSES */
+  const int32_t* latency;    /* host, >= 0 */
+  const uint32_t* flags;     /* host, GPA_F_* bits */
+} gpa_arch_desc;
+
+typedef struct {
+  int32_t max_fixpoint_sweeps;  /* reaching-definitions sweep limit; 0 = 64 */
+  int32_t max_search_nodes;     /* (block, predicate-set) nodes per general search; 0 = 65536 */
+  int32_t search_slots;         /* concurrent first-tier general searches; 0 = 32 per SM */
+  int32_t max_sources_per_use;  /* distinct sources merged per stalled use; 0 = 64 (max 64) */
+  int32_t small_search_nodes;   /* nodes per first-tier search slot; 0 = 512. A search that outgrows
+                                   it is redone in a max_search_nodes slot (one slot per SM) */
+  int32_t reserved[3];          /* must be 0 */
+} gpa_options;
+
+/* A program: n_functions functions laid out one after another. All arrays are
+ * host memory, read during gpa_load_program and copied; the caller may free
+ * them on return. Indices are global (over the whole program), int32 unless
+ * noted.
+ *  func_instr_off[n_functions+1], func_block_off[n_functions+1],
+ *  func_loop_off[n_functions+1]   ranges of each function's instructions,
+ *                                 blocks and loops (pc = index - func_instr_off[f]).
+ *  block_instr_off[n_blocks+1]    instructions of block b; every block has at least one.
+ *  succ_off[n_blocks+1], succ[n_succ]  CFG successors (blocks of the same function).
+ *                                 Block order: an edge u->v with v > u is a forward edge;
+ *                                 an edge with v <= u must go to the header of a loop
+ *                                 that contains u (a back edge). Every block must be
+ *                                 reachable from its function's first block.
+ *  opclass[n_instr] (uint8)       opcode class, < n_opclasses of the architecture table.
+ *  guard[n_instr] (uint8)         guard literal: 0 none, 1+i = @Pi, 8+i = @!Pi (i < 7).
+ *  iflags[n_instr] (uint8)        bit 0: instruction belongs to a math-library routine.
+ *  line[n_instr]                  source line id, < n_lines.
+ *  def_off[n_instr+1], def_res[n_def] (uint16)  resources written: resource | kind << 12,
+ *                                 kind 1 = write barrier, 2 = read barrier (B resources only).
+ *  use_off[n_instr+1], use_res[n_use] (uint16)  resources read: source registers, the guard
+ *                                 predicate, barriers in the wait mask. No duplicates in a list.
+ *  block_loop[n_blocks]           innermost loop containing the block, or -1.
+ *  loop_parent[n_loops]           enclosing loop or -1; loop_header[n_loops] its header block.
+ * Limits: n_functions < 65536, instructions per function < 2^24. */
+typedef struct {
+  int32_t n_functions, n_instr, n_blocks, n_loops, n_lines;
+  int32_t n_succ, n_def, n_use;
+  const int32_t* func_instr_off;
+  const int32_t* func_block_off;
+  const int32_t* func_loop_off;
+  const int32_t* block_instr_off;
+  const int32_t* succ_off;
+  const int32_t* succ;
+  const uint8_t* opclass;
+  const uint8_t* guard;
+  const uint8_t* iflags;
+  const int32_t* line;
+  const int32_t* def_off;
+  const uint16_t* def_res;
+  const int32_t* use_off;
+  const uint16_t* use_res;
+  const int32_t* block_loop;
+  const int32_t* loop_parent;
+  const int32_t* loop_header;
+} gpa_program_desc;
+
+/* Advice destination (host memory); any NULL field is skipped.
+ *  totals[n_functions*4]           T, A (active), L (latency), issued samples (Sec. 2.1, 5.2).
+ *  matched[n_functions*8]          matched samples M (Eq. 2) or M^L (Eq. 4) per optimizer.
+ *  speedup[n_functions*8]          Eq. 2 for optimizers 0-5, Eq. 4 for 6-7; T = 0 gives 1.0,
+ *                                  T = M gives +inf.
+ *  rank[n_functions*8]             optimizer ids by speedup, descending (ties: lower id).
+ *  n_hot[n_functions*8]            hotspots filled (0..5).
+ *  hot[n_functions*8*5*6]          per hotspot: def pc, use pc, def line, use line,
+ *                                  distance (shortest path), matched samples; -1 when unused.
+ *  loop_active[n_loops], loop_matched[n_loops], loop_speedup[n_loops]  Eq. 5 per loop scope.
+ *  line_stall[n_lines], line_latency[n_lines]  blamed stall samples per source line and their
+ *                                  latency-sample part. */
+typedef struct {
+  uint64_t* totals;
+  uint64_t* matched;
+  double* speedup;
+  int32_t* rank;
+  int32_t* n_hot;
+  int64_t* hot;
+  uint64_t* loop_active;
+  uint64_t* loop_matched;
+  double* loop_speedup;
+  uint64_t* line_stall;
+  uint64_t* line_latency;
+} gpa_advice;
+
+const char* gpa_status_string(gpa_status s);
+
+/* Fills *arch with the library's default table (host pointers to static
+ * storage): opcode classes IADD, IMAD, FFMA, ISETP, MOV, BRA, BAR, MEMBAR, LDG,
+ * STG, LDS, STS, LDL, STL, LDC, ATOM, F2F, MUFU, DFMA, EXIT in that order. */
+gpa_status gpa_arch_default(gpa_arch_desc* arch);
+
+/* Creates a context on the current CUDA device. arch and opts are copied;
+ * opts may be NULL. *out owns device memory until gpa_destroy. */
+gpa_status gpa_create(const gpa_arch_desc* arch, const gpa_options* opts, gpa_ctx** out);
+
+/* Synchronizes the device, frees every program and the context. */
+gpa_status gpa_destroy(gpa_ctx* ctx);
+
+/* Validates and copies a program to the device (synchronous) and allocates
+ * its counters and result buffers. *out receives the program id. */
+gpa_status gpa_load_program(gpa_ctx* ctx, const gpa_program_desc* prog, gpa_pid* out);
+
+/* Frees a program (synchronizes the device first). */
+gpa_status gpa_unload_program(gpa_ctx* ctx, gpa_pid pid);
+
+/* Zeroes the program's sample counters, invalid count and status word. */
+gpa_status gpa_reset_counts(gpa_ctx* ctx, gpa_pid pid, gpa_stream stream);
+
+/* Step (a), Sec. 2.1: adds n packed samples (device pointer, 8-byte aligned;
+ * borrowed until stream passes this call) to the program's counters.
+ * Layout, most significant bit first: kernel 16 | pc 24 | class 4 |
+ * latency flag 1 | sm 8 | 11 reserved bits. Samples with an unknown kernel,
+ * a pc past its function, class >= 12, SELECTED with the latency flag, or
+ * nonzero reserved bits are counted as invalid, not fatal. Counters
+ * accumulate across calls. */
+gpa_status gpa_ingest_samples(gpa_ctx* ctx, gpa_pid pid, const uint64_t* dev_samples, size_t n,
+                              gpa_stream stream);
+
+/* Step (a) from host memory: copies n samples in chunks through library
+ * staging buffers (pinned host memory makes the copies overlap the
+ * aggregation) and aggregates them. Returns when the copies are enqueued;
+ * host_samples must stay valid until stream completes this call. */
+gpa_status gpa_ingest_host_samples(gpa_ctx* ctx, gpa_pid pid, const uint64_t* host_samples, size_t n,
+                                   gpa_stream stream);
+
+/* Steps (b)-(c), Sec. 4: reaching definitions, backward slicing, pruning and
+ * apportioning over the counters ingested so far. Replaces any previous blame. */
+gpa_status gpa_blame(gpa_ctx* ctx, gpa_pid pid, gpa_stream stream);
+
+/* Step (d), Sec. 5: roll-up, optimizer matching, estimators and ranking. If out
+ * is not NULL the results are copied to it and the call synchronizes stream;
+ * with out == NULL they stay on the device (fetch later with gpa_get_advice). */
+gpa_status gpa_advise(gpa_ctx* ctx, gpa_pid pid, const gpa_advice* out, gpa_stream stream);
+
+/* Synchronizes stream and returns the program's device status word as a
+ * gpa_status (GPA_OK, GPA_ERR_NOT_CONVERGED, GPA_ERR_CAPACITY, ...). If info is
+ * not NULL: info[0] = invalid samples, info[1] = general (multi-block)
+ * searches run, info[2] = largest search in nodes, info[3] = fixpoint sweeps. */
+gpa_status gpa_sync_status(gpa_ctx* ctx, gpa_pid pid, gpa_stream stream, int64_t* info);
+
+/* Parity getters: synchronize stream and copy device results to host memory.
+ * counts[n_instr*24]: counts[pc*24 + class*2 + latency]; *invalid may be NULL. */
+gpa_status gpa_get_counts(gpa_ctx* ctx, gpa_pid pid, uint64_t* counts, uint64_t* invalid, gpa_stream stream);
+/* rin/rout[n_blocks*9]: bit r of block b's 9 words set iff some def of resource r
+ * reaches the entry/exit of b. */
+gpa_status gpa_get_reaching(gpa_ctx* ctx, gpa_pid pid, uint32_t* rin, uint32_t* rout, gpa_stream stream);
+/* blame[n_instr*24], same layout as counts. */
+gpa_status gpa_get_blame(gpa_ctx* ctx, gpa_pid pid, uint64_t* blame, gpa_stream stream);
+/* Surviving merged edges, sorted by (use, def). With all arrays NULL, only
+ * *n_edges is written. Otherwise each array has room for cap entries:
+ * use[], def[] global instruction indices; dmin/dlong shortest and longest
+ * source path; flags bit 0 write-after-read, 1 via barrier, 2 via register,
+ * 3 via predicate; share[cap*8] = blamed samples per (class 2,3,5,6) x latency flag. */
+gpa_status gpa_get_edges(gpa_ctx* ctx, gpa_pid pid, int64_t* n_edges, int64_t cap, int32_t* use, int32_t* def,
+                         int32_t* dmin, int32_t* dlong, uint32_t* flags, uint64_t* share, gpa_stream stream);
+/* Copies the advice computed by the last gpa_advise (see gpa_advice). */
+gpa_status gpa_get_advice(gpa_ctx* ctx, gpa_pid pid, const gpa_advice* out, gpa_stream stream);
+
+/* Kernel launches issued by this context since creation (for accounting). */
+int64_t gpa_launch_count(gpa_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GPA_H_ */

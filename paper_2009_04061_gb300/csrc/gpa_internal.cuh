@@ -1,0 +1,157 @@
+// Internal device-side layout and helpers of libgpa (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "gpa.h"
+
+namespace gpa {
+
+constexpr int kNumRes = 268;     // R0..R254, P0..P6, B0..B5
+constexpr int kPredBase = 255;
+constexpr int kBarBase = 262;
+constexpr int kWords = 9;        // 268 bits in 32-bit words
+constexpr int kCnt = 24;         // counters per instruction: class * 2 + latency flag
+constexpr uint16_t kAllLits = 0xFFFF;
+constexpr int kMaxLayers = 8;    // back-edge layers for longest paths (K <= 7)
+constexpr int kMaxSrc = 64;      // merged sources per stalled use (hard upper bound)
+
+// Bits of the per-program device status word.
+enum : unsigned long long {
+  ST_NOT_CONVERGED = 1, ST_CAPACITY = 2, ST_TIMEOUT = 4, ST_OVERFLOW = 8
+};
+// Slots of the per-program stats array (unsigned long long).
+enum {
+  SS_INVALID = 0, SS_GENERAL = 1, SS_MAX_NODES = 2, SS_SWEEPS = 3, SS_STATUS = 4,
+  SS_RAW_N = 5, SS_QUEUE_N = 6, SS_QUEUE_HEAD = 7, SS_OVF_N = 8, SS_OVF_HEAD = 9, SS_N = 10
+};
+
+struct Arch {
+  int32_t n_op;
+  int32_t lat[GPA_MAX_OPCLASSES];
+  uint32_t flags[GPA_MAX_OPCLASSES];
+};
+
+// Device view of one loaded program and its per-step buffers.
+struct Prog {
+  int32_t nf, ni, nb, nl, n_lines;
+  const int32_t* func_instr_off;
+  const int32_t* func_block_off;
+  const int32_t* func_loop_off;
+  const int32_t* block_instr_off;
+  const int32_t* succ_off;
+  const int32_t* succ;
+  const int32_t* pred_off;
+  const int32_t* pred;
+  const uint8_t* opclass;
+  const uint8_t* guard;
+  const uint8_t* iflags;
+  const int32_t* line;
+  const int32_t* def_off;
+  const uint16_t* def_res;
+  const int32_t* use_off;
+  const uint16_t* use_res;
+  const int32_t* block_loop;
+  const int32_t* loop_parent;
+  const int32_t* loop_header;
+  const int32_t* loop_depth;
+  const int32_t* instr_block;
+  const int32_t* block_func;
+  // step state
+  unsigned long long* cnt;        // ni * 24
+  unsigned long long* stats;      // SS_N
+  uint32_t* def_mask;             // nb * 9: resources defined in the block
+  uint32_t* uuse_mask;            // nb * 9: resources read by an unguarded instruction
+  int32_t* res_maxlat;            // nf * 268: largest latency of any def of the resource in the function
+  uint32_t* rin;                  // nb * 9
+  uint32_t* rout;                 // nb * 9
+  int32_t* head;                  // ni: raw-edge list head per use (-1 = none)
+  int4* raw;                      // raw edges: def, next, dmin, dlong | flags << 24
+  int64_t raw_cap;
+  int4* queue;                    // general searches: use, resource, start literal set, 0
+  int4* ovf_queue;                // general searches that outgrew a small scratch slot
+  int64_t queue_cap;
+  int32_t* edge_cnt;              // ni + 1 (exclusive scan in place -> offsets)
+  int32_t* edge_off;              // ni + 1
+  int32_t* e_use;
+  int32_t* e_def;
+  int32_t* e_dmin;
+  int32_t* e_dlong;
+  uint32_t* e_flags;
+  unsigned long long* e_share;    // edges * 8
+  int64_t edge_cap;
+  unsigned long long* blame;      // ni * 24
+  // advice
+  unsigned long long* a_totals;   // nf * 4
+  unsigned long long* a_matched;  // nf * 8
+  double* a_speedup;              // nf * 8
+  int32_t* a_rank;                // nf * 8
+  int32_t* a_nhot;                // nf * 8
+  long long* a_hot;               // nf * 8 * 5 * 6
+  unsigned long long* a_loop_active;
+  unsigned long long* a_loop_matched;
+  double* a_loop_speedup;
+  unsigned long long* a_line_stall;
+  unsigned long long* a_line_lat;
+};
+
+// Per-slot scratch of the general (multi-block) search.
+struct SearchScratch {
+  int32_t n_slots;
+  int32_t max_nodes;
+  int32_t edge_cap, occ_cap, src_cap, wall_cap;
+  int64_t slot_ints;   // ints per slot
+  int32_t* base;       // n_slots * slot_ints
+};
+
+__device__ __forceinline__ void set_status(const Prog& P, unsigned long long bits) {
+  atomicOr(&P.stats[SS_STATUS], bits);
+}
+
+// ---------------------------------------------------------------- Sec. 4 predicate literals
+// Literal set: bit i = Pi, bit 7+i = !Pi; kAllLits = the set holds "_".
+__device__ __forceinline__ uint16_t add_literal(uint16_t S, int g) {
+  if (S == kAllLits || g == 0) return kAllLits;
+  S = (uint16_t)(S | (1u << (g - 1)));  // literal 1..7 -> bit 0..6 (Pi), 8..14 -> bit 7..13 (!Pi)
+  uint32_t pos = S & 0x7Fu, neg = (S >> 7) & 0x7Fu;
+  return (pos & neg) ? kAllLits : S;
+}
+// "P contains p'": p' in P or "_" in P.
+__device__ __forceinline__ bool contains(uint16_t S, int g) {
+  if (S == kAllLits) return true;
+  if (g == 0) return false;
+  return (S >> (g - 1)) & 1u;
+}
+
+// Def kind of resource r at instruction x: -1 not defined, else 0/1/2.
+__device__ __forceinline__ int def_kind(const Prog& P, int x, int r) {
+  const int e1 = P.def_off[x + 1];
+  for (int e = P.def_off[x]; e < e1; ++e) {
+    uint32_t v = P.def_res[e];
+    if ((int)(v & 0x1FFu) == r) return (int)((v >> 12) & 3u);
+  }
+  return -1;
+}
+__device__ __forceinline__ bool uses_res(const Prog& P, int x, int r) {
+  const int e1 = P.use_off[x + 1];
+  for (int e = P.use_off[x]; e < e1; ++e)
+    if ((int)(P.use_res[e] & 0x1FFu) == r) return true;
+  return false;
+}
+
+// ---------------------------------------------------------------- launchers
+int grid_for(int64_t n, int threads, int sms);
+void launch_build_layout(const Prog& P, cudaStream_t st, int sms, int64_t* launches);
+void launch_build_preds(const Prog& P, int n_succ, int32_t* pred_off, int32_t* cursor, int32_t* tmp, cudaStream_t st,
+                        int sms, int64_t* launches);
+void launch_histogram(const Prog& P, const uint64_t* samples, size_t n, cudaStream_t st, int sms, int64_t* launches);
+void launch_dataflow(const Prog& P, const Arch& A, int max_sweeps, cudaStream_t st, int sms, int64_t* launches);
+void launch_blame(const Prog& P, const Arch& A, const SearchScratch& tier1, const SearchScratch& tier2, int max_src,
+                  int32_t* scan_tmp, cudaStream_t st, int sms, int64_t* launches);
+void launch_advise(const Prog& P, const Arch& A, cudaStream_t st, int sms, int64_t* launches);
+// Exclusive scan of n int32 values in place over buf[0..n], buf[n] receives the total.
+void scan_exclusive_inplace(int32_t* buf, int n, int32_t* tmp, cudaStream_t st, int64_t* launches);
+size_t scan_tmp_ints(int n);
+
+}  // namespace gpa

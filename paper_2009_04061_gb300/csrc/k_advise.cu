@@ -1,0 +1,217 @@
+// Step (d), Sec. 5: roll blame up to lines, loops and functions, match the
+// code optimizers of Table 2, estimate their speedups (Eq. 2 for stall
+// elimination, Eq. 4 for latency hiding, Eq. 5 per loop scope), rank them and
+// pick each optimizer's top five hotspots (def, use, distance).
+//
+// One CTA per function: threads stride over the function's instructions and
+// its merged edges (contiguous, since edges are ordered by use), reduce the
+// sums in shared memory, and thread 0 finishes the per-function results.
+#include "gpa_internal.cuh"
+
+namespace gpa {
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kHot = 5;
+enum { O_RR = 0, O_SR, O_FS, O_FM, O_WB, O_MT, O_LU, O_CR, N_O = 8 };
+
+struct Cand { unsigned long long v; int def, use, dist; };
+
+__device__ __forceinline__ bool better(const Cand& a, const Cand& b) {  // a ranks before b
+  if (a.v != b.v) return a.v > b.v;
+  if (a.def != b.def) return a.def < b.def;
+  return a.use < b.use;
+}
+__device__ __forceinline__ void top_insert(Cand* top, int& n, const Cand& c) {
+  if (c.v == 0) return;
+  if (n == kHot && !better(c, top[kHot - 1])) return;
+  int p = n < kHot ? n++ : kHot - 1;
+  while (p > 0 && better(c, top[p - 1])) { top[p] = top[p - 1]; --p; }
+  top[p] = c;
+}
+
+__device__ __forceinline__ double est(unsigned long long T, unsigned long long M) {
+  if (T == 0) return 1.0;
+  if (T == M) return __longlong_as_double(0x7FF0000000000000LL);  // +inf
+  return (double)T / (double)(T - M);
+}
+
+__device__ int innermost_loop(const Prog& P, int x) { return P.block_loop[P.instr_block[x]]; }
+
+__device__ int lca_loop(const Prog& P, int a, int b) {
+  if (a < 0 || b < 0) return -1;
+  int da = P.loop_depth[a], db = P.loop_depth[b];
+  while (da > db) { a = P.loop_parent[a]; --da; }
+  while (db > da) { b = P.loop_parent[b]; --db; }
+  while (a != b && a >= 0 && b >= 0) { a = P.loop_parent[a]; b = P.loop_parent[b]; }
+  return (a == b) ? a : -1;
+}
+
+// Matched samples of an edge per edge-based optimizer. Shares are indexed
+// class slot (exec, memory, sync, constant memory) * 2 + latency flag.
+struct EdgeMatch { unsigned long long rr, sr, lu, cr; };
+__device__ __forceinline__ EdgeMatch edge_match(const Prog& P, const Arch& A, int64_t e) {
+  const unsigned long long* sh = P.e_share + e * 8;
+  const uint32_t fl = A.flags[P.opclass[P.e_def[e]]];
+  const bool local = fl & GPA_F_LOCAL;
+  const bool global_mem = !local && !(fl & GPA_F_CONST);  // constant-memory stalls are never global
+  EdgeMatch m;
+  m.rr = local ? (sh[2] + sh[3] + sh[6] + sh[7]) : 0ull;                       // Register Reuse
+  m.sr = (fl & GPA_F_LONG_ARITH) ? (sh[0] + sh[1]) : 0ull;                    // Strength Reduction
+  m.cr = sh[1] + (global_mem ? sh[3] : 0ull);                                 // latency samples
+  m.lu = lca_loop(P, innermost_loop(P, P.e_def[e]), innermost_loop(P, P.e_use[e])) >= 0 ? m.cr : 0ull;
+  return m;
+}
+
+__global__ void __launch_bounds__(kThreads) k_advise(Prog P, Arch A) {
+  __shared__ unsigned long long red[12][kThreads / 32];
+  __shared__ unsigned long long tot[12];
+  __shared__ Cand cand[kThreads * kHot];
+  __shared__ int ncand[kThreads];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+
+  for (int f = blockIdx.x; f < P.nf; f += gridDim.x) {
+    const int i0 = P.func_instr_off[f], i1 = P.func_instr_off[f + 1];
+    // Edge ranges are clamped to the edge capacity (overflow is reported in the status word).
+    const int64_t e0 = min((int64_t)P.edge_off[i0], P.edge_cap), e1 = min((int64_t)P.edge_off[i1], P.edge_cap);
+    unsigned long long acc[12];
+#pragma unroll
+    for (int q = 0; q < 12; ++q) acc[q] = 0ull;
+    // acc: 0 T, 1 A, 2 L, 3 issued, 4 FS, 5 FM, 6 WB, 7 MT, 8 RR, 9 SR, 10 LU, 11 CR
+    for (int x = i0 + tid; x < i1; x += kThreads) {
+      const unsigned long long* c = P.cnt + (size_t)x * kCnt;
+      unsigned long long a = 0, l = 0, stall = 0;
+#pragma unroll
+      for (int e = 0; e < kCnt; ++e) {
+        if (e & 1) l += c[e]; else a += c[e];
+        if (e >= 2) stall += c[e];
+      }
+      acc[0] += a + l; acc[1] += a; acc[2] += l; acc[3] += c[0];
+      acc[4] += c[2] + c[3];
+      if (P.iflags[x] & 1) acc[5] += stall;
+      acc[6] += c[10] + c[11];
+      if (A.flags[P.opclass[x]] & GPA_F_GLOBAL) acc[7] += c[16] + c[17];
+      for (int lp = innermost_loop(P, x); lp >= 0; lp = P.loop_parent[lp])
+        if (a) atomicAdd(&P.a_loop_active[lp], a);
+      const unsigned long long* b = P.blame + (size_t)x * kCnt;
+      unsigned long long bs = 0, bl = 0;
+#pragma unroll
+      for (int e = 2; e < kCnt; ++e) { bs += b[e]; if (e & 1) bl += b[e]; }
+      if (bs) atomicAdd(&P.a_line_stall[P.line[x]], bs);
+      if (bl) atomicAdd(&P.a_line_lat[P.line[x]], bl);
+    }
+    for (int64_t e = e0 + tid; e < e1; e += kThreads) {
+      const EdgeMatch m = edge_match(P, A, e);
+      acc[8] += m.rr; acc[9] += m.sr; acc[10] += m.lu; acc[11] += m.cr;
+      if (m.lu) {
+        const int q = lca_loop(P, innermost_loop(P, P.e_def[e]), innermost_loop(P, P.e_use[e]));
+        for (int lp = q; lp >= 0; lp = P.loop_parent[lp]) atomicAdd(&P.a_loop_matched[lp], m.lu);
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 12; ++q) {
+      unsigned long long v = acc[q];
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane == 0) red[q][warp] = v;
+    }
+    __syncthreads();
+    if (tid < 12) {
+      unsigned long long v = 0;
+      for (int w = 0; w < kThreads / 32; ++w) v += red[tid][w];
+      tot[tid] = v;
+    }
+    __syncthreads();
+    const unsigned long long T = tot[0], Aact = tot[1];
+    if (tid == 0) {
+      unsigned long long M[N_O];
+      M[O_RR] = tot[8]; M[O_SR] = tot[9]; M[O_FS] = tot[4]; M[O_FM] = tot[5];
+      M[O_WB] = tot[6]; M[O_MT] = tot[7]; M[O_LU] = tot[10]; M[O_CR] = tot[11];
+      double sp[N_O];
+      for (int o = 0; o < N_O; ++o) {
+        const bool hide = (o == O_LU || o == O_CR);
+        sp[o] = est(T, hide ? min(Aact, M[o]) : M[o]);
+        P.a_matched[(size_t)f * N_O + o] = M[o];
+        P.a_speedup[(size_t)f * N_O + o] = sp[o];
+      }
+      int ord[N_O];
+      for (int o = 0; o < N_O; ++o) ord[o] = o;
+      for (int a = 1; a < N_O; ++a) {  // stable: ties keep the lower id first
+        int v = ord[a], b = a - 1;
+        while (b >= 0 && sp[ord[b]] < sp[v]) { ord[b + 1] = ord[b]; --b; }
+        ord[b + 1] = v;
+      }
+      for (int o = 0; o < N_O; ++o) P.a_rank[(size_t)f * N_O + o] = ord[o];
+      for (int q = 0; q < 4; ++q) P.a_totals[(size_t)f * 4 + q] = tot[q];
+    }
+    // Hotspots, one optimizer at a time: thread-local top five, then thread 0 merges.
+    for (int o = 0; o < N_O; ++o) {
+      Cand top[kHot];
+      int nt = 0;
+      const bool edge_based = (o == O_RR || o == O_SR || o == O_LU || o == O_CR);
+      if (edge_based) {
+        for (int64_t e = e0 + tid; e < e1; e += kThreads) {
+          const EdgeMatch m = edge_match(P, A, e);
+          const unsigned long long v = o == O_RR ? m.rr : o == O_SR ? m.sr : o == O_LU ? m.lu : m.cr;
+          top_insert(top, nt, Cand{v, P.e_def[e] - i0, P.e_use[e] - i0, P.e_dmin[e]});
+        }
+      } else {
+        for (int x = i0 + tid; x < i1; x += kThreads) {
+          const unsigned long long* c = P.cnt + (size_t)x * kCnt;
+          unsigned long long v = 0;
+          if (o == O_FS) v = c[2] + c[3];
+          else if (o == O_FM) { if (P.iflags[x] & 1) for (int e = 2; e < kCnt; ++e) v += c[e]; }
+          else if (o == O_WB) v = c[10] + c[11];
+          else if (A.flags[P.opclass[x]] & GPA_F_GLOBAL) v = c[16] + c[17];
+          top_insert(top, nt, Cand{v, x - i0, x - i0, 0});
+        }
+      }
+      for (int h = 0; h < nt; ++h) cand[tid * kHot + h] = top[h];
+      ncand[tid] = nt;
+      __syncthreads();
+      if (tid == 0) {
+        Cand best[kHot];
+        int nb = 0;
+        for (int t = 0; t < kThreads; ++t)
+          for (int h = 0; h < ncand[t]; ++h) top_insert(best, nb, cand[t * kHot + h]);
+        long long* out = P.a_hot + ((size_t)f * N_O + o) * kHot * 6;
+        for (int h = 0; h < kHot; ++h) {
+          if (h < nb) {
+            out[h * 6 + 0] = best[h].def; out[h * 6 + 1] = best[h].use;
+            out[h * 6 + 2] = P.line[i0 + best[h].def]; out[h * 6 + 3] = P.line[i0 + best[h].use];
+            out[h * 6 + 4] = best[h].dist; out[h * 6 + 5] = (long long)best[h].v;
+          } else {
+            for (int q = 0; q < 6; ++q) out[h * 6 + q] = -1;
+          }
+        }
+        P.a_nhot[(size_t)f * N_O + o] = nb;
+      }
+      __syncthreads();
+    }
+    // Eq. 5 per loop scope of this function (its loop counters were only touched by this CTA).
+    __threadfence_block();
+    __syncthreads();
+    for (int lp = P.func_loop_off[f] + tid; lp < P.func_loop_off[f + 1]; lp += kThreads) {
+      const unsigned long long al = __ldcg(&P.a_loop_active[lp]);
+      const unsigned long long ml = __ldcg(&P.a_loop_matched[lp]);
+      P.a_loop_speedup[lp] = est(T, min(al, ml));
+    }
+    __syncthreads();
+  }
+}
+
+}  // namespace
+
+void launch_advise(const Prog& P, const Arch& A, cudaStream_t st, int sms, int64_t* launches) {
+  if (P.nl > 0) {
+    cudaMemsetAsync(P.a_loop_active, 0, sizeof(unsigned long long) * P.nl, st);
+    cudaMemsetAsync(P.a_loop_matched, 0, sizeof(unsigned long long) * P.nl, st);
+  }
+  cudaMemsetAsync(P.a_line_stall, 0, sizeof(unsigned long long) * P.n_lines, st);
+  cudaMemsetAsync(P.a_line_lat, 0, sizeof(unsigned long long) * P.n_lines, st);
+  int blocks = P.nf < sms * 4 ? P.nf : sms * 4;
+  k_advise<<<blocks > 0 ? blocks : 1, kThreads, 0, st>>>(P, A);
+  ++*launches;
+}
+
+}  // namespace gpa

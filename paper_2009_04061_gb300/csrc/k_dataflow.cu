@@ -1,0 +1,141 @@
+// Step (b), first half: per-block resource summaries and the reaching-
+// definitions fixpoint at resource granularity (Sec. 4, backward slicing over
+// registers, predicates and virtual barrier registers).
+//
+// The classic def-site reaching definitions projected on resources reduces to
+// reachability of definitions: some def of r reaches the exit of b iff b
+// defines r or some def of r reaches its entry (an unpredicated def kills the
+// earlier defs of r but itself reaches on), and reaches the entry iff it
+// reaches the exit of a predecessor. So
+//   RIN[b] = OR over preds p of ROUT[p],   ROUT[b] = DEF[b] | RIN[b],
+// 268-bit masks in 9 words. The backward searches use ROUT to skip blocks no
+// def of the searched resource can leave.
+#include "gpa_internal.cuh"
+
+namespace gpa {
+
+namespace {
+
+// Warp per basic block: lanes over its instructions, one reduce-or per word.
+__global__ void k_block_masks(Prog P) {
+  const int lane = threadIdx.x & 31;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int n_warps = (gridDim.x * blockDim.x) >> 5;
+  for (int b = warp; b < P.nb; b += n_warps) {
+    uint32_t dm[kWords], um[kWords];
+#pragma unroll
+    for (int w = 0; w < kWords; ++w) { dm[w] = 0; um[w] = 0; }
+    const int x1 = P.block_instr_off[b + 1];
+    for (int x = P.block_instr_off[b] + lane; x < x1; x += 32) {
+      for (int e = P.def_off[x]; e < P.def_off[x + 1]; ++e) {
+        const int r = P.def_res[e] & 0x1FF;
+#pragma unroll
+        for (int w = 0; w < kWords; ++w) dm[w] |= ((r >> 5) == w) ? (1u << (r & 31)) : 0u;
+      }
+      if (P.guard[x] == 0) {
+        for (int e = P.use_off[x]; e < P.use_off[x + 1]; ++e) {
+          const int r = P.use_res[e] & 0x1FF;
+#pragma unroll
+          for (int w = 0; w < kWords; ++w) um[w] |= ((r >> 5) == w) ? (1u << (r & 31)) : 0u;
+        }
+      }
+    }
+#pragma unroll
+    for (int w = 0; w < kWords; ++w) {
+      const uint32_t d = __reduce_or_sync(0xffffffffu, dm[w]);
+      const uint32_t u = __reduce_or_sync(0xffffffffu, um[w]);
+      if (lane == w) {
+        P.def_mask[(size_t)b * kWords + w] = d;
+        P.uuse_mask[(size_t)b * kWords + w] = u;
+        P.rin[(size_t)b * kWords + w] = 0u;
+        P.rout[(size_t)b * kWords + w] = d;
+      }
+    }
+  }
+}
+
+// Largest latency of any def of each resource in each function: the distance
+// beyond which no def of that resource can pass the latency rule.
+__global__ void k_res_maxlat(Prog P, Arch A) {
+  for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < P.ni; x += gridDim.x * blockDim.x) {
+    const int f = P.block_func[P.instr_block[x]];
+    const int lat = A.lat[P.opclass[x]];
+    for (int e = P.def_off[x]; e < P.def_off[x + 1]; ++e)
+      atomicMax(&P.res_maxlat[(size_t)f * kNumRes + (P.def_res[e] & 0x1FF)], lat);
+  }
+}
+
+// Warp per function. Blocks are visited in layout order (a topological order
+// of the forward edges) 32 at a time, lane per block; inside a window the
+// lanes iterate until __ballot_sync reports no change, then move on. A full
+// pass without change ends the fixpoint; max_sweeps passes without reaching it
+// set ST_NOT_CONVERGED. Monotone OR updates from 0 make the result the least
+// fixpoint regardless of the visiting order.
+__global__ void k_reaching(Prog P, int max_sweeps) {
+  const int lane = threadIdx.x & 31;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int n_warps = (gridDim.x * blockDim.x) >> 5;
+  for (int f = warp; f < P.nf; f += n_warps) {
+    const int b0 = P.func_block_off[f], b1 = P.func_block_off[f + 1];
+    bool converged = false;
+    int sweep = 0;
+    for (; sweep < max_sweeps && !converged; ++sweep) {
+      bool changed_any = false;
+      for (int w0 = b0; w0 < b1; w0 += 32) {
+        const int b = w0 + lane;
+        const bool mine = b < b1;
+        for (int it = 0; it < 64; ++it) {
+          bool ch = false;
+          if (mine) {
+            uint32_t in[kWords];
+#pragma unroll
+            for (int w = 0; w < kWords; ++w) in[w] = 0u;
+            for (int e = P.pred_off[b]; e < P.pred_off[b + 1]; ++e) {
+              const volatile uint32_t* ro = P.rout + (size_t)P.pred[e] * kWords;
+#pragma unroll
+              for (int w = 0; w < kWords; ++w) in[w] |= ro[w];
+            }
+            volatile uint32_t* ri = P.rin + (size_t)b * kWords;
+            volatile uint32_t* ro = P.rout + (size_t)b * kWords;
+            const uint32_t* dm = P.def_mask + (size_t)b * kWords;
+#pragma unroll
+            for (int w = 0; w < kWords; ++w) {
+              const uint32_t o = dm[w] | in[w];
+              if (in[w] != ri[w] || o != ro[w]) ch = true;
+              ri[w] = in[w];
+              ro[w] = o;
+            }
+          }
+          __syncwarp();
+          if (!__ballot_sync(0xffffffffu, ch)) break;
+          changed_any = true;
+        }
+      }
+      converged = !changed_any;
+    }
+    if (lane == 0) {
+      if (!converged) set_status(P, ST_NOT_CONVERGED);
+      atomicMax(&P.stats[SS_SWEEPS], (unsigned long long)sweep);
+    }
+  }
+}
+
+}  // namespace
+
+void launch_dataflow(const Prog& P, const Arch& A, int max_sweeps, cudaStream_t st, int sms, int64_t* launches) {
+  const int threads = 256;
+  int64_t warps_needed = P.nb;
+  int blocks = (int)((warps_needed * 32 + threads - 1) / threads);
+  if (blocks > sms * 16) blocks = sms * 16;
+  if (blocks < 1) blocks = 1;
+  k_block_masks<<<blocks, threads, 0, st>>>(P);
+  int fblocks = (P.nf * 32 + 127) / 128;
+  if (fblocks > sms * 16) fblocks = sms * 16;
+  if (fblocks < 1) fblocks = 1;
+  k_reaching<<<fblocks, 128, 0, st>>>(P, max_sweeps);
+  cudaMemsetAsync(P.res_maxlat, 0, sizeof(int32_t) * (size_t)P.nf * kNumRes, st);
+  k_res_maxlat<<<grid_for(P.ni, 256, sms), 256, 0, st>>>(P, A);
+  *launches += 3;
+}
+
+}  // namespace gpa

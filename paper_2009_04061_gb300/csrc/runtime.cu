@@ -1,0 +1,594 @@
+// Host runtime behind the C ABI in include/gpa.h: context and program
+// registry, input validation, device memory, stream-ordered launches, the
+// chunked host-sample ingest, status words and parity getters.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <new>
+#include <vector>
+
+#include "gpa_internal.cuh"
+
+using namespace gpa;
+
+namespace {
+
+struct ProgramRec {
+  Prog P{};
+  int n_succ = 0, n_def = 0, n_use = 0;
+  int32_t* scan_tmp = nullptr;
+  std::vector<void*> allocs;
+};
+
+}  // namespace
+
+struct gpa_ctx {
+  int device = 0;
+  int sms = 0;
+  Arch arch{};
+  gpa_options opts{};
+  SearchScratch tier1{}, tier2{};
+  cudaEvent_t scratch_ev = nullptr;
+  std::map<gpa_pid, ProgramRec*> progs;
+  gpa_pid next_pid = 1;
+  int64_t launches = 0;
+  // staging for gpa_ingest_host_samples
+  uint64_t* stage[2] = {nullptr, nullptr};
+  size_t stage_n = 0;
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t ev_copied[2] = {nullptr, nullptr}, ev_used[2] = {nullptr, nullptr};
+};
+
+namespace {
+
+constexpr size_t kStageSamples = (size_t)64 << 20;  // 64M samples (512 MB) per staging buffer
+
+#define CK(x)                                   \
+  do {                                          \
+    if ((x) != cudaSuccess) return GPA_ERR_CUDA; \
+  } while (0)
+
+template <class T>
+gpa_status dev_alloc(ProgramRec* R, T** p, size_t n) {
+  void* q = nullptr;
+  if (cudaMalloc(&q, std::max<size_t>(n, 1) * sizeof(T)) != cudaSuccess) return GPA_ERR_OOM;
+  R->allocs.push_back(q);
+  *p = (T*)q;
+  return GPA_OK;
+}
+template <class T>
+gpa_status dev_copy(ProgramRec* R, const T** dst, const T* src, size_t n) {
+  T* p = nullptr;
+  gpa_status s = dev_alloc(R, &p, n);
+  if (s) return s;
+  if (n && cudaMemcpy(p, src, n * sizeof(T), cudaMemcpyHostToDevice) != cudaSuccess) return GPA_ERR_CUDA;
+  *dst = p;
+  return GPA_OK;
+}
+
+void free_program(ProgramRec* R) {
+  for (void* p : R->allocs) cudaFree(p);
+  delete R;
+}
+
+gpa_status scratch_alloc(SearchScratch* S, int slots, int nodes) {
+  S->n_slots = slots;
+  S->max_nodes = nodes;
+  S->edge_cap = 2 * nodes;
+  S->occ_cap = nodes;
+  S->src_cap = std::min(nodes, 1024);
+  S->wall_cap = nodes;
+  // blk S cov wall d k e0 e1 seen ord tmp q hused par fl (15) + layers + hash (2) + edges + occ (2) + src (5) +
+  // walls (3)
+  S->slot_ints = (int64_t)15 * nodes + (int64_t)kMaxLayers * nodes + 2 * (int64_t)nodes + S->edge_cap +
+                 2 * (int64_t)S->occ_cap + 5 * (int64_t)S->src_cap + 3 * (int64_t)S->wall_cap;
+  S->slot_ints = (S->slot_ints + 63) & ~(int64_t)63;
+  size_t bytes = (size_t)S->slot_ints * sizeof(int32_t) * (size_t)slots;
+  if (cudaMalloc(&S->base, bytes) != cudaSuccess) { S->base = nullptr; return GPA_ERR_OOM; }
+  // Hash tables start empty (-1); everything else is written before it is read.
+  if (cudaMemset(S->base, 0xFF, bytes) != cudaSuccess) return GPA_ERR_CUDA;
+  return GPA_OK;
+}
+
+ProgramRec* find(gpa_ctx* ctx, gpa_pid pid) {
+  if (!ctx) return nullptr;
+  auto it = ctx->progs.find(pid);
+  return it == ctx->progs.end() ? nullptr : it->second;
+}
+
+// ---------------------------------------------------------------- validation
+gpa_status validate(const gpa_program_desc* d, const Arch& A) {
+  const int nf = d->n_functions, ni = d->n_instr, nb = d->n_blocks, nl = d->n_loops;
+  if (nf < 1 || nf >= 65536 || ni < 1 || nb < nf || nl < 0 || d->n_lines < 1 || d->n_succ < 0 || d->n_def < 0 ||
+      d->n_use < 0)
+    return GPA_ERR_INVALID_PROGRAM;
+  if ((int64_t)ni * kCnt >= ((int64_t)1 << 32)) return GPA_ERR_INVALID_PROGRAM;
+  if (!d->func_instr_off || !d->func_block_off || !d->func_loop_off || !d->block_instr_off || !d->succ_off ||
+      !d->opclass || !d->guard || !d->iflags || !d->line || !d->def_off || !d->use_off || !d->block_loop)
+    return GPA_ERR_INVALID_ARG;
+  if ((d->n_succ && !d->succ) || (d->n_def && !d->def_res) || (d->n_use && !d->use_res) ||
+      (nl && (!d->loop_parent || !d->loop_header)))
+    return GPA_ERR_INVALID_ARG;
+  auto mono = [](const int32_t* a, int n, int last, bool strict) {
+    if (a[0] != 0 || a[n] != last) return false;
+    for (int i = 0; i < n; ++i)
+      if (strict ? a[i + 1] <= a[i] : a[i + 1] < a[i]) return false;
+    return true;
+  };
+  if (!mono(d->func_instr_off, nf, ni, true) || !mono(d->func_block_off, nf, nb, true) ||
+      !mono(d->func_loop_off, nf, nl, false) || !mono(d->block_instr_off, nb, ni, true) ||
+      !mono(d->succ_off, nb, d->n_succ, false) || !mono(d->def_off, ni, d->n_def, false) ||
+      !mono(d->use_off, ni, d->n_use, false))
+    return GPA_ERR_INVALID_PROGRAM;
+  std::vector<int> bfunc(nb), lfunc(nl);
+  for (int f = 0; f < nf; ++f) {
+    if (d->func_instr_off[f + 1] - d->func_instr_off[f] >= (1 << 24)) return GPA_ERR_INVALID_PROGRAM;
+    if (d->block_instr_off[d->func_block_off[f]] != d->func_instr_off[f]) return GPA_ERR_INVALID_PROGRAM;
+    for (int b = d->func_block_off[f]; b < d->func_block_off[f + 1]; ++b) bfunc[b] = f;
+    for (int l = d->func_loop_off[f]; l < d->func_loop_off[f + 1]; ++l) lfunc[l] = f;
+  }
+  for (int x = 0; x < ni; ++x) {
+    if (d->opclass[x] >= A.n_op || d->guard[x] > 14 || d->line[x] < 0 || d->line[x] >= d->n_lines)
+      return GPA_ERR_INVALID_PROGRAM;
+    uint32_t seen[kWords];
+    std::memset(seen, 0, sizeof seen);
+    for (int e = d->def_off[x]; e < d->def_off[x + 1]; ++e) {
+      const int r = d->def_res[e] & 0x1FF, kind = (d->def_res[e] >> 12) & 0xF;
+      if (r >= kNumRes || (d->def_res[e] & 0x0E00) || kind > 2 || (kind && r < kBarBase)) return GPA_ERR_INVALID_PROGRAM;
+      if (seen[r >> 5] >> (r & 31) & 1) return GPA_ERR_INVALID_PROGRAM;
+      seen[r >> 5] |= 1u << (r & 31);
+    }
+    std::memset(seen, 0, sizeof seen);
+    for (int e = d->use_off[x]; e < d->use_off[x + 1]; ++e) {
+      const int r = d->use_res[e];
+      if (r >= kNumRes) return GPA_ERR_INVALID_PROGRAM;
+      if (seen[r >> 5] >> (r & 31) & 1) return GPA_ERR_INVALID_PROGRAM;
+      seen[r >> 5] |= 1u << (r & 31);
+    }
+  }
+  for (int l = 0; l < nl; ++l) {
+    const int p = d->loop_parent[l], h = d->loop_header[l];
+    if (p < -1 || p >= nl || p == l || (p >= 0 && lfunc[p] != lfunc[l])) return GPA_ERR_INVALID_PROGRAM;
+    if (h < 0 || h >= nb || bfunc[h] != lfunc[l]) return GPA_ERR_INVALID_PROGRAM;
+    int depth = 0;
+    for (int q = l; q >= 0; q = d->loop_parent[q])
+      if (++depth > nl) return GPA_ERR_INVALID_PROGRAM;  // parent cycle
+  }
+  auto in_loop = [&](int b, int l) {
+    for (int q = d->block_loop[b]; q >= 0; q = d->loop_parent[q])
+      if (q == l) return true;
+    return false;
+  };
+  for (int b = 0; b < nb; ++b) {
+    const int q = d->block_loop[b];
+    if (q < -1 || q >= nl || (q >= 0 && lfunc[q] != bfunc[b])) return GPA_ERR_INVALID_PROGRAM;
+  }
+  for (int l = 0; l < nl; ++l)
+    if (!in_loop(d->loop_header[l], l)) return GPA_ERR_INVALID_PROGRAM;
+  for (int u = 0; u < nb; ++u) {
+    for (int e = d->succ_off[u]; e < d->succ_off[u + 1]; ++e) {
+      const int v = d->succ[e];
+      if (v < 0 || v >= nb || bfunc[v] != bfunc[u]) return GPA_ERR_INVALID_PROGRAM;
+      for (int e2 = d->succ_off[u]; e2 < e; ++e2)
+        if (d->succ[e2] == v) return GPA_ERR_INVALID_PROGRAM;
+      if (v <= u) {  // must be a back edge: v heads a loop that contains u
+        bool ok = false;
+        for (int q = d->block_loop[u]; q >= 0 && !ok; q = d->loop_parent[q]) ok = d->loop_header[q] == v;
+        if (!ok) return GPA_ERR_INVALID_PROGRAM;
+      }
+    }
+  }
+  // every block reachable from its function's entry
+  std::vector<char> reach(nb, 0);
+  std::vector<int> st;
+  for (int f = 0; f < nf; ++f) {
+    st.push_back(d->func_block_off[f]);
+    reach[d->func_block_off[f]] = 1;
+  }
+  while (!st.empty()) {
+    int b = st.back();
+    st.pop_back();
+    for (int e = d->succ_off[b]; e < d->succ_off[b + 1]; ++e)
+      if (!reach[d->succ[e]]) { reach[d->succ[e]] = 1; st.push_back(d->succ[e]); }
+  }
+  for (int b = 0; b < nb; ++b)
+    if (!reach[b]) return GPA_ERR_INVALID_PROGRAM;
+  return GPA_OK;
+}
+
+gpa_status status_from(unsigned long long st) {
+  if (st & ST_NOT_CONVERGED) return GPA_ERR_NOT_CONVERGED;
+  if (st & (ST_CAPACITY | ST_OVERFLOW)) return GPA_ERR_CAPACITY;
+  if (st & ST_TIMEOUT) return GPA_ERR_TIMEOUT;
+  return GPA_OK;
+}
+
+// Default opcode classes (order documented in gpa.h).
+const int32_t kDefLat[20] = {4, 5, 4, 4, 2, 0, 32, 32, 1024, 1024, 32, 32, 1024, 1024, 64, 1024, 16, 16, 8, 0};
+const uint32_t kDefFlags[20] = {
+    0, 0, 0, 0, 0, 0, GPA_F_SYNC, GPA_F_SYNC,
+    GPA_F_MEM | GPA_F_GLOBAL | GPA_F_VARLAT, GPA_F_MEM | GPA_F_GLOBAL | GPA_F_VARLAT,
+    GPA_F_SHARED | GPA_F_VARLAT, GPA_F_SHARED | GPA_F_VARLAT,
+    GPA_F_MEM | GPA_F_LOCAL | GPA_F_VARLAT, GPA_F_MEM | GPA_F_LOCAL | GPA_F_VARLAT,
+    GPA_F_MEM | GPA_F_CONST | GPA_F_VARLAT, GPA_F_MEM | GPA_F_GLOBAL | GPA_F_VARLAT,
+    GPA_F_LONG_ARITH | GPA_F_VARLAT, GPA_F_LONG_ARITH | GPA_F_VARLAT, 0, 0};
+
+}  // namespace
+
+extern "C" {
+
+const char* gpa_status_string(gpa_status s) {
+  switch (s) {
+    case GPA_OK: return "ok";
+    case GPA_ERR_INVALID_ARG: return "invalid argument";
+    case GPA_ERR_INVALID_PROGRAM: return "invalid program";
+    case GPA_ERR_CUDA: return "CUDA runtime error";
+    case GPA_ERR_NOT_CONVERGED: return "reaching-definitions fixpoint did not converge";
+    case GPA_ERR_CAPACITY: return "capacity exceeded";
+    case GPA_ERR_TIMEOUT: return "device wait timed out";
+    case GPA_ERR_NO_PROGRAM: return "no such program";
+    case GPA_ERR_OOM: return "out of device memory";
+    default: return "unknown status";
+  }
+}
+
+gpa_status gpa_arch_default(gpa_arch_desc* arch) {
+  if (!arch) return GPA_ERR_INVALID_ARG;
+  arch->n_opclasses = 20;
+  arch->latency = kDefLat;
+  arch->flags = kDefFlags;
+  return GPA_OK;
+}
+
+gpa_status gpa_create(const gpa_arch_desc* arch, const gpa_options* opts, gpa_ctx** out) {
+  if (!arch || !out || arch->n_opclasses < 1 || arch->n_opclasses > GPA_MAX_OPCLASSES || !arch->latency ||
+      !arch->flags)
+    return GPA_ERR_INVALID_ARG;
+  for (int o = 0; o < arch->n_opclasses; ++o)
+    if (arch->latency[o] < 0) return GPA_ERR_INVALID_ARG;
+  gpa_options o{};
+  if (opts) {
+    o = *opts;
+    for (int r : o.reserved)
+      if (r) return GPA_ERR_INVALID_ARG;
+    if (o.max_fixpoint_sweeps < 0 || o.max_search_nodes < 0 || o.search_slots < 0 || o.max_sources_per_use < 0 ||
+        o.max_sources_per_use > kMaxSrc || o.small_search_nodes < 0)
+      return GPA_ERR_INVALID_ARG;
+  }
+  auto* c = new (std::nothrow) gpa_ctx();
+  if (!c) return GPA_ERR_OOM;
+  if (cudaGetDevice(&c->device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess) {
+    delete c;
+    return GPA_ERR_CUDA;
+  }
+  c->arch.n_op = arch->n_opclasses;
+  for (int k = 0; k < arch->n_opclasses; ++k) { c->arch.lat[k] = arch->latency[k]; c->arch.flags[k] = arch->flags[k]; }
+  if (o.max_fixpoint_sweeps == 0) o.max_fixpoint_sweeps = 64;
+  if (o.max_search_nodes == 0) o.max_search_nodes = 65536;
+  if (o.search_slots == 0) o.search_slots = 32 * c->sms;
+  if (o.max_sources_per_use == 0) o.max_sources_per_use = kMaxSrc;
+  c->opts = o;
+  // Tier 1: many small slots for the common general search; tier 2: one large
+  // slot per SM for searches that overflow tier 1.
+  if (o.small_search_nodes == 0) o.small_search_nodes = 512;
+  int n1 = 2;
+  while (n1 < o.small_search_nodes && n1 < o.max_search_nodes) n1 <<= 1;
+  int n2 = 1;
+  while (n2 < o.max_search_nodes) n2 <<= 1;
+  gpa_status s = scratch_alloc(&c->tier1, o.search_slots, std::max(n1, 2));
+  if (!s) s = scratch_alloc(&c->tier2, c->sms, std::max(n2, 2));
+  if (!s && cudaEventCreateWithFlags(&c->scratch_ev, cudaEventDisableTiming) != cudaSuccess) s = GPA_ERR_CUDA;
+  if (s) {
+    if (c->tier1.base) cudaFree(c->tier1.base);
+    if (c->tier2.base) cudaFree(c->tier2.base);
+    delete c;
+    return s;
+  }
+  *out = c;
+  return GPA_OK;
+}
+
+gpa_status gpa_destroy(gpa_ctx* ctx) {
+  if (!ctx) return GPA_ERR_INVALID_ARG;
+  cudaDeviceSynchronize();
+  for (auto& kv : ctx->progs) free_program(kv.second);
+  if (ctx->tier1.base) cudaFree(ctx->tier1.base);
+  if (ctx->tier2.base) cudaFree(ctx->tier2.base);
+  for (int k = 0; k < 2; ++k) {
+    if (ctx->stage[k]) cudaFree(ctx->stage[k]);
+    if (ctx->ev_copied[k]) cudaEventDestroy(ctx->ev_copied[k]);
+    if (ctx->ev_used[k]) cudaEventDestroy(ctx->ev_used[k]);
+  }
+  if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
+  if (ctx->scratch_ev) cudaEventDestroy(ctx->scratch_ev);
+  delete ctx;
+  return GPA_OK;
+}
+
+gpa_status gpa_load_program(gpa_ctx* ctx, const gpa_program_desc* d, gpa_pid* out) {
+  if (!ctx || !d || !out) return GPA_ERR_INVALID_ARG;
+  gpa_status s = validate(d, ctx->arch);
+  if (s) return s;
+  auto* R = new (std::nothrow) ProgramRec();
+  if (!R) return GPA_ERR_OOM;
+  Prog& P = R->P;
+  P.nf = d->n_functions; P.ni = d->n_instr; P.nb = d->n_blocks; P.nl = d->n_loops; P.n_lines = d->n_lines;
+  R->n_succ = d->n_succ; R->n_def = d->n_def; R->n_use = d->n_use;
+  const size_t ni = P.ni, nb = P.nb, nl = P.nl, nf = P.nf;
+#define TRY(x)                        \
+  do {                                \
+    gpa_status t_ = (x);              \
+    if (t_) { free_program(R); return t_; } \
+  } while (0)
+  TRY(dev_copy(R, &P.func_instr_off, d->func_instr_off, nf + 1));
+  TRY(dev_copy(R, &P.func_block_off, d->func_block_off, nf + 1));
+  TRY(dev_copy(R, &P.func_loop_off, d->func_loop_off, nf + 1));
+  TRY(dev_copy(R, &P.block_instr_off, d->block_instr_off, nb + 1));
+  TRY(dev_copy(R, &P.succ_off, d->succ_off, nb + 1));
+  TRY(dev_copy(R, &P.succ, d->succ, (size_t)d->n_succ));
+  TRY(dev_copy(R, &P.opclass, d->opclass, ni));
+  TRY(dev_copy(R, &P.guard, d->guard, ni));
+  TRY(dev_copy(R, &P.iflags, d->iflags, ni));
+  TRY(dev_copy(R, &P.line, d->line, ni));
+  TRY(dev_copy(R, &P.def_off, d->def_off, ni + 1));
+  TRY(dev_copy(R, &P.def_res, d->def_res, (size_t)d->n_def));
+  TRY(dev_copy(R, &P.use_off, d->use_off, ni + 1));
+  TRY(dev_copy(R, &P.use_res, d->use_res, (size_t)d->n_use));
+  TRY(dev_copy(R, &P.block_loop, d->block_loop, nb));
+  TRY(dev_copy(R, &P.loop_parent, d->loop_parent, nl));
+  TRY(dev_copy(R, &P.loop_header, d->loop_header, nl));
+  int32_t *pred_off = nullptr, *pred = nullptr, *cursor = nullptr, *ldepth = nullptr, *iblock = nullptr,
+          *bfunc = nullptr;
+  TRY(dev_alloc(R, &pred_off, nb + 1));
+  TRY(dev_alloc(R, &pred, (size_t)d->n_succ));
+  TRY(dev_alloc(R, &cursor, nb));
+  TRY(dev_alloc(R, &ldepth, nl));
+  TRY(dev_alloc(R, &iblock, ni));
+  TRY(dev_alloc(R, &bfunc, nb));
+  TRY(dev_alloc(R, &P.res_maxlat, nf * kNumRes));
+  P.pred_off = pred_off; P.pred = pred; P.loop_depth = ldepth; P.instr_block = iblock; P.block_func = bfunc;
+  TRY(dev_alloc(R, &R->scan_tmp, scan_tmp_ints((int)std::max(ni, nb) + 1)));
+  TRY(dev_alloc(R, &P.cnt, ni * kCnt));
+  TRY(dev_alloc(R, &P.stats, (size_t)SS_N));
+  TRY(dev_alloc(R, &P.def_mask, nb * kWords));
+  TRY(dev_alloc(R, &P.uuse_mask, nb * kWords));
+  TRY(dev_alloc(R, &P.rin, nb * kWords));
+  TRY(dev_alloc(R, &P.rout, nb * kWords));
+  TRY(dev_alloc(R, &P.head, ni));
+  P.raw_cap = 2 * (int64_t)d->n_use + 1024;
+  TRY(dev_alloc(R, &P.raw, (size_t)P.raw_cap));
+  P.queue_cap = (int64_t)d->n_use + 1;
+  TRY(dev_alloc(R, &P.queue, (size_t)P.queue_cap));
+  TRY(dev_alloc(R, &P.ovf_queue, (size_t)P.queue_cap));
+  TRY(dev_alloc(R, &P.edge_off, ni + 1));
+  P.edge_cnt = P.edge_off;
+  P.edge_cap = P.raw_cap;
+  TRY(dev_alloc(R, &P.e_use, (size_t)P.edge_cap));
+  TRY(dev_alloc(R, &P.e_def, (size_t)P.edge_cap));
+  TRY(dev_alloc(R, &P.e_dmin, (size_t)P.edge_cap));
+  TRY(dev_alloc(R, &P.e_dlong, (size_t)P.edge_cap));
+  TRY(dev_alloc(R, &P.e_flags, (size_t)P.edge_cap));
+  TRY(dev_alloc(R, &P.e_share, (size_t)P.edge_cap * 8));
+  TRY(dev_alloc(R, &P.blame, ni * kCnt));
+  TRY(dev_alloc(R, &P.a_totals, nf * 4));
+  TRY(dev_alloc(R, &P.a_matched, nf * GPA_NUM_OPT));
+  TRY(dev_alloc(R, &P.a_speedup, nf * GPA_NUM_OPT));
+  TRY(dev_alloc(R, &P.a_rank, nf * GPA_NUM_OPT));
+  TRY(dev_alloc(R, &P.a_nhot, nf * GPA_NUM_OPT));
+  TRY(dev_alloc(R, &P.a_hot, nf * GPA_NUM_OPT * 5 * 6));
+  TRY(dev_alloc(R, &P.a_loop_active, nl));
+  TRY(dev_alloc(R, &P.a_loop_matched, nl));
+  TRY(dev_alloc(R, &P.a_loop_speedup, nl));
+  TRY(dev_alloc(R, &P.a_line_stall, (size_t)P.n_lines));
+  TRY(dev_alloc(R, &P.a_line_lat, (size_t)P.n_lines));
+  cudaStream_t st = nullptr;
+  if (cudaMemset(P.cnt, 0, ni * kCnt * sizeof(unsigned long long)) != cudaSuccess ||
+      cudaMemset(P.stats, 0, SS_N * sizeof(unsigned long long)) != cudaSuccess ||
+      cudaMemset(P.edge_off, 0, (ni + 1) * sizeof(int32_t)) != cudaSuccess) {
+    free_program(R);
+    return GPA_ERR_CUDA;
+  }
+  launch_build_layout(P, st, ctx->sms, &ctx->launches);
+  launch_build_preds(P, R->n_succ, pred_off, cursor, R->scan_tmp, st, ctx->sms, &ctx->launches);
+  if (cudaDeviceSynchronize() != cudaSuccess || cudaGetLastError() != cudaSuccess) {
+    free_program(R);
+    return GPA_ERR_CUDA;
+  }
+#undef TRY
+  const gpa_pid pid = ctx->next_pid++;
+  ctx->progs[pid] = R;
+  *out = pid;
+  return GPA_OK;
+}
+
+gpa_status gpa_unload_program(gpa_ctx* ctx, gpa_pid pid) {
+  ProgramRec* R = find(ctx, pid);
+  if (!R) return GPA_ERR_NO_PROGRAM;
+  cudaDeviceSynchronize();
+  free_program(R);
+  ctx->progs.erase(pid);
+  return GPA_OK;
+}
+
+gpa_status gpa_reset_counts(gpa_ctx* ctx, gpa_pid pid, gpa_stream stream) {
+  ProgramRec* R = find(ctx, pid);
+  if (!R) return GPA_ERR_NO_PROGRAM;
+  cudaStream_t st = (cudaStream_t)stream;
+  CK(cudaMemsetAsync(R->P.cnt, 0, (size_t)R->P.ni * kCnt * sizeof(unsigned long long), st));
+  CK(cudaMemsetAsync(R->P.stats, 0, SS_N * sizeof(unsigned long long), st));
+  return GPA_OK;
+}
+
+gpa_status gpa_ingest_samples(gpa_ctx* ctx, gpa_pid pid, const uint64_t* dev_samples, size_t n, gpa_stream stream) {
+  ProgramRec* R = find(ctx, pid);
+  if (!R) return GPA_ERR_NO_PROGRAM;
+  if (n == 0) return GPA_OK;
+  if (!dev_samples || (reinterpret_cast<uintptr_t>(dev_samples) & 7u)) return GPA_ERR_INVALID_ARG;
+  launch_histogram(R->P, dev_samples, n, (cudaStream_t)stream, ctx->sms, &ctx->launches);
+  CK(cudaGetLastError());
+  return GPA_OK;
+}
+
+gpa_status gpa_ingest_host_samples(gpa_ctx* ctx, gpa_pid pid, const uint64_t* host, size_t n, gpa_stream stream) {
+  ProgramRec* R = find(ctx, pid);
+  if (!R) return GPA_ERR_NO_PROGRAM;
+  if (n == 0) return GPA_OK;
+  if (!host) return GPA_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (!ctx->stage[0]) {
+    ctx->stage_n = kStageSamples;
+    for (int k = 0; k < 2; ++k) {
+      if (cudaMalloc(&ctx->stage[k], ctx->stage_n * sizeof(uint64_t)) != cudaSuccess) return GPA_ERR_OOM;
+      CK(cudaEventCreateWithFlags(&ctx->ev_copied[k], cudaEventDisableTiming));
+      CK(cudaEventCreateWithFlags(&ctx->ev_used[k], cudaEventDisableTiming));
+      CK(cudaEventRecord(ctx->ev_used[k], st));
+    }
+    CK(cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking));
+  }
+  // Double buffering: the copy of chunk c+1 overlaps the aggregation of chunk c.
+  CK(cudaStreamWaitEvent(ctx->copy_stream, ctx->ev_used[0], 0));
+  CK(cudaStreamWaitEvent(ctx->copy_stream, ctx->ev_used[1], 0));
+  size_t off = 0;
+  for (int c = 0; off < n; ++c) {
+    const int k = c & 1;
+    const size_t m = std::min(ctx->stage_n, n - off);
+    CK(cudaStreamWaitEvent(ctx->copy_stream, ctx->ev_used[k], 0));
+    CK(cudaMemcpyAsync(ctx->stage[k], host + off, m * sizeof(uint64_t), cudaMemcpyHostToDevice, ctx->copy_stream));
+    CK(cudaEventRecord(ctx->ev_copied[k], ctx->copy_stream));
+    CK(cudaStreamWaitEvent(st, ctx->ev_copied[k], 0));
+    launch_histogram(R->P, ctx->stage[k], m, st, ctx->sms, &ctx->launches);
+    CK(cudaEventRecord(ctx->ev_used[k], st));
+    off += m;
+  }
+  CK(cudaGetLastError());
+  return GPA_OK;
+}
+
+gpa_status gpa_blame(gpa_ctx* ctx, gpa_pid pid, gpa_stream stream) {
+  ProgramRec* R = find(ctx, pid);
+  if (!R) return GPA_ERR_NO_PROGRAM;
+  cudaStream_t st = (cudaStream_t)stream;
+  // per-step counters: general searches, largest search, sweeps, raw edges, queues
+  CK(cudaMemsetAsync(R->P.stats + SS_GENERAL, 0, sizeof(unsigned long long) * 3, st));
+  CK(cudaMemsetAsync(R->P.stats + SS_RAW_N, 0, sizeof(unsigned long long) * (SS_N - SS_RAW_N), st));
+  launch_dataflow(R->P, ctx->arch, ctx->opts.max_fixpoint_sweeps, st, ctx->sms, &ctx->launches);
+  // The search scratch is shared by the context's programs: order its users.
+  CK(cudaStreamWaitEvent(st, ctx->scratch_ev, 0));
+  launch_blame(R->P, ctx->arch, ctx->tier1, ctx->tier2, ctx->opts.max_sources_per_use, R->scan_tmp, st, ctx->sms,
+               &ctx->launches);
+  CK(cudaEventRecord(ctx->scratch_ev, st));
+  CK(cudaGetLastError());
+  return GPA_OK;
+}
+
+static gpa_status copy_advice(ProgramRec* R, const gpa_advice* out, cudaStream_t st) {
+  const Prog& P = R->P;
+  const size_t nf = P.nf, no = GPA_NUM_OPT;
+  auto cp = [&](void* dst, const void* src, size_t bytes) {
+    return (dst && bytes) ? cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, st) : cudaSuccess;
+  };
+  CK(cp(out->totals, P.a_totals, nf * 4 * 8));
+  CK(cp(out->matched, P.a_matched, nf * no * 8));
+  CK(cp(out->speedup, P.a_speedup, nf * no * 8));
+  CK(cp(out->rank, P.a_rank, nf * no * 4));
+  CK(cp(out->n_hot, P.a_nhot, nf * no * 4));
+  CK(cp(out->hot, P.a_hot, nf * no * 5 * 6 * 8));
+  CK(cp(out->loop_active, P.a_loop_active, (size_t)P.nl * 8));
+  CK(cp(out->loop_matched, P.a_loop_matched, (size_t)P.nl * 8));
+  CK(cp(out->loop_speedup, P.a_loop_speedup, (size_t)P.nl * 8));
+  CK(cp(out->line_stall, P.a_line_stall, (size_t)P.n_lines * 8));
+  CK(cp(out->line_latency, P.a_line_lat, (size_t)P.n_lines * 8));
+  CK(cudaStreamSynchronize(st));
+  return GPA_OK;
+}
+
+gpa_status gpa_advise(gpa_ctx* ctx, gpa_pid pid, const gpa_advice* out, gpa_stream stream) {
+  ProgramRec* R = find(ctx, pid);
+  if (!R) return GPA_ERR_NO_PROGRAM;
+  cudaStream_t st = (cudaStream_t)stream;
+  launch_advise(R->P, ctx->arch, st, ctx->sms, &ctx->launches);
+  CK(cudaGetLastError());
+  if (out) return copy_advice(R, out, st);
+  return GPA_OK;
+}
+
+gpa_status gpa_get_advice(gpa_ctx* ctx, gpa_pid pid, const gpa_advice* out, gpa_stream stream) {
+  ProgramRec* R = find(ctx, pid);
+  if (!R) return GPA_ERR_NO_PROGRAM;
+  if (!out) return GPA_ERR_INVALID_ARG;
+  return copy_advice(R, out, (cudaStream_t)stream);
+}
+
+gpa_status gpa_sync_status(gpa_ctx* ctx, gpa_pid pid, gpa_stream stream, int64_t* info) {
+  ProgramRec* R = find(ctx, pid);
+  if (!R) return GPA_ERR_NO_PROGRAM;
+  cudaStream_t st = (cudaStream_t)stream;
+  unsigned long long h[SS_N];
+  CK(cudaStreamSynchronize(st));
+  CK(cudaMemcpy(h, R->P.stats, sizeof h, cudaMemcpyDeviceToHost));
+  if (info) {
+    info[0] = (int64_t)h[SS_INVALID];
+    info[1] = (int64_t)h[SS_GENERAL];
+    info[2] = (int64_t)h[SS_MAX_NODES];
+    info[3] = (int64_t)h[SS_SWEEPS];
+  }
+  return status_from(h[SS_STATUS]);
+}
+
+gpa_status gpa_get_counts(gpa_ctx* ctx, gpa_pid pid, uint64_t* counts, uint64_t* invalid, gpa_stream stream) {
+  ProgramRec* R = find(ctx, pid);
+  if (!R) return GPA_ERR_NO_PROGRAM;
+  cudaStream_t st = (cudaStream_t)stream;
+  CK(cudaStreamSynchronize(st));
+  if (counts) CK(cudaMemcpy(counts, R->P.cnt, (size_t)R->P.ni * kCnt * 8, cudaMemcpyDeviceToHost));
+  if (invalid) CK(cudaMemcpy(invalid, R->P.stats + SS_INVALID, 8, cudaMemcpyDeviceToHost));
+  return GPA_OK;
+}
+
+gpa_status gpa_get_reaching(gpa_ctx* ctx, gpa_pid pid, uint32_t* rin, uint32_t* rout, gpa_stream stream) {
+  ProgramRec* R = find(ctx, pid);
+  if (!R) return GPA_ERR_NO_PROGRAM;
+  CK(cudaStreamSynchronize((cudaStream_t)stream));
+  if (rin) CK(cudaMemcpy(rin, R->P.rin, (size_t)R->P.nb * kWords * 4, cudaMemcpyDeviceToHost));
+  if (rout) CK(cudaMemcpy(rout, R->P.rout, (size_t)R->P.nb * kWords * 4, cudaMemcpyDeviceToHost));
+  return GPA_OK;
+}
+
+gpa_status gpa_get_blame(gpa_ctx* ctx, gpa_pid pid, uint64_t* blame, gpa_stream stream) {
+  ProgramRec* R = find(ctx, pid);
+  if (!R) return GPA_ERR_NO_PROGRAM;
+  if (!blame) return GPA_ERR_INVALID_ARG;
+  CK(cudaStreamSynchronize((cudaStream_t)stream));
+  CK(cudaMemcpy(blame, R->P.blame, (size_t)R->P.ni * kCnt * 8, cudaMemcpyDeviceToHost));
+  return GPA_OK;
+}
+
+gpa_status gpa_get_edges(gpa_ctx* ctx, gpa_pid pid, int64_t* n_edges, int64_t cap, int32_t* use, int32_t* def,
+                         int32_t* dmin, int32_t* dlong, uint32_t* flags, uint64_t* share, gpa_stream stream) {
+  ProgramRec* R = find(ctx, pid);
+  if (!R) return GPA_ERR_NO_PROGRAM;
+  if (!n_edges) return GPA_ERR_INVALID_ARG;
+  CK(cudaStreamSynchronize((cudaStream_t)stream));
+  int32_t total = 0;
+  CK(cudaMemcpy(&total, R->P.edge_off + R->P.ni, 4, cudaMemcpyDeviceToHost));
+  if (total > R->P.edge_cap) total = (int32_t)R->P.edge_cap;
+  *n_edges = total;
+  const size_t m = (size_t)std::min<int64_t>(total, cap < 0 ? 0 : cap);
+  if (m) {
+    if (use) CK(cudaMemcpy(use, R->P.e_use, m * 4, cudaMemcpyDeviceToHost));
+    if (def) CK(cudaMemcpy(def, R->P.e_def, m * 4, cudaMemcpyDeviceToHost));
+    if (dmin) CK(cudaMemcpy(dmin, R->P.e_dmin, m * 4, cudaMemcpyDeviceToHost));
+    if (dlong) CK(cudaMemcpy(dlong, R->P.e_dlong, m * 4, cudaMemcpyDeviceToHost));
+    if (flags) CK(cudaMemcpy(flags, R->P.e_flags, m * 4, cudaMemcpyDeviceToHost));
+    if (share) CK(cudaMemcpy(share, R->P.e_share, m * 8 * 8, cudaMemcpyDeviceToHost));
+  }
+  return GPA_OK;
+}
+
+int64_t gpa_launch_count(gpa_ctx* ctx) { return ctx ? ctx->launches : -1; }
+
+}  // extern "C"

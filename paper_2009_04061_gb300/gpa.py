@@ -1,0 +1,362 @@
+"""ctypes binding of libgpa.so (include/gpa.h), argument marshalling only.
+
+Every step of the stall-blame path runs in the library's CUDA kernels; this
+module converts numpy arrays and torch tensors into the pointers and sizes
+the C ABI takes. Functions keep the C names (gpa_create, gpa_load_program,
+gpa_ingest_samples, gpa_blame, gpa_advise, ...); Context and Program wrap
+them for convenience. Importing fails loudly when libgpa.so is missing.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libgpa.so")
+HEADER = os.path.join(os.path.dirname(HERE), "include", "gpa.h")
+
+GPA_OK = 0
+STATUS = {0: "GPA_OK", -1: "GPA_ERR_INVALID_ARG", -2: "GPA_ERR_INVALID_PROGRAM", -3: "GPA_ERR_CUDA",
+          -4: "GPA_ERR_NOT_CONVERGED", -5: "GPA_ERR_CAPACITY", -6: "GPA_ERR_TIMEOUT", -7: "GPA_ERR_NO_PROGRAM",
+          -8: "GPA_ERR_OOM"}
+NUM_OPT = 8
+OPT_NAMES = ["REGISTER_REUSE", "STRENGTH_REDUCTION", "FUNCTION_SPLIT", "FAST_MATH", "WARP_BALANCE",
+             "MEMORY_TRANSACTION_REDUCTION", "LOOP_UNROLLING", "CODE_REORDERING"]
+
+
+class GpaError(RuntimeError):
+    def __init__(self, status: int, what: str = ""):
+        self.status = status
+        super().__init__(f"{what}: {STATUS.get(status, status)}")
+
+
+class gpa_arch_desc(ctypes.Structure):
+    _fields_ = [("n_opclasses", ctypes.c_int32), ("latency", ctypes.c_void_p), ("flags", ctypes.c_void_p)]
+
+
+class gpa_options(ctypes.Structure):
+    _fields_ = [("max_fixpoint_sweeps", ctypes.c_int32), ("max_search_nodes", ctypes.c_int32),
+                ("search_slots", ctypes.c_int32), ("max_sources_per_use", ctypes.c_int32),
+                ("small_search_nodes", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+
+
+_PROG_ARRAYS = ["func_instr_off", "func_block_off", "func_loop_off", "block_instr_off", "succ_off", "succ",
+                "opclass", "guard", "iflags", "line", "def_off", "def_res", "use_off", "use_res", "block_loop",
+                "loop_parent", "loop_header"]
+_PROG_DTYPES = dict(opclass=np.uint8, guard=np.uint8, iflags=np.uint8, def_res=np.uint16, use_res=np.uint16)
+
+
+class gpa_program_desc(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_int32) for k in ("n_functions", "n_instr", "n_blocks", "n_loops", "n_lines", "n_succ",
+                                             "n_def", "n_use")] + [(k, ctypes.c_void_p) for k in _PROG_ARRAYS]
+
+
+_ADV = ["totals", "matched", "speedup", "rank", "n_hot", "hot", "loop_active", "loop_matched", "loop_speedup",
+        "line_stall", "line_latency"]
+
+
+class gpa_advice(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_void_p) for k in _ADV]
+
+
+_lib = None
+
+
+def library() -> ctypes.CDLL:
+    """Loads libgpa.so; raises if it was not built (no fallback exists)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libgpa.so not built ({LIB_PATH}); run paper_2009_04061_gb300/build.py")
+    lib = ctypes.CDLL(LIB_PATH)
+    vp, i32, i64, u32 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32
+    sig = {
+        "gpa_status_string": ([i32], ctypes.c_char_p),
+        "gpa_arch_default": ([vp], i32),
+        "gpa_create": ([vp, vp, vp], i32),
+        "gpa_destroy": ([vp], i32),
+        "gpa_load_program": ([vp, vp, vp], i32),
+        "gpa_unload_program": ([vp, u32], i32),
+        "gpa_reset_counts": ([vp, u32, vp], i32),
+        "gpa_ingest_samples": ([vp, u32, vp, ctypes.c_size_t, vp], i32),
+        "gpa_ingest_host_samples": ([vp, u32, vp, ctypes.c_size_t, vp], i32),
+        "gpa_blame": ([vp, u32, vp], i32),
+        "gpa_advise": ([vp, u32, vp, vp], i32),
+        "gpa_sync_status": ([vp, u32, vp, vp], i32),
+        "gpa_get_counts": ([vp, u32, vp, vp, vp], i32),
+        "gpa_get_reaching": ([vp, u32, vp, vp, vp], i32),
+        "gpa_get_blame": ([vp, u32, vp, vp], i32),
+        "gpa_get_edges": ([vp, u32, vp, i64, vp, vp, vp, vp, vp, vp, vp], i32),
+        "gpa_get_advice": ([vp, u32, vp, vp], i32),
+        "gpa_launch_count": ([vp], i64),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = lib
+    return lib
+
+
+def header_functions() -> list[str]:
+    """Names of the entry points declared in include/gpa.h."""
+    with open(HEADER) as f:
+        text = f.read()
+    return sorted(set(re.findall(r"^(?![\s/*#])[\w\s\*]+?\b(gpa_\w+)\s*\(", text, flags=re.M)))
+
+
+def _p(a) -> ctypes.c_void_p:
+    if a is None:
+        return ctypes.c_void_p(0)
+    if isinstance(a, int):
+        return ctypes.c_void_p(a)
+    if hasattr(a, "data_ptr"):
+        return ctypes.c_void_p(a.data_ptr())
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _stream(stream) -> ctypes.c_void_p:
+    if stream is None:
+        return ctypes.c_void_p(0)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _check(st: int, what: str):
+    if st != GPA_OK:
+        raise GpaError(st, what)
+
+
+# ---------------------------------------------------------------- C-named wrappers
+def gpa_arch_default():
+    a = gpa_arch_desc()
+    _check(library().gpa_arch_default(ctypes.byref(a)), "gpa_arch_default")
+    n = a.n_opclasses
+    lat = np.ctypeslib.as_array(ctypes.cast(a.latency, ctypes.POINTER(ctypes.c_int32)), (n,)).copy()
+    fl = np.ctypeslib.as_array(ctypes.cast(a.flags, ctypes.POINTER(ctypes.c_uint32)), (n,)).copy()
+    return lat, fl
+
+
+def gpa_create(arch=None, options: dict | None = None):
+    lat, fl = arch if arch is not None else gpa_arch_default()
+    lat = np.ascontiguousarray(lat, dtype=np.int32)
+    fl = np.ascontiguousarray(fl, dtype=np.uint32)
+    a = gpa_arch_desc(lat.size, _p(lat), _p(fl))
+    o = gpa_options()
+    for k, v in (options or {}).items():
+        setattr(o, k, int(v))
+    ctx = ctypes.c_void_p()
+    _check(library().gpa_create(ctypes.byref(a), ctypes.byref(o), ctypes.byref(ctx)), "gpa_create")
+    return ctx
+
+
+def gpa_destroy(ctx):
+    _check(library().gpa_destroy(ctx), "gpa_destroy")
+
+
+def program_desc(arrays: dict):
+    """gpa_program_desc over host arrays (kept alive in the returned tuple)."""
+    keep = {}
+    for k in _PROG_ARRAYS:
+        a = np.ascontiguousarray(arrays[k], dtype=_PROG_DTYPES.get(k, np.int32))
+        keep[k] = a if a.size else np.zeros(1, dtype=a.dtype)
+    d = gpa_program_desc(int(arrays["n_functions"]), int(arrays["n_instr"]), int(arrays["n_blocks"]),
+                         int(arrays["n_loops"]), int(arrays["n_lines"]), int(np.asarray(arrays["succ"]).size),
+                         int(np.asarray(arrays["def_res"]).size), int(np.asarray(arrays["use_res"]).size),
+                         *[_p(keep[k]) for k in _PROG_ARRAYS])
+    return d, keep
+
+
+def gpa_load_program(ctx, arrays: dict) -> int:
+    d, keep = program_desc(arrays)
+    pid = ctypes.c_uint32()
+    st = library().gpa_load_program(ctx, ctypes.byref(d), ctypes.byref(pid))
+    del keep
+    _check(st, "gpa_load_program")
+    return pid.value
+
+
+def gpa_unload_program(ctx, pid):
+    _check(library().gpa_unload_program(ctx, pid), "gpa_unload_program")
+
+
+def gpa_reset_counts(ctx, pid, stream=None):
+    _check(library().gpa_reset_counts(ctx, pid, _stream(stream)), "gpa_reset_counts")
+
+
+def gpa_ingest_samples(ctx, pid, dev_samples, n: int | None = None, stream=None):
+    """dev_samples: a CUDA tensor of 64-bit samples (or a raw device pointer with n)."""
+    if n is None:
+        n = dev_samples.numel()
+    _check(library().gpa_ingest_samples(ctx, pid, _p(dev_samples), n, _stream(stream)), "gpa_ingest_samples")
+
+
+def gpa_ingest_host_samples(ctx, pid, host_samples, n: int | None = None, stream=None):
+    if n is None:
+        n = host_samples.numel() if hasattr(host_samples, "numel") else host_samples.size
+    _check(library().gpa_ingest_host_samples(ctx, pid, _p(host_samples), n, _stream(stream)),
+           "gpa_ingest_host_samples")
+
+
+def gpa_blame(ctx, pid, stream=None):
+    _check(library().gpa_blame(ctx, pid, _stream(stream)), "gpa_blame")
+
+
+def _advice_buffers(shape):
+    nf, nl, nlines = shape
+    return dict(totals=np.zeros((nf, 4), np.uint64), matched=np.zeros((nf, NUM_OPT), np.uint64),
+                speedup=np.zeros((nf, NUM_OPT), np.float64), rank=np.zeros((nf, NUM_OPT), np.int32),
+                n_hot=np.zeros((nf, NUM_OPT), np.int32), hot=np.zeros((nf, NUM_OPT, 5, 6), np.int64),
+                loop_active=np.zeros(max(nl, 1), np.uint64), loop_matched=np.zeros(max(nl, 1), np.uint64),
+                loop_speedup=np.zeros(max(nl, 1), np.float64), line_stall=np.zeros(max(nlines, 1), np.uint64),
+                line_latency=np.zeros(max(nlines, 1), np.uint64))
+
+
+def _trim(b, shape):
+    nf, nl, nlines = shape
+    for k in ("loop_active", "loop_matched", "loop_speedup"):
+        b[k] = b[k][:nl]
+    for k in ("line_stall", "line_latency"):
+        b[k] = b[k][:nlines]
+    return b
+
+
+def gpa_advise(ctx, pid, shape=None, stream=None):
+    """shape = (n_functions, n_loops, n_lines) to fetch results, or None to keep them on the device."""
+    if shape is None:
+        _check(library().gpa_advise(ctx, pid, None, _stream(stream)), "gpa_advise")
+        return None
+    b = _advice_buffers(shape)
+    adv = gpa_advice(*[_p(b[k]) for k in _ADV])
+    _check(library().gpa_advise(ctx, pid, ctypes.byref(adv), _stream(stream)), "gpa_advise")
+    return _trim(b, shape)
+
+
+def gpa_get_advice(ctx, pid, shape, stream=None):
+    b = _advice_buffers(shape)
+    adv = gpa_advice(*[_p(b[k]) for k in _ADV])
+    _check(library().gpa_get_advice(ctx, pid, ctypes.byref(adv), _stream(stream)), "gpa_get_advice")
+    return _trim(b, shape)
+
+
+def gpa_sync_status(ctx, pid, stream=None):
+    info = np.zeros(4, np.int64)
+    st = library().gpa_sync_status(ctx, pid, _stream(stream), _p(info))
+    return st, dict(invalid=int(info[0]), general_searches=int(info[1]), max_nodes=int(info[2]),
+                    sweeps=int(info[3]))
+
+
+def gpa_get_counts(ctx, pid, n_instr: int, stream=None):
+    c = np.zeros(n_instr * 24, np.uint64)
+    bad = np.zeros(1, np.uint64)
+    _check(library().gpa_get_counts(ctx, pid, _p(c), _p(bad), _stream(stream)), "gpa_get_counts")
+    return c.reshape(n_instr, 12, 2), int(bad[0])
+
+
+def gpa_get_reaching(ctx, pid, n_blocks: int, stream=None):
+    rin = np.zeros(n_blocks * 9, np.uint32)
+    rout = np.zeros(n_blocks * 9, np.uint32)
+    _check(library().gpa_get_reaching(ctx, pid, _p(rin), _p(rout), _stream(stream)), "gpa_get_reaching")
+    return rin.reshape(-1, 9), rout.reshape(-1, 9)
+
+
+def gpa_get_blame(ctx, pid, n_instr: int, stream=None):
+    b = np.zeros(n_instr * 24, np.uint64)
+    _check(library().gpa_get_blame(ctx, pid, _p(b), _stream(stream)), "gpa_get_blame")
+    return b.reshape(n_instr, 12, 2)
+
+
+def gpa_get_edges(ctx, pid, stream=None):
+    n = ctypes.c_int64()
+    lib = library()
+    _check(lib.gpa_get_edges(ctx, pid, ctypes.byref(n), 0, None, None, None, None, None, None, _stream(stream)),
+           "gpa_get_edges")
+    m = n.value
+    a = dict(j=np.zeros(max(m, 1), np.int32), i=np.zeros(max(m, 1), np.int32), dmin=np.zeros(max(m, 1), np.int32),
+             dlong=np.zeros(max(m, 1), np.int32), flags=np.zeros(max(m, 1), np.uint32),
+             share=np.zeros(max(m, 1) * 8, np.uint64))
+    _check(lib.gpa_get_edges(ctx, pid, ctypes.byref(n), m, _p(a["j"]), _p(a["i"]), _p(a["dmin"]), _p(a["dlong"]),
+                             _p(a["flags"]), _p(a["share"]), _stream(stream)), "gpa_get_edges")
+    out = {k: v[:m] for k, v in a.items() if k != "share"}
+    out["share"] = a["share"][:m * 8].reshape(m, 4, 2)
+    return out
+
+
+def gpa_launch_count(ctx) -> int:
+    return int(library().gpa_launch_count(ctx))
+
+
+# ---------------------------------------------------------------- convenience objects
+class Context:
+    def __init__(self, arch=None, options: dict | None = None):
+        self.handle = gpa_create(arch, options)
+
+    def load_program(self, arrays) -> "Program":
+        a = arrays.arrays if hasattr(arrays, "arrays") else arrays
+        return Program(self, gpa_load_program(self.handle, a), a)
+
+    def launches(self) -> int:
+        return gpa_launch_count(self.handle)
+
+    def close(self):
+        if self.handle:
+            gpa_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+class Program:
+    def __init__(self, ctx: Context, pid: int, arrays: dict):
+        self.ctx, self.pid = ctx, pid
+        self.n_instr, self.n_blocks = int(arrays["n_instr"]), int(arrays["n_blocks"])
+        self.shape = (int(arrays["n_functions"]), int(arrays["n_loops"]), int(arrays["n_lines"]))
+
+    @property
+    def h(self):
+        return self.ctx.handle
+
+    def reset(self, stream=None):
+        gpa_reset_counts(self.h, self.pid, stream)
+
+    def ingest(self, dev_samples, n=None, stream=None):
+        gpa_ingest_samples(self.h, self.pid, dev_samples, n, stream)
+
+    def ingest_host(self, host_samples, n=None, stream=None):
+        gpa_ingest_host_samples(self.h, self.pid, host_samples, n, stream)
+
+    def blame(self, stream=None):
+        gpa_blame(self.h, self.pid, stream)
+
+    def advise(self, fetch: bool = True, stream=None):
+        return gpa_advise(self.h, self.pid, self.shape if fetch else None, stream)
+
+    def status(self, stream=None):
+        return gpa_sync_status(self.h, self.pid, stream)
+
+    def counts(self, stream=None):
+        return gpa_get_counts(self.h, self.pid, self.n_instr, stream)
+
+    def reaching(self, stream=None):
+        return gpa_get_reaching(self.h, self.pid, self.n_blocks, stream)
+
+    def blame_counts(self, stream=None):
+        return gpa_get_blame(self.h, self.pid, self.n_instr, stream)
+
+    def edges(self, stream=None):
+        return gpa_get_edges(self.h, self.pid, stream)
+
+    def advice(self, stream=None):
+        return gpa_get_advice(self.h, self.pid, self.shape, stream)
+
+    def unload(self):
+        gpa_unload_program(self.h, self.pid)

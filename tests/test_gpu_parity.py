@@ -1,0 +1,189 @@
+"""CUDA path (through the C ABI) against the CPU oracle, element by element:
+counts, reaching masks, merged edges with their distances and shares, blame,
+and advice. Bit-exact for every integer; FP64 speedups within 1e-12 relative."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from bruteforce import tiny_program
+from parity import ARCH, assert_advice_equal, assert_edges_equal, assert_full_parity, gpu_run, oracle_run
+from progbuild import I, counts, program
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import paper_2009_04061_gb300 as g
+    c = g.Context(ARCH)
+    yield c
+    c.close()
+
+
+def dev(samples):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(samples).view(np.int64)).cuda()
+
+
+def test_paper_examples_blame(ctx):
+    import test_oracle as T
+    for prog, cnt_entries in [
+        (T.fig4(), {(7, 0, 0): 10, (4, 0, 0): 20, (5, 0, 0): 7, (10, 3, 0): 100, (10, 2, 1): 9}),
+        (T.one_block([I("LDG", ["R0"], ["R2", "R3"], wb=0), I("IADD", ["R5"], ["R6", "R7"]),
+                      I("BRA", [], [], wait=[0])]), {(0, 0, 0): 5, (2, 3, 0): 40, (2, 3, 1): 60}),
+        (T.diamond(False), {(0, 0, 0): 3, (5, 3, 1): 30, (3, 2, 0): 4}),
+        (T.diamond(True), {(0, 0, 0): 3, (6, 3, 1): 30, (4, 2, 0): 4}),
+    ]:
+        ss = []
+        for (pc, c, l), v in cnt_entries.items():
+            ss += [(0 << 48) | (pc << 24) | (c << 20) | (l << 19)] * v
+        s = np.array(ss, dtype=np.uint64)
+        g = gpu_run(ctx, prog, dev(s))
+        R = oracle_run(prog, s)
+        assert_full_parity(g, R)
+
+
+@pytest.mark.parametrize("seed", range(16))
+def test_tiny_guarded_programs(ctx, seed):
+    P = tiny_program(seed, n_instr=25 + seed, n_loops=seed % 3, guard_pct=20 + 3 * seed)
+    s = P.samples(20_000, seed=seed)
+    g = gpu_run(ctx, P, dev(s))
+    assert_full_parity(g, oracle_run(P, s))
+
+
+def test_plain_workload(ctx):
+    ps, ns, kz = synth.workload("plain")
+    P = synth.make_program(ps, kz)
+    s = P.samples(ns)
+    g = gpu_run(ctx, P, dev(s))
+    assert_full_parity(g, oracle_run(P, s))
+
+
+def test_rodinia_workload_with_invalid_and_ragged_tail(ctx):
+    ps, _, kz = synth.workload("rodinia")
+    P = synth.make_program(ps, kz)
+    s = P.samples(2_000_003, invalid_ppm=3000)      # odd count: scalar tail
+    g = gpu_run(ctx, P, dev(s))
+    R = oracle_run(P, s)
+    assert R["invalid"] > 0
+    assert_full_parity(g, R)
+
+
+def test_misaligned_start_and_edge_sizes(ctx):
+    ps, _, kz = synth.workload("plain")
+    P = synth.make_program(ps, kz)
+    s = P.samples(10_001)
+    d = dev(s)
+    for lo, hi in [(1, 10_001), (1, 2), (0, 1), (3, 4), (0, 0)]:
+        g = gpu_run(ctx, P, d[lo:hi])
+        cnt, bad = oracle.histogram(P, s[lo:hi])
+        assert np.array_equal(g["counts"], cnt) and g["invalid"] == bad
+
+
+def test_all_invalid_samples(ctx):
+    ps, _, kz = synth.workload("plain")
+    P = synth.make_program(ps, kz)
+    bad = np.array([(5 << 48), (0 << 48) | (300 << 24), (0 << 48) | (13 << 20), (1 << 19), 7], dtype=np.uint64)
+    g = gpu_run(ctx, P, dev(np.tile(bad, 1000)))
+    assert g["invalid"] == 5000 and int(g["counts"].sum()) == 0
+    assert int(g["blame"].sum()) == 0 and g["status"] == 0
+
+
+def test_batched_subset_of_uneven_functions(ctx):
+    rng = np.random.default_rng(5)
+    ps = synth.batched_params(60, rng, 5)
+    P = synth.make_program(ps, 1.0)
+    s = P.samples(6_000_000, seed=5)
+    g = gpu_run(ctx, P, dev(s))
+    assert_full_parity(g, oracle_run(P, s))
+
+
+def test_host_ingest_equals_device_ingest(ctx):
+    ps, _, kz = synth.workload("rodinia")
+    P = synth.make_program(ps, kz)
+    s = P.samples(1_000_000, seed=3)
+    import torch
+    h = torch.from_numpy(s.view(np.int64)).pin_memory()
+    g1 = gpu_run(ctx, P, None, host=h)
+    g2 = gpu_run(ctx, P, dev(s))
+    assert np.array_equal(g1["counts"], g2["counts"]) and np.array_equal(g1["blame"], g2["blame"])
+
+
+def test_plain_per_function_equals_batched(ctx):
+    """Each function loaded alone gives the same results as in the batched program."""
+    rng = np.random.default_rng(9)
+    ps = synth.batched_params(12, rng, 9)
+    P = synth.make_program(ps, 1.0)
+    s = P.samples(2_000_000, seed=9)
+    gb = gpu_run(ctx, P, dev(s))
+    k = (s >> np.uint64(48)).astype(np.int64)
+    for f in range(P.n_functions):
+        Pf = synth.make_program([ps[f]], 1.0)
+        sf = s[k == f] & ~np.uint64(0xFFFF << 48)
+        gf = gpu_run(ctx, Pf, dev(sf))
+        i0, i1 = P.func_instr_off[f], P.func_instr_off[f + 1]
+        assert np.array_equal(gf["blame"], gb["blame"][i0:i1])
+        assert np.array_equal(gf["advice"]["speedup"][0], gb["advice"]["speedup"][f])
+        # pcs, distance and samples of every hotspot (line ids are offset per program)
+        assert np.array_equal(gf["advice"]["hot"][0][..., [0, 1, 4, 5]], gb["advice"]["hot"][f][..., [0, 1, 4, 5]])
+
+
+def test_fixpoint_sweep_limit_reports_not_converged():
+    import paper_2009_04061_gb300 as g
+    with g.Context(ARCH, dict(max_fixpoint_sweeps=1)) as c:
+        ps, ns, kz = synth.workload("plain")
+        P = synth.make_program(ps, kz)
+        r = gpu_run(c, P, dev(P.samples(1000)))
+        assert r["status"] == -4
+
+
+def test_invalid_program_rejected(ctx):
+    import paper_2009_04061_gb300 as g
+    bad = program([([[I("IADD", ["R1"], ["R2"])], [I("EXIT")]], [[1], [0]], [])])  # back edge without a loop
+    with pytest.raises(g.GpaError) as e:
+        ctx.load_program(bad)
+    assert e.value.status == -2
+
+
+def test_small_search_slots_overflow_to_large_tier():
+    """A tiny first-tier slot forces general searches into the second tier; results stay exact."""
+    import paper_2009_04061_gb300 as g
+    with g.Context(ARCH, dict(small_search_nodes=4, search_slots=64)) as c:
+        rng = np.random.default_rng(11)
+        P = synth.make_program(synth.batched_params(20, rng, 11), 1.0)
+        s = P.samples(1_000_000, seed=11)
+        r = gpu_run(c, P, dev(s))
+        assert r["info"]["general_searches"] > 0 and r["info"]["max_nodes"] > 4
+        assert_full_parity(r, oracle_run(P, s))
+
+
+def test_full_batched_workload_sampled_functions(ctx):
+    """The bench's workload at full size (2,000 functions, 5e8 samples): invariants over the
+    whole program, and five functions (smallest to largest) against the oracle element by element."""
+    import torch
+    ps, n, kz = synth.workload("batched")
+    P = synth.make_program(ps, kz)
+    host = torch.empty(n, dtype=torch.int64)
+    s = P.samples(n, out=host.numpy().view(np.uint64))
+    g = gpu_run(ctx, P, host.cuda())
+    assert g["status"] == 0, g["info"]
+    assert int(g["counts"].sum()) + g["invalid"] == n
+    assert np.array_equal(g["blame"].sum(0), g["counts"].sum(0))          # conservation per class and flag
+    sizes = np.diff(P.func_instr_off)
+    picks = sorted({int(np.argmin(np.abs(sizes - t))) for t in (60, 400, 1500, 5000, 20000)})
+    k = s >> np.uint64(48)
+    for f in picks:
+        sf = s[k == np.uint64(f)]
+        cnt, bad = oracle.histogram(P, sf)
+        R = oracle.analyze(P, ARCH, cnt, f, f + 1)
+        i0, i1 = int(P.func_instr_off[f]), int(P.func_instr_off[f + 1])
+        b0, b1 = int(P.func_block_off[f]), int(P.func_block_off[f + 1])
+        l0, l1 = int(P.func_loop_off[f]), int(P.func_loop_off[f + 1])
+        assert np.array_equal(g["counts"][i0:i1], cnt[i0:i1]), f
+        rin, rout = oracle.reaching(P, f, f + 1)
+        assert np.array_equal(g["rin"][b0:b1], rin) and np.array_equal(g["rout"][b0:b1], rout), f
+        assert np.array_equal(g["blame"][i0:i1], R["blame"]), f
+        assert_edges_equal(g["edges"], R["edges"], i0, i1)
+        ga = {key: v for key, v in g["advice"].items()}
+        assert_advice_equal(ga, R, f, f + 1, l0, l1)
