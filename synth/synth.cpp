@@ -79,7 +79,13 @@ struct Gen {
   Rng rng;
   FnParams p;
   Fn fn;
-  std::vector<int> recent;
+  // Register allocation model: temporaries have short live ranges and their
+  // registers are reused once dead; parameters (base pointers, sizes) are
+  // loaded at entry and never redefined; each loop owns an induction variable.
+  std::vector<int> live_reg, live_uses;   // live temporaries, oldest first
+  std::vector<int> addr_reg, addr_uses;   // live 64-bit address temporaries (first register of the pair)
+  uint8_t rstate[256];                    // 0 free, 1 temporary, 2 long lived
+  std::vector<int> params, param_pairs, ivs;
   int8_t wbar[256], rbar[256];
   int bar_prod[6];
   bool bar_read[6];
@@ -96,6 +102,7 @@ struct Gen {
   explicit Gen(const FnParams& fp) : rng(fp.seed), p(fp) {
     std::memset(wbar, -1, sizeof wbar);
     std::memset(rbar, -1, sizeof rbar);
+    std::memset(rstate, 0, sizeof rstate);
     for (int k = 0; k < 6; ++k) { bar_prod[k] = -1; bar_read[k] = false; }
     for (int r = 0; r < 256; ++r) arith_at[r] = -1000000;
     for (int o = 0; o < N_OP; ++o) mix[o] = 0;
@@ -121,24 +128,75 @@ struct Gen {
     return IADD;
   }
 
+  void free_reg(int r) { if (rstate[r] == 1) rstate[r] = 0; }
   int pick_src() {
-    if (!recent.empty() && rng.coin(0.85)) {
-      int w = (int)std::min<size_t>(12, recent.size());
-      int k = std::min(rng.below(w), rng.below(w));
-      return recent[recent.size() - 1 - k];
+    const double u = rng.uni();
+    if (u < 0.08 && !params.empty()) return params[rng.below((int)params.size())];
+    if (u < 0.16 && !ivs.empty()) return ivs[rng.below((int)ivs.size())];
+    if (!live_reg.empty()) {
+      const int w = (int)std::min<size_t>(6, live_reg.size());
+      const int k = std::min(rng.below(w), rng.below(w));
+      const int idx = (int)live_reg.size() - 1 - k;
+      const int r = live_reg[idx];
+      if (--live_uses[idx] <= 0) {
+        free_reg(r);
+        live_reg.erase(live_reg.begin() + idx);
+        live_uses.erase(live_uses.begin() + idx);
+      }
+      return r;
     }
-    return rng.below(p.n_regs);
+    if (!params.empty()) return params[rng.below((int)params.size())];
+    return 0;
   }
-  int pick_dst(int width) {
-    int r = rng.below(p.n_regs - width + 1);
-    r -= r % width;
-    return r;
+  int n_uses() { int k = 1; while (k < 6 && rng.coin(0.45)) ++k; return k; }
+  void evict_oldest() {
+    if (!live_reg.empty()) {
+      free_reg(live_reg[0]);
+      live_reg.erase(live_reg.begin()); live_uses.erase(live_uses.begin());
+    } else if (!addr_reg.empty()) {
+      free_reg(addr_reg[0]); free_reg(addr_reg[0] + 1);
+      addr_reg.erase(addr_reg.begin()); addr_uses.erase(addr_uses.begin());
+    }
+  }
+  // An aligned run of `width` free registers, preferring low numbers as an allocator does.
+  int alloc(int width) {
+    for (int tries = 0; tries < 64; ++tries) {
+      int seen = 0, pick = -1;
+      const int skip = rng.below(4);
+      for (int r = 0; r + width <= p.n_regs; r += width) {
+        bool ok = true;
+        for (int t = 0; t < width; ++t) ok = ok && rstate[r + t] == 0;
+        if (!ok) continue;
+        pick = r;
+        if (seen++ == skip) break;
+      }
+      if (pick >= 0) return pick;
+      if (live_reg.empty() && addr_reg.empty()) break;
+      evict_oldest();
+    }
+    return 0;
+  }
+  int new_temp(int width) {
+    const int d = alloc(width);
+    for (int t = 0; t < width; ++t) {
+      rstate[d + t] = 1;
+      live_reg.push_back(d + t);
+      live_uses.push_back(n_uses());
+    }
+    return d;
   }
   int pick_pair() {
-    int r = (!recent.empty() && rng.coin(0.7)) ? pick_src() : rng.below(p.n_regs);
-    r &= ~1;
-    if (r + 1 >= p.n_regs) r = (p.n_regs - 2) & ~1;
-    return r;
+    if (!addr_reg.empty() && rng.coin(0.6)) {
+      const int idx = (int)addr_reg.size() - 1;
+      const int r = addr_reg[idx];
+      if (--addr_uses[idx] <= 0) {
+        free_reg(r); free_reg(r + 1);
+        addr_reg.erase(addr_reg.begin() + idx); addr_uses.erase(addr_uses.begin() + idx);
+      }
+      return r;
+    }
+    if (!param_pairs.empty()) return param_pairs[rng.below((int)param_pairs.size())];
+    return 0;
   }
   static void add_unique(std::vector<uint16_t>& v, int x) {
     for (uint16_t y : v) if ((y & 0x1FF) == (x & 0x1FF)) return;
@@ -161,20 +219,31 @@ struct Gen {
   }
 
   // guard: -1 draw at random, 0 none, else the literal (1+i for Pi, 8+i for !Pi).
-  Ins build(Op op, int guard, int forced_dst = -1) {
+  Ins build(Op op, int guard, int forced_dst = -1, int forced_w = 1) {
     Ins in;
     in.op = (uint8_t)op;
     std::vector<int> srcs, dsts;
     int pdef = -1;
     auto dst_w = [&](int w) {
-      int d = forced_dst >= 0 ? forced_dst - forced_dst % w : pick_dst(w);
-      if (d + w > p.n_regs) d = p.n_regs - w - (p.n_regs - w) % w;
-      for (int t = 0; t < w; ++t) dsts.push_back(d + t);
+      const int d = forced_dst >= 0 ? forced_dst : new_temp(w);
+      for (int t = 0; t < (forced_dst >= 0 ? forced_w : w); ++t) dsts.push_back(d + t);
     };
     auto pair = [&]() { int a = pick_pair(); srcs.push_back(a); srcs.push_back(a + 1); };
     switch (op) {
       case IADD: dst_w(1); srcs.push_back(pick_src()); srcs.push_back(pick_src()); break;
-      case IMAD: case FFMA:
+      case IMAD:
+        if (forced_dst < 0 && rng.coin(0.3)) {  // wide multiply-add producing a 64-bit address
+          const int a = alloc(2);
+          rstate[a] = rstate[a + 1] = 1;
+          addr_reg.push_back(a); addr_uses.push_back(n_uses());
+          dsts.push_back(a); dsts.push_back(a + 1);
+          srcs.push_back(pick_src()); srcs.push_back(pick_src());
+          const int b = pick_pair(); srcs.push_back(b); srcs.push_back(b + 1);
+        } else {
+          dst_w(1); for (int t = 0; t < 3; ++t) srcs.push_back(pick_src());
+        }
+        break;
+      case FFMA:
         dst_w(1); for (int t = 0; t < 3; ++t) srcs.push_back(pick_src()); break;
       case DFMA: dst_w(2); pair(); pair(); break;
       case MOV: dst_w(1); srcs.push_back(pick_src()); break;
@@ -187,7 +256,7 @@ struct Gen {
       case STS: srcs.push_back(pick_src()); srcs.push_back(pick_src()); break;
       case LDL: dst_w(1); srcs.push_back(pick_src()); break;
       case STL: srcs.push_back(pick_src()); srcs.push_back(pick_src()); break;
-      case LDC: dst_w(rng.coin(0.7) ? 1 : 2); if (rng.coin(0.5)) srcs.push_back(pick_src()); break;
+      case LDC: dst_w(rng.coin(0.7) ? 1 : 2); if (forced_dst < 0 && rng.coin(0.5)) srcs.push_back(pick_src()); break;
       case ATOM: dst_w(1); pair(); srcs.push_back(pick_src()); break;
       default: break;  // BRA, BAR, MEMBAR, EXIT
     }
@@ -247,9 +316,7 @@ struct Gen {
       if (!wset) wbar[d] = -1;
       rbar[d] = -1;
       arith_at[d] = fixed_lat ? icount : -1000000;
-      recent.push_back(d);
     }
-    if (recent.size() > 32) recent.erase(recent.begin(), recent.begin() + (recent.size() - 32));
     if (pdef >= 0 && std::find(preds.begin(), preds.end(), pdef) == preds.end()) preds.push_back(pdef);
     if (op == MUFU) in.flags |= 1;  // instruction stands for a math-library call
     if (rng.coin(0.35)) ++line;
@@ -265,7 +332,7 @@ struct Gen {
       if (t + 1 < n && !preds.empty() && rng.coin(0.3 * p.guard_pct / 100.0)) {
         // A complementary guarded pair defining one register (the Fig. 4a shape).
         int pk = preds[rng.below((int)preds.size())];
-        int d = pick_dst(1);
+        int d = new_temp(1);
         fn.blocks[b].ins.push_back(build(LDG, 1 + pk, d));
         fn.blocks[b].ins.push_back(build(rng.coin(0.5) ? LDC : IMAD, 8 + pk, d));
         ++t;
@@ -275,8 +342,9 @@ struct Gen {
     }
   }
 
-  void end_cbr(int b, int target, bool negate) {
+  void end_cbr(int b, int target, bool negate, int cond_src = -1) {
     Ins s = build(ISETP, 0);
+    if (cond_src >= 0) add_unique(s.uses, kRegBase + cond_src);
     int pk = -1;
     for (uint16_t d : s.defs) if ((d & 0x1FF) >= kPredBase && (d & 0x1FF) < kBarBase) pk = (d & 0x1FF) - kPredBase;
     fn.blocks[b].ins.push_back(s);
@@ -333,26 +401,62 @@ struct Gen {
     }
   }
 
+  // Induction variable: set in the block that falls into the loop, stepped in the latch.
+  int iv_begin() {
+    const int iv = alloc(1);
+    rstate[iv] = 2;
+    fn.blocks.back().ins.push_back(build(MOV, 0, iv));
+    ivs.push_back(iv);
+    return iv;
+  }
+  void iv_step(int b, int iv) {
+    Ins st = build(IADD, 0, iv);
+    add_unique(st.uses, kRegBase + iv);
+    fn.blocks[b].ins.push_back(st);
+  }
+  void iv_end(int iv) { ivs.pop_back(); rstate[iv] = 0; }
+
   void loop(int node, int budget) {
     int parent = cur_loop;
     int id = (int)fn.loops.size();
     fn.loops.emplace_back();
     fn.loops[id].parent = parent;
     cur_loop = id;
+    const int iv = iv_begin();
     if (rng.coin(0.4)) {  // while loop: test at the top, unconditional latch
-      int h = new_block(); fill(h, rng.range(0, 2)); end_cbr(h, -1, true);
+      int h = new_block(); fill(h, rng.range(0, 2)); end_cbr(h, -1, true, iv);
       fn.loops[id].header = h; fn.loops[id].first = h;
       seq(std::max(6, budget - 8), lnodes[node].kids);
-      int l = new_block(); fill(l, rng.range(1, 4)); end_br(l, h);
+      int l = new_block(); fill(l, rng.range(1, 3)); iv_step(l, iv); end_br(l, h);
       fn.loops[id].last = l;
       fn.blocks[h].target = l + 1;
     } else {              // do-while loop: test in the latch
       int first = (int)fn.blocks.size();
       seq(std::max(6, budget - 6), lnodes[node].kids);
-      int l = new_block(); fill(l, rng.range(1, 4)); end_cbr(l, first, false);
+      int l = new_block(); fill(l, rng.range(1, 3)); iv_step(l, iv); end_cbr(l, first, false, iv);
       fn.loops[id].header = first; fn.loops[id].first = first; fn.loops[id].last = l;
     }
+    iv_end(iv);
     cur_loop = parent;
+  }
+
+  // Kernel parameters: base-pointer pairs and scalars loaded from constant
+  // memory at entry and live for the whole function.
+  void prologue(int b) {
+    const int npairs = std::max(1, std::min(4, p.n_regs / 24));
+    const int nsingle = std::max(1, std::min(4, p.n_regs / 24));
+    for (int k = 0; k < npairs; ++k) {
+      const int r = alloc(2);
+      rstate[r] = rstate[r + 1] = 2;
+      param_pairs.push_back(r);
+      fn.blocks[b].ins.push_back(build(LDC, 0, r, 2));
+    }
+    for (int k = 0; k < nsingle; ++k) {
+      const int r = alloc(1);
+      rstate[r] = 2;
+      params.push_back(r);
+      fn.blocks[b].ins.push_back(build(LDC, 0, r, 1));
+    }
   }
 
   void seq(int budget, const std::vector<int>& kids) {
@@ -397,25 +501,30 @@ struct Gen {
       }
     }
     for (int r : roots) compute_weight(r);
-    seq(std::max(8, p.n_instr - 4), roots);
+    const int e0 = new_block();
+    prologue(e0);
+    fill(e0, rng.range(2, 6));
+    seq(std::max(8, p.n_instr - 4 - (int)fn.blocks[e0].ins.size()), roots);
     int e = new_block(); fill(e, 2); fn.blocks[e].ins.push_back(build(EXIT_, 0)); fn.blocks[e].term = 3;
   }
 
   // One function of 200 instructions in 12 blocks: two entry blocks, an
   // if/else diamond, a do-while loop of four blocks, two tail blocks.
   void template_c1() {
-    int b0 = new_block(); fill(b0, 18);
+    int b0 = new_block(); prologue(b0); fill(b0, 18 - (int)fn.blocks[b0].ins.size());
     int b1 = new_block(); fill(b1, 16);
     int c = new_block(); fill(c, 12); end_cbr(c, -1, rng.coin(0.5));
     int t = new_block(); fill(t, 19); end_br(t, -1);
     int e = new_block(); fill(e, 18);
-    int j = new_block(); fill(j, 16);
+    int j = new_block(); fill(j, 15);
     fn.blocks[c].target = e; fn.blocks[t].target = j;
     fn.loops.emplace_back();
+    const int iv = iv_begin();
     int h = new_block(); fill(h, 20);
     int m1 = new_block(); fill(m1, 18);
     int m2 = new_block(); fill(m2, 20);
-    int l = new_block(); fill(l, 14); end_cbr(l, h, false);
+    int l = new_block(); fill(l, 13); iv_step(l, iv); end_cbr(l, h, false, iv);
+    iv_end(iv);
     fn.loops[0].header = h; fn.loops[0].first = h; fn.loops[0].last = l; fn.loops[0].parent = -1;
     int x1 = new_block(); fill(x1, 14);
     int x2 = new_block(); fill(x2, 9); fn.blocks[x2].ins.push_back(build(EXIT_, 0)); fn.blocks[x2].term = 3;
