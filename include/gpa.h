@@ -98,12 +98,14 @@ typedef struct {
 
 typedef struct {
   int32_t max_fixpoint_sweeps;  /* reaching-definitions sweep limit; 0 = 64 */
-  int32_t max_search_nodes;     /* (block, predicate-set) nodes per general search; 0 = 65536 */
-  int32_t search_slots;         /* concurrent first-tier general searches; 0 = 32 per SM */
+  int32_t max_search_nodes;     /* (block, predicate-set) nodes of the largest general search; 0 = 65536 */
+  int32_t search_slots;         /* warps with a max_search_nodes global-memory arena; 0 = one per SM */
   int32_t max_sources_per_use;  /* distinct sources merged per stalled use; 0 = 64 (max 64) */
-  int32_t small_search_nodes;   /* nodes per first-tier search slot; 0 = 512. A search that outgrows
-                                   it is redone in a max_search_nodes slot (one slot per SM) */
-  int32_t reserved[3];          /* must be 0 */
+  int32_t small_search_nodes;   /* nodes of the shared-memory arena of a first-tier search warp; 0 = 128
+                                   (max 1024). A search that outgrows it is redone in the next tier */
+  int32_t mid_search_nodes;     /* nodes of the second tier's shared-memory arenas (three warps per SM
+                                   up to 512 nodes, one up to 1024); 0 = min(512, max_search_nodes) */
+  int32_t reserved[2];          /* must be 0 */
 } gpa_options;
 
 /* A program: n_functions functions laid out one after another. All arrays are

@@ -24,7 +24,8 @@ enum : unsigned long long {
 // Slots of the per-program stats array (unsigned long long).
 enum {
   SS_INVALID = 0, SS_GENERAL = 1, SS_MAX_NODES = 2, SS_SWEEPS = 3, SS_STATUS = 4,
-  SS_RAW_N = 5, SS_QUEUE_N = 6, SS_QUEUE_HEAD = 7, SS_OVF_N = 8, SS_OVF_HEAD = 9, SS_N = 10
+  SS_RAW_N = 5, SS_QUEUE_N = 6, SS_QUEUE_HEAD = 7, SS_OVF_N = 8, SS_OVF_HEAD = 9, SS_OVF2_N = 10,
+  SS_OVF2_HEAD = 11, SS_N = 12
 };
 
 struct Arch {
@@ -58,6 +59,9 @@ struct Prog {
   const int32_t* loop_depth;
   const int32_t* instr_block;
   const int32_t* block_func;
+  const int32_t* ev_off;          // nb + 1: per-block event lists
+  const uint32_t* events;         // defs and unguarded reads, bottom-up: resource | def << 9 |
+                                  // kind << 10 | guard << 12 | position in block << 16
   // step state
   unsigned long long* cnt;        // ni * 24
   unsigned long long* stats;      // SS_N
@@ -96,13 +100,11 @@ struct Prog {
   unsigned long long* a_line_lat;
 };
 
-// Per-slot scratch of the general (multi-block) search.
-struct SearchScratch {
-  int32_t n_slots;
-  int32_t max_nodes;
-  int32_t edge_cap, occ_cap, src_cap, wall_cap;
-  int64_t slot_ints;   // ints per slot
-  int32_t* base;       // n_slots * slot_ints
+// Per-warp arenas of the general (multi-block) search.
+struct SearchArena {
+  int32_t nodes, src, layers, warps;
+  int64_t bytes;   // per warp
+  char* global;    // tier 2 only: warps * bytes
 };
 
 __device__ __forceinline__ void set_status(const Prog& P, unsigned long long bits) {
@@ -140,6 +142,30 @@ __device__ __forceinline__ bool uses_res(const Prog& P, int x, int r) {
   return false;
 }
 
+__device__ __forceinline__ bool stalled(const Prog& P, int j) {
+  const unsigned long long* c = P.cnt + (size_t)j * kCnt;
+  return (c[4] | c[5] | c[6] | c[7] | c[10] | c[11] | c[12] | c[13]) != 0ull;
+}
+
+// Raw edge (j <- i through r) onto j's list.
+__device__ __forceinline__ void emit_raw(const Prog& P, const Arch& A, int j, int i, int r, int kind, int dmin,
+                                         int dlong) {
+  uint32_t fl = r >= kBarBase ? 2u : (r >= kPredBase ? 8u : 4u);
+  // Write-after-read (Sec. 4, Fig. 6): the variable-latency def reads a
+  // register that the use writes, and they are linked through a read barrier.
+  if (r >= kBarBase && kind == 2 && (A.flags[P.opclass[i]] & GPA_F_VARLAT)) {
+    for (int e = P.def_off[j]; e < P.def_off[j + 1]; ++e) {
+      const int rr = P.def_res[e] & 0x1FF;
+      if (rr < kPredBase && uses_res(P, i, rr)) { fl |= 1u; break; }
+    }
+  }
+  if (dmin >= (1 << 24) || dlong >= (1 << 24)) { set_status(P, ST_CAPACITY); return; }
+  const unsigned long long slot = atomicAdd(&P.stats[SS_RAW_N], 1ull);
+  if (slot >= (unsigned long long)P.raw_cap) { set_status(P, ST_CAPACITY); return; }
+  const int next = atomicExch(&P.head[j], (int)slot);
+  P.raw[slot] = make_int4(i, next, dmin, dlong | (int)(fl << 24));
+}
+
 // ---------------------------------------------------------------- launchers
 int grid_for(int64_t n, int threads, int sms);
 void launch_build_layout(const Prog& P, cudaStream_t st, int sms, int64_t* launches);
@@ -147,8 +173,12 @@ void launch_build_preds(const Prog& P, int n_succ, int32_t* pred_off, int32_t* c
                         int sms, int64_t* launches);
 void launch_histogram(const Prog& P, const uint64_t* samples, size_t n, cudaStream_t st, int sms, int64_t* launches);
 void launch_dataflow(const Prog& P, const Arch& A, int max_sweeps, cudaStream_t st, int sms, int64_t* launches);
-void launch_blame(const Prog& P, const Arch& A, const SearchScratch& tier1, const SearchScratch& tier2, int max_src,
-                  int32_t* scan_tmp, cudaStream_t st, int sms, int64_t* launches);
+void launch_blame(const Prog& P, const Arch& A, const SearchArena* tiers, int max_src, int32_t* scan_tmp,
+                  cudaStream_t st, int sms, int64_t* launches);
+void launch_search(const Prog& P, const Arch& A, const SearchArena* tiers, cudaStream_t st, int64_t* launches);
+int64_t search_arena_bytes(int nodes, int src, int layers);
+void launch_build_events(const Prog& P, int32_t* ev_off, uint32_t* events, int32_t* tmp, cudaStream_t st, int sms,
+                         int64_t* launches);
 void launch_advise(const Prog& P, const Arch& A, cudaStream_t st, int sms, int64_t* launches);
 // Exclusive scan of n int32 values in place over buf[0..n], buf[n] receives the total.
 void scan_exclusive_inplace(int32_t* buf, int n, int32_t* tmp, cudaStream_t st, int64_t* launches);

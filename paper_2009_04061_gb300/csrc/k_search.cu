@@ -1,0 +1,642 @@
+// Step (b)/(c), general backward searches (Sec. 4): immediate sources of a
+// stalled use j through resource r whose value may come from outside j's
+// block, with the three pruning rules evaluated over the set of source paths.
+//
+// One warp per (use, resource) task. The graph of (block, literal set) nodes
+// lives in a per-warp arena: shared memory for the common small searches,
+// a large global-memory arena for the few that outgrow it (same code). Lanes
+// scan node blocks in parallel through per-block event lists (defs and
+// unguarded reads, bottom-up), relax shortest distances in parallel with
+// shared-memory atomics, and check sources in parallel; lane 0 does the
+// short sequential steps (hash inserts, sorts of large lists, reachability
+// re-runs, the layered longest path) in the arena.
+//
+// Node 0 is the part of j's block above j, already scanned by the local pass
+// (its sources are settled there). A node's d is the shortest distance from
+// the last instruction of its block to j. Pass A grows the graph in distance
+// order up to `bound`, the largest latency of any def of r in the function: a
+// source farther than that fails rule 3 whatever the rest of the graph holds.
+// Only if some source is within its latency does pass B complete the graph,
+// which rule 2 and the longest paths need.
+#include "gpa_internal.cuh"
+
+namespace gpa {
+
+namespace {
+
+constexpr int kInf = 0x3FFFFFFF;
+constexpr uint32_t kBackBit = 0x80000000u;
+constexpr int kExpanded = 1;
+constexpr int kWarpsPerCta = 4;
+
+struct Arena {
+  int N, E, O, SRC, L;
+  int *blk, *S, *cov, *wall, *k, *e0, *e1, *fl, *seen, *ord, *tmp, *grp, *q;  // per node
+  unsigned long long* dpk;  // (shortest distance << 32) | parent node
+  unsigned long long* sdb;  // per source: (shortest distance << 32) | nearest occurrence
+  int *dl, *ht, *hused, *eto, *on, *ox, *onext;
+  int *wblk, *wpos, *wneed;
+  int *si, *sk, *sp, *shead;
+  int* ctr;  // 0 nodes, 1 edges, 2 occurrences, 3 hash slots used, 4 overflow, 5 scratch
+};
+
+__host__ __device__ inline int64_t arena_bytes(int N, int SRC, int L) {
+  const int64_t E = 2 * (int64_t)N, O = N;
+  int64_t ints = 13 * (int64_t)N + (int64_t)L * N + 2 * (int64_t)N + N + E + 3 * O + 3 * (int64_t)N + 4 * (int64_t)SRC + 8;
+  return 8 * (int64_t)N + 8 * (int64_t)SRC + ((ints * 4 + 15) & ~(int64_t)15);
+}
+
+__device__ Arena carve(char* base, int N, int SRC, int L) {
+  Arena a;
+  a.N = N; a.E = 2 * N; a.O = N; a.SRC = SRC; a.L = L;
+  a.dpk = reinterpret_cast<unsigned long long*>(base);
+  a.sdb = a.dpk + N;
+  int* p = reinterpret_cast<int*>(base + 8 * (int64_t)N + 8 * (int64_t)SRC);
+  int** node_arrays[13] = {&a.blk, &a.S, &a.cov, &a.wall, &a.k, &a.e0, &a.e1, &a.fl, &a.seen, &a.ord, &a.tmp, &a.grp, &a.q};
+  for (int t = 0; t < 13; ++t) { *node_arrays[t] = p; p += N; }
+  a.dl = p; p += (int64_t)L * N;
+  a.ht = p; p += 2 * N;
+  a.hused = p; p += N;
+  a.eto = p; p += a.E;
+  a.on = p; p += a.O; a.ox = p; p += a.O; a.onext = p; p += a.O;
+  a.wblk = p; p += N; a.wpos = p; p += N; a.wneed = p; p += N;
+  a.si = p; p += SRC; a.sk = p; p += SRC; a.sp = p; p += SRC; a.shead = p; p += SRC;
+  a.ctr = p;
+  return a;
+}
+
+__device__ __forceinline__ uint32_t node_hash(int blk, int S) {
+  uint32_t h = (uint32_t)blk * 0x9E3779B1u ^ ((uint32_t)S * 0x85EBCA77u);
+  h ^= h >> 15;
+  return h;
+}
+
+__device__ __forceinline__ int dist_of(const Arena& a, int u) { return (int)(a.dpk[u] >> 32); }
+__device__ __forceinline__ int par_of(const Arena& a, int u) { return (int)(a.dpk[u] & 0xFFFFFFFFull); }
+
+// Warp-wide exclusive prefix count of `pred`; returns this lane's slot and sets *total.
+__device__ __forceinline__ int warp_slot(bool pred, int* total) {
+  const unsigned m = __ballot_sync(0xffffffffu, pred);
+  *total = __popc(m);
+  return __popc(m & ((1u << (threadIdx.x & 31)) - 1u));
+}
+
+// Returns false when the search outgrew the arena (nothing emitted).
+__device__ bool warp_search(const Prog& P, const Arch& A, const Arena& a, int j, int r, uint16_t S0, int bound) {
+  const int lane = threadIdx.x & 31;
+  const int gj = P.guard[j];
+  const int b0 = P.instr_block[j];
+  const int first0 = P.block_instr_off[b0];
+  const int w = r >> 5;
+  const uint32_t bit = 1u << (r & 31);
+  const uint32_t hmask = (uint32_t)(2 * a.N - 1);
+  volatile int* ctr = a.ctr;
+
+  if (lane == 0) {
+    ctr[0] = 1; ctr[1] = 0; ctr[2] = 0; ctr[3] = 0; ctr[4] = 0;
+    a.blk[0] = b0; a.S[0] = (int)S0 | ((int)S0 << 16); a.cov[0] = first0; a.wall[0] = -1; a.fl[0] = 0;
+    a.dpk[0] = 0ull; a.k[0] = 0; a.e0[0] = 0; a.e1[0] = 0;
+  }
+  __syncwarp();
+
+  // Self-check of the arena invariants before any indexed access: an edge range
+  // inside [0, edges) and targets inside [0, nodes). A violation is recorded
+  // as ST_OVERFLOW and the access skipped.
+  auto edges_ok = [&](int u, int n_now) {
+    const int e0 = a.e0[u], e1 = a.e1[u];
+    if (e0 < 0 || e1 < e0 || e1 > a.E || e1 > ctr[1]) { set_status(P, ST_OVERFLOW); return false; }
+    for (int e = e0; e < e1; ++e)
+      if ((a.eto[e] & 0x7FFFFFFF) >= n_now) { set_status(P, ST_OVERFLOW); return false; }
+    return true;
+  };
+  auto wout = [&](int u) {
+    return u == 0 ? (j - first0 + 1) : (P.block_instr_off[a.blk[u] + 1] - P.block_instr_off[a.blk[u]]);
+  };
+  auto last_of = [&](int u) { return P.block_instr_off[a.blk[u] + 1] - 1; };
+
+  // Scan node u's block bottom-up through its event list (one lane). Records
+  // occurrences, the literal set leaving the top, the covering position and
+  // the first unguarded reader of r met (the wall). Sets a.fl[u] bit 2 if the
+  // scan stopped (covered).
+  auto scan = [&](int u) {
+    uint16_t S = (uint16_t)(a.S[u] & 0xFFFF);
+    bool stop = false;
+    if (u != 0) {
+      const int B = a.blk[u];
+      const int first = P.block_instr_off[B];
+      int cov = first, wall = -1;
+      if ((P.def_mask[(size_t)B * kWords + w] | P.uuse_mask[(size_t)B * kWords + w]) & bit) {
+        int last_def_pos = -1;
+        const int ev1 = P.ev_off[B + 1];
+        for (int e = P.ev_off[B]; e < ev1; ++e) {
+          const uint32_t ev = P.events[e];
+          if ((int)(ev & 0x1FFu) != r) continue;
+          const int pos = (int)(ev >> 16), x = first + pos;
+          if (ev & 0x200u) {  // def of r
+            last_def_pos = pos;
+            if (!contains(S, gj) && !(B == b0 && x < j)) {  // sources above j in its block are settled
+              const int o = atomicAdd((int*)&a.ctr[2], 1);
+              if (o < a.O) { a.on[o] = u; a.ox[o] = x; } else { a.ctr[4] = 1; }
+            }
+            S = add_literal(S, (int)((ev >> 12) & 0xFu));
+            if (contains(S, gj)) { stop = true; cov = x; break; }
+          } else if (wall < 0 && pos != last_def_pos && x != j) {  // unguarded reader of r
+            wall = x;
+          }
+        }
+      }
+      a.cov[u] = cov;
+      a.wall[u] = wall;
+    }
+    a.S[u] = (a.S[u] & 0xFFFF) | ((int)S << 16);
+    a.fl[u] |= kExpanded | (stop ? 4 : 0);
+  };
+
+  // Link the predecessors of the listed nodes, lanes over nodes. Edge ranges
+  // come from a warp prefix count; the (block, literal set) nodes are found or
+  // added with a warp-synchronous insert: a lane claims an empty slot with
+  // atomicCAS, allocates and publishes the node in the same round, and lanes
+  // that met a claim in progress retry the slot in the next round.
+  auto link_chunk = [&](const int* lst, int cnt) {
+    const bool mine = lane < cnt;
+    const int u = mine ? lst[lane] : 0;
+    const int B = mine ? a.blk[u] : 0;
+    const int Sout = mine ? ((a.S[u] >> 16) & 0xFFFF) : 0;
+    const bool open = mine && !(a.fl[u] & 4);
+    int deg = 0;
+    if (open)
+      for (int q = P.pred_off[B]; q < P.pred_off[B + 1]; ++q)
+        deg += (P.rout[(size_t)P.pred[q] * kWords + w] & bit) ? 1 : 0;
+    int incl = deg;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    const int ne = ctr[1];
+    if (ne + total > a.E) { if (lane == 0) ctr[4] = 1; __syncwarp(); return; }
+    if (mine) { a.e0[u] = ne + incl - deg; a.e1[u] = ne + incl; }
+    int maxdeg = deg;
+    for (int o = 16; o > 0; o >>= 1) maxdeg = max(maxdeg, __shfl_xor_sync(0xffffffffu, maxdeg, o));
+    int qp = open ? P.pred_off[B] : 0;
+    for (int kk = 0; kk < maxdeg; ++kk) {
+      bool pending = kk < deg;
+      int p = -1;
+      if (pending) {
+        while (!(P.rout[(size_t)P.pred[qp] * kWords + w] & bit)) ++qp;
+        p = P.pred[qp++];
+      }
+      uint32_t h = pending ? (node_hash(p, Sout) & hmask) : 0;
+      int v = -1;
+      for (int round = 0; round < 4 * (int)hmask + 64; ++round) {
+        if (!__any_sync(0xffffffffu, pending)) break;
+        if (pending) {
+          const int c = a.ht[h];
+          if (c >= 0) {
+            if (a.blk[c] == p && (a.S[c] & 0xFFFF) == Sout) { v = c; pending = false; }
+            else h = (h + 1) & hmask;
+          } else if (c == -1) {
+            if (atomicCAS(&a.ht[h], -1, -2 - lane) == -1) {
+              const int nv = atomicAdd((int*)&a.ctr[0], 1);
+              if (nv >= a.N) {
+                a.ctr[4] = 1; a.ht[h] = -1; pending = false;
+              } else {
+                a.blk[nv] = p; a.S[nv] = Sout; a.wall[nv] = -1; a.cov[nv] = 0; a.fl[nv] = 0; a.k[nv] = kInf;
+                a.e0[nv] = 0; a.e1[nv] = 0;  // no out-edges until the node is expanded
+                a.dpk[nv] = ((unsigned long long)kInf << 32) | 0xFFFFFFFFull;
+                a.hused[atomicAdd((int*)&a.ctr[3], 1)] = (int)h;
+                __threadfence_block();
+                a.ht[h] = nv;
+                v = nv; pending = false;
+              }
+            }
+          }  // c <= -2: another lane is publishing this slot; look again next round
+        }
+        __syncwarp();
+      }
+      if (pending) a.ctr[4] = 1;  // the round limit is a bound, not expected to be reached
+      if (kk < deg && v >= 0) a.eto[a.e0[u] + kk] = v | (p >= B ? (int)kBackBit : 0);
+    }
+    __syncwarp();
+    if (lane == 0) ctr[1] = ne + total;
+    __syncwarp();
+  };
+
+  // Expand every listed node: parallel scans, then parallel linking.
+  auto expand_list = [&](const int* list, int cnt) {
+    for (int c0 = 0; c0 < cnt; c0 += 32) {
+      if (c0 + lane < cnt) scan(list[c0 + lane]);
+      __syncwarp();
+      if (ctr[4]) return;
+      link_chunk(list + c0, min(32, cnt - c0));
+      if (ctr[4]) return;
+    }
+  };
+
+  // Worklist relaxation from the listed nodes: improved targets join the next
+  // frontier once (flag bit 8 of fl). mode 0: shortest distance with parent
+  // (64-bit atomicMin on (d << 32) | parent); mode 1: fewest back edges.
+  // Frontiers live in ord / grp, which are free until rule 2.
+  auto relax_from = [&](const int* start, int cnt, int mode) {
+    int* cur = a.ord;
+    int* nxt = a.grp;
+    for (int t = lane; t < cnt; t += 32) cur[t] = start[t];
+    if (lane == 0) ctr[5] = 0;
+    __syncwarp();
+    int fsize = cnt;
+    while (fsize > 0) {
+      for (int f0 = 0; f0 < fsize; f0 += 32) {
+        if (f0 + lane >= fsize) continue;
+        const int u = cur[f0 + lane];
+        atomicAnd(&a.fl[u], ~8);
+        const int n_now = ctr[0];
+        if (!edges_ok(u, n_now)) continue;
+        if (mode == 0) {
+          const int du = dist_of(a, u);
+          if (du >= kInf) continue;
+          const unsigned long long nd = (unsigned long long)(du + wout(u)) << 32 | (unsigned)u;
+          for (int e = a.e0[u]; e < a.e1[u]; ++e) {
+            const int v = a.eto[e] & 0x7FFFFFFF;
+            if (nd < a.dpk[v] && atomicMin(&a.dpk[v], nd) > nd && !(atomicOr(&a.fl[v], 8) & 8))
+              nxt[atomicAdd((int*)&a.ctr[5], 1)] = v;
+          }
+        } else {
+          const int ku = a.k[u];
+          if (ku >= kInf) continue;
+          for (int e = a.e0[u]; e < a.e1[u]; ++e) {
+            const int v = a.eto[e] & 0x7FFFFFFF;
+            const int kb = ku + (int)((uint32_t)a.eto[e] >> 31);
+            if (kb < a.k[v] && atomicMin(&a.k[v], kb) > kb && !(atomicOr(&a.fl[v], 8) & 8))
+              nxt[atomicAdd((int*)&a.ctr[5], 1)] = v;
+          }
+        }
+      }
+      __syncwarp();
+      fsize = ctr[5];
+      __syncwarp();
+      if (lane == 0) ctr[5] = 0;
+      int* sw = cur; cur = nxt; nxt = sw;
+      __syncwarp();
+    }
+  };
+
+  // Pass A: expand in waves the nodes within the bound, relaxing from each wave.
+  int* list = a.q;
+  while (!ctr[4]) {
+    const int n = ctr[0];
+    int cnt = 0;
+    for (int u0 = 0; u0 < n; u0 += 32) {
+      const int u = u0 + lane;
+      const bool want = u < n && !(a.fl[u] & kExpanded) && dist_of(a, u) <= bound;
+      int tot;
+      const int at = warp_slot(want, &tot);
+      if (want) list[cnt + at] = u;
+      cnt += tot;
+    }
+    __syncwarp();
+    if (cnt == 0) break;
+    expand_list(list, cnt);
+    if (ctr[4]) break;
+    relax_from(list, cnt, 0);
+  }
+  // A source within its latency?
+  bool cand = false;
+  if (!ctr[4]) {
+    const int no = min(ctr[2], a.O);
+    for (int o = lane; o < no && !cand; o += 32) {
+      const int u = a.on[o];
+      cand = dist_of(a, u) + (last_of(u) - a.ox[o]) <= A.lat[P.opclass[a.ox[o]]];
+    }
+    cand = __any_sync(0xffffffffu, cand);
+  }
+  // Pass B: complete the graph.
+  if (cand) {
+    while (!ctr[4]) {
+      const int n = ctr[0];
+      int cnt = 0;
+      for (int u0 = 0; u0 < n; u0 += 32) {
+        const int u = u0 + lane;
+        const bool want = u < n && !(a.fl[u] & kExpanded);
+        int tot;
+        const int at = warp_slot(want, &tot);
+        if (want) list[cnt + at] = u;
+        cnt += tot;
+      }
+      __syncwarp();
+      if (cnt == 0) break;
+      expand_list(list, cnt);
+    }
+  }
+  // Clear the hash slots this search used.
+  const int nh = ctr[3];
+  for (int t = lane; t < nh; t += 32) a.ht[a.hused[t]] = -1;
+  __syncwarp();
+  const int n = ctr[0];
+  if (lane == 0) {
+    atomicAdd(&P.stats[SS_GENERAL], 1ull);
+    atomicMax(&P.stats[SS_MAX_NODES], (unsigned long long)n);
+  }
+  if (ctr[4]) return false;
+  if (!cand) return true;
+
+  // Shortest distance with parents, and fewest back edges, over the whole graph.
+  for (int u = lane; u < n; u += 32) {
+    a.dpk[u] = u == 0 ? 0ull : (((unsigned long long)kInf << 32) | 0xFFFFFFFFull);
+    a.k[u] = u == 0 ? 0 : kInf;
+    a.fl[u] &= ~8;
+  }
+  if (lane == 0) a.q[0] = 0;
+  __syncwarp();
+  relax_from(a.q, 1, 0);
+  relax_from(a.q, 1, 1);
+
+  // Sources: a warp-synchronous hash keyed by instruction gives each source an
+  // index; per source, 64-bit atomicMin keeps (shortest distance, its
+  // occurrence), atomicMin the fewest back edges, and the occurrences are
+  // chained into a list.
+  const int no = ctr[2];
+  if (lane == 0) { ctr[3] = 0; ctr[5] = 0; }
+  __syncwarp();
+  const uint32_t smask = (uint32_t)(2 * a.SRC - 1);
+  for (int o0 = 0; o0 < no; o0 += 32) {
+    const int o = o0 + lane;
+    bool pending = o < no;
+    const int x = pending ? a.ox[o] : -1;
+    uint32_t h = pending ? (((uint32_t)x * 0x9E3779B1u) >> 7) & smask : 0;
+    int m = -1;
+    for (int round = 0; round < 4 * (int)smask + 64; ++round) {
+      if (!__any_sync(0xffffffffu, pending)) break;
+      if (pending) {
+        const int c = a.ht[h];
+        if (c >= 0) {
+          if (a.si[c] == x) { m = c; pending = false; } else h = (h + 1) & smask;
+        } else if (c == -1) {
+          if (atomicCAS(&a.ht[h], -1, -2 - lane) == -1) {
+            const int nm = atomicAdd((int*)&a.ctr[5], 1);
+            if (nm >= a.SRC) {
+              a.ctr[4] = 1; a.ht[h] = -1; pending = false;
+            } else {
+              a.si[nm] = x; a.sk[nm] = kInf; a.shead[nm] = -1; a.sp[nm] = 0;
+              a.sdb[nm] = ~0ull;
+              a.hused[atomicAdd((int*)&a.ctr[3], 1)] = (int)h;
+              __threadfence_block();
+              a.ht[h] = nm;
+              m = nm; pending = false;
+            }
+          }
+        }
+      }
+      __syncwarp();
+    }
+    if (pending) a.ctr[4] = 1;
+    if (m >= 0) {
+      const int u = a.on[o];
+      const int dist = dist_of(a, u) + (last_of(u) - x);
+      atomicMin(&a.sdb[m], ((unsigned long long)dist << 32) | (unsigned)o);
+      atomicMin(&a.sk[m], a.k[u]);
+      a.onext[o] = atomicExch(&a.shead[m], o);
+    }
+    __syncwarp();
+  }
+  {
+    const int nh2 = ctr[3];
+    for (int t = lane; t < nh2; t += 32) a.ht[a.hused[t]] = -1;
+  }
+  __syncwarp();
+  if (ctr[4]) return false;
+  const int nsrc = ctr[5];
+  int alive = 0;
+  for (int m = lane; m < nsrc; m += 32) {
+    a.sp[m] = (int)(a.sdb[m] >> 32) > A.lat[P.opclass[a.si[m]]] ? 1 : 0;  // rule 3
+    alive += a.sp[m] ? 0 : 1;
+  }
+  for (int o = 16; o > 0; o >>= 1) alive += __shfl_xor_sync(0xffffffffu, alive, o);
+  __syncwarp();
+  if (alive == 0) return true;
+
+  // Rule 2. Wall groups, one per block: a hash keyed by block with atomicMax
+  // of the positions (the unguarded reader met first from the bottom truncates
+  // at least as much as any other reader of that block). A wall can only block
+  // source i if it lies on the parent chain of i's nearest occurrence.
+  if (lane == 0) { ctr[3] = 0; ctr[5] = 0; }
+  __syncwarp();
+  for (int u0 = 0; u0 < n; u0 += 32) {
+    const int u = u0 + lane;
+    bool pending = u < n && u != 0 && a.wall[u] >= 0;
+    const int B = pending ? a.blk[u] : -1;
+    uint32_t h = pending ? (((uint32_t)B * 0x9E3779B1u) >> 5) & hmask : 0;
+    int g = -1;
+    for (int round = 0; round < 4 * (int)hmask + 64; ++round) {
+      if (!__any_sync(0xffffffffu, pending)) break;
+      if (pending) {
+        const int c = a.ht[h];
+        if (c >= 0) {
+          if (a.wblk[c] == B) { g = c; pending = false; } else h = (h + 1) & hmask;
+        } else if (c == -1) {
+          if (atomicCAS(&a.ht[h], -1, -2 - lane) == -1) {
+            const int ng = atomicAdd((int*)&a.ctr[5], 1);
+            a.wblk[ng] = B; a.wpos[ng] = -1; a.wneed[ng] = 0;
+            a.hused[atomicAdd((int*)&a.ctr[3], 1)] = (int)h;
+            __threadfence_block();
+            a.ht[h] = ng;
+            g = ng; pending = false;
+          }
+        }
+      }
+      __syncwarp();
+    }
+    if (pending) a.ctr[4] = 1;
+    if (u < n) a.grp[u] = g;
+    if (g >= 0) atomicMax(&a.wpos[g], a.wall[u]);
+    __syncwarp();
+  }
+  {
+    const int nh2 = ctr[3];
+    for (int t = lane; t < nh2; t += 32) a.ht[a.hused[t]] = -1;
+  }
+  __syncwarp();
+  if (ctr[4]) return false;
+  const int nw = ctr[5];
+  for (int m = lane; m < nsrc; m += 32) {
+    if (a.sp[m]) continue;
+    const int o = (int)(a.sdb[m] & 0xFFFFFFFFull), u = a.on[o];
+    if (u != 0 && a.wall[u] > a.ox[o]) a.wneed[a.grp[u]] = 1;
+    for (int v = par_of(a, u), hops = 0; v > 0 && hops < n; v = par_of(a, v), ++hops)
+      if (a.wall[v] >= 0) a.wneed[a.grp[v]] = 1;
+  }
+  for (int u = lane; u < n; u += 32) a.seen[u] = 0;
+  __syncwarp();
+  for (int t = 0; t < nw; ++t) {
+    if (!a.wneed[t] || alive == 0) continue;
+    const int WB = a.wblk[t], WP = a.wpos[t], epoch = t + 1;
+    auto trunc = [&](int u) { return u != 0 && a.blk[u] == WB && a.cov[u] <= WP; };
+    // Level-synchronous reachability from the root, frontiers in q / tmp.
+    int* cur = a.q;
+    int* nxt = a.tmp;
+    if (lane == 0) { cur[0] = 0; a.seen[0] = epoch; ctr[5] = 0; }
+    int fsize = 1;
+    __syncwarp();
+    while (fsize > 0) {
+      for (int f0 = 0; f0 < fsize; f0 += 32) {
+        if (f0 + lane < fsize) {
+          const int u = cur[f0 + lane];
+          if (!trunc(u) && edges_ok(u, n))
+            for (int e = a.e0[u]; e < a.e1[u]; ++e) {
+              const int v = a.eto[e] & 0x7FFFFFFF;
+              if (a.seen[v] != epoch && atomicExch(&a.seen[v], epoch) != epoch)
+                nxt[atomicAdd((int*)&a.ctr[5], 1)] = v;
+            }
+        }
+      }
+      __syncwarp();
+      fsize = ctr[5];
+      __syncwarp();
+      if (lane == 0) ctr[5] = 0;
+      int* sw = cur; cur = nxt; nxt = sw;
+      __syncwarp();
+    }
+    int dropped = 0;
+    for (int m = lane; m < nsrc; m += 32) {
+      if (a.sp[m]) continue;
+      bool reach = false;
+      for (int o = a.shead[m]; o >= 0 && !reach; o = a.onext[o]) {
+        const int u = a.on[o];
+        if (a.seen[u] == epoch && !(trunc(u) && a.ox[o] < WP)) reach = true;
+      }
+      if (!reach) { a.sp[m] = 1; ++dropped; }
+    }
+    for (int o = 16; o > 0; o >>= 1) dropped += __shfl_xor_sync(0xffffffffu, dropped, o);
+    alive -= dropped;
+    __syncwarp();
+  }
+  if (alive == 0) return true;
+
+  // Longest path with exactly K back edges: layer = back edges used. Each
+  // layer is a DAG over the forward edges, processed in topological order by
+  // level-synchronous Kahn frontiers; back edges feed the next layer.
+  int maxK = 0;
+  for (int m = lane; m < nsrc; m += 32) if (!a.sp[m]) maxK = max(maxK, a.sk[m]);
+  for (int o = 16; o > 0; o >>= 1) maxK = max(maxK, __shfl_xor_sync(0xffffffffu, maxK, o));
+  if (maxK >= a.L) return false;
+  for (int t = lane; t < (maxK + 1) * n; t += 32) a.dl[(t / n) * a.N + (t % n)] = -1;
+  for (int u = lane; u < n; u += 32) a.ord[u] = 0;
+  __syncwarp();
+  for (int u = lane; u < n; u += 32)
+    for (int e = a.e0[u]; e < a.e1[u]; ++e)
+      if (!((uint32_t)a.eto[e] >> 31)) atomicAdd(&a.ord[a.eto[e] & 0x7FFFFFFF], 1);
+  if (lane == 0) a.dl[0] = 0;
+  __syncwarp();
+  for (int l = 0; l <= maxK; ++l) {
+    int* dll = a.dl + (int64_t)l * a.N;
+    if (lane == 0) ctr[5] = 0;
+    __syncwarp();
+    for (int u = lane; u < n; u += 32) {
+      a.seen[u] = a.ord[u];  // remaining forward in-edges
+      if (a.ord[u] == 0) a.q[atomicAdd((int*)&a.ctr[5], 1)] = u;
+    }
+    __syncwarp();
+    int fsize = ctr[5];
+    int* cur = a.q;
+    int* nxt = a.tmp;
+    __syncwarp();
+    if (lane == 0) ctr[5] = 0;
+    __syncwarp();
+    while (fsize > 0) {
+      for (int f0 = 0; f0 < fsize; f0 += 32) {
+        if (f0 + lane < fsize) {
+          const int u = cur[f0 + lane];
+          const int cv = dll[u];
+          const int nd = cv + wout(u);
+          for (int e = a.e0[u]; e < a.e1[u]; ++e) {
+            const int v = a.eto[e] & 0x7FFFFFFF;
+            const bool back = (uint32_t)a.eto[e] >> 31;
+            if (back) {
+              if (cv >= 0 && l + 1 <= maxK) atomicMax(&a.dl[(int64_t)(l + 1) * a.N + v], nd);
+            } else {
+              if (cv >= 0) atomicMax(&dll[v], nd);
+              if (atomicSub(&a.seen[v], 1) == 1) nxt[atomicAdd((int*)&a.ctr[5], 1)] = v;
+            }
+          }
+        }
+      }
+      __syncwarp();
+      fsize = ctr[5];
+      __syncwarp();
+      if (lane == 0) ctr[5] = 0;
+      int* sw = cur; cur = nxt; nxt = sw;
+      __syncwarp();
+    }
+  }
+  for (int m = lane; m < nsrc; m += 32) {
+    if (a.sp[m]) continue;
+    const int K = a.sk[m];
+    int best = -1;
+    for (int o = a.shead[m]; o >= 0; o = a.onext[o]) {
+      const int u = a.on[o];
+      const int dlu = a.dl[(int64_t)K * a.N + u];
+      if (dlu >= 0) best = max(best, dlu + last_of(u) - a.ox[o]);
+    }
+    if (best < 1) { set_status(P, ST_CAPACITY); continue; }
+    emit_raw(P, A, j, a.si[m], r, def_kind(P, a.si[m], r), (int)(a.sdb[m] >> 32), best);
+  }
+  __syncwarp();
+  return true;
+}
+
+// Persistent work-stealing warps over one queue. Tiers 1 and 2 keep the arena
+// in shared memory (tier 1: several warps per CTA, small arenas; tier 2: one
+// warp per CTA, a large arena); tier 3 uses global-memory arenas. A search that
+// outgrows its tier is queued for the next one.
+__global__ void __launch_bounds__(kWarpsPerCta * 32) k_search_warp(Prog P, Arch A, SearchArena SA, int tier) {
+  extern __shared__ __align__(16) char smem[];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int gw = blockIdx.x * (blockDim.x >> 5) + wid;
+  char* base = tier < 3 ? smem + (int64_t)wid * SA.bytes : SA.global + (int64_t)gw * SA.bytes;
+  const Arena a = carve(base, SA.nodes, SA.src, SA.layers);
+  for (int t = lane; t < 2 * SA.nodes; t += 32) a.ht[t] = -1;
+  __syncwarp();
+  // tier 1 reads the local pass's queue, tier 2 the first overflow queue, and
+  // tier 3 the second, which reuses the first queue's storage.
+  const int4* q = tier == 2 ? P.ovf_queue : P.queue;
+  const int n_slot = tier == 1 ? SS_QUEUE_N : tier == 2 ? SS_OVF_N : SS_OVF2_N;
+  const int h_slot = tier == 1 ? SS_QUEUE_HEAD : tier == 2 ? SS_OVF_HEAD : SS_OVF2_HEAD;
+  unsigned long long nq = P.stats[n_slot];
+  if (nq > (unsigned long long)P.queue_cap) nq = (unsigned long long)P.queue_cap;
+  while (true) {
+    unsigned long long t = 0;
+    if (lane == 0) t = atomicAdd(&P.stats[h_slot], 1ull);
+    t = __shfl_sync(0xffffffffu, t, 0);
+    if (t >= nq) break;
+    const int4 task = q[t];
+    const int f = P.block_func[P.instr_block[task.x]];
+    const int bound = P.res_maxlat[(size_t)f * kNumRes + task.y];
+    const bool ok = warp_search(P, A, a, task.x, task.y, (uint16_t)task.z, bound);
+    if (ok || lane != 0) continue;
+    if (tier < 3) {
+      const int o_slot = tier == 1 ? SS_OVF_N : SS_OVF2_N;
+      int4* oq = tier == 1 ? P.ovf_queue : P.queue;
+      const unsigned long long o = atomicAdd(&P.stats[o_slot], 1ull);
+      if (o < (unsigned long long)P.queue_cap) oq[o] = task; else set_status(P, ST_CAPACITY);
+    } else {
+      set_status(P, ST_CAPACITY);
+    }
+  }
+}
+
+}  // namespace
+
+int64_t search_arena_bytes(int nodes, int src, int layers) { return arena_bytes(nodes, src, layers); }
+
+void launch_search(const Prog& P, const Arch& A, const SearchArena* tiers, cudaStream_t st, int64_t* launches) {
+  // Contexts may use different arena sizes: set each launch's requirement.
+  const size_t smem1 = (size_t)tiers[0].bytes * kWarpsPerCta;
+  cudaFuncSetAttribute(k_search_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem1);
+  k_search_warp<<<tiers[0].warps / kWarpsPerCta, kWarpsPerCta * 32, smem1, st>>>(P, A, tiers[0], 1);
+  const size_t smem2 = (size_t)tiers[1].bytes;
+  cudaFuncSetAttribute(k_search_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2);
+  k_search_warp<<<tiers[1].warps, 32, smem2, st>>>(P, A, tiers[1], 2);
+  k_search_warp<<<tiers[2].warps, 32, 0, st>>>(P, A, tiers[2], 3);
+  *launches += 3;
+}
+
+}  // namespace gpa

@@ -103,7 +103,46 @@ __global__ void k_loop_depth(Prog P) {
   }
 }
 
+// Per-block event lists for the backward scans: for each instruction from the
+// last to the first, its defs (with kind and guard) and, if unguarded, its reads.
+__global__ void k_ev_count(Prog P, int32_t* cnt) {
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < P.nb; b += gridDim.x * blockDim.x) {
+    int c = 0;
+    for (int x = P.block_instr_off[b]; x < P.block_instr_off[b + 1]; ++x) {
+      c += P.def_off[x + 1] - P.def_off[x];
+      if (P.guard[x] == 0) c += P.use_off[x + 1] - P.use_off[x];
+    }
+    cnt[b] = c;
+  }
+}
+
+__global__ void k_ev_fill(Prog P, const int32_t* ev_off, uint32_t* events) {
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < P.nb; b += gridDim.x * blockDim.x) {
+    const int first = P.block_instr_off[b];
+    int o = ev_off[b];
+    for (int x = P.block_instr_off[b + 1] - 1; x >= first; --x) {
+      const uint32_t pos = (uint32_t)(x - first) << 16;
+      const uint32_t g = P.guard[x];
+      for (int e = P.def_off[x]; e < P.def_off[x + 1]; ++e) {
+        const uint32_t v = P.def_res[e];
+        events[o++] = (v & 0x1FFu) | 0x200u | (((v >> 12) & 3u) << 10) | (g << 12) | pos;
+      }
+      if (g == 0)
+        for (int e = P.use_off[x]; e < P.use_off[x + 1]; ++e) events[o++] = (P.use_res[e] & 0x1FFu) | pos;
+    }
+  }
+}
+
 }  // namespace
+
+void launch_build_events(const Prog& P, int32_t* ev_off, uint32_t* events, int32_t* tmp, cudaStream_t st, int sms,
+                         int64_t* launches) {
+  k_ev_count<<<grid_for(P.nb, 256, sms), 256, 0, st>>>(P, ev_off);
+  ++*launches;
+  scan_exclusive_inplace(ev_off, P.nb, tmp, st, launches);
+  k_ev_fill<<<grid_for(P.nb, 256, sms), 256, 0, st>>>(P, ev_off, events);
+  ++*launches;
+}
 
 int grid_for(int64_t n, int threads, int sms) {
   int64_t g = (n + threads - 1) / threads;

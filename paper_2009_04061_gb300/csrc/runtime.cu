@@ -30,7 +30,7 @@ struct gpa_ctx {
   int sms = 0;
   Arch arch{};
   gpa_options opts{};
-  SearchScratch tier1{}, tier2{};
+  SearchArena tier[3]{};
   cudaEvent_t scratch_ev = nullptr;
   std::map<gpa_pid, ProgramRec*> progs;
   gpa_pid next_pid = 1;
@@ -74,25 +74,6 @@ void free_program(ProgramRec* R) {
   delete R;
 }
 
-gpa_status scratch_alloc(SearchScratch* S, int slots, int nodes) {
-  S->n_slots = slots;
-  S->max_nodes = nodes;
-  S->edge_cap = 2 * nodes;
-  S->occ_cap = nodes;
-  S->src_cap = std::min(nodes, 1024);
-  S->wall_cap = nodes;
-  // blk S cov wall d k e0 e1 seen ord tmp q hused par fl (15) + layers + hash (2) + edges + occ (2) + src (5) +
-  // walls (3)
-  S->slot_ints = (int64_t)15 * nodes + (int64_t)kMaxLayers * nodes + 2 * (int64_t)nodes + S->edge_cap +
-                 2 * (int64_t)S->occ_cap + 5 * (int64_t)S->src_cap + 3 * (int64_t)S->wall_cap;
-  S->slot_ints = (S->slot_ints + 63) & ~(int64_t)63;
-  size_t bytes = (size_t)S->slot_ints * sizeof(int32_t) * (size_t)slots;
-  if (cudaMalloc(&S->base, bytes) != cudaSuccess) { S->base = nullptr; return GPA_ERR_OOM; }
-  // Hash tables start empty (-1); everything else is written before it is read.
-  if (cudaMemset(S->base, 0xFF, bytes) != cudaSuccess) return GPA_ERR_CUDA;
-  return GPA_OK;
-}
-
 ProgramRec* find(gpa_ctx* ctx, gpa_pid pid) {
   if (!ctx) return nullptr;
   auto it = ctx->progs.find(pid);
@@ -124,6 +105,8 @@ gpa_status validate(const gpa_program_desc* d, const Arch& A) {
       !mono(d->use_off, ni, d->n_use, false))
     return GPA_ERR_INVALID_PROGRAM;
   std::vector<int> bfunc(nb), lfunc(nl);
+  for (int b = 0; b < nb; ++b)
+    if (d->block_instr_off[b + 1] - d->block_instr_off[b] > 65535) return GPA_ERR_INVALID_PROGRAM;
   for (int f = 0; f < nf; ++f) {
     if (d->func_instr_off[f + 1] - d->func_instr_off[f] >= (1 << 24)) return GPA_ERR_INVALID_PROGRAM;
     if (d->block_instr_off[d->func_block_off[f]] != d->func_instr_off[f]) return GPA_ERR_INVALID_PROGRAM;
@@ -255,7 +238,7 @@ gpa_status gpa_create(const gpa_arch_desc* arch, const gpa_options* opts, gpa_ct
     for (int r : o.reserved)
       if (r) return GPA_ERR_INVALID_ARG;
     if (o.max_fixpoint_sweeps < 0 || o.max_search_nodes < 0 || o.search_slots < 0 || o.max_sources_per_use < 0 ||
-        o.max_sources_per_use > kMaxSrc || o.small_search_nodes < 0)
+        o.max_sources_per_use > kMaxSrc || o.small_search_nodes < 0 || o.mid_search_nodes < 0)
       return GPA_ERR_INVALID_ARG;
   }
   auto* c = new (std::nothrow) gpa_ctx();
@@ -269,22 +252,40 @@ gpa_status gpa_create(const gpa_arch_desc* arch, const gpa_options* opts, gpa_ct
   for (int k = 0; k < arch->n_opclasses; ++k) { c->arch.lat[k] = arch->latency[k]; c->arch.flags[k] = arch->flags[k]; }
   if (o.max_fixpoint_sweeps == 0) o.max_fixpoint_sweeps = 64;
   if (o.max_search_nodes == 0) o.max_search_nodes = 65536;
-  if (o.search_slots == 0) o.search_slots = 32 * c->sms;
+  if (o.search_slots == 0) o.search_slots = c->sms;
   if (o.max_sources_per_use == 0) o.max_sources_per_use = kMaxSrc;
+  if (o.small_search_nodes == 0) o.small_search_nodes = 128;
   c->opts = o;
-  // Tier 1: many small slots for the common general search; tier 2: one large
-  // slot per SM for searches that overflow tier 1.
-  if (o.small_search_nodes == 0) o.small_search_nodes = 512;
-  int n1 = 2;
-  while (n1 < o.small_search_nodes && n1 < o.max_search_nodes) n1 <<= 1;
-  int n2 = 1;
-  while (n2 < o.max_search_nodes) n2 <<= 1;
-  gpa_status s = scratch_alloc(&c->tier1, o.search_slots, std::max(n1, 2));
-  if (!s) s = scratch_alloc(&c->tier2, c->sms, std::max(n2, 2));
+  // Tier 1: four warps per CTA with small shared-memory arenas, three CTAs per
+  // SM. Tier 2: three one-warp CTAs per SM with larger shared-memory arenas
+  // (one per SM beyond 512 nodes). Tier 3: warps
+  // with global-memory arenas for the rare searches beyond that. Node
+  // capacities are powers of two (hash masks).
+  int n1 = 2, n3 = 2;
+  while (n1 < o.small_search_nodes && n1 < 1024) n1 <<= 1;
+  while (n3 < o.max_search_nodes) n3 <<= 1;
+  int n2 = 2;
+  const int want2 = o.mid_search_nodes ? o.mid_search_nodes : std::min(512, n3);
+  while (n2 < want2 && n2 < 1024) n2 <<= 1;
+  n2 = std::max(n1, n2);
+  SearchArena* T = c->tier;
+  T[0].nodes = n1; T[0].src = std::min(n1, 64); T[0].layers = 4; T[0].warps = 12 * c->sms;
+  T[1].nodes = n2; T[1].src = std::min(n2, 256); T[1].layers = 4; T[1].warps = (n2 <= 512 ? 3 : 1) * c->sms;
+  T[2].nodes = n3; T[2].src = std::min(n3, 1024); T[2].layers = kMaxLayers; T[2].warps = o.search_slots;
+  for (int t = 0; t < 3; ++t) {
+    T[t].bytes = search_arena_bytes(T[t].nodes, T[t].src, T[t].layers);
+    T[t].global = nullptr;
+  }
+  gpa_status s = GPA_OK;
+  if (T[0].bytes * 4 > 220 * 1024 || T[1].bytes > 220 * 1024) s = GPA_ERR_INVALID_ARG;
+  if (!s && cudaMalloc(&T[2].global, (size_t)T[2].bytes * T[2].warps) != cudaSuccess) {
+    T[2].global = nullptr;
+    s = GPA_ERR_OOM;
+  }
+  if (!s && cudaMemset(T[2].global, 0, (size_t)T[2].bytes * T[2].warps) != cudaSuccess) s = GPA_ERR_CUDA;
   if (!s && cudaEventCreateWithFlags(&c->scratch_ev, cudaEventDisableTiming) != cudaSuccess) s = GPA_ERR_CUDA;
   if (s) {
-    if (c->tier1.base) cudaFree(c->tier1.base);
-    if (c->tier2.base) cudaFree(c->tier2.base);
+    if (c->tier[2].global) cudaFree(c->tier[2].global);
     delete c;
     return s;
   }
@@ -296,8 +297,7 @@ gpa_status gpa_destroy(gpa_ctx* ctx) {
   if (!ctx) return GPA_ERR_INVALID_ARG;
   cudaDeviceSynchronize();
   for (auto& kv : ctx->progs) free_program(kv.second);
-  if (ctx->tier1.base) cudaFree(ctx->tier1.base);
-  if (ctx->tier2.base) cudaFree(ctx->tier2.base);
+  if (ctx->tier[2].global) cudaFree(ctx->tier[2].global);
   for (int k = 0; k < 2; ++k) {
     if (ctx->stage[k]) cudaFree(ctx->stage[k]);
     if (ctx->ev_copied[k]) cudaEventDestroy(ctx->ev_copied[k]);
@@ -349,6 +349,11 @@ gpa_status gpa_load_program(gpa_ctx* ctx, const gpa_program_desc* d, gpa_pid* ou
   TRY(dev_alloc(R, &ldepth, nl));
   TRY(dev_alloc(R, &iblock, ni));
   TRY(dev_alloc(R, &bfunc, nb));
+  int32_t* ev_off = nullptr;
+  uint32_t* events = nullptr;
+  TRY(dev_alloc(R, &ev_off, nb + 1));
+  TRY(dev_alloc(R, &events, (size_t)d->n_def + (size_t)d->n_use));
+  P.ev_off = ev_off; P.events = events;
   TRY(dev_alloc(R, &P.res_maxlat, nf * kNumRes));
   P.pred_off = pred_off; P.pred = pred; P.loop_depth = ldepth; P.instr_block = iblock; P.block_func = bfunc;
   TRY(dev_alloc(R, &R->scan_tmp, scan_tmp_ints((int)std::max(ni, nb) + 1)));
@@ -394,6 +399,7 @@ gpa_status gpa_load_program(gpa_ctx* ctx, const gpa_program_desc* d, gpa_pid* ou
   }
   launch_build_layout(P, st, ctx->sms, &ctx->launches);
   launch_build_preds(P, R->n_succ, pred_off, cursor, R->scan_tmp, st, ctx->sms, &ctx->launches);
+  launch_build_events(P, ev_off, events, R->scan_tmp, st, ctx->sms, &ctx->launches);
   if (cudaDeviceSynchronize() != cudaSuccess || cudaGetLastError() != cudaSuccess) {
     free_program(R);
     return GPA_ERR_CUDA;
@@ -478,8 +484,7 @@ gpa_status gpa_blame(gpa_ctx* ctx, gpa_pid pid, gpa_stream stream) {
   launch_dataflow(R->P, ctx->arch, ctx->opts.max_fixpoint_sweeps, st, ctx->sms, &ctx->launches);
   // The search scratch is shared by the context's programs: order its users.
   CK(cudaStreamWaitEvent(st, ctx->scratch_ev, 0));
-  launch_blame(R->P, ctx->arch, ctx->tier1, ctx->tier2, ctx->opts.max_sources_per_use, R->scan_tmp, st, ctx->sms,
-               &ctx->launches);
+  launch_blame(R->P, ctx->arch, ctx->tier, ctx->opts.max_sources_per_use, R->scan_tmp, st, ctx->sms, &ctx->launches);
   CK(cudaEventRecord(ctx->scratch_ev, st));
   CK(cudaGetLastError());
   return GPA_OK;

@@ -147,9 +147,10 @@ def test_invalid_program_rejected(ctx):
 
 
 def test_small_search_slots_overflow_to_large_tier():
-    """A tiny first-tier slot forces general searches into the second tier; results stay exact."""
+    """Tiny first- and second-tier arenas force general searches through all three tiers
+    (shared memory, larger shared memory, global memory); results stay exact."""
     import paper_2009_04061_gb300 as g
-    with g.Context(ARCH, dict(small_search_nodes=4, search_slots=64)) as c:
+    with g.Context(ARCH, dict(small_search_nodes=4, mid_search_nodes=16, search_slots=64)) as c:
         rng = np.random.default_rng(11)
         P = synth.make_program(synth.batched_params(20, rng, 11), 1.0)
         s = P.samples(1_000_000, seed=11)
