@@ -257,6 +257,30 @@ gpa_status gpa_get_advice(gpa_ctx* ctx, gpa_pid pid, const gpa_advice* out, gpa_
 /* Kernel launches issued by this context since creation (for accounting). */
 int64_t gpa_launch_count(gpa_ctx* ctx);
 
+/* In-place exclusive prefix sum of n int32 values on the device: dev_buf[k]
+ * becomes the sum of the inputs before k and *dev_total (device memory) the sum
+ * of all n. The paper has no counterpart: this is the scan the library uses
+ * for its own offsets (edges per use, events per block, predecessors).
+ *
+ * It allocates nothing, unlike the rest of the library, which owns
+ * cudaMalloc'd buffers. It is for callers that cannot call cudaMalloc at the
+ * point where they need a scan: code recorded into a CUDA graph (allocation is
+ * not allowed during stream capture), code that runs inside another
+ * framework's memory pool and must not grow the process's device footprint,
+ * or a profiler callback that must not perturb the application it measures.
+ * Its scratch (the per-tile sums) is a fixed static device array of
+ * (4096 + 64) int32 that every device loading the library holds until exit.
+ *
+ * Limits and behaviour: 0 <= n <= 16,777,216; larger n returns
+ * GPA_ERR_CAPACITY, a null pointer or negative n GPA_ERR_INVALID_ARG, and
+ * nothing is launched. The first call on a device looks up the scratch
+ * address on that device (cudaGetSymbolAddress); make that first call before
+ * any stream capture. Every call shares the one scratch array and leaves its
+ * contents behind (nothing in it needs to start at zero): calls that overlap on
+ * the GPU, on different streams or from different threads, race and give
+ * wrong results. The call is asynchronous on stream. */
+gpa_status gpa_exclusive_scan_noalloc(int32_t* dev_buf, int64_t n, int32_t* dev_total, gpa_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -94,6 +94,7 @@ def library() -> ctypes.CDLL:
         "gpa_get_edges": ([vp, u32, vp, i64, vp, vp, vp, vp, vp, vp, vp], i32),
         "gpa_get_advice": ([vp, u32, vp, vp], i32),
         "gpa_launch_count": ([vp], i64),
+        "gpa_exclusive_scan_noalloc": ([vp, i64, vp, vp], i32),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -290,6 +291,15 @@ def gpa_get_edges(ctx, pid, stream=None):
 
 def gpa_launch_count(ctx) -> int:
     return int(library().gpa_launch_count(ctx))
+
+
+def gpa_exclusive_scan_noalloc(dev_buf, dev_total, n: int | None = None, stream=None):
+    """In-place exclusive scan of an int32 CUDA tensor; the total goes to dev_total (int32, 1 element).
+    Allocates no device memory (fixed static scratch, see include/gpa.h)."""
+    if n is None:
+        n = dev_buf.numel()
+    _check(library().gpa_exclusive_scan_noalloc(_p(dev_buf), n, _p(dev_total), _stream(stream)),
+           "gpa_exclusive_scan_noalloc")
 
 
 # ---------------------------------------------------------------- convenience objects
