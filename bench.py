@@ -49,7 +49,9 @@ def parse():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-functions", type=int, default=40, help="functions in the CPU-baseline sample")
+    ap.add_argument("--cpu-functions", type=int, default=200, help="functions in the CPU-baseline sample")
+    ap.add_argument("--functions", type=int, default=0, help="keep only the first N functions (profiling runs)")
+    ap.add_argument("--search-slots", type=int, default=0, help="third-tier search warps (0 = library default)")
     return ap.parse_args()
 
 
@@ -127,8 +129,10 @@ class Clocks:
                 "samples": len(rows)}
 
 
-def make_workload(name: str, seed: int, n_override: int = 0):
+def make_workload(name: str, seed: int, n_override: int = 0, functions: int = 0):
     ps, ns, kz = synth.workload(name, seed=seed)
+    if functions:
+        ps = ps[:functions]
     P = synth.make_program(ps, kz, kseed=seed)
     return P, (n_override or ns)
 
@@ -194,11 +198,11 @@ def main():
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
 
-    P, n = make_workload(a.workload, a.seed + rank, a.samples)
+    P, n = make_workload(a.workload, a.seed + rank, a.samples, a.functions)
     host = torch.empty(n, dtype=torch.int64).pin_memory()
     P.samples(n, seed=a.seed + rank, out=host.numpy().view(np.uint64))
     d = host.to(dev, non_blocking=False)
-    ctx = gpa.Context(synth.default_arch())
+    ctx = gpa.Context(synth.default_arch(), {"search_slots": a.search_slots} if a.search_slots else None)
     prog = ctx.load_program(P)
     stream = torch.cuda.current_stream(dev)
 
@@ -316,7 +320,9 @@ def main():
                        "sample_bytes_per_gpu": 8 * n, "l2": "inputs (samples) larger than L2, no flush",
                        "parallelism": f"replicas x{world}, no collective on the data path"},
             "analysed_instrs_per_s": instr_per_s, "phases_ms": phase,
-            "general_searches": info["general_searches"], "gpu_launches": launches,
+            "general_searches": info["general_searches"], "search_tiers": [
+                info["general_searches"], info["tier2_searches"], info["tier3_searches"]],
+            "largest_search_nodes": info["max_nodes"], "gpu_launches": launches,
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
         }
         print(json.dumps(line), flush=True)

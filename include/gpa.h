@@ -98,8 +98,8 @@ typedef struct {
 
 typedef struct {
   int32_t max_fixpoint_sweeps;  /* reaching-definitions sweep limit; 0 = 64 */
-  int32_t max_search_nodes;     /* (block, predicate-set) nodes of the largest general search; 0 = 65536 */
-  int32_t search_slots;         /* warps with a max_search_nodes global-memory arena; 0 = one per SM */
+  int32_t max_search_nodes;     /* (block, predicate-set) nodes of the largest general search; 0 = 32768 */
+  int32_t search_slots;         /* warps with a max_search_nodes global-memory arena; 0 = four per SM */
   int32_t max_sources_per_use;  /* distinct sources merged per stalled use; 0 = 64 (max 64) */
   int32_t small_search_nodes;   /* nodes of the shared-memory arena of a first-tier search warp; 0 = 128
                                    (max 1024). A search that outgrows it is redone in the next tier */
@@ -232,8 +232,10 @@ gpa_status gpa_advise(gpa_ctx* ctx, gpa_pid pid, const gpa_advice* out, gpa_stre
 
 /* Synchronizes stream and returns the program's device status word as a
  * gpa_status (GPA_OK, GPA_ERR_NOT_CONVERGED, GPA_ERR_CAPACITY, ...). If info is
- * not NULL: info[0] = invalid samples, info[1] = general (multi-block)
- * searches run, info[2] = largest search in nodes, info[3] = fixpoint sweeps. */
+ * not NULL it must have room for 6 values: info[0] = invalid samples,
+ * info[1] = general (multi-block) searches run, info[2] = largest search in
+ * nodes, info[3] = fixpoint sweeps, info[4] and info[5] = searches handed on to
+ * the second and third search tiers by the last gpa_blame. */
 gpa_status gpa_sync_status(gpa_ctx* ctx, gpa_pid pid, gpa_stream stream, int64_t* info);
 
 /* Parity getters: synchronize stream and copy device results to host memory.

@@ -1,12 +1,15 @@
 // Step (a), Sec. 2.1: aggregate packed PC samples into per-(instruction,
 // stall class, latency flag) counters.
 //
-// HBM-bound stream: 8 bytes read per sample. Each warp reads 32 x 16-byte
-// vectors per load round (two samples per lane, four rounds in flight), with
-// non-allocating loads so the sample stream does not evict the counters from
-// L2. Lanes holding the same counter are merged with match.any and the leader
-// issues one 64-bit atomic add for the group, so hot instructions (Zipf-skewed
-// hotness) cost one L2 atomic per warp rather than one per sample.
+// HBM-bound stream: 8 bytes read per sample. Persistent CTAs (three per SM)
+// stream 16-byte vectors with non-allocating loads, double-buffered in
+// registers so the next round's loads are in flight while the current round
+// is counted. Counting goes through a per-CTA shared-memory hash of hot
+// counters (8,192 u32 key/value pairs): lanes holding the same counter are
+// first merged with match.any, the group leader adds into the hash, and a key
+// that finds no slot within a few probes goes straight to its 64-bit global
+// counter. The hash is flushed to the global counters when three quarters
+// full and at the end. With Zipf-skewed hotness most samples stay on chip.
 #include "gpa_internal.cuh"
 
 namespace gpa {
@@ -14,15 +17,16 @@ namespace gpa {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kUnroll = 4;
-constexpr int kSmemFuncs = 8192;
+constexpr int kUnroll = 4;           // 16-byte vectors per thread per round
+constexpr int kCtasPerSm = 3;
+constexpr int kHash = 8192;          // entries per CTA (64 KB of shared memory)
+constexpr int kProbes = 8;
+constexpr int kSmemFuncs = 4096;     // function offsets cached in shared memory
 constexpr uint32_t kNoKey = 0xFFFFFFFFu;
 
 __device__ __forceinline__ ulonglong2 load_stream(const ulonglong2* p) {
   ulonglong2 v;
-  asm volatile("ld.global.nc.L1::no_allocate.v2.u64 {%0, %1}, [%2];"
-               : "=l"(v.x), "=l"(v.y)
-               : "l"(p));
+  asm volatile("ld.global.nc.L1::no_allocate.v2.u64 {%0, %1}, [%2];" : "=l"(v.x), "=l"(v.y) : "l"(p));
   return v;
 }
 
@@ -32,42 +36,79 @@ __device__ __forceinline__ uint32_t sample_key(uint64_t s, const int32_t* foff, 
   const uint32_t pc = (uint32_t)(s >> 24) & 0xFFFFFFu;
   const uint32_t cls = (uint32_t)(s >> 20) & 0xFu;
   const uint32_t lat = (uint32_t)(s >> 19) & 1u;
-  bool ok = kernel < (uint32_t)nf && cls < 12u && !(cls == 0u && lat) && (s & 0x7FFull) == 0ull;
+  const bool ok = kernel < (uint32_t)nf && cls < 12u && !(cls == 0u && lat) && (s & 0x7FFull) == 0ull;
   if (!ok) return kNoKey;
   const int32_t lo = foff[kernel];
   if (pc >= (uint32_t)(foff[kernel + 1] - lo)) return kNoKey;
   return ((uint32_t)lo + pc) * 24u + cls * 2u + lat;
 }
 
-__device__ __forceinline__ void count(uint32_t key, bool in_range, unsigned long long* cnt, uint32_t& bad) {
+struct Hash {
+  uint32_t* key;
+  uint32_t* val;
+  int* fill;
+};
+
+__device__ __forceinline__ void hash_add(const Hash& H, uint32_t k, uint32_t c, unsigned long long* cnt) {
+  uint32_t h = (k * 2654435761u) >> (32 - 13);  // 13 = log2(kHash)
+#pragma unroll 1
+  for (int p = 0; p < kProbes; ++p) {
+    const uint32_t cur = H.key[h];
+    if (cur == k) { atomicAdd(&H.val[h], c); return; }
+    if (cur == kNoKey) {
+      const uint32_t prev = atomicCAS(&H.key[h], kNoKey, k);
+      if (prev == kNoKey) { atomicAdd(H.fill, 1); atomicAdd(&H.val[h], c); return; }
+      if (prev == k) { atomicAdd(&H.val[h], c); return; }
+    }
+    h = (h + 1) & (kHash - 1);
+  }
+  atomicAdd(cnt + k, (unsigned long long)c);  // no room nearby: count in global memory
+}
+
+__device__ __forceinline__ void count(uint32_t key, bool in_range, const Hash& H, unsigned long long* cnt,
+                                      uint32_t& bad) {
   const uint32_t k = in_range ? key : kNoKey;
   if (in_range && key == kNoKey) ++bad;
   const unsigned peers = __match_any_sync(0xffffffffu, k);
   const int lane = threadIdx.x & 31;
-  if (k != kNoKey && lane == __ffs(peers) - 1) atomicAdd(cnt + k, (unsigned long long)__popc(peers));
+  if (k != kNoKey && lane == __ffs(peers) - 1) hash_add(H, k, (uint32_t)__popc(peers), cnt);
+}
+
+__device__ void flush(const Hash& H, unsigned long long* cnt) {
+  for (int t = threadIdx.x; t < kHash; t += blockDim.x) {
+    const uint32_t k = H.key[t];
+    if (k != kNoKey) {
+      atomicAdd(cnt + k, (unsigned long long)H.val[t]);
+      H.key[t] = kNoKey;
+      H.val[t] = 0u;
+    }
+  }
 }
 
 __global__ void __launch_bounds__(kThreads) k_histogram(Prog P, const uint64_t* __restrict__ s, int64_t n,
                                                        int head) {
-  extern __shared__ int32_t s_off[];
-  const bool smem = P.nf <= kSmemFuncs;
-  if (smem) {
+  extern __shared__ __align__(16) uint32_t sm[];
+  Hash H{sm, sm + kHash, reinterpret_cast<int*>(sm + 2 * kHash)};
+  int32_t* s_off = reinterpret_cast<int32_t*>(sm + 2 * kHash + 4);
+  const bool smem_off = P.nf <= kSmemFuncs;
+  for (int t = threadIdx.x; t < kHash; t += blockDim.x) { H.key[t] = kNoKey; H.val[t] = 0u; }
+  if (threadIdx.x == 0) *H.fill = 0;
+  if (smem_off)
     for (int i = threadIdx.x; i <= P.nf; i += blockDim.x) s_off[i] = P.func_instr_off[i];
-    __syncthreads();
-  }
-  const int32_t* foff = smem ? s_off : P.func_instr_off;
+  __syncthreads();
+  const int32_t* foff = smem_off ? s_off : P.func_instr_off;
   const int lane = threadIdx.x & 31;
   uint32_t bad = 0;
 
-  // Scalar head (an 8-byte-aligned start) and tail (odd count).
+  // Scalar head (an 8-byte-aligned start) and tail (odd count): global atomics.
   const int64_t n2 = (n - head) / 2;
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     for (int64_t t = 0; t < head; ++t) {
-      uint32_t k = sample_key(s[t], foff, P.nf);
+      const uint32_t k = sample_key(s[t], foff, P.nf);
       if (k == kNoKey) ++bad; else atomicAdd(P.cnt + k, 1ull);
     }
     for (int64_t t = head + 2 * n2; t < n; ++t) {
-      uint32_t k = sample_key(s[t], foff, P.nf);
+      const uint32_t k = sample_key(s[t], foff, P.nf);
       if (k == kNoKey) ++bad; else atomicAdd(P.cnt + k, 1ull);
     }
   }
@@ -76,21 +117,50 @@ __global__ void __launch_bounds__(kThreads) k_histogram(Prog P, const uint64_t* 
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t n_warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const int64_t step = n_warps * 32 * kUnroll;
-  for (int64_t c = warp * 32 * kUnroll; c < n2; c += step) {
-    ulonglong2 v[kUnroll];
-    bool in[kUnroll];
+  ulonglong2 cur[kUnroll], nxt[kUnroll];
+  bool in_cur[kUnroll], in_nxt[kUnroll];
+  int64_t c = warp * 32 * kUnroll;
+  auto load_round = [&](int64_t base, ulonglong2* v, bool* in) {
 #pragma unroll
     for (int u = 0; u < kUnroll; ++u) {
-      const int64_t idx = c + u * 32 + lane;
+      const int64_t idx = base + u * 32 + lane;
       in[u] = idx < n2;
       v[u] = in[u] ? load_stream(v2 + idx) : make_ulonglong2(0ull, 0ull);
     }
+  };
+  load_round(c, cur, in_cur);
+  int round = 0, since_flush = 0;
+  // The loop bound is uniform per CTA (rounds are counted from the CTA's first
+  // warp) so that every thread reaches the block-wide flush barriers.
+  const int64_t cta_first = (int64_t)blockIdx.x * (blockDim.x >> 5) * 32 * kUnroll;
+  const int64_t rounds = cta_first < n2 ? (n2 - cta_first + step - 1) / step : 0;
+  for (int64_t r = 0; r < rounds; ++r) {
+    load_round(c + step, nxt, in_nxt);
 #pragma unroll
     for (int u = 0; u < kUnroll; ++u) {
-      count(sample_key(v[u].x, foff, P.nf), in[u], P.cnt, bad);
-      count(sample_key(v[u].y, foff, P.nf), in[u], P.cnt, bad);
+      count(sample_key(cur[u].x, foff, P.nf), in_cur[u], H, P.cnt, bad);
+      count(sample_key(cur[u].y, foff, P.nf), in_cur[u], H, P.cnt, bad);
+    }
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) { cur[u] = nxt[u]; in_cur[u] = in_nxt[u]; }
+    c += step;
+    if (++round == 16) {  // every 16 rounds: flush when the hash is three quarters full
+      round = 0;
+      __syncthreads();
+      // (also every 4,096 rounds, which keeps each 32-bit count below 2^24)
+      const bool full = *H.fill > kHash * 3 / 4 || ++since_flush >= 256;
+      __syncthreads();
+      if (full) {
+        since_flush = 0;
+        flush(H, P.cnt);
+        __syncthreads();
+        if (threadIdx.x == 0) *H.fill = 0;
+        __syncthreads();
+      }
     }
   }
+  __syncthreads();
+  flush(H, P.cnt);
   // One invalid-count atomic per warp.
   for (int o = 16; o > 0; o >>= 1) bad += __shfl_xor_sync(0xffffffffu, bad, o);
   if (lane == 0 && bad) atomicAdd(&P.stats[SS_INVALID], (unsigned long long)bad);
@@ -103,10 +173,12 @@ void launch_histogram(const Prog& P, const uint64_t* samples, size_t n, cudaStre
   const int head = (reinterpret_cast<uintptr_t>(samples) & 15u) ? 1 : 0;
   const int64_t vecs = ((int64_t)n - head) / 2;
   int64_t blocks = (vecs + (int64_t)kThreads * kUnroll - 1) / ((int64_t)kThreads * kUnroll);
-  const int64_t cap = (int64_t)sms * 8;  // 8 x 256 threads per SM resident
+  const int64_t cap = (int64_t)sms * kCtasPerSm;
   if (blocks > cap) blocks = cap;
   if (blocks < 1) blocks = 1;
-  const size_t smem = P.nf <= kSmemFuncs ? sizeof(int32_t) * (size_t)(P.nf + 1) : 0;
+  const size_t smem = sizeof(uint32_t) * (2 * (size_t)kHash + 4) +
+                      (P.nf <= kSmemFuncs ? sizeof(int32_t) * (size_t)(P.nf + 1) : 0);
+  cudaFuncSetAttribute(k_histogram, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   k_histogram<<<(int)blocks, kThreads, smem, st>>>(P, samples, (int64_t)n, head);
   ++*launches;
 }

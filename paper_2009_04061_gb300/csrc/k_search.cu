@@ -92,8 +92,13 @@ __device__ bool warp_search(const Prog& P, const Arch& A, const Arena& a, int j,
   const uint32_t hmask = (uint32_t)(2 * a.N - 1);
   volatile int* ctr = a.ctr;
 
+  // Unexpanded nodes are kept in a list (alternating between seen and tmp,
+  // both free until rule 2): ubuf holds ctr[6] of them.
+  int* ubuf = a.seen;
+  int* ukeep = a.tmp;
   if (lane == 0) {
-    ctr[0] = 1; ctr[1] = 0; ctr[2] = 0; ctr[3] = 0; ctr[4] = 0;
+    ctr[0] = 1; ctr[1] = 0; ctr[2] = 0; ctr[3] = 0; ctr[4] = 0; ctr[6] = 1;
+    ubuf[0] = 0;
     a.blk[0] = b0; a.S[0] = (int)S0 | ((int)S0 << 16); a.cov[0] = first0; a.wall[0] = -1; a.fl[0] = 0;
     a.dpk[0] = 0ull; a.k[0] = 0; a.e0[0] = 0; a.e1[0] = 0;
   }
@@ -205,6 +210,7 @@ __device__ bool warp_search(const Prog& P, const Arch& A, const Arena& a, int j,
                 a.e0[nv] = 0; a.e1[nv] = 0;  // no out-edges until the node is expanded
                 a.dpk[nv] = ((unsigned long long)kInf << 32) | 0xFFFFFFFFull;
                 a.hused[atomicAdd((int*)&a.ctr[3], 1)] = (int)h;
+                ubuf[atomicAdd((int*)&a.ctr[6], 1)] = nv;
                 __threadfence_block();
                 a.ht[h] = nv;
                 v = nv; pending = false;
@@ -280,20 +286,35 @@ __device__ bool warp_search(const Prog& P, const Arch& A, const Arena& a, int j,
     }
   };
 
-  // Pass A: expand in waves the nodes within the bound, relaxing from each wave.
+  // Split the unexpanded list: nodes to expand now (into list) and the rest,
+  // which stay unexpanded (all of them when bound < 0).
   int* list = a.q;
-  while (!ctr[4]) {
-    const int n = ctr[0];
-    int cnt = 0;
-    for (int u0 = 0; u0 < n; u0 += 32) {
-      const int u = u0 + lane;
-      const bool want = u < n && !(a.fl[u] & kExpanded) && dist_of(a, u) <= bound;
-      int tot;
-      const int at = warp_slot(want, &tot);
-      if (want) list[cnt + at] = u;
-      cnt += tot;
+  auto take_wave = [&](int lim) {
+    const int m = ctr[6];
+    int cnt = 0, kept = 0;
+    for (int i0 = 0; i0 < m; i0 += 32) {
+      const int i = i0 + lane;
+      const int u = i < m ? ubuf[i] : 0;
+      const bool now = i < m && (lim < 0 || dist_of(a, u) <= lim);
+      const bool keep = i < m && !now;
+      int tot_now, tot_keep;
+      const int at_now = warp_slot(now, &tot_now);
+      const int at_keep = warp_slot(keep, &tot_keep);
+      if (now) list[cnt + at_now] = u;
+      if (keep) ukeep[kept + at_keep] = u;
+      cnt += tot_now;
+      kept += tot_keep;
     }
     __syncwarp();
+    int* sw = ubuf; ubuf = ukeep; ukeep = sw;
+    if (lane == 0) ctr[6] = kept;
+    __syncwarp();
+    return cnt;
+  };
+
+  // Pass A: expand in waves the nodes within the bound, relaxing from each wave.
+  while (!ctr[4]) {
+    const int cnt = take_wave(bound);
     if (cnt == 0) break;
     expand_list(list, cnt);
     if (ctr[4]) break;
@@ -312,17 +333,7 @@ __device__ bool warp_search(const Prog& P, const Arch& A, const Arena& a, int j,
   // Pass B: complete the graph.
   if (cand) {
     while (!ctr[4]) {
-      const int n = ctr[0];
-      int cnt = 0;
-      for (int u0 = 0; u0 < n; u0 += 32) {
-        const int u = u0 + lane;
-        const bool want = u < n && !(a.fl[u] & kExpanded);
-        int tot;
-        const int at = warp_slot(want, &tot);
-        if (want) list[cnt + at] = u;
-        cnt += tot;
-      }
-      __syncwarp();
+      const int cnt = take_wave(-1);
       if (cnt == 0) break;
       expand_list(list, cnt);
     }

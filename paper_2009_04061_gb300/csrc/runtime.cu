@@ -251,8 +251,8 @@ gpa_status gpa_create(const gpa_arch_desc* arch, const gpa_options* opts, gpa_ct
   c->arch.n_op = arch->n_opclasses;
   for (int k = 0; k < arch->n_opclasses; ++k) { c->arch.lat[k] = arch->latency[k]; c->arch.flags[k] = arch->flags[k]; }
   if (o.max_fixpoint_sweeps == 0) o.max_fixpoint_sweeps = 64;
-  if (o.max_search_nodes == 0) o.max_search_nodes = 65536;
-  if (o.search_slots == 0) o.search_slots = c->sms;
+  if (o.max_search_nodes == 0) o.max_search_nodes = 32768;
+  if (o.search_slots == 0) o.search_slots = 4 * c->sms;
   if (o.max_sources_per_use == 0) o.max_sources_per_use = kMaxSrc;
   if (o.small_search_nodes == 0) o.small_search_nodes = 128;
   c->opts = o;
@@ -540,6 +540,8 @@ gpa_status gpa_sync_status(gpa_ctx* ctx, gpa_pid pid, gpa_stream stream, int64_t
     info[1] = (int64_t)h[SS_GENERAL];
     info[2] = (int64_t)h[SS_MAX_NODES];
     info[3] = (int64_t)h[SS_SWEEPS];
+    info[4] = (int64_t)h[SS_OVF_N];
+    info[5] = (int64_t)h[SS_OVF2_N];
   }
   return status_from(h[SS_STATUS]);
 }

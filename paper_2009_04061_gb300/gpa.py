@@ -247,10 +247,10 @@ def gpa_get_advice(ctx, pid, shape, stream=None):
 
 
 def gpa_sync_status(ctx, pid, stream=None):
-    info = np.zeros(4, np.int64)
+    info = np.zeros(6, np.int64)
     st = library().gpa_sync_status(ctx, pid, _stream(stream), _p(info))
     return st, dict(invalid=int(info[0]), general_searches=int(info[1]), max_nodes=int(info[2]),
-                    sweeps=int(info[3]))
+                    sweeps=int(info[3]), tier2_searches=int(info[4]), tier3_searches=int(info[5]))
 
 
 def gpa_get_counts(ctx, pid, n_instr: int, stream=None):
