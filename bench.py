@@ -49,7 +49,8 @@ def parse():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-functions", type=int, default=200, help="functions in the CPU-baseline sample")
+    ap.add_argument("--cpu-functions", type=int, default=100, help="functions in the CPU-baseline sample")
+    ap.add_argument("--cpu-samples", type=int, default=3_000_000, help="sample cap of the CPU-baseline sample")
     ap.add_argument("--functions", type=int, default=0, help="keep only the first N functions (profiling runs)")
     ap.add_argument("--search-slots", type=int, default=0, help="third-tier search warps (0 = library default)")
     return ap.parse_args()
@@ -137,14 +138,20 @@ def make_workload(name: str, seed: int, n_override: int = 0, functions: int = 0)
     return P, (n_override or ns)
 
 
-def cpu_sample(P, n_total: int, k_funcs: int, seed: int):
-    """The oracle's bounded sample: the first k_funcs functions with all their samples
-    from the first min(n_total, 5e7) samples of the stream."""
-    m = min(n_total, 50_000_000)
-    s = P.samples(m, seed=seed)
-    k = (s >> np.uint64(48)).astype(np.int64)
-    sub = np.ascontiguousarray(s[k < k_funcs])
-    return sub, m
+def cpu_sample(P, n_total: int, k_funcs: int, seed: int, cap: int):
+    """The oracle's bounded sample: functions 0..k_funcs-1 with the samples of their
+    launch runs, in stream order, up to `cap` samples (regenerated run by run from
+    the counter-based stream, so they are the very samples the GPU counts)."""
+    starts, kern = P.launch_runs(n_total, seed=seed)
+    parts, got = [], 0
+    for r in np.flatnonzero(kern < k_funcs):
+        take = min(int(starts[r + 1] - starts[r]), cap - got)
+        if take <= 0:
+            break
+        parts.append(P.samples(take, seed=seed, n0=int(starts[r]), total=n_total))
+        got += take
+    sub = np.concatenate(parts) if parts else np.zeros(0, np.uint64)
+    return sub, got
 
 
 def run_oracle_once(P, sub, k_funcs):
@@ -162,15 +169,15 @@ def reference_arm(a):
         return
     P, n = make_workload(a.workload, a.seed, a.samples)
     k_funcs = min(P.n_functions, max(1, a.cpu_functions // 4))
-    sub, m = cpu_sample(P, n, k_funcs, a.seed)
+    sub, m = cpu_sample(P, n, k_funcs, a.seed, max(1, a.cpu_samples // 4))
     for _ in range(a.warmup):
         run_oracle_once(P, sub, k_funcs)
     ts = [run_oracle_once(P, sub, k_funcs) for _ in range(a.steps)]
     t = statistics.mean(ts)
     v = sub.size / t
     instr = int(P.func_instr_off[k_funcs])
-    sample = (f"functions 0..{k_funcs - 1} of the {a.workload} workload ({instr} instructions) with their "
-              f"{sub.size} samples from the first {m} of the stream")
+    sample = (f"functions 0..{k_funcs - 1} of the {a.workload} workload ({instr} instructions) with the "
+              f"first {sub.size} samples of their launch runs")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": a.gpus, "steps": a.steps,
         "warmup": a.warmup, "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak",
@@ -304,11 +311,11 @@ def main():
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         k_funcs = min(P.n_functions, a.cpu_functions)
-        sub, m = cpu_sample(P, n, k_funcs, a.seed)
+        sub, m = cpu_sample(P, n, k_funcs, a.seed, a.cpu_samples)
         t = run_oracle_once(P, sub, k_funcs)
         cpu = {"value": sub.size / t, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": f"functions 0..{k_funcs - 1} ({int(P.func_instr_off[k_funcs])} instructions) with their "
-                         f"{sub.size} samples from the first {m} of the stream; {t:.1f} s single-threaded"}
+                         f"the first {sub.size} samples of their launch runs; {t:.1f} s single-threaded"}
 
     if rank == 0:
         line = {

@@ -232,11 +232,22 @@ gpa_status gpa_advise(gpa_ctx* ctx, gpa_pid pid, const gpa_advice* out, gpa_stre
 
 /* Synchronizes stream and returns the program's device status word as a
  * gpa_status (GPA_OK, GPA_ERR_NOT_CONVERGED, GPA_ERR_CAPACITY, ...). If info is
- * not NULL it must have room for 6 values: info[0] = invalid samples,
+ * not NULL it must have room for 8 values: info[0] = invalid samples,
  * info[1] = general (multi-block) searches run, info[2] = largest search in
  * nodes, info[3] = fixpoint sweeps, info[4] and info[5] = searches handed on to
- * the second and third search tiers by the last gpa_blame. */
+ * the second and third search tiers by the last gpa_blame, info[6] and
+ * info[7] = the stalled use (global instruction index) and the resource of
+ * the largest search. */
 gpa_status gpa_sync_status(gpa_ctx* ctx, gpa_pid pid, gpa_stream stream, int64_t* info);
+
+/* Diagnostic: per search tier (3) the SM cycles summed over the searches of the
+ * last gpa_blame in six phases: building the graph, shortest distances and
+ * fewest back edges, sources and rule 3, rule 2, longest paths and emission,
+ * and (not cycles) the number of rule-2 reachability runs. out must hold 18
+ * values, tier-major. All zero unless the library was built with
+ * -DGPA_PHASE_TIMING (the timers cost a few atomics per search). Synchronizes
+ * stream. */
+gpa_status gpa_get_search_profile(gpa_ctx* ctx, gpa_pid pid, uint64_t* out, gpa_stream stream);
 
 /* Parity getters: synchronize stream and copy device results to host memory.
  * counts[n_instr*24]: counts[pc*24 + class*2 + latency]; *invalid may be NULL. */

@@ -2,7 +2,8 @@
 
 Translation units compile in parallel into _build/, then link into
 libgpa.so beside this file. Rebuilds only when a source or header is newer
-than the library.
+than the library or the extra flags changed. GPA_NVCC_FLAGS adds flags to
+every compile (e.g. -DGPA_PHASE_TIMING for the search phase timers).
 """
 from __future__ import annotations
 
@@ -37,8 +38,17 @@ def sources():
     return sorted(glob.glob(os.path.join(CSRC, "*.cu")))
 
 
+STAMP = os.path.join(BUILD, "flags.txt")
+
+
+def _env_flags():
+    return os.environ.get("GPA_NVCC_FLAGS", "").split()
+
+
 def _stale() -> bool:
     if not os.path.exists(LIB):
+        return True
+    if (open(STAMP).read() if os.path.exists(STAMP) else "") != " ".join(_env_flags()):
         return True
     t = os.path.getmtime(LIB)
     deps = sources() + glob.glob(os.path.join(CSRC, "*.cuh")) + [os.path.join(INCLUDE, "gpa.h"), __file__]
@@ -50,7 +60,7 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
         return LIB
     os.makedirs(BUILD, exist_ok=True)
     cc = nvcc()
-    extra = ["-Xptxas", "-v"] if ptxas_info else []
+    extra = (["-Xptxas", "-v"] if ptxas_info else []) + _env_flags()
 
     def one(src):
         obj = os.path.join(BUILD, os.path.basename(src) + ".o")
@@ -72,6 +82,8 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
     os.replace(tmp, LIB)
+    with open(STAMP, "w") as f:
+        f.write(" ".join(_env_flags()))
     return LIB
 
 

@@ -25,7 +25,11 @@ enum : unsigned long long {
 enum {
   SS_INVALID = 0, SS_GENERAL = 1, SS_MAX_NODES = 2, SS_SWEEPS = 3, SS_STATUS = 4,
   SS_RAW_N = 5, SS_QUEUE_N = 6, SS_QUEUE_HEAD = 7, SS_OVF_N = 8, SS_OVF_HEAD = 9, SS_OVF2_N = 10,
-  SS_OVF2_HEAD = 11, SS_N = 12
+  SS_OVF2_HEAD = 11, SS_MAX_TASK = 12,
+  // Per-tier search phase cycles (3 tiers x 6), filled only when built with
+  // -DGPA_PHASE_TIMING: graph, distances, sources, rule 2, longest paths,
+  // and the count of rule-2 reachability runs.
+  SS_PHASE = 13, SS_N = 13 + 18
 };
 
 struct Arch {

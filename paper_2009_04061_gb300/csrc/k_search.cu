@@ -82,8 +82,21 @@ __device__ __forceinline__ int warp_slot(bool pred, int* total) {
 }
 
 // Returns false when the search outgrew the arena (nothing emitted).
-__device__ bool warp_search(const Prog& P, const Arch& A, const Arena& a, int j, int r, uint16_t S0, int bound) {
+__device__ bool warp_search(const Prog& P, const Arch& A, const Arena& a, int j, int r, uint16_t S0, int bound,
+                            int tier) {
   const int lane = threadIdx.x & 31;
+#ifdef GPA_PHASE_TIMING
+  long long t_prev = clock64();
+  auto phase = [&](int i) {
+    if (lane == 0) {
+      const long long t = clock64();
+      atomicAdd(&P.stats[SS_PHASE + (tier - 1) * 6 + i], (unsigned long long)(t - t_prev));
+      t_prev = t;
+    }
+  };
+#else
+  auto phase = [](int) {};
+#endif
   const int gj = P.guard[j];
   const int b0 = P.instr_block[j];
   const int first0 = P.block_instr_off[b0];
@@ -346,7 +359,9 @@ __device__ bool warp_search(const Prog& P, const Arch& A, const Arena& a, int j,
   if (lane == 0) {
     atomicAdd(&P.stats[SS_GENERAL], 1ull);
     atomicMax(&P.stats[SS_MAX_NODES], (unsigned long long)n);
+    atomicMax(&P.stats[SS_MAX_TASK], ((unsigned long long)n << 40) | ((unsigned long long)r << 31) | (unsigned)j);
   }
+  phase(0);
   if (ctr[4]) return false;
   if (!cand) return true;
 
@@ -360,6 +375,7 @@ __device__ bool warp_search(const Prog& P, const Arch& A, const Arena& a, int j,
   __syncwarp();
   relax_from(a.q, 1, 0);
   relax_from(a.q, 1, 1);
+  phase(1);
 
   // Sources: a warp-synchronous hash keyed by instruction gives each source an
   // index; per source, 64-bit atomicMin keeps (shortest distance, its
@@ -423,6 +439,7 @@ __device__ bool warp_search(const Prog& P, const Arch& A, const Arena& a, int j,
   }
   for (int o = 16; o > 0; o >>= 1) alive += __shfl_xor_sync(0xffffffffu, alive, o);
   __syncwarp();
+  phase(2);
   if (alive == 0) return true;
 
   // Rule 2. Wall groups, one per block: a hash keyed by block with atomicMax
@@ -479,6 +496,9 @@ __device__ bool warp_search(const Prog& P, const Arch& A, const Arena& a, int j,
   __syncwarp();
   for (int t = 0; t < nw; ++t) {
     if (!a.wneed[t] || alive == 0) continue;
+#ifdef GPA_PHASE_TIMING
+    if (lane == 0) atomicAdd(&P.stats[SS_PHASE + (tier - 1) * 6 + 5], 1ull);
+#endif
     const int WB = a.wblk[t], WP = a.wpos[t], epoch = t + 1;
     auto trunc = [&](int u) { return u != 0 && a.blk[u] == WB && a.cov[u] <= WP; };
     // Level-synchronous reachability from the root, frontiers in q / tmp.
@@ -520,6 +540,7 @@ __device__ bool warp_search(const Prog& P, const Arch& A, const Arena& a, int j,
     alive -= dropped;
     __syncwarp();
   }
+  phase(3);
   if (alive == 0) return true;
 
   // Longest path with exactly K back edges: layer = back edges used. Each
@@ -591,6 +612,7 @@ __device__ bool warp_search(const Prog& P, const Arch& A, const Arena& a, int j,
     emit_raw(P, A, j, a.si[m], r, def_kind(P, a.si[m], r), (int)(a.sdb[m] >> 32), best);
   }
   __syncwarp();
+  phase(4);
   return true;
 }
 
@@ -621,7 +643,7 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32) k_search_warp(Prog P, Arch 
     const int4 task = q[t];
     const int f = P.block_func[P.instr_block[task.x]];
     const int bound = P.res_maxlat[(size_t)f * kNumRes + task.y];
-    const bool ok = warp_search(P, A, a, task.x, task.y, (uint16_t)task.z, bound);
+    const bool ok = warp_search(P, A, a, task.x, task.y, (uint16_t)task.z, bound, tier);
     if (ok || lane != 0) continue;
     if (tier < 3) {
       const int o_slot = tier == 1 ? SS_OVF_N : SS_OVF2_N;

@@ -542,8 +542,19 @@ gpa_status gpa_sync_status(gpa_ctx* ctx, gpa_pid pid, gpa_stream stream, int64_t
     info[3] = (int64_t)h[SS_SWEEPS];
     info[4] = (int64_t)h[SS_OVF_N];
     info[5] = (int64_t)h[SS_OVF2_N];
+    info[6] = (int64_t)(h[SS_MAX_TASK] & 0x7FFFFFFFull);     // use of the largest search
+    info[7] = (int64_t)((h[SS_MAX_TASK] >> 31) & 0x1FFull);  // its resource
   }
   return status_from(h[SS_STATUS]);
+}
+
+gpa_status gpa_get_search_profile(gpa_ctx* ctx, gpa_pid pid, uint64_t* out, gpa_stream stream) {
+  ProgramRec* R = find(ctx, pid);
+  if (!R) return GPA_ERR_NO_PROGRAM;
+  if (!out) return GPA_ERR_INVALID_ARG;
+  CK(cudaStreamSynchronize((cudaStream_t)stream));
+  CK(cudaMemcpy(out, R->P.stats + SS_PHASE, 18 * sizeof(uint64_t), cudaMemcpyDeviceToHost));
+  return GPA_OK;
 }
 
 gpa_status gpa_get_counts(gpa_ctx* ctx, gpa_pid pid, uint64_t* counts, uint64_t* invalid, gpa_stream stream) {

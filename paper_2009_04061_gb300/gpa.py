@@ -89,6 +89,7 @@ def library() -> ctypes.CDLL:
         "gpa_advise": ([vp, u32, vp, vp], i32),
         "gpa_sync_status": ([vp, u32, vp, vp], i32),
         "gpa_get_counts": ([vp, u32, vp, vp, vp], i32),
+        "gpa_get_search_profile": ([vp, u32, vp, vp], i32),
         "gpa_get_reaching": ([vp, u32, vp, vp, vp], i32),
         "gpa_get_blame": ([vp, u32, vp, vp], i32),
         "gpa_get_edges": ([vp, u32, vp, i64, vp, vp, vp, vp, vp, vp, vp], i32),
@@ -247,10 +248,18 @@ def gpa_get_advice(ctx, pid, shape, stream=None):
 
 
 def gpa_sync_status(ctx, pid, stream=None):
-    info = np.zeros(6, np.int64)
+    info = np.zeros(8, np.int64)
     st = library().gpa_sync_status(ctx, pid, _stream(stream), _p(info))
     return st, dict(invalid=int(info[0]), general_searches=int(info[1]), max_nodes=int(info[2]),
-                    sweeps=int(info[3]), tier2_searches=int(info[4]), tier3_searches=int(info[5]))
+                    sweeps=int(info[3]), tier2_searches=int(info[4]), tier3_searches=int(info[5]),
+                    largest_use=int(info[6]), largest_resource=int(info[7]))
+
+
+def gpa_get_search_profile(ctx, pid, stream=None) -> np.ndarray:
+    """Per-tier search phase cycles, shape (3, 6); zeros unless built with -DGPA_PHASE_TIMING."""
+    out = np.zeros(18, np.uint64)
+    _check(library().gpa_get_search_profile(ctx, pid, _p(out), _stream(stream)), "gpa_get_search_profile")
+    return out.reshape(3, 6)
 
 
 def gpa_get_counts(ctx, pid, n_instr: int, stream=None):
@@ -356,6 +365,9 @@ class Program:
 
     def counts(self, stream=None):
         return gpa_get_counts(self.h, self.pid, self.n_instr, stream)
+
+    def search_profile(self, stream=None):
+        return gpa_get_search_profile(self.h, self.pid, stream)
 
     def reaching(self, stream=None):
         return gpa_get_reaching(self.h, self.pid, self.n_blocks, stream)

@@ -99,7 +99,11 @@ def _L():
         lib.synth_program_sizes.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
         lib.synth_program_copy.argtypes = [ctypes.c_void_p] + [ctypes.c_void_p] * 19
         lib.synth_samples.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int64, ctypes.c_int64,
-                                      ctypes.c_void_p, ctypes.c_uint32, ctypes.c_int32]
+                                      ctypes.c_void_p, ctypes.c_uint32, ctypes.c_int32, ctypes.c_int64,
+                                      ctypes.c_int32]
+        lib.synth_launch_runs.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int64, ctypes.c_void_p,
+                                          ctypes.c_void_p, ctypes.c_int64]
+        lib.synth_launch_runs.restype = ctypes.c_int64
         _lib = lib
     return _lib
 
@@ -144,16 +148,33 @@ class Program:
         return int(self.arrays["n_loops"])
 
     def samples(self, n: int, seed: int = 0, n0: int = 0, invalid_ppm: int = 0, threads: int = 0,
-                out: np.ndarray | None = None) -> np.ndarray:
-        """Packed samples [n0, n0+n) of the stream `seed` (counter based)."""
+                out: np.ndarray | None = None, total: int | None = None, order: str = "launch") -> np.ndarray:
+        """Packed samples [n0, n0+n) of the stream `seed` (counter based).
+
+        order "launch": the stream of `total` samples (default n0 + n) is a
+        sequence of kernel-launch runs, each holding one kernel's samples, as a
+        profiler that serializes kernels delivers them; see launch_runs().
+        order "interleaved": every sample draws its kernel independently.
+        """
         if out is None:
             out = np.empty(n, dtype=np.uint64)
         assert out.dtype == np.uint64 and out.size >= n and out.flags.c_contiguous
+        tot = n0 + n if total is None else int(total)
+        assert tot >= n0 + n, "slice beyond the end of the stream"
         if threads <= 0:
             threads = os.cpu_count() or 1
         if n:
-            _L().synth_samples(self.handle, ctypes.c_uint64(seed), n0, n, _ptr(out), invalid_ppm, threads)
+            _L().synth_samples(self.handle, ctypes.c_uint64(seed), n0, n, _ptr(out), invalid_ppm, threads, tot,
+                               {"interleaved": 0, "launch": 1}[order])
         return out
+
+    def launch_runs(self, total: int, seed: int = 0):
+        """(starts[n_runs + 1], kernels[n_runs]) of the launch-ordered stream of `total` samples."""
+        nr = _L().synth_launch_runs(self.handle, ctypes.c_uint64(seed), total, None, None, 0)
+        starts = np.zeros(nr + 1, np.int64)
+        kernels = np.zeros(max(nr, 1), np.int32)[:nr]
+        _L().synth_launch_runs(self.handle, ctypes.c_uint64(seed), total, _ptr(starts), _ptr(kernels), nr)
+        return starts, kernels
 
     def __del__(self):
         h = self.__dict__.get("handle")

@@ -737,26 +737,84 @@ void synth_program_copy(void* h, int32_t* func_instr_off, int32_t* func_block_of
   cp(block_loop, P->block_loop); cp(loop_parent, P->loop_parent); cp(loop_header, P->loop_header);
 }
 
+// Launch layout of a stream of `total` samples (Sec. 2.1: the profiler
+// serializes kernel executions, so each launch's samples arrive as one run).
+// Kernel k receives its share of `total` by cumulative rounding of the Zipf
+// kernel weights, split into 1-8 launches (seeded); the launches of all
+// kernels run in a seeded random order. starts has n_runs + 1 entries.
+static void launch_runs(const Program& P, uint64_t seed, int64_t total, std::vector<int64_t>& starts,
+                        std::vector<int32_t>& kernels) {
+  const uint64_t ktot = P.kcum.back();
+  auto share_end = [&](int k) {  // floor(total * kcum[k] / ktot) without overflow
+    const unsigned __int128 x = (unsigned __int128)(uint64_t)total * P.kcum[k];
+    return (int64_t)(x / ktot);
+  };
+  std::vector<std::pair<int32_t, int64_t>> runs;  // (kernel, length)
+  int64_t prev = 0;
+  const uint64_t ls = mix64(seed ^ 0xA0761D6478BD642FULL);
+  for (int k = 0; k < P.nf; ++k) {
+    const int64_t end = share_end(k), nk = end - prev;
+    prev = end;
+    if (nk <= 0) continue;
+    int64_t L = 1 + (int64_t)(mix64(ls + (uint64_t)(k + 1) * kGolden) % 8);
+    if (L > nk) L = nk;
+    for (int64_t t = 0; t < L; ++t) runs.emplace_back(k, nk * (t + 1) / L - nk * t / L);
+  }
+  Rng r(seed ^ 0xE7037ED1A0B428DBULL);
+  for (size_t i = runs.size(); i > 1; --i) std::swap(runs[i - 1], runs[r.below((int)i)]);
+  starts.assign(1, 0);
+  kernels.clear();
+  for (auto& x : runs) { kernels.push_back(x.first); starts.push_back(starts.back() + x.second); }
+}
+
+// Run layout for callers: returns the number of runs; fills starts[0..n_runs]
+// and kernels[0..n_runs-1] when cap >= n_runs.
+int64_t synth_launch_runs(void* h, uint64_t seed, int64_t total, int64_t* starts, int32_t* kernels, int64_t cap) {
+  std::vector<int64_t> st;
+  std::vector<int32_t> kr;
+  launch_runs(*(Program*)h, seed, total, st, kr);
+  const int64_t nr = (int64_t)kr.size();
+  if (cap >= nr) {
+    std::memcpy(starts, st.data(), sizeof(int64_t) * (size_t)(nr + 1));
+    if (nr) std::memcpy(kernels, kr.data(), sizeof(int32_t) * (size_t)nr);
+  }
+  return nr;
+}
+
 // Packed samples [n0, n0+n) of stream `seed`:
 //   kernel (16b) | pc (24b) | class (4b) | latency flag (1b) | sm (8b) | 11 reserved zero bits.
+// order 0: the kernel of every sample is drawn independently (kernels interleaved);
+// order 1: launch runs as laid out by launch_runs for a stream of `total` samples
+// (total <= 0 means n0 + n).
 // invalid_ppm injects malformed samples (bad kernel, pc, class, or SELECTED+latency).
 void synth_samples(void* h, uint64_t seed, int64_t n0, int64_t n, uint64_t* out, uint32_t invalid_ppm,
-                   int32_t n_threads) {
+                   int32_t n_threads, int64_t total, int32_t order) {
   auto* P = (Program*)h;
   const uint64_t base = mix64(seed ^ 0xD1B54A32D192ED03ULL);
   const uint64_t ktot = P->kcum.back();
+  std::vector<int64_t> rstart;
+  std::vector<int32_t> rkern;
+  if (order == 1) launch_runs(*P, seed, std::max<int64_t>(total, n0 + n), rstart, rkern);
   int nt = std::max<int64_t>(1, std::min<int64_t>(n_threads, (n + 65535) / 65536));
   std::vector<std::thread> th;
   for (int t = 0; t < nt; ++t) {
     th.emplace_back([&, t]() {
       int64_t lo = n * t / nt, hi = n * (t + 1) / nt;
+      size_t run = 0;
       for (int64_t q = lo; q < hi; ++q) {
         uint64_t idx = (uint64_t)(n0 + q);
         uint64_t d0 = mix64(base + (3 * idx + 1) * kGolden);
         uint64_t d1 = mix64(base + (3 * idx + 2) * kGolden);
         uint64_t d2 = mix64(base + (3 * idx + 3) * kGolden);
-        uint64_t v0 = (d0 >> 16) % ktot;
-        int k = (int)(std::upper_bound(P->kcum.begin(), P->kcum.end(), v0) - P->kcum.begin());
+        int k;
+        if (order == 1) {
+          if (q == lo || (int64_t)idx >= rstart[run + 1])
+            run = (size_t)(std::upper_bound(rstart.begin(), rstart.end(), (int64_t)idx) - rstart.begin()) - 1;
+          k = run < rkern.size() ? rkern[run] : rkern.back();
+        } else {
+          uint64_t v0 = (d0 >> 16) % ktot;
+          k = (int)(std::upper_bound(P->kcum.begin(), P->kcum.end(), v0) - P->kcum.begin());
+        }
         int lo_i = P->func_instr_off[k], hi_i = P->func_instr_off[k + 1];
         uint64_t ftot = P->wcum[hi_i - 1];
         uint64_t v1 = (d1 >> 16) % ftot;

@@ -1,0 +1,53 @@
+"""The seeded input generator: counter-based slices and launch-ordered streams.
+
+The generator holds none of the analysis arithmetic; these tests pin the
+properties the parity tests and the benchmark rely on."""
+import numpy as np
+import pytest
+
+import synth
+
+
+@pytest.fixture(scope="module")
+def prog():
+    params, _, kz = synth.workload("rodinia", 0)
+    return synth.make_program(params, kz, 0)
+
+
+def kernels_of(s):
+    return (s >> np.uint64(48)).astype(np.int64)
+
+
+@pytest.mark.parametrize("order", ["launch", "interleaved"])
+def test_slices_regenerate_the_stream(prog, order):
+    n = 300_001
+    full = prog.samples(n, seed=3, order=order)
+    a = prog.samples(123_457, seed=3, total=n, order=order)
+    b = prog.samples(n - 123_457, seed=3, n0=123_457, total=n, order=order)
+    assert np.array_equal(full, np.concatenate([a, b]))
+
+
+def test_launch_runs_are_kernel_contiguous(prog):
+    n = 1_000_000
+    starts, kern = prog.launch_runs(n, seed=1)
+    assert starts[0] == 0 and starts[-1] == n and np.all(np.diff(starts) > 0)
+    s = prog.samples(n, seed=1)
+    k = kernels_of(s)
+    for r in range(len(kern)):
+        assert np.all(k[starts[r]:starts[r + 1]] == kern[r])
+    # each kernel gets 1-8 launches, and its share follows the kernel weights
+    per = np.bincount(kern, minlength=prog.n_functions)
+    assert per.max() <= 8 and per.min() >= 1
+
+
+def test_launch_shares_match_interleaved_in_expectation(prog):
+    n = 2_000_000
+    a = np.bincount(kernels_of(prog.samples(n, seed=2)), minlength=prog.n_functions) / n
+    b = np.bincount(kernels_of(prog.samples(n, seed=2, order="interleaved")), minlength=prog.n_functions) / n
+    assert np.abs(a - b).max() < 0.01
+
+
+def test_single_kernel_orders_agree():
+    params, ns, kz = synth.workload("plain", 0)
+    P = synth.make_program(params, kz, 0)
+    assert np.array_equal(P.samples(ns), P.samples(ns, order="interleaved"))
