@@ -243,10 +243,14 @@ gpa_status gpa_sync_status(gpa_ctx* ctx, gpa_pid pid, gpa_stream stream, int64_t
 /* Diagnostic: per search tier (3) the SM cycles summed over the searches of the
  * last gpa_blame in six phases: building the graph, shortest distances and
  * fewest back edges, sources and rule 3, rule 2, longest paths and emission,
- * and (not cycles) the number of rule-2 reachability runs. out must hold 18
- * values, tier-major. All zero unless the library was built with
- * -DGPA_PHASE_TIMING (the timers cost a few atomics per search). Synchronizes
- * stream. */
+ * and (not cycles) the number of rule-2 reachability runs; out[0..17],
+ * tier-major. Then out[18..33] = searches by floor(log2(nodes)) (the last
+ * slot holds 2^15 nodes and more) and out[34] = searches that completed their
+ * graph past the latency bound; out[35] = the slowest search's cycles << 20 |
+ * its nodes, out[36] its rule-2 runs, out[37..41] its cycles in the first
+ * five phases. out must hold 42 values. All zero unless the
+ * library was built with -DGPA_PHASE_TIMING (the timers cost a few atomics per
+ * search). Synchronizes stream. */
 gpa_status gpa_get_search_profile(gpa_ctx* ctx, gpa_pid pid, uint64_t* out, gpa_stream stream);
 
 /* Parity getters: synchronize stream and copy device results to host memory.

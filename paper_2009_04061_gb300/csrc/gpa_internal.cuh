@@ -29,7 +29,11 @@ enum {
   // Per-tier search phase cycles (3 tiers x 6), filled only when built with
   // -DGPA_PHASE_TIMING: graph, distances, sources, rule 2, longest paths,
   // and the count of rule-2 reachability runs.
-  SS_PHASE = 13, SS_N = 13 + 18
+  // With -DGPA_PHASE_TIMING also: searches by log2 of their node count (16
+  // slots) and the searches that needed pass B (1 slot).
+  // And the slowest search: (cycles << 20 | nodes), its rule-2 runs and the
+  // cycles of its five phases.
+  SS_PHASE = 13, SS_SIZES = 31, SS_PASSB = 47, SS_SLOW = 48, SS_N = 55
 };
 
 struct Arch {

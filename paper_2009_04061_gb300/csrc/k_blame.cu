@@ -17,8 +17,10 @@
 //    resource inside j's block. It settles every source of that block
 //    (their only path is the straight segment) and stops at coverage or at
 //    the first unguarded reader of r (that reader lies on every path beyond,
-//    so nothing further can survive rule 2). Uses whose value may come from
-//    another block are queued.
+//    so nothing further can survive rule 2). If every predecessor block
+//    through which a def of r arrives covers j's guard, those predecessors
+//    are settled here too (one path per source); otherwise the (use,
+//    resource) pair is queued.
 //  * k_search_warp (k_search.cu): persistent warps pull queued (use,
 //    resource) pairs and explore the (block, literal set) graph.
 //  * k_merge_count / scan / k_apportion: merge sources per use, apportion in
@@ -36,6 +38,39 @@ namespace {
 
 __device__ __forceinline__ int dep_class(int ci) {
   return ci == 0 ? GPA_EXEC_DEPENDENCY : ci == 1 ? GPA_MEMORY_DEPENDENCY : ci == 2 ? GPA_SYNC : GPA_CONSTANT_MEMORY_DEPENDENCY;
+}
+
+// Scans predecessor block p of j's block b0 bottom-up for resource r, from
+// the literal set S left at the top of b0. Returns true if p covers j's
+// guard. With emit, emits p's sources that survive rules 2 and 3: when every
+// predecessor covers, a source has exactly one def-clear path (from j up to
+// the top of b0, into p at its bottom and up to the source), so its shortest
+// and longest distances are that path's length d0 + (last(p) - x), and
+// rule 2 reduces to an unguarded reader of r below it in p (met first in the
+// bottom-up scan). Defs above j in b0 are settled by the in-block scan.
+__device__ bool scan_pred(const Prog& P, const Arch& A, int j, int r, int gj, int b0, int p, uint16_t S, int d0,
+                          bool emit) {
+  const int first = P.block_instr_off[p], last = P.block_instr_off[p + 1] - 1;
+  bool wall = false;
+  int last_def_pos = -1;
+  const int ev1 = P.ev_off[p + 1];
+  for (int t = P.ev_off[p]; t < ev1; ++t) {
+    const uint32_t ev = P.events[t];
+    if ((int)(ev & 0x1FFu) != r) continue;
+    const int pos = (int)(ev >> 16), x = first + pos;
+    if (ev & 0x200u) {
+      last_def_pos = pos;
+      if (emit && !contains(S, gj) && !(p == b0 && x < j)) {
+        const int d = d0 + (last - x);
+        if (!wall && d <= A.lat[P.opclass[x]]) emit_raw(P, A, j, x, r, (int)((ev >> 10) & 3u), d, d);
+      }
+      S = add_literal(S, (int)((ev >> 12) & 0xFu));
+      if (contains(S, gj)) return true;
+    } else if (!wall && pos != last_def_pos && x != j) {
+      wall = true;
+    }
+  }
+  return false;
 }
 
 __global__ void k_search_local(Prog P, Arch A) {
@@ -70,16 +105,33 @@ __global__ void k_search_local(Prog P, Arch A) {
         }
       }
       if (blocked) continue;
+      // Predecessors through which a def of r reaches b0 (distinct blocks).
+      // If each covers j's guard inside itself, resolve here; otherwise queue
+      // the general search.
       const int w = r >> 5;
       const uint32_t bit = 1u << (r & 31);
-      for (int q = P.pred_off[b0]; q < P.pred_off[b0 + 1]; ++q) {
-        if (P.rout[(size_t)P.pred[q] * kWords + w] & bit) {
-          const unsigned long long t = atomicAdd(&P.stats[SS_QUEUE_N], 1ull);
-          if (t < (unsigned long long)P.queue_cap) P.queue[t] = make_int4(j, r, (int)S, 0);
-          else set_status(P, ST_CAPACITY);
-          break;
-        }
+      const int q0 = P.pred_off[b0], q1 = P.pred_off[b0 + 1];
+      auto counts = [&](int q) {
+        const int p = P.pred[q];
+        if (!(P.rout[(size_t)p * kWords + w] & bit)) return false;
+        for (int q2 = q0; q2 < q; ++q2) if (P.pred[q2] == p) return false;
+        return true;
+      };
+      bool any = false, all_cover = true;
+      for (int q = q0; q < q1 && all_cover; ++q) {
+        if (!counts(q)) continue;
+        any = true;
+        all_cover = scan_pred(P, A, j, r, gj, b0, P.pred[q], S, pj + 1, false);
       }
+      if (!any) continue;
+      if (all_cover) {
+        for (int q = q0; q < q1; ++q)
+          if (counts(q)) scan_pred(P, A, j, r, gj, b0, P.pred[q], S, pj + 1, true);
+        continue;
+      }
+      const unsigned long long t = atomicAdd(&P.stats[SS_QUEUE_N], 1ull);
+      if (t < (unsigned long long)P.queue_cap) P.queue[t] = make_int4(j, r, (int)S, 0);
+      else set_status(P, ST_CAPACITY);
     }
   }
 }

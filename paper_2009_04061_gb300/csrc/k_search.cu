@@ -46,7 +46,7 @@ __host__ __device__ inline int64_t arena_bytes(int N, int SRC, int L) {
   return 8 * (int64_t)N + 8 * (int64_t)SRC + ((ints * 4 + 15) & ~(int64_t)15);
 }
 
-__device__ Arena carve(char* base, int N, int SRC, int L) {
+__device__ Arena carve(char* base, int N, int SRC, int L, int* ctr) {
   Arena a;
   a.N = N; a.E = 2 * N; a.O = N; a.SRC = SRC; a.L = L;
   a.dpk = reinterpret_cast<unsigned long long*>(base);
@@ -61,7 +61,7 @@ __device__ Arena carve(char* base, int N, int SRC, int L) {
   a.on = p; p += a.O; a.ox = p; p += a.O; a.onext = p; p += a.O;
   a.wblk = p; p += N; a.wpos = p; p += N; a.wneed = p; p += N;
   a.si = p; p += SRC; a.sk = p; p += SRC; a.sp = p; p += SRC; a.shead = p; p += SRC;
-  a.ctr = p;
+  a.ctr = ctr;
   return a;
 }
 
@@ -87,11 +87,22 @@ __device__ bool warp_search(const Prog& P, const Arch& A, const Arena& a, int j,
   const int lane = threadIdx.x & 31;
 #ifdef GPA_PHASE_TIMING
   long long t_prev = clock64();
+  const long long t_begin = t_prev;
+  unsigned long long ph[5] = {0, 0, 0, 0, 0};
+  unsigned long long r2runs = 0;
   auto phase = [&](int i) {
     if (lane == 0) {
       const long long t = clock64();
       atomicAdd(&P.stats[SS_PHASE + (tier - 1) * 6 + i], (unsigned long long)(t - t_prev));
+      ph[i] = (unsigned long long)(t - t_prev);
       t_prev = t;
+      if (i == 4 || i == 0) {
+        const unsigned long long key = ((unsigned long long)(t - t_begin) << 20) | (unsigned long long)min(((volatile int*)a.ctr)[0], 0xFFFFF);
+        if (atomicMax(&P.stats[SS_SLOW], key) < key) {
+          P.stats[SS_SLOW + 1] = r2runs;
+          for (int q = 0; q < 5; ++q) P.stats[SS_SLOW + 2 + q] = ph[q];
+        }
+      }
     }
   };
 #else
@@ -117,15 +128,19 @@ __device__ bool warp_search(const Prog& P, const Arch& A, const Arena& a, int j,
   }
   __syncwarp();
 
-  // Self-check of the arena invariants before any indexed access: an edge range
-  // inside [0, edges) and targets inside [0, nodes). A violation is recorded
-  // as ST_OVERFLOW and the access skipped.
-  auto edges_ok = [&](int u, int n_now) {
+  // Self-checks of the arena invariants before indexed accesses: an edge
+  // range inside [0, edges) here, each target inside [0, nodes) where it is
+  // read (target_ok). A violation is recorded as ST_OVERFLOW and the access
+  // skipped.
+  auto edges_ok = [&](int u, int) {
     const int e0 = a.e0[u], e1 = a.e1[u];
     if (e0 < 0 || e1 < e0 || e1 > a.E || e1 > ctr[1]) { set_status(P, ST_OVERFLOW); return false; }
-    for (int e = e0; e < e1; ++e)
-      if ((a.eto[e] & 0x7FFFFFFF) >= n_now) { set_status(P, ST_OVERFLOW); return false; }
     return true;
+  };
+  auto target_ok = [&](int v, int n_now) {
+    if ((unsigned)v < (unsigned)n_now) return true;
+    set_status(P, ST_OVERFLOW);
+    return false;
   };
   auto wout = [&](int u) {
     return u == 0 ? (j - first0 + 1) : (P.block_instr_off[a.blk[u] + 1] - P.block_instr_off[a.blk[u]]);
@@ -276,6 +291,7 @@ __device__ bool warp_search(const Prog& P, const Arch& A, const Arena& a, int j,
           const unsigned long long nd = (unsigned long long)(du + wout(u)) << 32 | (unsigned)u;
           for (int e = a.e0[u]; e < a.e1[u]; ++e) {
             const int v = a.eto[e] & 0x7FFFFFFF;
+            if (!target_ok(v, n_now)) break;
             if (nd < a.dpk[v] && atomicMin(&a.dpk[v], nd) > nd && !(atomicOr(&a.fl[v], 8) & 8))
               nxt[atomicAdd((int*)&a.ctr[5], 1)] = v;
           }
@@ -284,6 +300,7 @@ __device__ bool warp_search(const Prog& P, const Arch& A, const Arena& a, int j,
           if (ku >= kInf) continue;
           for (int e = a.e0[u]; e < a.e1[u]; ++e) {
             const int v = a.eto[e] & 0x7FFFFFFF;
+            if (!target_ok(v, n_now)) break;
             const int kb = ku + (int)((uint32_t)a.eto[e] >> 31);
             if (kb < a.k[v] && atomicMin(&a.k[v], kb) > kb && !(atomicOr(&a.fl[v], 8) & 8))
               nxt[atomicAdd((int*)&a.ctr[5], 1)] = v;
@@ -360,6 +377,10 @@ __device__ bool warp_search(const Prog& P, const Arch& A, const Arena& a, int j,
     atomicAdd(&P.stats[SS_GENERAL], 1ull);
     atomicMax(&P.stats[SS_MAX_NODES], (unsigned long long)n);
     atomicMax(&P.stats[SS_MAX_TASK], ((unsigned long long)n << 40) | ((unsigned long long)r << 31) | (unsigned)j);
+#ifdef GPA_PHASE_TIMING
+    atomicAdd(&P.stats[SS_SIZES + min(15, 31 - __clz(max(n, 1)))], 1ull);
+    if (cand) atomicAdd(&P.stats[SS_PASSB], 1ull);
+#endif
   }
   phase(0);
   if (ctr[4]) return false;
@@ -492,31 +513,61 @@ __device__ bool warp_search(const Prog& P, const Arch& A, const Arena& a, int j,
     for (int v = par_of(a, u), hops = 0; v > 0 && hops < n; v = par_of(a, v), ++hops)
       if (a.wall[v] >= 0) a.wneed[a.grp[v]] = 1;
   }
-  for (int u = lane; u < n; u += 32) a.seen[u] = 0;
+  // The needed groups, compacted into ord (free until the longest paths).
+  int nl = 0;
+  for (int t0 = 0; t0 < nw; t0 += 32) {
+    const bool need = t0 + lane < nw && a.wneed[t0 + lane];
+    int tot;
+    const int at = warp_slot(need, &tot);
+    if (need) a.ord[nl + at] = t0 + lane;
+    nl += tot;
+  }
+  for (int t = lane; t < nw; t += 32) a.wneed[t] = 0;
   __syncwarp();
-  for (int t = 0; t < nw; ++t) {
-    if (!a.wneed[t] || alive == 0) continue;
+  // Bit-parallel reachability over up to 32 groups at a time: bit b of
+  // reach[u] (kept in seen) says u is reachable from the root without passing
+  // the wall of the batch's b-th group. A node truncated by a group (each node
+  // of its block that has a wall) passes every bit on but that group's.
+  // wneed[g] holds g's bit + 1 while g is in the batch.
+  int* reach = a.seen;
+  for (int b0 = 0; b0 < nl && alive > 0; b0 += 32) {
+    const int nbits = min(32, nl - b0);
+    const unsigned full = nbits == 32 ? 0xFFFFFFFFu : ((1u << nbits) - 1u);
 #ifdef GPA_PHASE_TIMING
     if (lane == 0) atomicAdd(&P.stats[SS_PHASE + (tier - 1) * 6 + 5], 1ull);
+    ++r2runs;
 #endif
-    const int WB = a.wblk[t], WP = a.wpos[t], epoch = t + 1;
-    auto trunc = [&](int u) { return u != 0 && a.blk[u] == WB && a.cov[u] <= WP; };
-    // Level-synchronous reachability from the root, frontiers in q / tmp.
+    if (lane < nbits) a.wneed[a.ord[b0 + lane]] = lane + 1;
+    for (int u = lane; u < n; u += 32) reach[u] = u == 0 ? (int)full : 0;
+    __syncwarp();
+    auto pass_mask = [&](int u) {
+      const int g = u != 0 ? a.grp[u] : -1;
+      const int b = g >= 0 ? a.wneed[g] : 0;
+      return b ? ~(1u << (b - 1)) : 0xFFFFFFFFu;
+    };
     int* cur = a.q;
     int* nxt = a.tmp;
-    if (lane == 0) { cur[0] = 0; a.seen[0] = epoch; ctr[5] = 0; }
+    if (lane == 0) { cur[0] = 0; ctr[5] = 0; }
     int fsize = 1;
     __syncwarp();
     while (fsize > 0) {
+      // Clear the queued flags of the whole frontier first: bits that arrive
+      // at a frontier node during this round queue it again.
+      for (int f = lane; f < fsize; f += 32) atomicAnd(&a.fl[cur[f]], ~8);
+      __syncwarp();
       for (int f0 = 0; f0 < fsize; f0 += 32) {
-        if (f0 + lane < fsize) {
-          const int u = cur[f0 + lane];
-          if (!trunc(u) && edges_ok(u, n))
-            for (int e = a.e0[u]; e < a.e1[u]; ++e) {
-              const int v = a.eto[e] & 0x7FFFFFFF;
-              if (a.seen[v] != epoch && atomicExch(&a.seen[v], epoch) != epoch)
-                nxt[atomicAdd((int*)&a.ctr[5], 1)] = v;
-            }
+        if (f0 + lane >= fsize) continue;
+        const int u = cur[f0 + lane];
+        if (!edges_ok(u, n)) continue;
+        const unsigned m = (unsigned)atomicOr(&reach[u], 0) & pass_mask(u);
+        if (!m) continue;
+        for (int e = a.e0[u]; e < a.e1[u]; ++e) {
+          const int v = a.eto[e] & 0x7FFFFFFF;
+          if (!target_ok(v, n)) break;
+          const unsigned add = m & ~(unsigned)reach[v];
+          if (!add) continue;
+          const unsigned old = (unsigned)atomicOr(&reach[v], (int)add);
+          if ((old | add) != old && !(atomicOr(&a.fl[v], 8) & 8)) nxt[atomicAdd((int*)&a.ctr[5], 1)] = v;
         }
       }
       __syncwarp();
@@ -526,18 +577,26 @@ __device__ bool warp_search(const Prog& P, const Arch& A, const Arena& a, int j,
       int* sw = cur; cur = nxt; nxt = sw;
       __syncwarp();
     }
+    // A source survives the batch if, for every group, one of its occurrences
+    // is reached without passing that group's wall (an occurrence above the
+    // wall inside a truncated node is cut too).
     int dropped = 0;
     for (int m = lane; m < nsrc; m += 32) {
       if (a.sp[m]) continue;
-      bool reach = false;
-      for (int o = a.shead[m]; o >= 0 && !reach; o = a.onext[o]) {
+      unsigned ok = 0;
+      for (int o = a.shead[m]; o >= 0 && (ok & full) != full; o = a.onext[o]) {
         const int u = a.on[o];
-        if (a.seen[u] == epoch && !(trunc(u) && a.ox[o] < WP)) reach = true;
+        unsigned r = (unsigned)reach[u];
+        const int g = u != 0 ? a.grp[u] : -1;
+        if (g >= 0 && a.wneed[g] && a.ox[o] < a.wpos[g]) r &= ~(1u << (a.wneed[g] - 1));
+        ok |= r;
       }
-      if (!reach) { a.sp[m] = 1; ++dropped; }
+      if ((ok & full) != full) { a.sp[m] = 1; ++dropped; }
     }
     for (int o = 16; o > 0; o >>= 1) dropped += __shfl_xor_sync(0xffffffffu, dropped, o);
     alive -= dropped;
+    __syncwarp();
+    if (lane < nbits) a.wneed[a.ord[b0 + lane]] = 0;
     __syncwarp();
   }
   phase(3);
@@ -625,7 +684,10 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32) k_search_warp(Prog P, Arch 
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int gw = blockIdx.x * (blockDim.x >> 5) + wid;
   char* base = tier < 3 ? smem + (int64_t)wid * SA.bytes : SA.global + (int64_t)gw * SA.bytes;
-  const Arena a = carve(base, SA.nodes, SA.src, SA.layers);
+  // The search counters live in shared memory in every tier (the arena of
+  // tier 3 is in global memory): frontier sizes are read after every round.
+  __shared__ int s_ctr[kWarpsPerCta][8];
+  const Arena a = carve(base, SA.nodes, SA.src, SA.layers, s_ctr[wid]);
   for (int t = lane; t < 2 * SA.nodes; t += 32) a.ht[t] = -1;
   __syncwarp();
   // tier 1 reads the local pass's queue, tier 2 the first overflow queue, and

@@ -553,7 +553,7 @@ gpa_status gpa_get_search_profile(gpa_ctx* ctx, gpa_pid pid, uint64_t* out, gpa_
   if (!R) return GPA_ERR_NO_PROGRAM;
   if (!out) return GPA_ERR_INVALID_ARG;
   CK(cudaStreamSynchronize((cudaStream_t)stream));
-  CK(cudaMemcpy(out, R->P.stats + SS_PHASE, 18 * sizeof(uint64_t), cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(out, R->P.stats + SS_PHASE, 42 * sizeof(uint64_t), cudaMemcpyDeviceToHost));
   return GPA_OK;
 }
 
