@@ -33,7 +33,9 @@ enum {
   // slots) and the searches that needed pass B (1 slot).
   // And the slowest search: (cycles << 20 | nodes), its rule-2 runs and the
   // cycles of its five phases.
-  SS_PHASE = 13, SS_SIZES = 31, SS_PASSB = 47, SS_SLOW = 48, SS_N = 55
+  SS_PHASE = 13, SS_SIZES = 31, SS_PASSB = 47, SS_SLOW = 48,
+  SS_REACH_HEAD = 55,  // next entry of reach_order for the staged fixpoint
+  SS_N = 56
 };
 
 struct Arch {
@@ -45,6 +47,8 @@ struct Arch {
 // Device view of one loaded program and its per-step buffers.
 struct Prog {
   int32_t nf, ni, nb, nl, n_lines;
+  int32_t reach_smem;             // shared memory of the staged fixpoint: the largest need that fits
+                                  // (functions needing more use the global-memory fixpoint)
   const int32_t* func_instr_off;
   const int32_t* func_block_off;
   const int32_t* func_loop_off;
@@ -67,6 +71,7 @@ struct Prog {
   const int32_t* loop_depth;
   const int32_t* instr_block;
   const int32_t* block_func;
+  const int32_t* reach_order;     // nf: functions by block count, largest first
   const int32_t* ev_off;          // nb + 1: per-block event lists
   const uint32_t* events;         // defs and unguarded reads, bottom-up: resource | def << 9 |
                                   // kind << 10 | guard << 12 | position in block << 16
@@ -181,6 +186,13 @@ void launch_build_preds(const Prog& P, int n_succ, int32_t* pred_off, int32_t* c
                         int sms, int64_t* launches);
 void launch_histogram(const Prog& P, const uint64_t* samples, size_t n, cudaStream_t st, int sms, int64_t* launches);
 void launch_dataflow(const Prog& P, const Arch& A, int max_sweeps, cudaStream_t st, int sms, int64_t* launches);
+
+// Shared memory the staged reaching-definitions fixpoint needs for a function
+// of nbf blocks and ne predecessor entries, and the most it may use.
+__host__ __device__ inline int64_t reach_smem_need(int64_t nbf, int64_t ne) {
+  return 4 * kWords * nbf + 4 * (nbf + 1) + 4 * ne;
+}
+constexpr int64_t kReachSmemCap = 200 * 1024;
 void launch_blame(const Prog& P, const Arch& A, const SearchArena* tiers, int max_src, int32_t* scan_tmp,
                   cudaStream_t st, int sms, int64_t* launches);
 void launch_search(const Prog& P, const Arch& A, const SearchArena* tiers, cudaStream_t st, int64_t* launches);

@@ -317,6 +317,15 @@ gpa_status gpa_load_program(gpa_ctx* ctx, const gpa_program_desc* d, gpa_pid* ou
   if (!R) return GPA_ERR_OOM;
   Prog& P = R->P;
   P.nf = d->n_functions; P.ni = d->n_instr; P.nb = d->n_blocks; P.nl = d->n_loops; P.n_lines = d->n_lines;
+  // Staged fixpoint: the largest per-function need within the cap (edges stay
+  // inside their function, so a function's predecessor entries are its
+  // blocks' successor entries).
+  P.reach_smem = 0;
+  for (int f = 0; f < d->n_functions; ++f) {
+    const int b0 = d->func_block_off[f], b1 = d->func_block_off[f + 1];
+    const int64_t need = reach_smem_need(b1 - b0, (int64_t)d->succ_off[b1] - d->succ_off[b0]);
+    if (b1 > b0 && need <= kReachSmemCap && need > P.reach_smem) P.reach_smem = (int32_t)need;
+  }
   R->n_succ = d->n_succ; R->n_def = d->n_def; R->n_use = d->n_use;
   const size_t ni = P.ni, nb = P.nb, nl = P.nl, nf = P.nf;
 #define TRY(x)                        \
@@ -325,6 +334,14 @@ gpa_status gpa_load_program(gpa_ctx* ctx, const gpa_program_desc* d, gpa_pid* ou
     if (t_) { free_program(R); return t_; } \
   } while (0)
   TRY(dev_copy(R, &P.func_instr_off, d->func_instr_off, nf + 1));
+  {
+    std::vector<int32_t> order(nf);
+    for (size_t f = 0; f < nf; ++f) order[f] = (int32_t)f;
+    std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
+      return d->func_block_off[a + 1] - d->func_block_off[a] > d->func_block_off[b + 1] - d->func_block_off[b];
+    });
+    TRY(dev_copy(R, &P.reach_order, order.data(), nf));
+  }
   TRY(dev_copy(R, &P.func_block_off, d->func_block_off, nf + 1));
   TRY(dev_copy(R, &P.func_loop_off, d->func_loop_off, nf + 1));
   TRY(dev_copy(R, &P.block_instr_off, d->block_instr_off, nb + 1));
