@@ -49,8 +49,15 @@ def parse():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-functions", type=int, default=100, help="functions in the CPU-baseline sample")
-    ap.add_argument("--cpu-samples", type=int, default=3_000_000, help="sample cap of the CPU-baseline sample")
+    ap.add_argument("--cpu-functions", type=int, default=250, help="functions in the CPU-baseline sample")
+    ap.add_argument("--cpu-samples", type=int, default=8_000_000, help="sample cap of the CPU-baseline sample")
+    ap.add_argument("--serving", action="store_true", help="run the serving workload instead")
+    ap.add_argument("--sessions", type=int, default=200, help="serving: sessions")
+    ap.add_argument("--rate", type=float, default=200.0, help="serving: mean arrivals per second")
+    ap.add_argument("--slots", type=int, default=8, help="serving: concurrent sessions")
+    ap.add_argument("--budget-gb", type=float, default=64.0, help="serving: device-memory admission budget")
+    ap.add_argument("--plain-workload", default="rodinia",
+                    help="workload of the batched-vs-plain comparison ('' to skip)")
     ap.add_argument("--functions", type=int, default=0, help="keep only the first N functions (profiling runs)")
     ap.add_argument("--search-slots", type=int, default=0, help="third-tier search warps (0 = library default)")
     return ap.parse_args()
@@ -154,6 +161,97 @@ def cpu_sample(P, n_total: int, k_funcs: int, seed: int, cap: int):
     return sub, got
 
 
+def plain_vs_batched(gpa, workload: str, seed: int, dev, stream, reps: int = 3) -> dict:
+    """Samples/s of one batched program over all functions of `workload` against one
+    program per function (the plain form), each fed its own launch runs; same GPU,
+    same samples, eager steps (reset, ingest, blame, advise kept on the device)."""
+    import torch
+    P, n = make_workload(workload, seed, 0, 0)
+    s = P.samples(n, seed=seed)
+    ctx = gpa.Context(synth.default_arch())
+    try:
+        progs, inputs = [ctx.load_program(P)], [torch.from_numpy(s.view(np.int64)).to(dev)]
+        plain, plain_in = [], []
+        for f in range(P.n_functions):
+            plain.append(ctx.load_program(synth.subprogram(P.arrays, f, f + 1)))
+            plain_in.append(torch.from_numpy(synth.rebase_samples(s, f, f + 1).view(np.int64)).to(dev))
+
+        def run(ps, xs):
+            for p_, x in zip(ps, xs):
+                p_.reset(stream)
+                if x.numel():
+                    p_.ingest(x, stream=stream)
+                p_.blame(stream)
+                p_.advise(fetch=False, stream=stream)
+
+        out = {}
+        for name, ps, xs in (("batched", progs, inputs), ("plain", plain, plain_in)):
+            run(ps, xs)
+            torch.cuda.synchronize(dev)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(reps):
+                run(ps, xs)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            ms = e0.elapsed_time(e1) / reps
+            out[name] = {"value": n / (ms / 1e3), "ms_per_step": ms}
+            for p_ in ps:
+                st, _ = p_.status(stream)
+                if st != 0:
+                    raise SystemExit(f"device status {st} in the {name} form")
+        return {"workload": workload, "functions": P.n_functions, "samples": n, "unit": UNIT,
+                "batched": out["batched"], "plain": out["plain"],
+                "speedup": out["batched"]["value"] / out["plain"]["value"]}
+    finally:
+        ctx.close()
+
+
+def serving_bench(a, gpa, dev):
+    """Serving workload: Poisson session arrivals through the continuous-batching
+    server against the same sessions one at a time. Prints one JSON line."""
+    import torch
+    from paper_2009_04061_gb300.serving import Server, Session, latency_summary, one_at_a_time, serve
+    arch = synth.default_arch()
+    specs = synth.serving_sessions(a.sessions, seed=a.seed, rate_per_s=a.rate)
+    sessions, keep = [], []
+    for i, d in enumerate(specs):
+        P = synth.make_program(d["params"], 1.0, d["seed"])
+        host = torch.empty(d["n_samples"], dtype=torch.int64).pin_memory()
+        P.samples(d["n_samples"], seed=d["seed"], out=host.numpy().view(np.uint64))
+        keep.append(host)
+        sessions.append(Session(i, P.arrays, host.numpy().view(np.uint64)))
+    arrivals = [d["t_arrival"] for d in specs]
+    budget = int(a.budget_gb * (1 << 30))
+    srv = Server(arch, slots=a.slots, budget_bytes=budget)
+    try:
+        # warm each slot (lazy staging buffers, first-launch costs) with a small session
+        small = min(range(len(sessions)), key=lambda i: sessions[i].samples.size)
+        serve(srv, [sessions[small]] * a.slots, [0.0] * a.slots)
+        torch.cuda.synchronize(dev)
+        with Clocks(torch.cuda.current_device()) as clk:
+            res = serve(srv, sessions, arrivals)
+    finally:
+        srv.close()
+    mix = latency_summary(res)
+    t_seq, res1 = one_at_a_time(arch, sessions)
+    seq = latency_summary(res1)
+    n = sum(s.samples.size for s in sessions)
+    print(json.dumps({
+        "metric": METRIC, "value": mix["samples_per_s"], "unit": UNIT, "n_gpus": 1, "steps": 1,
+        "warmup": 1, "ms_per_step": mix["span_s"] * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": {"workload": "serving", "sessions": len(sessions), "rate_per_s": a.rate, "slots": a.slots,
+                   "budget_gb": a.budget_gb, "samples": n,
+                   "instructions": int(sum(int(s.program["n_instr"]) for s in sessions))},
+        "latency_ms": {"p50": mix["p50_ms"], "p99": mix["p99_ms"], "mean": mix["mean_ms"], "max": mix["max_ms"]},
+        "one_at_a_time": {"value": n / t_seq, "unit": UNIT, "seconds": t_seq,
+                          "latency_ms_without_queueing": {"p50": seq["p50_ms"], "p99": seq["p99_ms"]}},
+        "speedup_vs_one_at_a_time": mix["samples_per_s"] / (n / t_seq),
+        "clocks": clk.summary(),
+    }), flush=True)
+
+
 def run_oracle_once(P, sub, k_funcs):
     import oracle
     arch = synth.default_arch()
@@ -204,6 +302,12 @@ def main():
         dist.init_process_group("gloo")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    if a.serving:
+        if rank == 0:
+            serving_bench(a, gpa, dev)
+        if world > 1:
+            dist.destroy_process_group()
+        return
 
     P, n = make_workload(a.workload, a.seed + rank, a.samples, a.functions)
     host = torch.empty(n, dtype=torch.int64).pin_memory()
@@ -214,9 +318,9 @@ def main():
     stream = torch.cuda.current_stream(dev)
 
     def step(ev=None):
+        prog.reset(stream)
         if ev:
             ev[0].record(stream)
-        prog.reset(stream)
         prog.ingest(d, stream=stream)
         if ev:
             ev[1].record(stream)
@@ -235,25 +339,40 @@ def main():
     cnt, bad = prog.counts(stream)
     assert int(cnt.sum()) + bad == n, "counts do not add up to the samples ingested"
 
-    if world > 1:
-        dist.barrier()
+    # Eager steps: the phase split and the aggregation kernel's launch time
+    # (the roofline's denominator), from events around each call.
     torch.cuda.synchronize(dev)
     evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(a.steps)]
-    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    l0 = ctx.launches()
-    with Clocks(local) as clk:
-        start.record(stream)
-        for k in range(a.steps):
-            step(evs[k])
-        end.record(stream)
-        torch.cuda.synchronize(dev)
-    launches = ctx.launches() - l0
-    ms = start.elapsed_time(end) / a.steps
+    for k in range(a.steps):
+        step(evs[k])
+    torch.cuda.synchronize(dev)
     phase = {
         "ingest_ms": statistics.mean(e[0].elapsed_time(e[1]) for e in evs),
         "blame_ms": statistics.mean(e[1].elapsed_time(e[2]) for e in evs),
         "advise_ms": statistics.mean(e[2].elapsed_time(e[3]) for e in evs),
     }
+    eager_ms = statistics.mean(e[0].elapsed_time(e[3]) for e in evs)
+
+    # The timed steps: the whole step captured once as a CUDA graph, one graph
+    # launch per step.
+    prog.capture_step(d)
+    prog.launch_step(stream)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    l0 = ctx.launches()
+    with Clocks(local) as clk:
+        start.record(stream)
+        for k in range(a.steps):
+            prog.launch_step(stream)
+        end.record(stream)
+        torch.cuda.synchronize(dev)
+    launches = ctx.launches() - l0
+    ms = start.elapsed_time(end) / a.steps
+    st, info = prog.status(stream)
+    if st != 0:
+        raise SystemExit(f"device status {st} after the timed steps: {info}")
     if world > 1:
         t = torch.tensor([ms], dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -263,19 +382,11 @@ def main():
     value = world * n / (ms / 1e3)
     instr_per_s = world * P.n_instr / (ms / 1e3)
 
-    # Roofline of the dominant kernel. The aggregation reads 8 algorithmic bytes per
-    # sample; the reset memset that shares its phase is timed apart here.
+    # Roofline of the aggregation kernel: 8 algorithmic bytes per sample over
+    # its launch time in the eager steps above (the reset memset runs before
+    # the first event).
     hbm_peak, peak_kind = load_peaks()
-    e_a, e_b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    hist_ms = []
-    for _ in range(3):
-        prog.reset(stream)
-        e_a.record(stream)
-        prog.ingest(d, stream=stream)
-        e_b.record(stream)
-        torch.cuda.synchronize(dev)
-        hist_ms.append(e_a.elapsed_time(e_b))
-    t_hist = statistics.median(hist_ms) / 1e3
+    t_hist = phase["ingest_ms"] / 1e3
     achieved = 8.0 * n / t_hist / 1e9
     tr = traffic_record("k_histogram")
     roofline = {"kernel": "k_histogram", "bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
@@ -317,6 +428,10 @@ def main():
                "sample": f"functions 0..{k_funcs - 1} ({int(P.func_instr_off[k_funcs])} instructions) with their "
                          f"the first {sub.size} samples of their launch runs; {t:.1f} s single-threaded"}
 
+    bvp = None
+    if rank == 0 and world == 1 and a.plain_workload:
+        bvp = plain_vs_batched(gpa, a.plain_workload, a.seed, dev, stream)
+
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
@@ -326,11 +441,13 @@ def main():
                        "blocks": P.n_blocks, "loops": P.n_loops, "samples_per_gpu": n,
                        "sample_bytes_per_gpu": 8 * n, "l2": "inputs (samples) larger than L2, no flush",
                        "parallelism": f"replicas x{world}, no collective on the data path"},
-            "analysed_instrs_per_s": instr_per_s, "phases_ms": phase,
+            "analysed_instrs_per_s": instr_per_s, "phases_ms": phase, "eager_ms_per_step": eager_ms,
+            "cuda_graph": True,
             "general_searches": info["general_searches"], "search_tiers": [
                 info["general_searches"], info["tier2_searches"], info["tier3_searches"]],
             "largest_search_nodes": info["max_nodes"], "gpu_launches": launches,
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+            "batched_vs_plain": bvp,
         }
         print(json.dumps(line), flush=True)
     prog.unload()

@@ -194,12 +194,27 @@ gpa_status gpa_create(const gpa_arch_desc* arch, const gpa_options* opts, gpa_ct
 /* Synchronizes the device, frees every program and the context. */
 gpa_status gpa_destroy(gpa_ctx* ctx);
 
-/* Validates and copies a program to the device (synchronous) and allocates
- * its counters and result buffers. *out receives the program id. */
+/* Validates and copies a program to the device and allocates its counters
+ * and result buffers (stream-ordered allocations on the context's own build
+ * stream; returns when they are done, without waiting for other streams).
+ * *out receives the program id. */
 gpa_status gpa_load_program(gpa_ctx* ctx, const gpa_program_desc* prog, gpa_pid* out);
+
+/* Device bytes gpa_load_program would request for prog under ctx (validated
+ * like a load; nothing is allocated or copied), for admission control. */
+gpa_status gpa_program_footprint(gpa_ctx* ctx, const gpa_program_desc* prog, int64_t* bytes);
+
+/* Device bytes requested for a loaded program (equal to its footprint). */
+gpa_status gpa_program_bytes(gpa_ctx* ctx, gpa_pid pid, int64_t* bytes);
 
 /* Frees a program (synchronizes the device first). */
 gpa_status gpa_unload_program(gpa_ctx* ctx, gpa_pid pid);
+
+/* Frees a program in stream order: its device memory is released once the
+ * work queued on stream so far has finished, without waiting on the host.
+ * All of the program's work must have been queued on stream, or on streams
+ * that stream waits for. The program id is invalid on return. */
+gpa_status gpa_unload_program_async(gpa_ctx* ctx, gpa_pid pid, gpa_stream stream);
 
 /* Zeroes the program's sample counters, invalid count and status word. */
 gpa_status gpa_reset_counts(gpa_ctx* ctx, gpa_pid pid, gpa_stream stream);
@@ -239,6 +254,20 @@ gpa_status gpa_advise(gpa_ctx* ctx, gpa_pid pid, const gpa_advice* out, gpa_stre
  * info[7] = the stalled use (global instruction index) and the resource of
  * the largest search. */
 gpa_status gpa_sync_status(gpa_ctx* ctx, gpa_pid pid, gpa_stream stream, int64_t* info);
+
+/* Captures one whole step of the program into a CUDA graph owned by the
+ * program (replacing any earlier one): zero the counters, ingest n samples
+ * from dev_samples (device pointer, 8-byte aligned, which must stay valid
+ * and hold the step's input whenever the graph runs), blame, and compute the
+ * advice (left on the device; gpa_get_advice copies it). Nothing runs at
+ * capture, and nothing on the step path allocates, so the graph needs no
+ * warm-up. Capture errors return GPA_ERR_CUDA and leave the previous graph
+ * in place. */
+gpa_status gpa_step_capture(gpa_ctx* ctx, gpa_pid pid, const uint64_t* dev_samples, size_t n);
+
+/* Launches the captured step on stream, ordered after earlier users of the
+ * context's search scratch. GPA_ERR_INVALID_ARG if nothing was captured. */
+gpa_status gpa_step_launch(gpa_ctx* ctx, gpa_pid pid, gpa_stream stream);
 
 /* Diagnostic: per search tier (3) the SM cycles summed over the searches of the
  * last gpa_blame in six phases: building the graph, shortest distances and

@@ -35,7 +35,8 @@ enum {
   // cycles of its five phases.
   SS_PHASE = 13, SS_SIZES = 31, SS_PASSB = 47, SS_SLOW = 48,
   SS_REACH_HEAD = 55,  // next entry of reach_order for the staged fixpoint
-  SS_N = 56
+  SS_OVF3_N = 56, SS_OVF3_HEAD = 57,  // searches handed on to the program's own fourth tier
+  SS_N = 58
 };
 
 struct Arch {
@@ -49,6 +50,11 @@ struct Prog {
   int32_t nf, ni, nb, nl, n_lines;
   int32_t reach_smem;             // shared memory of the staged fixpoint: the largest need that fits
                                   // (functions needing more use the global-memory fixpoint)
+  // Fourth search tier, sized for this program's largest function (0 nodes:
+  // none): searches that outgrow the context's third tier.
+  int32_t t4_nodes, t4_src, t4_warps;
+  int64_t t4_bytes;               // per warp
+  char* t4_arena;                 // t4_warps * t4_bytes, global memory
   const int32_t* func_instr_off;
   const int32_t* func_block_off;
   const int32_t* func_loop_off;
@@ -72,6 +78,7 @@ struct Prog {
   const int32_t* instr_block;
   const int32_t* block_func;
   const int32_t* reach_order;     // nf: functions by block count, largest first
+  const int32_t* block_minreach;  // nb: smallest block reachable from the block (itself included)
   const int32_t* ev_off;          // nb + 1: per-block event lists
   const uint32_t* events;         // defs and unguarded reads, bottom-up: resource | def << 9 |
                                   // kind << 10 | guard << 12 | position in block << 16
@@ -81,6 +88,7 @@ struct Prog {
   uint32_t* def_mask;             // nb * 9: resources defined in the block
   uint32_t* uuse_mask;            // nb * 9: resources read by an unguarded instruction
   int32_t* res_maxlat;            // nf * 268: largest latency of any def of the resource in the function
+  uint32_t* res_guards;           // nf * 268: guard literals of the resource's defs in the function
   uint32_t* rin;                  // nb * 9
   uint32_t* rout;                 // nb * 9
   int32_t* head;                  // ni: raw-edge list head per use (-1 = none)
@@ -117,7 +125,7 @@ struct Prog {
 struct SearchArena {
   int32_t nodes, src, layers, warps;
   int64_t bytes;   // per warp
-  char* global;    // tier 2 only: warps * bytes
+  char* global;    // global-memory tiers: warps * bytes
 };
 
 __device__ __forceinline__ void set_status(const Prog& P, unsigned long long bits) {
@@ -131,6 +139,18 @@ __device__ __forceinline__ uint16_t add_literal(uint16_t S, int g) {
   S = (uint16_t)(S | (1u << (g - 1)));  // literal 1..7 -> bit 0..6 (Pi), 8..14 -> bit 7..13 (!Pi)
   uint32_t pos = S & 0x7Fu, neg = (S >> 7) & 0x7Fu;
   return (pos & neg) ? kAllLits : S;
+}
+// Literals of a set that can still matter to a search for a use guarded by
+// g through a resource whose defs carry the guard literals `guards`: g
+// itself, and each literal whose complement some def may still add (only
+// such a literal can complete a Pi / !Pi pair). Dropping the others merges
+// literal sets that give every continuation the same coverage outcomes.
+__device__ __forceinline__ uint16_t live_literals(uint32_t guards, int g) {
+  const uint32_t comp = ((guards & 0x7Fu) << 7) | ((guards >> 7) & 0x7Fu);
+  return (uint16_t)(comp | (g ? 1u << (g - 1) : 0u));
+}
+__device__ __forceinline__ uint16_t keep_literals(uint16_t S, uint16_t live) {
+  return S == kAllLits ? S : (uint16_t)(S & live);
 }
 // "P contains p'": p' in P or "_" in P.
 __device__ __forceinline__ bool contains(uint16_t S, int g) {

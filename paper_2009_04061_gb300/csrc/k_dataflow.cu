@@ -56,14 +56,19 @@ __global__ void k_block_masks(Prog P) {
   }
 }
 
-// Largest latency of any def of each resource in each function: the distance
-// beyond which no def of that resource can pass the latency rule.
+// Largest latency of any def of each resource in each function (the
+// distance beyond which no def of that resource can pass the latency rule),
+// and the guard literals its defs carry there.
 __global__ void k_res_maxlat(Prog P, Arch A) {
   for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < P.ni; x += gridDim.x * blockDim.x) {
     const int f = P.block_func[P.instr_block[x]];
     const int lat = A.lat[P.opclass[x]];
-    for (int e = P.def_off[x]; e < P.def_off[x + 1]; ++e)
-      atomicMax(&P.res_maxlat[(size_t)f * kNumRes + (P.def_res[e] & 0x1FF)], lat);
+    const int g = P.guard[x];
+    for (int e = P.def_off[x]; e < P.def_off[x + 1]; ++e) {
+      const size_t k = (size_t)f * kNumRes + (P.def_res[e] & 0x1FF);
+      atomicMax(&P.res_maxlat[k], lat);
+      if (g) atomicOr(&P.res_guards[k], 1u << (g - 1));
+    }
   }
 }
 
@@ -216,6 +221,7 @@ void launch_dataflow(const Prog& P, const Arch& A, int max_sweeps, cudaStream_t 
   if (fblocks < 1) fblocks = 1;
   k_reaching<<<fblocks, 128, 0, st>>>(P, max_sweeps);
   cudaMemsetAsync(P.res_maxlat, 0, sizeof(int32_t) * (size_t)P.nf * kNumRes, st);
+  cudaMemsetAsync(P.res_guards, 0, sizeof(uint32_t) * (size_t)P.nf * kNumRes, st);
   k_res_maxlat<<<grid_for(P.ni, 256, sms), 256, 0, st>>>(P, A);
   *launches += 3;
 }

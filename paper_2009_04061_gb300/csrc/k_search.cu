@@ -83,7 +83,7 @@ __device__ __forceinline__ int warp_slot(bool pred, int* total) {
 
 // Returns false when the search outgrew the arena (nothing emitted).
 __device__ bool warp_search(const Prog& P, const Arch& A, const Arena& a, int j, int r, uint16_t S0, int bound,
-                            int tier) {
+                            uint16_t live, int tier) {
   const int lane = threadIdx.x & 31;
 #ifdef GPA_PHASE_TIMING
   long long t_prev = clock64();
@@ -123,6 +123,7 @@ __device__ bool warp_search(const Prog& P, const Arch& A, const Arena& a, int j,
   if (lane == 0) {
     ctr[0] = 1; ctr[1] = 0; ctr[2] = 0; ctr[3] = 0; ctr[4] = 0; ctr[6] = 1;
     ubuf[0] = 0;
+    S0 = keep_literals(S0, live);
     a.blk[0] = b0; a.S[0] = (int)S0 | ((int)S0 << 16); a.cov[0] = first0; a.wall[0] = -1; a.fl[0] = 0;
     a.dpk[0] = 0ull; a.k[0] = 0; a.e0[0] = 0; a.e1[0] = 0;
   }
@@ -181,7 +182,7 @@ __device__ bool warp_search(const Prog& P, const Arch& A, const Arena& a, int j,
       a.cov[u] = cov;
       a.wall[u] = wall;
     }
-    a.S[u] = (a.S[u] & 0xFFFF) | ((int)S << 16);
+    a.S[u] = (a.S[u] & 0xFFFF) | ((int)keep_literals(S, live) << 16);
     a.fl[u] |= kExpanded | (stop ? 4 : 0);
   };
 
@@ -316,8 +317,16 @@ __device__ bool warp_search(const Prog& P, const Arch& A, const Arena& a, int j,
     }
   };
 
+  // Pass B only needs the nodes that can lie on a path from a candidate
+  // source up to j: the node's block must be reachable in the CFG from the
+  // candidate's block, so it is not below that block's smallest reachable
+  // block. cand_low is the least of these over the candidates.
+  int cand_low = 0;
+  auto relevant = [&](int u) { return a.blk[u] >= cand_low; };
+
   // Split the unexpanded list: nodes to expand now (into list) and the rest,
-  // which stay unexpanded (all of them when bound < 0).
+  // which stay unexpanded (all of them when bound < 0; in pass B, nodes off
+  // every candidate's paths are dropped from the list for good).
   int* list = a.q;
   auto take_wave = [&](int lim) {
     const int m = ctr[6];
@@ -325,8 +334,8 @@ __device__ bool warp_search(const Prog& P, const Arch& A, const Arena& a, int j,
     for (int i0 = 0; i0 < m; i0 += 32) {
       const int i = i0 + lane;
       const int u = i < m ? ubuf[i] : 0;
-      const bool now = i < m && (lim < 0 || dist_of(a, u) <= lim);
-      const bool keep = i < m && !now;
+      const bool now = i < m && (lim < 0 ? relevant(u) : dist_of(a, u) <= lim);
+      const bool keep = i < m && !now && lim >= 0;
       int tot_now, tot_keep;
       const int at_now = warp_slot(now, &tot_now);
       const int at_keep = warp_slot(keep, &tot_keep);
@@ -350,15 +359,22 @@ __device__ bool warp_search(const Prog& P, const Arch& A, const Arena& a, int j,
     if (ctr[4]) break;
     relax_from(list, cnt, 0);
   }
-  // A source within its latency?
+  // A source within its latency? (Every candidate is found by pass A: a
+  // source farther than the bound fails rule 3.)
   bool cand = false;
   if (!ctr[4]) {
     const int no = min(ctr[2], a.O);
-    for (int o = lane; o < no && !cand; o += 32) {
+    int low = 0x7FFFFFFF;
+    for (int o = lane; o < no; o += 32) {
       const int u = a.on[o];
-      cand = dist_of(a, u) + (last_of(u) - a.ox[o]) <= A.lat[P.opclass[a.ox[o]]];
+      if (dist_of(a, u) + (last_of(u) - a.ox[o]) <= A.lat[P.opclass[a.ox[o]]]) {
+        cand = true;
+        low = min(low, P.block_minreach[a.blk[u]]);
+      }
     }
     cand = __any_sync(0xffffffffu, cand);
+    for (int o = 16; o > 0; o >>= 1) low = min(low, __shfl_xor_sync(0xffffffffu, low, o));
+    cand_low = low;
   }
   // Pass B: complete the graph.
   if (cand) {
@@ -690,11 +706,12 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32) k_search_warp(Prog P, Arch 
   const Arena a = carve(base, SA.nodes, SA.src, SA.layers, s_ctr[wid]);
   for (int t = lane; t < 2 * SA.nodes; t += 32) a.ht[t] = -1;
   __syncwarp();
-  // tier 1 reads the local pass's queue, tier 2 the first overflow queue, and
-  // tier 3 the second, which reuses the first queue's storage.
-  const int4* q = tier == 2 ? P.ovf_queue : P.queue;
-  const int n_slot = tier == 1 ? SS_QUEUE_N : tier == 2 ? SS_OVF_N : SS_OVF2_N;
-  const int h_slot = tier == 1 ? SS_QUEUE_HEAD : tier == 2 ? SS_OVF_HEAD : SS_OVF2_HEAD;
+  // tier 1 reads the local pass's queue, tier 2 the first overflow queue,
+  // tier 3 the second, which reuses the first queue's storage, and tier 4
+  // the third, which reuses the first overflow queue's.
+  const int4* q = (tier == 2 || tier == 4) ? P.ovf_queue : P.queue;
+  const int n_slot = tier == 1 ? SS_QUEUE_N : tier == 2 ? SS_OVF_N : tier == 3 ? SS_OVF2_N : SS_OVF3_N;
+  const int h_slot = tier == 1 ? SS_QUEUE_HEAD : tier == 2 ? SS_OVF_HEAD : tier == 3 ? SS_OVF2_HEAD : SS_OVF3_HEAD;
   unsigned long long nq = P.stats[n_slot];
   if (nq > (unsigned long long)P.queue_cap) nq = (unsigned long long)P.queue_cap;
   while (true) {
@@ -705,11 +722,12 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32) k_search_warp(Prog P, Arch 
     const int4 task = q[t];
     const int f = P.block_func[P.instr_block[task.x]];
     const int bound = P.res_maxlat[(size_t)f * kNumRes + task.y];
-    const bool ok = warp_search(P, A, a, task.x, task.y, (uint16_t)task.z, bound, tier);
+    const uint16_t live = live_literals(P.res_guards[(size_t)f * kNumRes + task.y], P.guard[task.x]);
+    const bool ok = warp_search(P, A, a, task.x, task.y, (uint16_t)task.z, bound, live, tier);
     if (ok || lane != 0) continue;
-    if (tier < 3) {
-      const int o_slot = tier == 1 ? SS_OVF_N : SS_OVF2_N;
-      int4* oq = tier == 1 ? P.ovf_queue : P.queue;
+    if (tier < 3 || (tier == 3 && P.t4_nodes > 0)) {
+      const int o_slot = tier == 1 ? SS_OVF_N : tier == 2 ? SS_OVF2_N : SS_OVF3_N;
+      int4* oq = tier == 2 ? P.queue : P.ovf_queue;
       const unsigned long long o = atomicAdd(&P.stats[o_slot], 1ull);
       if (o < (unsigned long long)P.queue_cap) oq[o] = task; else set_status(P, ST_CAPACITY);
     } else {
@@ -732,6 +750,11 @@ void launch_search(const Prog& P, const Arch& A, const SearchArena* tiers, cudaS
   k_search_warp<<<tiers[1].warps, 32, smem2, st>>>(P, A, tiers[1], 2);
   k_search_warp<<<tiers[2].warps, 32, 0, st>>>(P, A, tiers[2], 3);
   *launches += 3;
+  if (P.t4_nodes > 0) {
+    SearchArena t4{P.t4_nodes, P.t4_src, kMaxLayers, P.t4_warps, P.t4_bytes, P.t4_arena};
+    k_search_warp<<<P.t4_warps, 32, 0, st>>>(P, A, t4, 4);
+    ++*launches;
+  }
 }
 
 }  // namespace gpa

@@ -18,6 +18,13 @@ namespace {
 
 struct ProgramRec {
   Prog P{};
+  bool dry = false;                     // count bytes only (gpa_program_footprint)
+  cudaStream_t build = nullptr;         // stream of the stream-ordered allocations and copies
+  int64_t bytes = 0;                    // device bytes requested for the program
+  cudaGraphExec_t step_exec = nullptr;  // captured step (gpa_step_capture)
+  int64_t step_launches = 0;            // kernels in it
+  int32_t *pred_off = nullptr, *cursor = nullptr, *ev_off = nullptr;  // build scratch kept from allocation
+  uint32_t* events = nullptr;
   int n_succ = 0, n_def = 0, n_use = 0;
   int32_t* scan_tmp = nullptr;
   std::vector<void*> allocs;
@@ -39,6 +46,8 @@ struct gpa_ctx {
   uint64_t* stage[2] = {nullptr, nullptr};
   size_t stage_n = 0;
   cudaStream_t copy_stream = nullptr;
+  cudaStream_t capture_stream = nullptr;  // private stream for gpa_step_capture
+  cudaStream_t build_stream = nullptr;    // program allocation, copies and layout builds
   cudaEvent_t ev_copied[2] = {nullptr, nullptr}, ev_used[2] = {nullptr, nullptr};
 };
 
@@ -53,8 +62,14 @@ constexpr size_t kStageSamples = (size_t)64 << 20;  // 64M samples (512 MB) per 
 
 template <class T>
 gpa_status dev_alloc(ProgramRec* R, T** p, size_t n) {
+  const size_t bytes = std::max<size_t>(n, 1) * sizeof(T);
+  R->bytes += (int64_t)bytes;
+  if (R->dry) {  // counting only: a pointer that is never used
+    *p = nullptr;
+    return GPA_OK;
+  }
   void* q = nullptr;
-  if (cudaMalloc(&q, std::max<size_t>(n, 1) * sizeof(T)) != cudaSuccess) return GPA_ERR_OOM;
+  if (cudaMallocAsync(&q, bytes, R->build) != cudaSuccess) return GPA_ERR_OOM;
   R->allocs.push_back(q);
   *p = (T*)q;
   return GPA_OK;
@@ -64,12 +79,16 @@ gpa_status dev_copy(ProgramRec* R, const T** dst, const T* src, size_t n) {
   T* p = nullptr;
   gpa_status s = dev_alloc(R, &p, n);
   if (s) return s;
-  if (n && cudaMemcpy(p, src, n * sizeof(T), cudaMemcpyHostToDevice) != cudaSuccess) return GPA_ERR_CUDA;
+  if (!R->dry && n && cudaMemcpyAsync(p, src, n * sizeof(T), cudaMemcpyHostToDevice, R->build) != cudaSuccess)
+    return GPA_ERR_CUDA;
   *dst = p;
   return GPA_OK;
 }
 
+// Frees a program whose work has finished (the callers synchronize first).
 void free_program(ProgramRec* R) {
+  if (R->step_exec) cudaGraphExecDestroy(R->step_exec);
+  if (R->build) cudaStreamSynchronize(R->build);
   for (void* p : R->allocs) cudaFree(p);
   delete R;
 }
@@ -284,8 +303,10 @@ gpa_status gpa_create(const gpa_arch_desc* arch, const gpa_options* opts, gpa_ct
   }
   if (!s && cudaMemset(T[2].global, 0, (size_t)T[2].bytes * T[2].warps) != cudaSuccess) s = GPA_ERR_CUDA;
   if (!s && cudaEventCreateWithFlags(&c->scratch_ev, cudaEventDisableTiming) != cudaSuccess) s = GPA_ERR_CUDA;
+  if (!s && cudaStreamCreateWithFlags(&c->build_stream, cudaStreamNonBlocking) != cudaSuccess) s = GPA_ERR_CUDA;
   if (s) {
     if (c->tier[2].global) cudaFree(c->tier[2].global);
+    if (c->scratch_ev) cudaEventDestroy(c->scratch_ev);
     delete c;
     return s;
   }
@@ -304,17 +325,16 @@ gpa_status gpa_destroy(gpa_ctx* ctx) {
     if (ctx->ev_used[k]) cudaEventDestroy(ctx->ev_used[k]);
   }
   if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
+  if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
+  if (ctx->build_stream) cudaStreamDestroy(ctx->build_stream);
   if (ctx->scratch_ev) cudaEventDestroy(ctx->scratch_ev);
   delete ctx;
   return GPA_OK;
 }
 
-gpa_status gpa_load_program(gpa_ctx* ctx, const gpa_program_desc* d, gpa_pid* out) {
-  if (!ctx || !d || !out) return GPA_ERR_INVALID_ARG;
-  gpa_status s = validate(d, ctx->arch);
-  if (s) return s;
-  auto* R = new (std::nothrow) ProgramRec();
-  if (!R) return GPA_ERR_OOM;
+// Allocates (or, with R->dry, only counts) the program's device memory and
+// copies its arrays. On failure the caller frees R.
+static gpa_status alloc_program(const gpa_program_desc* d, ProgramRec* R, int tier3_nodes) {
   Prog& P = R->P;
   P.nf = d->n_functions; P.ni = d->n_instr; P.nb = d->n_blocks; P.nl = d->n_loops; P.n_lines = d->n_lines;
   // Staged fixpoint: the largest per-function need within the cap (edges stay
@@ -331,7 +351,7 @@ gpa_status gpa_load_program(gpa_ctx* ctx, const gpa_program_desc* d, gpa_pid* ou
 #define TRY(x)                        \
   do {                                \
     gpa_status t_ = (x);              \
-    if (t_) { free_program(R); return t_; } \
+    if (t_) return t_;                \
   } while (0)
   TRY(dev_copy(R, &P.func_instr_off, d->func_instr_off, nf + 1));
   {
@@ -341,6 +361,18 @@ gpa_status gpa_load_program(gpa_ctx* ctx, const gpa_program_desc* d, gpa_pid* ou
       return d->func_block_off[a + 1] - d->func_block_off[a] > d->func_block_off[b + 1] - d->func_block_off[b];
     });
     TRY(dev_copy(R, &P.reach_order, order.data(), nf));
+    // Smallest block reachable from each block: a min fixpoint over
+    // successors, swept in descending block order (forward edges point up, so
+    // each sweep settles every forward path; back edges need a few more).
+    std::vector<int32_t> mr(nb);
+    for (size_t b = 0; b < nb; ++b) mr[b] = (int32_t)b;
+    for (bool changed = true; changed;) {
+      changed = false;
+      for (size_t b = nb; b-- > 0;)
+        for (int e = d->succ_off[b]; e < d->succ_off[b + 1]; ++e)
+          if (mr[d->succ[e]] < mr[b]) { mr[b] = mr[d->succ[e]]; changed = true; }
+    }
+    TRY(dev_copy(R, &P.block_minreach, mr.data(), nb));
   }
   TRY(dev_copy(R, &P.func_block_off, d->func_block_off, nf + 1));
   TRY(dev_copy(R, &P.func_loop_off, d->func_loop_off, nf + 1));
@@ -372,6 +404,7 @@ gpa_status gpa_load_program(gpa_ctx* ctx, const gpa_program_desc* d, gpa_pid* ou
   TRY(dev_alloc(R, &events, (size_t)d->n_def + (size_t)d->n_use));
   P.ev_off = ev_off; P.events = events;
   TRY(dev_alloc(R, &P.res_maxlat, nf * kNumRes));
+  TRY(dev_alloc(R, &P.res_guards, nf * kNumRes));
   P.pred_off = pred_off; P.pred = pred; P.loop_depth = ldepth; P.instr_block = iblock; P.block_func = bfunc;
   TRY(dev_alloc(R, &R->scan_tmp, scan_tmp_ints((int)std::max(ni, nb) + 1)));
   TRY(dev_alloc(R, &P.cnt, ni * kCnt));
@@ -407,21 +440,80 @@ gpa_status gpa_load_program(gpa_ctx* ctx, const gpa_program_desc* d, gpa_pid* ou
   TRY(dev_alloc(R, &P.a_loop_speedup, nl));
   TRY(dev_alloc(R, &P.a_line_stall, (size_t)P.n_lines));
   TRY(dev_alloc(R, &P.a_line_lat, (size_t)P.n_lines));
-  cudaStream_t st = nullptr;
-  if (cudaMemset(P.cnt, 0, ni * kCnt * sizeof(unsigned long long)) != cudaSuccess ||
-      cudaMemset(P.stats, 0, SS_N * sizeof(unsigned long long)) != cudaSuccess ||
-      cudaMemset(P.edge_off, 0, (ni + 1) * sizeof(int32_t)) != cudaSuccess) {
+  // Fourth search tier: room for 16 literal sets per block of the largest
+  // function, when that is more than the context's third tier holds.
+  {
+    int64_t mb = 1;
+    for (int f = 0; f < d->n_functions; ++f) mb = std::max<int64_t>(mb, d->func_block_off[f + 1] - d->func_block_off[f]);
+    int64_t n4 = 2;
+    while (n4 < 16 * mb && n4 < ((int64_t)1 << 20)) n4 <<= 1;
+    P.t4_nodes = 0; P.t4_arena = nullptr; P.t4_bytes = 0; P.t4_warps = 0; P.t4_src = 0;
+    if (n4 > tier3_nodes) {
+      P.t4_nodes = (int32_t)n4;
+      P.t4_src = (int32_t)std::min<int64_t>(n4, 4096);
+      P.t4_warps = 16;
+      P.t4_bytes = search_arena_bytes(P.t4_nodes, P.t4_src, kMaxLayers);
+      TRY(dev_alloc(R, &P.t4_arena, (size_t)P.t4_bytes * P.t4_warps));
+    }
+  }
+#undef TRY
+  R->pred_off = pred_off; R->cursor = cursor; R->ev_off = ev_off; R->events = events;
+  return GPA_OK;
+}
+
+gpa_status gpa_program_footprint(gpa_ctx* ctx, const gpa_program_desc* d, int64_t* bytes) {
+  if (!ctx || !d || !bytes) return GPA_ERR_INVALID_ARG;
+  gpa_status s = validate(d, ctx->arch);
+  if (s) return s;
+  ProgramRec R;
+  R.dry = true;
+  s = alloc_program(d, &R, ctx->tier[2].nodes);
+  if (s) return s;
+  *bytes = R.bytes;
+  return GPA_OK;
+}
+
+gpa_status gpa_program_bytes(gpa_ctx* ctx, gpa_pid pid, int64_t* bytes) {
+  ProgramRec* R = find(ctx, pid);
+  if (!R) return GPA_ERR_NO_PROGRAM;
+  if (!bytes) return GPA_ERR_INVALID_ARG;
+  *bytes = R->bytes;
+  return GPA_OK;
+}
+
+gpa_status gpa_load_program(gpa_ctx* ctx, const gpa_program_desc* d, gpa_pid* out) {
+  if (!ctx || !d || !out) return GPA_ERR_INVALID_ARG;
+  gpa_status s = validate(d, ctx->arch);
+  if (s) return s;
+  auto* R = new (std::nothrow) ProgramRec();
+  if (!R) return GPA_ERR_OOM;
+  R->build = ctx->build_stream;
+  s = alloc_program(d, R, ctx->tier[2].nodes);
+  if (s) { free_program(R); return s; }
+  Prog& P = R->P;
+  const size_t ni = P.ni;
+  int32_t *pred_off = R->pred_off, *cursor = R->cursor, *ev_off = R->ev_off;
+  uint32_t* events = R->events;
+  // Everything of the load runs on the context's build stream, which is then
+  // synchronized: other streams' work is not waited for.
+  cudaStream_t st = R->build;
+  if (cudaMemsetAsync(P.cnt, 0, ni * kCnt * sizeof(unsigned long long), st) != cudaSuccess ||
+      cudaMemsetAsync(P.stats, 0, SS_N * sizeof(unsigned long long), st) != cudaSuccess ||
+      cudaMemsetAsync(P.edge_off, 0, (ni + 1) * sizeof(int32_t), st) != cudaSuccess) {
+    free_program(R);
+    return GPA_ERR_CUDA;
+  }
+  if (P.t4_arena && cudaMemsetAsync(P.t4_arena, 0, (size_t)P.t4_bytes * P.t4_warps, st) != cudaSuccess) {
     free_program(R);
     return GPA_ERR_CUDA;
   }
   launch_build_layout(P, st, ctx->sms, &ctx->launches);
   launch_build_preds(P, R->n_succ, pred_off, cursor, R->scan_tmp, st, ctx->sms, &ctx->launches);
   launch_build_events(P, ev_off, events, R->scan_tmp, st, ctx->sms, &ctx->launches);
-  if (cudaDeviceSynchronize() != cudaSuccess || cudaGetLastError() != cudaSuccess) {
+  if (cudaStreamSynchronize(st) != cudaSuccess || cudaGetLastError() != cudaSuccess) {
     free_program(R);
     return GPA_ERR_CUDA;
   }
-#undef TRY
   const gpa_pid pid = ctx->next_pid++;
   ctx->progs[pid] = R;
   *out = pid;
@@ -435,6 +527,22 @@ gpa_status gpa_unload_program(gpa_ctx* ctx, gpa_pid pid) {
   free_program(R);
   ctx->progs.erase(pid);
   return GPA_OK;
+}
+
+gpa_status gpa_unload_program_async(gpa_ctx* ctx, gpa_pid pid, gpa_stream stream) {
+  ProgramRec* R = find(ctx, pid);
+  if (!R) return GPA_ERR_NO_PROGRAM;
+  cudaStream_t st = (cudaStream_t)stream;
+  // The captured graph, if any, is freed when an in-flight launch completes.
+  if (R->step_exec) cudaGraphExecDestroy(R->step_exec);
+  R->step_exec = nullptr;
+  gpa_status s = GPA_OK;
+  for (void* p : R->allocs)
+    if (cudaFreeAsync(p, st) != cudaSuccess) s = GPA_ERR_CUDA;
+  R->allocs.clear();
+  delete R;
+  ctx->progs.erase(pid);
+  return s;
 }
 
 gpa_status gpa_reset_counts(gpa_ctx* ctx, gpa_pid pid, gpa_stream stream) {
@@ -491,19 +599,71 @@ gpa_status gpa_ingest_host_samples(gpa_ctx* ctx, gpa_pid pid, const uint64_t* ho
   return GPA_OK;
 }
 
-gpa_status gpa_blame(gpa_ctx* ctx, gpa_pid pid, gpa_stream stream) {
-  ProgramRec* R = find(ctx, pid);
-  if (!R) return GPA_ERR_NO_PROGRAM;
-  cudaStream_t st = (cudaStream_t)stream;
+// Steps (b)-(c) on stream st. With order_scratch, waits for and marks the
+// context's shared search scratch (a captured step does this around its
+// graph launch instead).
+static gpa_status blame_body(gpa_ctx* ctx, ProgramRec* R, cudaStream_t st, bool order_scratch) {
   // per-step counters: general searches, largest search, sweeps, raw edges, queues
   CK(cudaMemsetAsync(R->P.stats + SS_GENERAL, 0, sizeof(unsigned long long) * 3, st));
   CK(cudaMemsetAsync(R->P.stats + SS_RAW_N, 0, sizeof(unsigned long long) * (SS_N - SS_RAW_N), st));
   launch_dataflow(R->P, ctx->arch, ctx->opts.max_fixpoint_sweeps, st, ctx->sms, &ctx->launches);
   // The search scratch is shared by the context's programs: order its users.
-  CK(cudaStreamWaitEvent(st, ctx->scratch_ev, 0));
+  if (order_scratch) CK(cudaStreamWaitEvent(st, ctx->scratch_ev, 0));
   launch_blame(R->P, ctx->arch, ctx->tier, ctx->opts.max_sources_per_use, R->scan_tmp, st, ctx->sms, &ctx->launches);
-  CK(cudaEventRecord(ctx->scratch_ev, st));
+  if (order_scratch) CK(cudaEventRecord(ctx->scratch_ev, st));
   CK(cudaGetLastError());
+  return GPA_OK;
+}
+
+gpa_status gpa_blame(gpa_ctx* ctx, gpa_pid pid, gpa_stream stream) {
+  ProgramRec* R = find(ctx, pid);
+  if (!R) return GPA_ERR_NO_PROGRAM;
+  return blame_body(ctx, R, (cudaStream_t)stream, true);
+}
+
+gpa_status gpa_step_capture(gpa_ctx* ctx, gpa_pid pid, const uint64_t* dev_samples, size_t n) {
+  ProgramRec* R = find(ctx, pid);
+  if (!R) return GPA_ERR_NO_PROGRAM;
+  if (n && (!dev_samples || (reinterpret_cast<uintptr_t>(dev_samples) & 7u))) return GPA_ERR_INVALID_ARG;
+  if (!ctx->capture_stream) CK(cudaStreamCreateWithFlags(&ctx->capture_stream, cudaStreamNonBlocking));
+  cudaStream_t cs = ctx->capture_stream;
+  const int64_t l0 = ctx->launches;
+  CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+  gpa_status s = GPA_OK;
+  if (cudaMemsetAsync(R->P.cnt, 0, (size_t)R->P.ni * kCnt * sizeof(unsigned long long), cs) != cudaSuccess ||
+      cudaMemsetAsync(R->P.stats, 0, SS_N * sizeof(unsigned long long), cs) != cudaSuccess)
+    s = GPA_ERR_CUDA;
+  if (!s && n) launch_histogram(R->P, dev_samples, n, cs, ctx->sms, &ctx->launches);
+  if (!s) s = blame_body(ctx, R, cs, false);
+  if (!s) launch_advise(R->P, ctx->arch, cs, ctx->sms, &ctx->launches);
+  cudaGraph_t g = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(cs, &g);
+  const int64_t kernels = ctx->launches - l0;
+  ctx->launches = l0;  // nothing ran yet
+  if (s || e != cudaSuccess || !g) {
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    return s ? s : GPA_ERR_CUDA;
+  }
+  cudaGraphExec_t ex = nullptr;
+  const cudaError_t ei = cudaGraphInstantiate(&ex, g, 0);
+  cudaGraphDestroy(g);
+  if (ei != cudaSuccess) { cudaGetLastError(); return GPA_ERR_CUDA; }
+  if (R->step_exec) cudaGraphExecDestroy(R->step_exec);
+  R->step_exec = ex;
+  R->step_launches = kernels;
+  return GPA_OK;
+}
+
+gpa_status gpa_step_launch(gpa_ctx* ctx, gpa_pid pid, gpa_stream stream) {
+  ProgramRec* R = find(ctx, pid);
+  if (!R) return GPA_ERR_NO_PROGRAM;
+  if (!R->step_exec) return GPA_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  CK(cudaStreamWaitEvent(st, ctx->scratch_ev, 0));
+  CK(cudaGraphLaunch(R->step_exec, st));
+  CK(cudaEventRecord(ctx->scratch_ev, st));
+  ctx->launches += R->step_launches;
   return GPA_OK;
 }
 

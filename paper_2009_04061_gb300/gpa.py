@@ -90,6 +90,11 @@ def library() -> ctypes.CDLL:
         "gpa_sync_status": ([vp, u32, vp, vp], i32),
         "gpa_get_counts": ([vp, u32, vp, vp, vp], i32),
         "gpa_get_search_profile": ([vp, u32, vp, vp], i32),
+        "gpa_step_capture": ([vp, u32, vp, ctypes.c_size_t], i32),
+        "gpa_program_footprint": ([vp, vp, vp], i32),
+        "gpa_program_bytes": ([vp, u32, vp], i32),
+        "gpa_unload_program_async": ([vp, u32, vp], i32),
+        "gpa_step_launch": ([vp, u32, vp], i32),
         "gpa_get_reaching": ([vp, u32, vp, vp, vp], i32),
         "gpa_get_blame": ([vp, u32, vp, vp], i32),
         "gpa_get_edges": ([vp, u32, vp, i64, vp, vp, vp, vp, vp, vp, vp], i32),
@@ -184,6 +189,26 @@ def gpa_load_program(ctx, arrays: dict) -> int:
     return pid.value
 
 
+def gpa_program_footprint(ctx, arrays: dict) -> int:
+    """Device bytes a load of `arrays` would request (nothing is allocated)."""
+    d, keep = program_desc(arrays)
+    b = ctypes.c_int64()
+    st = library().gpa_program_footprint(ctx, ctypes.byref(d), ctypes.byref(b))
+    del keep
+    _check(st, "gpa_program_footprint")
+    return b.value
+
+
+def gpa_program_bytes(ctx, pid) -> int:
+    b = ctypes.c_int64()
+    _check(library().gpa_program_bytes(ctx, pid, ctypes.byref(b)), "gpa_program_bytes")
+    return b.value
+
+
+def gpa_unload_program_async(ctx, pid, stream=None):
+    _check(library().gpa_unload_program_async(ctx, pid, _stream(stream)), "gpa_unload_program_async")
+
+
 def gpa_unload_program(ctx, pid):
     _check(library().gpa_unload_program(ctx, pid), "gpa_unload_program")
 
@@ -253,6 +278,17 @@ def gpa_sync_status(ctx, pid, stream=None):
     return st, dict(invalid=int(info[0]), general_searches=int(info[1]), max_nodes=int(info[2]),
                     sweeps=int(info[3]), tier2_searches=int(info[4]), tier3_searches=int(info[5]),
                     largest_use=int(info[6]), largest_resource=int(info[7]))
+
+
+def gpa_step_capture(ctx, pid, dev_samples, n: int | None = None):
+    """Capture reset + ingest + blame + advise of the program into a CUDA graph."""
+    if n is None:
+        n = dev_samples.numel()
+    _check(library().gpa_step_capture(ctx, pid, _p(dev_samples) if n else None, n), "gpa_step_capture")
+
+
+def gpa_step_launch(ctx, pid, stream=None):
+    _check(library().gpa_step_launch(ctx, pid, _stream(stream)), "gpa_step_launch")
 
 
 def gpa_get_search_profile(ctx, pid, stream=None) -> np.ndarray:
@@ -326,6 +362,10 @@ class Context:
     def launches(self) -> int:
         return gpa_launch_count(self.handle)
 
+    def footprint(self, arrays) -> int:
+        a = arrays.arrays if hasattr(arrays, "arrays") else arrays
+        return gpa_program_footprint(self.handle, a)
+
     def close(self):
         if self.handle:
             gpa_destroy(self.handle)
@@ -369,6 +409,18 @@ class Program:
     def counts(self, stream=None):
         return gpa_get_counts(self.h, self.pid, self.n_instr, stream)
 
+    def device_bytes(self) -> int:
+        return gpa_program_bytes(self.h, self.pid)
+
+    def capture_step(self, dev_samples, n=None):
+        gpa_step_capture(self.h, self.pid, dev_samples, n)
+
+    def launch_step(self, stream=None):
+        gpa_step_launch(self.h, self.pid, stream)
+
+    def get_advice(self, stream=None):
+        return gpa_get_advice(self.h, self.pid, self.shape, stream)
+
     def search_profile(self, stream=None):
         return gpa_get_search_profile(self.h, self.pid, stream)
 
@@ -386,3 +438,7 @@ class Program:
 
     def unload(self):
         gpa_unload_program(self.h, self.pid)
+
+    def unload_async(self, stream=None):
+        """Free in stream order after the work queued on `stream` (no host wait)."""
+        gpa_unload_program_async(self.h, self.pid, stream)

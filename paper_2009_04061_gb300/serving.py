@@ -1,0 +1,191 @@
+"""Continuous-batching analysis server over the C ABI.
+
+Profiling sessions (a program and its packed samples) arrive over time. A
+session is admitted as soon as a slot is free and the device-memory budget
+has room for its program: a slot is a context of its own (own search scratch,
+own sample staging) with its own CUDA stream, so admitted sessions run side
+by side on the device while later ones queue. For each admitted session the
+slot's stream carries ingest (from pinned host memory) -> blame -> advice;
+completion is polled through a CUDA event, the advice copied out, and the
+program freed in stream order, so no call waits for other slots' work.
+
+Latency is ingest-to-advice: from a session's arrival (its submission) to
+its advice being on the host.
+"""
+from __future__ import annotations
+
+import collections
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import gpa
+
+
+@dataclass
+class Session:
+    sid: int
+    program: dict                 # program arrays (the gpa_program_desc fields)
+    samples: np.ndarray           # packed uint64 samples, host memory (pinned for overlap)
+    t_arrival: float = 0.0        # seconds on the server's clock
+
+
+@dataclass
+class Result:
+    sid: int
+    advice: dict
+    n_samples: int
+    t_arrival: float
+    t_admit: float
+    t_done: float
+    device_bytes: int
+    counts: np.ndarray | None = None
+    blame: np.ndarray | None = None
+
+    @property
+    def latency(self) -> float:
+        return self.t_done - self.t_arrival
+
+
+@dataclass
+class _Slot:
+    ctx: object
+    stream: object
+    session: Session | None = None
+    prog: object = None
+    event: object = None
+    t_admit: float = 0.0
+    bytes: int = 0
+    keep: object = field(default=None, repr=False)
+
+
+class Server:
+    """slots: concurrent sessions; budget_bytes: device memory the admitted
+    sessions' programs may hold together; keep_results: also return counts
+    and blame (for checking results against a session run alone)."""
+
+    def __init__(self, arch, slots: int = 4, budget_bytes: int = 64 << 30, options: dict | None = None,
+                 keep_results: bool = False):
+        import torch
+        self._torch = torch
+        self.slots = [_Slot(gpa.Context(arch, options), torch.cuda.Stream()) for _ in range(slots)]
+        self.budget = int(budget_bytes)
+        self.used = 0
+        self.pending: collections.deque[Session] = collections.deque()
+        self.keep_results = keep_results
+        self.t0 = time.perf_counter()
+
+    def now(self) -> float:
+        return time.perf_counter() - self.t0
+
+    def submit(self, s: Session, t_arrival: float | None = None):
+        s.t_arrival = self.now() if t_arrival is None else t_arrival
+        self.pending.append(s)
+
+    def busy(self) -> int:
+        return sum(1 for sl in self.slots if sl.session is not None)
+
+    def _admit(self, sl: _Slot, s: Session, need: int):
+        prog = sl.ctx.load_program(s.program)
+        st = sl.stream
+        prog.reset(st)
+        if s.samples.size:
+            prog.ingest_host(s.samples, stream=st)
+        prog.blame(st)
+        prog.advise(fetch=False, stream=st)
+        ev = self._torch.cuda.Event()
+        ev.record(st)
+        sl.session, sl.prog, sl.event, sl.t_admit, sl.bytes = s, prog, ev, self.now(), need
+        self.used += need
+
+    def _finish(self, sl: _Slot) -> Result:
+        s, prog, st = sl.session, sl.prog, sl.stream
+        st_code, info = prog.status(st)
+        if st_code != 0:
+            raise RuntimeError(f"session {s.sid}: device status {st_code} ({info})")
+        adv = prog.get_advice(st)
+        counts = blame = None
+        if self.keep_results:
+            counts, _ = prog.counts(st)
+            blame = prog.blame_counts(st)
+        r = Result(s.sid, adv, int(s.samples.size), s.t_arrival, sl.t_admit, self.now(), sl.bytes, counts, blame)
+        prog.unload_async(st)
+        self.used -= sl.bytes
+        sl.session = sl.prog = sl.event = None
+        sl.bytes = 0
+        return r
+
+    def poll(self) -> list[Result]:
+        """Collect finished sessions, then admit waiting ones (in arrival order)
+        while a slot is free and the budget allows."""
+        done = [self._finish(sl) for sl in self.slots if sl.session is not None and sl.event.query()]
+        while self.pending:
+            free = [sl for sl in self.slots if sl.session is None]
+            if not free:
+                break
+            s = self.pending[0]
+            need = free[0].ctx.footprint(s.program)
+            if need > self.budget:
+                raise ValueError(f"session {s.sid} needs {need} bytes, more than the whole budget")
+            if self.used + need > self.budget:
+                break
+            self.pending.popleft()
+            self._admit(free[0], s, need)
+        return done
+
+    def close(self):
+        for sl in self.slots:
+            if sl.session is not None:
+                sl.stream.synchronize()
+                self._finish(sl)
+            sl.ctx.close()
+
+
+def serve(server: Server, sessions: list[Session], arrivals: list[float], idle_sleep: float = 1e-4) -> list[Result]:
+    """Replays `sessions` arriving at `arrivals` (seconds from now) through the
+    server and returns their results in completion order."""
+    order = np.argsort(np.asarray(arrivals), kind="stable")
+    start = server.now()
+    out: list[Result] = []
+    k = 0
+    while len(out) < len(sessions):
+        t = server.now() - start
+        while k < len(order) and arrivals[order[k]] <= t:
+            i = order[k]
+            server.submit(sessions[i], start + arrivals[i])
+            k += 1
+        got = server.poll()
+        out += got
+        if not got and (k == len(order) or server.busy() == len(server.slots)):
+            time.sleep(idle_sleep)
+    return out
+
+
+def one_at_a_time(arch, sessions: list[Session], options: dict | None = None) -> tuple[float, list[Result]]:
+    """The same sessions run back to back on one context and stream, each
+    waiting for the previous one; returns (seconds, results)."""
+    srv = Server(arch, slots=1, budget_bytes=1 << 62, options=options)
+    try:
+        t0 = time.perf_counter()
+        out = []
+        for s in sessions:
+            srv.submit(s)
+            while True:
+                got = srv.poll()
+                if got:
+                    out += got
+                    break
+                time.sleep(1e-4)
+        return time.perf_counter() - t0, out
+    finally:
+        srv.close()
+
+
+def latency_summary(results: list[Result]) -> dict:
+    lat = np.array([r.latency for r in results]) * 1e3
+    span = max(r.t_done for r in results) - min(r.t_arrival for r in results)
+    n = sum(r.n_samples for r in results)
+    return {"sessions": len(results), "samples": n, "p50_ms": float(np.percentile(lat, 50)),
+            "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(lat.mean()), "max_ms": float(lat.max()),
+            "samples_per_s": n / span, "span_s": span}

@@ -287,3 +287,48 @@ def serving_sessions(n_sessions: int, seed: int = 0, rate_per_s: float = 200.0, 
         out.append(dict(t_arrival=t, params=batched_params(nf, rng, seed, base=s * 1000), n_samples=ns,
                         seed=seed * 7777 + s))
     return out
+
+
+# ---------------------------------------------------------------- slicing
+def subprogram(arrays: dict, f_lo: int, f_hi: int) -> dict:
+    """The arrays of functions [f_lo, f_hi) as a program of their own (all
+    instruction, block, loop and line indices rebased to start at 0)."""
+    a = arrays.arrays if hasattr(arrays, "arrays") else arrays
+    fi, fb, fl, fn = (np.asarray(a[k]) for k in ("func_instr_off", "func_block_off", "func_loop_off",
+                                                  "func_line_off"))
+    i0, i1, b0, b1 = int(fi[f_lo]), int(fi[f_hi]), int(fb[f_lo]), int(fb[f_hi])
+    l0, l1, n0, n1 = int(fl[f_lo]), int(fl[f_hi]), int(fn[f_lo]), int(fn[f_hi])
+    so, do, uo = (np.asarray(a[k]) for k in ("succ_off", "def_off", "use_off"))
+    s0, s1, d0, d1, u0, u1 = int(so[b0]), int(so[b1]), int(do[i0]), int(do[i1]), int(uo[i0]), int(uo[i1])
+
+    def loops(x):
+        x = np.asarray(x).astype(np.int32)
+        return np.where(x >= 0, x - l0, -1).astype(np.int32)
+
+    out = dict(
+        func_instr_off=(fi[f_lo:f_hi + 1] - i0).astype(np.int32),
+        func_block_off=(fb[f_lo:f_hi + 1] - b0).astype(np.int32),
+        func_loop_off=(fl[f_lo:f_hi + 1] - l0).astype(np.int32),
+        func_line_off=(fn[f_lo:f_hi + 1] - n0).astype(np.int32),
+        block_instr_off=(np.asarray(a["block_instr_off"])[b0:b1 + 1] - i0).astype(np.int32),
+        succ_off=(so[b0:b1 + 1] - s0).astype(np.int32),
+        succ=(np.asarray(a["succ"])[s0:s1] - b0).astype(np.int32),
+        def_off=(do[i0:i1 + 1] - d0).astype(np.int32), def_res=np.asarray(a["def_res"])[d0:d1].copy(),
+        use_off=(uo[i0:i1 + 1] - u0).astype(np.int32), use_res=np.asarray(a["use_res"])[u0:u1].copy(),
+        line=(np.asarray(a["line"])[i0:i1] - n0).astype(np.int32),
+        block_loop=loops(np.asarray(a["block_loop"])[b0:b1]),
+        loop_parent=loops(np.asarray(a["loop_parent"])[l0:l1]),
+        loop_header=(np.asarray(a["loop_header"])[l0:l1] - b0).astype(np.int32),
+        n_functions=f_hi - f_lo, n_instr=i1 - i0, n_blocks=b1 - b0, n_loops=l1 - l0, n_lines=n1 - n0,
+    )
+    for k in ("opclass", "guard", "iflags", "prof"):
+        out[k] = np.asarray(a[k])[i0:i1].copy()
+    return out
+
+
+def rebase_samples(samples: np.ndarray, f_lo: int, f_hi: int) -> np.ndarray:
+    """The samples of kernels [f_lo, f_hi), their kernel field shifted down by f_lo."""
+    s = np.asarray(samples, dtype=np.uint64)
+    k = s >> np.uint64(48)
+    keep = (k >= np.uint64(f_lo)) & (k < np.uint64(f_hi))
+    return (s[keep] - (np.uint64(f_lo) << np.uint64(48))).astype(np.uint64)

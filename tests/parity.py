@@ -11,17 +11,24 @@ ARCH = synth.default_arch()
 RTOL = 1e-12
 
 
-def gpu_run(ctx, prog, samples_dev, stream=None, host=None, advise=True):
-    """Load, ingest (device tensor, or host array if `host`), blame, advise; returns a dict of results."""
+def gpu_run(ctx, prog, samples_dev, stream=None, host=None, advise=True, graph_launches=0):
+    """Load, ingest (device tensor, or host array if `host`), blame, advise; returns a dict of results.
+    With graph_launches > 0 the step is captured as a CUDA graph and launched that many times instead."""
     P = ctx.load_program(prog)
     try:
-        P.reset(stream)
-        if host is not None:
-            P.ingest_host(host, stream=stream)
-        elif samples_dev is not None and samples_dev.numel():
-            P.ingest(samples_dev, stream=stream)
-        P.blame(stream)
-        adv = P.advise(fetch=True, stream=stream) if advise else None
+        if graph_launches:
+            P.capture_step(samples_dev)
+            for _ in range(graph_launches):
+                P.launch_step(stream)
+            adv = P.get_advice(stream)
+        else:
+            P.reset(stream)
+            if host is not None:
+                P.ingest_host(host, stream=stream)
+            elif samples_dev is not None and samples_dev.numel():
+                P.ingest(samples_dev, stream=stream)
+            P.blame(stream)
+            adv = P.advise(fetch=True, stream=stream) if advise else None
         st, info = P.status(stream)
         cnt, bad = P.counts(stream)
         rin, rout = P.reaching(stream)

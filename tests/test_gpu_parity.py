@@ -159,6 +159,19 @@ def test_small_search_slots_overflow_to_large_tier():
         assert_full_parity(r, oracle_run(P, s))
 
 
+def test_fourth_tier_program_arena():
+    """A third tier of 32 nodes sends the larger searches on to the program's own
+    fourth tier (sized from its largest function); results stay exact."""
+    import paper_2009_04061_gb300 as g
+    with g.Context(ARCH, dict(small_search_nodes=4, mid_search_nodes=8, max_search_nodes=32, search_slots=32)) as c:
+        rng = np.random.default_rng(12)
+        P = synth.make_program(synth.batched_params(12, rng, 12), 1.0)
+        s = P.samples(1_000_000, seed=12)
+        r = gpu_run(c, P, dev(s))
+        assert r["status"] == 0 and r["info"]["max_nodes"] > 32
+        assert_full_parity(r, oracle_run(P, s))
+
+
 def test_full_batched_workload_sampled_functions(ctx):
     """The bench's workload at full size (2,000 functions, 5e8 samples): invariants over the
     whole program, and five functions (smallest to largest) against the oracle element by element."""
@@ -188,3 +201,18 @@ def test_full_batched_workload_sampled_functions(ctx):
         assert_edges_equal(g["edges"], R["edges"], i0, i1)
         ga = {key: v for key, v in g["advice"].items()}
         assert_advice_equal(ga, R, f, f + 1, l0, l1)
+
+
+def test_graph_step_matches_eager(ctx):
+    """The CUDA-graph step (reset, ingest, blame, advise) gives the eager step's results, launch after launch."""
+    ps, ns, kz = synth.workload("rodinia", 1)
+    P = synth.make_program(ps, kz, 1)
+    s = dev(P.samples(ns, seed=1))
+    eager = gpu_run(ctx, P, s)
+    graph = gpu_run(ctx, P, s, graph_launches=3)
+    assert graph["status"] == 0
+    for k in ("counts", "invalid", "rin", "rout", "blame"):
+        assert np.array_equal(np.asarray(eager[k]), np.asarray(graph[k])), k
+    assert_edges_equal(graph["edges"], eager["edges"])
+    for k in eager["advice"]:
+        assert np.array_equal(eager["advice"][k], graph["advice"][k]), k

@@ -51,3 +51,26 @@ def test_single_kernel_orders_agree():
     params, ns, kz = synth.workload("plain", 0)
     P = synth.make_program(params, kz, 0)
     assert np.array_equal(P.samples(ns), P.samples(ns, order="interleaved"))
+
+
+def test_subprogram_matches_the_batch():
+    """A function cut out of a batch (indices rebased) with its own samples
+    gives the oracle the same blame and edges as inside the batch."""
+    import oracle
+    params, ns, kz = synth.workload("rodinia", 0)
+    P = synth.make_program(params, kz, 0)
+    s = P.samples(ns // 4)
+    arch = synth.default_arch()
+    cnt, _ = oracle.histogram(P, s)
+    for f in (0, 7):
+        R = oracle.analyze(P, arch, cnt, f, f + 1)
+        sub = synth.subprogram(P.arrays, f, f + 1)
+        c_f, bad = oracle.histogram(sub, synth.rebase_samples(s, f, f + 1))
+        assert bad == 0
+        R_f = oracle.analyze(sub, arch, c_f)
+        i0 = int(P.func_instr_off[f])
+        assert np.array_equal(R["blame"], R_f["blame"])
+        assert np.array_equal(R["edges"]["j"] - i0, R_f["edges"]["j"])
+        assert np.array_equal(R["edges"]["i"] - i0, R_f["edges"]["i"])
+        assert np.array_equal(R["edges"]["share"], R_f["edges"]["share"])
+        assert np.array_equal(R["speedup"], R_f["speedup"])
