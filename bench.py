@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-functions", type=int, default=250, help="functions in the CPU-baseline sample")
     ap.add_argument("--cpu-samples", type=int, default=8_000_000, help="sample cap of the CPU-baseline sample")
+    ap.add_argument("--autotune", action="store_true",
+                    help="tune the launch schedule on the workload first and time the tuned one")
     ap.add_argument("--serving", action="store_true", help="run the serving workload instead")
     ap.add_argument("--sessions", type=int, default=200, help="serving: sessions")
     ap.add_argument("--rate", type=float, default=200.0, help="serving: mean arrivals per second")
@@ -159,6 +161,22 @@ def cpu_sample(P, n_total: int, k_funcs: int, seed: int, cap: int):
         got += take
     sub = np.concatenate(parts) if parts else np.zeros(0, np.uint64)
     return sub, got
+
+
+def reduce_max(x: float, world: int) -> float:
+    """The largest x over the ranks (x itself at one rank)."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def weak_value(n_per_rank: int, ms: float, world: int) -> float:
+    """Whole-job samples/s: every rank processed n_per_rank in ms (the slowest rank's time)."""
+    return world * n_per_rank / (ms / 1e3)
 
 
 def plain_vs_batched(gpa, workload: str, seed: int, dev, stream, reps: int = 3) -> dict:
@@ -313,7 +331,18 @@ def main():
     host = torch.empty(n, dtype=torch.int64).pin_memory()
     P.samples(n, seed=a.seed + rank, out=host.numpy().view(np.uint64))
     d = host.to(dev, non_blocking=False)
-    ctx = gpa.Context(synth.default_arch(), {"search_slots": a.search_slots} if a.search_slots else None)
+    opts = {"search_slots": a.search_slots} if a.search_slots else {}
+    tuned = None
+    if a.autotune:
+        from paper_2009_04061_gb300 import autotune
+        stream0 = torch.cuda.current_stream(dev)
+        with gpa.Context(synth.default_arch(), opts or None) as c0:
+            fixed_ms = autotune.time_step(c0, P.arrays, d, stream0)
+        best, table = autotune.tune(synth.default_arch(), P.arrays, d, stream0)
+        tuned = {"fixed_ms_per_step": fixed_ms, "tuned_ms_per_step": min(t for _, t in table),
+                 "options": best, "candidates_tried": len(table)}
+        opts = best
+    ctx = gpa.Context(synth.default_arch(), opts or None)
     prog = ctx.load_program(P)
     stream = torch.cuda.current_stream(dev)
 
@@ -373,13 +402,11 @@ def main():
     st, info = prog.status(stream)
     if st != 0:
         raise SystemExit(f"device status {st} after the timed steps: {info}")
+    ms = reduce_max(ms, world)
     if world > 1:
-        t = torch.tensor([ms], dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
         dist.barrier()
     clocks = clk.summary()
-    value = world * n / (ms / 1e3)
+    value = weak_value(n, ms, world)
     instr_per_s = world * P.n_instr / (ms / 1e3)
 
     # Roofline of the aggregation kernel: 8 algorithmic bytes per sample over
@@ -412,11 +439,8 @@ def main():
             prog.blame(stream)
             adv = prog.advise(fetch=True, stream=stream)  # synchronizes the stream
         te = (time.perf_counter() - t0) / reps
-        if world > 1:
-            t = torch.tensor([te], dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            te = float(t.item())
-        e2e = {"value": world * n / te, "unit": UNIT, "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": d2h,
+        te = reduce_max(te, world)
+        e2e = {"value": weak_value(n, te * 1e3, world), "unit": UNIT, "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": d2h,
                "ms_per_step": te * 1e3}
 
     cpu = None
@@ -447,7 +471,7 @@ def main():
                 info["general_searches"], info["tier2_searches"], info["tier3_searches"]],
             "largest_search_nodes": info["max_nodes"], "gpu_launches": launches,
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
-            "batched_vs_plain": bvp,
+            "batched_vs_plain": bvp, "autotune": tuned, "options": opts,
         }
         print(json.dumps(line), flush=True)
     prog.unload()

@@ -1,11 +1,12 @@
 // Step (a), Sec. 2.1: aggregate packed PC samples into per-(instruction,
 // stall class, latency flag) counters.
 //
-// HBM-bound stream: 8 bytes read per sample. Persistent CTAs (three per SM)
-// stream 16-byte vectors with non-allocating loads, double-buffered in
+// HBM-bound stream: 8 bytes read per sample. Persistent CTAs (three per SM
+// in the default variant) stream 16-byte vectors with non-allocating loads,
+// double-buffered in
 // registers so the next round's loads are in flight while the current round
 // is counted. Counting goes through a per-CTA shared-memory hash of hot
-// counters (8,192 u32 key/value pairs): lanes holding the same counter are
+// counters (8,192 u32 key/value pairs by default): lanes holding the same counter are
 // first merged with match.any, the group leader adds into the hash, and a key
 // that finds no slot within a few probes goes straight to its 64-bit global
 // counter. The hash is flushed to the global counters when three quarters
@@ -16,11 +17,7 @@ namespace gpa {
 
 namespace {
 
-constexpr int kThreads = 256;
 constexpr int kUnroll = 4;           // 16-byte vectors per thread per round
-constexpr int kCtasPerSm = 3;
-constexpr int kHash = 8192;          // entries per CTA (64 KB of shared memory)
-constexpr int kProbes = 8;
 constexpr int kSmemFuncs = 4096;     // function offsets cached in shared memory
 constexpr uint32_t kNoKey = 0xFFFFFFFFu;
 
@@ -49,10 +46,12 @@ struct Hash {
   int* fill;
 };
 
+template <int HASH_LOG2, int PROBES>
 __device__ __forceinline__ void hash_add(const Hash& H, uint32_t k, uint32_t c, unsigned long long* cnt) {
-  uint32_t h = (k * 2654435761u) >> (32 - 13);  // 13 = log2(kHash)
+  constexpr int kHash = 1 << HASH_LOG2;
+  uint32_t h = (k * 2654435761u) >> (32 - HASH_LOG2);
 #pragma unroll 1
-  for (int p = 0; p < kProbes; ++p) {
+  for (int p = 0; p < PROBES; ++p) {
     const uint32_t cur = H.key[h];
     if (cur == k) { atomicAdd(&H.val[h], c); return; }
     if (cur == kNoKey) {
@@ -65,16 +64,19 @@ __device__ __forceinline__ void hash_add(const Hash& H, uint32_t k, uint32_t c, 
   atomicAdd(cnt + k, (unsigned long long)c);  // no room nearby: count in global memory
 }
 
+template <int HASH_LOG2, int PROBES>
 __device__ __forceinline__ void count(uint32_t key, bool in_range, const Hash& H, unsigned long long* cnt,
                                       uint32_t& bad) {
   const uint32_t k = in_range ? key : kNoKey;
   if (in_range && key == kNoKey) ++bad;
   const unsigned peers = __match_any_sync(0xffffffffu, k);
   const int lane = threadIdx.x & 31;
-  if (k != kNoKey && lane == __ffs(peers) - 1) hash_add(H, k, (uint32_t)__popc(peers), cnt);
+  if (k != kNoKey && lane == __ffs(peers) - 1) hash_add<HASH_LOG2, PROBES>(H, k, (uint32_t)__popc(peers), cnt);
 }
 
+template <int HASH_LOG2>
 __device__ void flush(const Hash& H, unsigned long long* cnt) {
+  constexpr int kHash = 1 << HASH_LOG2;
   for (int t = threadIdx.x; t < kHash; t += blockDim.x) {
     const uint32_t k = H.key[t];
     if (k != kNoKey) {
@@ -85,8 +87,10 @@ __device__ void flush(const Hash& H, unsigned long long* cnt) {
   }
 }
 
-__global__ void __launch_bounds__(kThreads) k_histogram(Prog P, const uint64_t* __restrict__ s, int64_t n,
-                                                       int head) {
+template <int THREADS, int HASH_LOG2, int PROBES>
+__global__ void __launch_bounds__(THREADS) k_histogram(Prog P, const uint64_t* __restrict__ s, int64_t n,
+                                                      int head) {
+  constexpr int kHash = 1 << HASH_LOG2;
   extern __shared__ __align__(16) uint32_t sm[];
   Hash H{sm, sm + kHash, reinterpret_cast<int*>(sm + 2 * kHash)};
   int32_t* s_off = reinterpret_cast<int32_t*>(sm + 2 * kHash + 4);
@@ -138,8 +142,8 @@ __global__ void __launch_bounds__(kThreads) k_histogram(Prog P, const uint64_t* 
     load_round(c + step, nxt, in_nxt);
 #pragma unroll
     for (int u = 0; u < kUnroll; ++u) {
-      count(sample_key(cur[u].x, foff, P.nf), in_cur[u], H, P.cnt, bad);
-      count(sample_key(cur[u].y, foff, P.nf), in_cur[u], H, P.cnt, bad);
+      count<HASH_LOG2, PROBES>(sample_key(cur[u].x, foff, P.nf), in_cur[u], H, P.cnt, bad);
+      count<HASH_LOG2, PROBES>(sample_key(cur[u].y, foff, P.nf), in_cur[u], H, P.cnt, bad);
     }
 #pragma unroll
     for (int u = 0; u < kUnroll; ++u) { cur[u] = nxt[u]; in_cur[u] = in_nxt[u]; }
@@ -152,7 +156,7 @@ __global__ void __launch_bounds__(kThreads) k_histogram(Prog P, const uint64_t* 
       __syncthreads();
       if (full) {
         since_flush = 0;
-        flush(H, P.cnt);
+        flush<HASH_LOG2>(H, P.cnt);
         __syncthreads();
         if (threadIdx.x == 0) *H.fill = 0;
         __syncthreads();
@@ -160,26 +164,39 @@ __global__ void __launch_bounds__(kThreads) k_histogram(Prog P, const uint64_t* 
     }
   }
   __syncthreads();
-  flush(H, P.cnt);
+  flush<HASH_LOG2>(H, P.cnt);
   // One invalid-count atomic per warp.
   for (int o = 16; o > 0; o >>= 1) bad += __shfl_xor_sync(0xffffffffu, bad, o);
   if (lane == 0 && bad) atomicAdd(&P.stats[SS_INVALID], (unsigned long long)bad);
 }
 
-}  // namespace
-
-void launch_histogram(const Prog& P, const uint64_t* samples, size_t n, cudaStream_t st, int sms, int64_t* launches) {
-  if (n == 0) return;
+template <int THREADS, int HASH_LOG2, int PROBES>
+static void launch_variant(const Prog& P, const uint64_t* samples, size_t n, cudaStream_t st, int sms,
+                           int ctas_per_sm) {
   const int head = (reinterpret_cast<uintptr_t>(samples) & 15u) ? 1 : 0;
   const int64_t vecs = ((int64_t)n - head) / 2;
-  int64_t blocks = (vecs + (int64_t)kThreads * kUnroll - 1) / ((int64_t)kThreads * kUnroll);
-  const int64_t cap = (int64_t)sms * kCtasPerSm;
+  int64_t blocks = (vecs + (int64_t)THREADS * kUnroll - 1) / ((int64_t)THREADS * kUnroll);
+  const int64_t cap = (int64_t)sms * ctas_per_sm;
   if (blocks > cap) blocks = cap;
   if (blocks < 1) blocks = 1;
-  const size_t smem = sizeof(uint32_t) * (2 * (size_t)kHash + 4) +
+  const size_t smem = sizeof(uint32_t) * (2 * ((size_t)1 << HASH_LOG2) + 4) +
                       (P.nf <= kSmemFuncs ? sizeof(int32_t) * (size_t)(P.nf + 1) : 0);
-  cudaFuncSetAttribute(k_histogram, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  k_histogram<<<(int)blocks, kThreads, smem, st>>>(P, samples, (int64_t)n, head);
+  auto* k = k_histogram<THREADS, HASH_LOG2, PROBES>;
+  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k<<<(int)blocks, THREADS, smem, st>>>(P, samples, (int64_t)n, head);
+}
+
+}  // namespace
+
+// variant 0: 8,192-entry hash, 256 threads, 3 CTAs per SM, 8 probes (default);
+// 1: 8,192 entries, 512 threads, 2 CTAs per SM, 4 probes; 2: 16,384 entries,
+// 1,024 threads, 1 CTA per SM, 4 probes.
+void launch_histogram(const Prog& P, const uint64_t* samples, size_t n, cudaStream_t st, int sms, int64_t* launches,
+                      int variant) {
+  if (n == 0) return;
+  if (variant == 1) launch_variant<512, 13, 4>(P, samples, n, st, sms, 2);
+  else if (variant == 2) launch_variant<1024, 14, 4>(P, samples, n, st, sms, 1);
+  else launch_variant<256, 13, 8>(P, samples, n, st, sms, 3);
   ++*launches;
 }
 

@@ -216,3 +216,29 @@ def test_graph_step_matches_eager(ctx):
     assert_edges_equal(graph["edges"], eager["edges"])
     for k in eager["advice"]:
         assert np.array_equal(eager["advice"][k], graph["advice"][k]), k
+
+
+def test_histogram_variants_agree():
+    """Every aggregation variant the autotuner may pick gives the oracle's counts."""
+    import paper_2009_04061_gb300 as g
+    ps, _, kz = synth.workload("rodinia")
+    P = synth.make_program(ps, kz)
+    s = P.samples(3_000_001, invalid_ppm=2000, seed=4)
+    cnt, bad = oracle.histogram(P, s)
+    d = dev(s)
+    for v in (0, 1, 2):
+        with g.Context(ARCH, dict(hist_variant=v)) as c:
+            r = gpu_run(c, P, d, advise=False)
+            assert np.array_equal(r["counts"], cnt) and r["invalid"] == bad, v
+
+
+def test_autotune_picks_a_timed_candidate():
+    import torch
+    from paper_2009_04061_gb300 import autotune
+    ps, ns, kz = synth.workload("plain")
+    P = synth.make_program(ps, kz)
+    d = dev(P.samples(ns))
+    cands = [dict(hist_variant=0, small_search_nodes=64, mid_search_nodes=256, search_slots=152),
+             dict(hist_variant=1, small_search_nodes=128, mid_search_nodes=512, search_slots=304)]
+    best, table = autotune.tune(ARCH, P.arrays, d, torch.cuda.current_stream(), cands=cands, reps=1)
+    assert best in [t[0] for t in table] and all(ms > 0 for _, ms in table)
