@@ -208,6 +208,17 @@ void launch_histogram(const Prog& P, const uint64_t* samples, size_t n, cudaStre
                       int variant);
 void launch_dataflow(const Prog& P, const Arch& A, int max_sweeps, cudaStream_t st, int sms, int64_t* launches);
 
+// Lets kernel func take up to the device's opt-in shared memory per block.
+// Every launch and captured graph node of a kernel then sees the same limit
+// (each requests only what it uses), whatever ran before it.
+template <class F>
+inline void allow_max_smem(F func) {
+  int dev = 0, optin = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+}
+
 // Shared memory the staged reaching-definitions fixpoint needs for a function
 // of nbf blocks and ne predecessor entries, and the most it may use.
 __host__ __device__ inline int64_t reach_smem_need(int64_t nbf, int64_t ne) {

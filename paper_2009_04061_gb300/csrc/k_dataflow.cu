@@ -208,7 +208,7 @@ void launch_dataflow(const Prog& P, const Arch& A, int max_sweeps, cudaStream_t 
   if (blocks < 1) blocks = 1;
   k_block_masks<<<blocks, threads, 0, st>>>(P);
   if (P.reach_smem > 0) {
-    cudaFuncSetAttribute(k_reaching_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, P.reach_smem);
+    allow_max_smem(k_reaching_smem);
     int per_sm = (int)((200 * 1024) / (P.reach_smem + 1024));
     if (per_sm < 1) per_sm = 1;
     if (per_sm > 16) per_sm = 16;

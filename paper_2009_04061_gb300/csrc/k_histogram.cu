@@ -182,7 +182,7 @@ static void launch_variant(const Prog& P, const uint64_t* samples, size_t n, cud
   const size_t smem = sizeof(uint32_t) * (2 * ((size_t)1 << HASH_LOG2) + 4) +
                       (P.nf <= kSmemFuncs ? sizeof(int32_t) * (size_t)(P.nf + 1) : 0);
   auto* k = k_histogram<THREADS, HASH_LOG2, PROBES>;
-  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  allow_max_smem(k);
   k<<<(int)blocks, THREADS, smem, st>>>(P, samples, (int64_t)n, head);
 }
 

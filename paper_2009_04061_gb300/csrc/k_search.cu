@@ -741,12 +741,11 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32) k_search_warp(Prog P, Arch 
 int64_t search_arena_bytes(int nodes, int src, int layers) { return arena_bytes(nodes, src, layers); }
 
 void launch_search(const Prog& P, const Arch& A, const SearchArena* tiers, cudaStream_t st, int64_t* launches) {
-  // Contexts may use different arena sizes: set each launch's requirement.
+  // Each launch requests its own tier's arena size.
   const size_t smem1 = (size_t)tiers[0].bytes * kWarpsPerCta;
-  cudaFuncSetAttribute(k_search_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem1);
+  allow_max_smem(k_search_warp);
   k_search_warp<<<tiers[0].warps / kWarpsPerCta, kWarpsPerCta * 32, smem1, st>>>(P, A, tiers[0], 1);
   const size_t smem2 = (size_t)tiers[1].bytes;
-  cudaFuncSetAttribute(k_search_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2);
   k_search_warp<<<tiers[1].warps, 32, smem2, st>>>(P, A, tiers[1], 2);
   k_search_warp<<<tiers[2].warps, 32, 0, st>>>(P, A, tiers[2], 3);
   *launches += 3;
