@@ -211,12 +211,15 @@ void launch_dataflow(const Prog& P, const Arch& A, int max_sweeps, cudaStream_t 
 // Lets kernel func take up to the device's opt-in shared memory per block.
 // Every launch and captured graph node of a kernel then sees the same limit
 // (each requests only what it uses), whatever ran before it.
+// The dynamic limit is the opt-in maximum less the kernel's static shared memory.
 template <class F>
 inline void allow_max_smem(F func) {
   int dev = 0, optin = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+  cudaFuncAttributes fa{};
+  cudaFuncGetAttributes(&fa, func);
+  cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
 }
 
 // Shared memory the staged reaching-definitions fixpoint needs for a function
