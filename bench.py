@@ -51,6 +51,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-functions", type=int, default=250, help="functions in the CPU-baseline sample")
     ap.add_argument("--cpu-samples", type=int, default=8_000_000, help="sample cap of the CPU-baseline sample")
+    ap.add_argument("--hist-variant", type=int, default=None, help="aggregation kernel variant (gpa_options)")
     ap.add_argument("--autotune", action="store_true",
                     help="tune the launch schedule on the workload first and time the tuned one")
     ap.add_argument("--serving", action="store_true", help="run the serving workload instead")
@@ -332,6 +333,8 @@ def main():
     P.samples(n, seed=a.seed + rank, out=host.numpy().view(np.uint64))
     d = host.to(dev, non_blocking=False)
     opts = {"search_slots": a.search_slots} if a.search_slots else {}
+    if a.hist_variant is not None:
+        opts["hist_variant"] = a.hist_variant
     tuned = None
     if a.autotune:
         from paper_2009_04061_gb300 import autotune
@@ -415,8 +418,9 @@ def main():
     hbm_peak, peak_kind = load_peaks()
     t_hist = phase["ingest_ms"] / 1e3
     achieved = 8.0 * n / t_hist / 1e9
-    tr = traffic_record("k_histogram")
-    roofline = {"kernel": "k_histogram", "bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+    kname = "k_histogram_runs" if not opts.get("hist_variant") else "k_histogram"
+    tr = traffic_record(kname)
+    roofline = {"kernel": kname, "bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                 "frac": achieved / hbm_peak, "peak_kind": f"{peak_kind} (copy bandwidth)",
                 "traffic": (tr["dram_bytes_per_sample"] * n) if tr else None,
                 "algorithmic_bytes": 8 * n, "launch_ms": t_hist * 1e3}

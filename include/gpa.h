@@ -105,9 +105,12 @@ typedef struct {
                                    (max 1024). A search that outgrows it is redone in the next tier */
   int32_t mid_search_nodes;     /* nodes of the second tier's shared-memory arenas (three warps per SM
                                    up to 512 nodes, one up to 1024); 0 = min(512, max_search_nodes) */
-  int32_t hist_variant;         /* aggregation kernel: 0 = 8,192-entry shared-memory hash, 256 threads,
-                                   3 CTAs per SM (default); 1 = 8,192 entries, 512 threads, 2 CTAs per SM;
-                                   2 = 16,384 entries, 1,024 threads, 1 CTA per SM */
+  int32_t hist_variant;         /* aggregation kernel: 0 (default) = one CTA per SM over a contiguous
+                                   segment, shared memory used per kernel-launch run as a direct-indexed
+                                   window of that kernel's counters or as a hash; grid-strided with a
+                                   shared-memory hash: 1 = 8,192 entries, 512 threads, 2 CTAs per SM;
+                                   2 = 16,384 entries, 1,024 threads, 1 CTA per SM; 3 = 8,192 entries,
+                                   256 threads, 3 CTAs per SM */
   int32_t reserved[1];          /* must be 0 */
 } gpa_options;
 

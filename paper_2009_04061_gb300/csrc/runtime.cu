@@ -258,7 +258,7 @@ gpa_status gpa_create(const gpa_arch_desc* arch, const gpa_options* opts, gpa_ct
       if (r) return GPA_ERR_INVALID_ARG;
     if (o.max_fixpoint_sweeps < 0 || o.max_search_nodes < 0 || o.search_slots < 0 || o.max_sources_per_use < 0 ||
         o.max_sources_per_use > kMaxSrc || o.small_search_nodes < 0 || o.mid_search_nodes < 0 ||
-        o.hist_variant < 0 || o.hist_variant > 2)
+        o.hist_variant < 0 || o.hist_variant > 3)
       return GPA_ERR_INVALID_ARG;
   }
   auto* c = new (std::nothrow) gpa_ctx();

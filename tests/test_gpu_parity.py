@@ -226,10 +226,26 @@ def test_histogram_variants_agree():
     s = P.samples(3_000_001, invalid_ppm=2000, seed=4)
     cnt, bad = oracle.histogram(P, s)
     d = dev(s)
-    for v in (0, 1, 2):
+    for v in (0, 1, 2, 3):
         with g.Context(ARCH, dict(hist_variant=v)) as c:
             r = gpu_run(c, P, d, advise=False)
             assert np.array_equal(r["counts"], cnt) and r["invalid"] == bad, v
+            for lo, hi in [(1, 3_000_001), (0, 1), (5, 4101), (3, 3)]:  # unaligned, tiny, one tile, empty
+                r = gpu_run(c, P, d[lo:hi], advise=False)
+                c2, b2 = oracle.histogram(P, s[lo:hi])
+                assert np.array_equal(r["counts"], c2) and r["invalid"] == b2, (v, lo, hi)
+    # one hot counter far past the 16-bit window counters' spill point
+    hot = np.full(1_000_003, s[0], dtype=np.uint64)
+    ch, bh = oracle.histogram(P, hot)
+    with g.Context(ARCH, dict(hist_variant=0)) as c:
+        r = gpu_run(c, P, dev(hot), advise=False)
+        assert np.array_equal(r["counts"], ch) and r["invalid"] == bh
+    # a stream with interleaved kernels (every tile straddles many kernels)
+    si = P.samples(1_000_000, seed=6, order="interleaved")
+    ci, bi = oracle.histogram(P, si)
+    with g.Context(ARCH, dict(hist_variant=0)) as c:
+        r = gpu_run(c, P, dev(si), advise=False)
+        assert np.array_equal(r["counts"], ci) and r["invalid"] == bi
 
 
 def test_autotune_picks_a_timed_candidate():
