@@ -283,7 +283,8 @@ gpa_status gpa_step_launch(gpa_ctx* ctx, gpa_pid pid, gpa_stream stream);
  * slot holds 2^15 nodes and more) and out[34] = searches that completed their
  * graph past the latency bound; out[35] = the slowest search's cycles << 20 |
  * its nodes, out[36] its rule-2 runs, out[37..41] its cycles in the first
- * five phases. out must hold 42 values. All zero unless the
+ * five phases; out[42..57] the cycles of the searches by floor(log2(nodes)).
+ * out must hold 58 values. All zero unless the
  * library was built with -DGPA_PHASE_TIMING (the timers cost a few atomics per
  * search). Synchronizes stream. */
 gpa_status gpa_get_search_profile(gpa_ctx* ctx, gpa_pid pid, uint64_t* out, gpa_stream stream);

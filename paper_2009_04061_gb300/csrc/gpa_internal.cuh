@@ -36,7 +36,8 @@ enum {
   SS_PHASE = 13, SS_SIZES = 31, SS_PASSB = 47, SS_SLOW = 48,
   SS_REACH_HEAD = 55,  // next entry of reach_order for the staged fixpoint
   SS_OVF3_N = 56, SS_OVF3_HEAD = 57,  // searches handed on to the program's own fourth tier
-  SS_N = 58
+  SS_SIZE_CYC = 58,  // with -DGPA_PHASE_TIMING: cycles of the searches by log2 of their node count (16)
+  SS_N = 74
 };
 
 struct Arch {
@@ -79,6 +80,8 @@ struct Prog {
   const int32_t* block_func;
   const int32_t* reach_order;     // nf: functions by block count, largest first
   const int32_t* block_minreach;  // nb: smallest block reachable from the block (itself included)
+  const int4* block_meta;         // 2 per block: {first instr, end instr, first event, end event},
+                                  // {first pred, end pred, 0, 0} (one 32-byte line for the searches)
   const int32_t* ev_off;          // nb + 1: per-block event lists
   const uint32_t* events;         // defs and unguarded reads, bottom-up: resource | def << 9 |
                                   // kind << 10 | guard << 12 | position in block << 16
@@ -87,6 +90,7 @@ struct Prog {
   unsigned long long* stats;      // SS_N
   uint32_t* def_mask;             // nb * 9: resources defined in the block
   uint32_t* uuse_mask;            // nb * 9: resources read by an unguarded instruction
+  uint32_t* touch_mask;           // nb * 9: DEF | UUSE (blocks a search must scan)
   int32_t* res_maxlat;            // nf * 268: largest latency of any def of the resource in the function
   uint32_t* res_guards;           // nf * 268: guard literals of the resource's defs in the function
   uint32_t* rin;                  // nb * 9
@@ -232,6 +236,7 @@ void launch_blame(const Prog& P, const Arch& A, const SearchArena* tiers, int ma
                   cudaStream_t st, int sms, int64_t* launches);
 void launch_search(const Prog& P, const Arch& A, const SearchArena* tiers, cudaStream_t st, int64_t* launches);
 int64_t search_arena_bytes(int nodes, int src, int layers);
+void launch_build_meta(const Prog& P, int4* meta, cudaStream_t st, int sms, int64_t* launches);
 void launch_build_events(const Prog& P, int32_t* ev_off, uint32_t* events, int32_t* tmp, cudaStream_t st, int sms,
                          int64_t* launches);
 void launch_advise(const Prog& P, const Arch& A, cudaStream_t st, int sms, int64_t* launches);

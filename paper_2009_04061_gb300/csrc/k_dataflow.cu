@@ -49,6 +49,7 @@ __global__ void k_block_masks(Prog P) {
       if (lane == w) {
         P.def_mask[(size_t)b * kWords + w] = d;
         P.uuse_mask[(size_t)b * kWords + w] = u;
+        P.touch_mask[(size_t)b * kWords + w] = d | u;
         P.rin[(size_t)b * kWords + w] = 0u;
         P.rout[(size_t)b * kWords + w] = d;
       }

@@ -88,6 +88,7 @@ __device__ bool warp_search(const Prog& P, const Arch& A, const Arena& a, int j,
 #ifdef GPA_PHASE_TIMING
   long long t_prev = clock64();
   const long long t_begin = t_prev;
+  long long t_prev_total = t_prev;
   unsigned long long ph[5] = {0, 0, 0, 0, 0};
   unsigned long long r2runs = 0;
   auto phase = [&](int i) {
@@ -97,6 +98,10 @@ __device__ bool warp_search(const Prog& P, const Arch& A, const Arena& a, int j,
       ph[i] = (unsigned long long)(t - t_prev);
       t_prev = t;
       if (i == 4 || i == 0) {
+        const int nn = max(((volatile int*)a.ctr)[0], 1);
+        if (i == 4 || i == 0)
+          atomicAdd(&P.stats[SS_SIZE_CYC + min(15, 31 - __clz(nn))], (unsigned long long)(t - t_prev_total));
+        t_prev_total = t;
         const unsigned long long key = ((unsigned long long)(t - t_begin) << 20) | (unsigned long long)min(((volatile int*)a.ctr)[0], 0xFFFFF);
         if (atomicMax(&P.stats[SS_SLOW], key) < key) {
           P.stats[SS_SLOW + 1] = r2runs;
@@ -110,7 +115,7 @@ __device__ bool warp_search(const Prog& P, const Arch& A, const Arena& a, int j,
 #endif
   const int gj = P.guard[j];
   const int b0 = P.instr_block[j];
-  const int first0 = P.block_instr_off[b0];
+  const int first0 = P.block_meta[2 * (size_t)b0].x;
   const int w = r >> 5;
   const uint32_t bit = 1u << (r & 31);
   const uint32_t hmask = (uint32_t)(2 * a.N - 1);
@@ -144,9 +149,11 @@ __device__ bool warp_search(const Prog& P, const Arch& A, const Arena& a, int j,
     return false;
   };
   auto wout = [&](int u) {
-    return u == 0 ? (j - first0 + 1) : (P.block_instr_off[a.blk[u] + 1] - P.block_instr_off[a.blk[u]]);
+    if (u == 0) return j - first0 + 1;
+    const int4 m = P.block_meta[2 * (size_t)a.blk[u]];
+    return m.y - m.x;
   };
-  auto last_of = [&](int u) { return P.block_instr_off[a.blk[u] + 1] - 1; };
+  auto last_of = [&](int u) { return P.block_meta[2 * (size_t)a.blk[u]].y - 1; };
 
   // Scan node u's block bottom-up through its event list (one lane). Records
   // occurrences, the literal set leaving the top, the covering position and
@@ -157,25 +164,33 @@ __device__ bool warp_search(const Prog& P, const Arch& A, const Arena& a, int j,
     bool stop = false;
     if (u != 0) {
       const int B = a.blk[u];
-      const int first = P.block_instr_off[B];
+      const int4 m = P.block_meta[2 * (size_t)B];
+      const int first = m.x;
       int cov = first, wall = -1;
-      if ((P.def_mask[(size_t)B * kWords + w] | P.uuse_mask[(size_t)B * kWords + w]) & bit) {
+      if (P.touch_mask[(size_t)B * kWords + w] & bit) {
         int last_def_pos = -1;
-        const int ev1 = P.ev_off[B + 1];
-        for (int e = P.ev_off[B]; e < ev1; ++e) {
-          const uint32_t ev = P.events[e];
-          if ((int)(ev & 0x1FFu) != r) continue;
-          const int pos = (int)(ev >> 16), x = first + pos;
-          if (ev & 0x200u) {  // def of r
-            last_def_pos = pos;
-            if (!contains(S, gj) && !(B == b0 && x < j)) {  // sources above j in its block are settled
-              const int o = atomicAdd((int*)&a.ctr[2], 1);
-              if (o < a.O) { a.on[o] = u; a.ox[o] = x; } else { a.ctr[4] = 1; }
+        // Events four at a time: independent read-only loads in flight together
+        // (a sentinel resource 511 pads the last group).
+        for (int e0 = m.z; e0 < m.w && !stop; e0 += 4) {
+          uint32_t evs[4];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) evs[q] = e0 + q < m.w ? __ldg(&P.events[e0 + q]) : 0x1FFu;
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const uint32_t ev = evs[q];
+            if (stop || (int)(ev & 0x1FFu) != r) continue;
+            const int pos = (int)(ev >> 16), x = first + pos;
+            if (ev & 0x200u) {  // def of r
+              last_def_pos = pos;
+              if (!contains(S, gj) && !(B == b0 && x < j)) {  // sources above j in its block are settled
+                const int o = atomicAdd((int*)&a.ctr[2], 1);
+                if (o < a.O) { a.on[o] = u; a.ox[o] = x; } else { a.ctr[4] = 1; }
+              }
+              S = add_literal(S, (int)((ev >> 12) & 0xFu));
+              if (contains(S, gj)) { stop = true; cov = x; }
+            } else if (wall < 0 && pos != last_def_pos && x != j) {  // unguarded reader of r
+              wall = x;
             }
-            S = add_literal(S, (int)((ev >> 12) & 0xFu));
-            if (contains(S, gj)) { stop = true; cov = x; break; }
-          } else if (wall < 0 && pos != last_def_pos && x != j) {  // unguarded reader of r
-            wall = x;
           }
         }
       }
@@ -198,9 +213,10 @@ __device__ bool warp_search(const Prog& P, const Arch& A, const Arena& a, int j,
     const int Sout = mine ? ((a.S[u] >> 16) & 0xFFFF) : 0;
     const bool open = mine && !(a.fl[u] & 4);
     int deg = 0;
+    const int4 pm = open ? P.block_meta[2 * (size_t)B + 1] : make_int4(0, 0, 0, 0);
     if (open)
-      for (int q = P.pred_off[B]; q < P.pred_off[B + 1]; ++q)
-        deg += (P.rout[(size_t)P.pred[q] * kWords + w] & bit) ? 1 : 0;
+      for (int q = pm.x; q < pm.y; ++q)
+        deg += (P.rout[(size_t)__ldg(&P.pred[q]) * kWords + w] & bit) ? 1 : 0;
     int incl = deg;
     for (int o = 1; o < 32; o <<= 1) {
       const int y = __shfl_up_sync(0xffffffffu, incl, o);
@@ -212,7 +228,7 @@ __device__ bool warp_search(const Prog& P, const Arch& A, const Arena& a, int j,
     if (mine) { a.e0[u] = ne + incl - deg; a.e1[u] = ne + incl; }
     int maxdeg = deg;
     for (int o = 16; o > 0; o >>= 1) maxdeg = max(maxdeg, __shfl_xor_sync(0xffffffffu, maxdeg, o));
-    int qp = open ? P.pred_off[B] : 0;
+    int qp = pm.x;
     for (int kk = 0; kk < maxdeg; ++kk) {
       bool pending = kk < deg;
       int p = -1;

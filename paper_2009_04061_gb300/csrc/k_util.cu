@@ -144,6 +144,18 @@ void launch_build_events(const Prog& P, int32_t* ev_off, uint32_t* events, int32
   ++*launches;
 }
 
+__global__ void k_block_meta(Prog P, int4* meta) {
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < P.nb; b += gridDim.x * blockDim.x) {
+    meta[2 * (size_t)b] = make_int4(P.block_instr_off[b], P.block_instr_off[b + 1], P.ev_off[b], P.ev_off[b + 1]);
+    meta[2 * (size_t)b + 1] = make_int4(P.pred_off[b], P.pred_off[b + 1], 0, 0);
+  }
+}
+
+void launch_build_meta(const Prog& P, int4* meta, cudaStream_t st, int sms, int64_t* launches) {
+  k_block_meta<<<grid_for(P.nb, 256, sms), 256, 0, st>>>(P, meta);
+  ++*launches;
+}
+
 int grid_for(int64_t n, int threads, int sms) {
   int64_t g = (n + threads - 1) / threads;
   int64_t cap = (int64_t)sms * 8;

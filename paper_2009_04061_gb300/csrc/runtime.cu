@@ -25,6 +25,7 @@ struct ProgramRec {
   int64_t step_launches = 0;            // kernels in it
   int32_t *pred_off = nullptr, *cursor = nullptr, *ev_off = nullptr;  // build scratch kept from allocation
   uint32_t* events = nullptr;
+  int4* meta = nullptr;
   int n_succ = 0, n_def = 0, n_use = 0;
   int32_t* scan_tmp = nullptr;
   std::vector<void*> allocs;
@@ -411,6 +412,9 @@ static gpa_status alloc_program(const gpa_program_desc* d, ProgramRec* R, int ti
   TRY(dev_alloc(R, &P.cnt, ni * kCnt));
   TRY(dev_alloc(R, &P.stats, (size_t)SS_N));
   TRY(dev_alloc(R, &P.def_mask, nb * kWords));
+  TRY(dev_alloc(R, &P.touch_mask, nb * kWords));
+  TRY(dev_alloc(R, &R->meta, 2 * nb));
+  P.block_meta = R->meta;
   TRY(dev_alloc(R, &P.uuse_mask, nb * kWords));
   TRY(dev_alloc(R, &P.rin, nb * kWords));
   TRY(dev_alloc(R, &P.rout, nb * kWords));
@@ -511,6 +515,7 @@ gpa_status gpa_load_program(gpa_ctx* ctx, const gpa_program_desc* d, gpa_pid* ou
   launch_build_layout(P, st, ctx->sms, &ctx->launches);
   launch_build_preds(P, R->n_succ, pred_off, cursor, R->scan_tmp, st, ctx->sms, &ctx->launches);
   launch_build_events(P, ev_off, events, R->scan_tmp, st, ctx->sms, &ctx->launches);
+  launch_build_meta(P, R->meta, st, ctx->sms, &ctx->launches);
   if (cudaStreamSynchronize(st) != cudaSuccess || cudaGetLastError() != cudaSuccess) {
     free_program(R);
     return GPA_ERR_CUDA;
@@ -732,6 +737,7 @@ gpa_status gpa_get_search_profile(gpa_ctx* ctx, gpa_pid pid, uint64_t* out, gpa_
   if (!out) return GPA_ERR_INVALID_ARG;
   CK(cudaStreamSynchronize((cudaStream_t)stream));
   CK(cudaMemcpy(out, R->P.stats + SS_PHASE, 42 * sizeof(uint64_t), cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(out + 42, R->P.stats + SS_SIZE_CYC, 16 * sizeof(uint64_t), cudaMemcpyDeviceToHost));
   return GPA_OK;
 }
 
