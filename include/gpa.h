@@ -255,8 +255,10 @@ gpa_status gpa_advise(gpa_ctx* ctx, gpa_pid pid, const gpa_advice* out, gpa_stre
  * gpa_status (GPA_OK, GPA_ERR_NOT_CONVERGED, GPA_ERR_CAPACITY, ...). If info is
  * not NULL it must have room for 8 values: info[0] = invalid samples,
  * info[1] = general (multi-block) searches run, info[2] = largest search in
- * nodes, info[3] = fixpoint sweeps, info[4] and info[5] = searches handed on to
- * the second and third search tiers by the last gpa_blame, info[6] and
+ * nodes, info[3] = fixpoint sweeps, info[4] and info[5] = searches run by the
+ * second and third search tiers in the last gpa_blame (handed on by a smaller
+ * tier, or queued there directly because an earlier step of the program found
+ * them that large), info[6] and
  * info[7] = the stalled use (global instruction index) and the resource of
  * the largest search. */
 gpa_status gpa_sync_status(gpa_ctx* ctx, gpa_pid pid, gpa_stream stream, int64_t* info);

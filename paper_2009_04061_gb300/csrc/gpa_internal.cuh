@@ -37,7 +37,8 @@ enum {
   SS_REACH_HEAD = 55,  // next entry of reach_order for the staged fixpoint
   SS_OVF3_N = 56, SS_OVF3_HEAD = 57,  // searches handed on to the program's own fourth tier
   SS_SIZE_CYC = 58,  // with -DGPA_PHASE_TIMING: cycles of the searches by log2 of their node count (16)
-  SS_N = 74
+  SS_HINT3_N = 74,   // searches queued straight for the third tier (from the top of `queue`)
+  SS_N = 75
 };
 
 struct Arch {
@@ -98,7 +99,9 @@ struct Prog {
   int32_t* head;                  // ni: raw-edge list head per use (-1 = none)
   int4* raw;                      // raw edges: def, next, dmin, dlong | flags << 24
   int64_t raw_cap;
-  int4* queue;                    // general searches: use, resource, start literal set, 0
+  int4* queue;                    // general searches: use, resource, start literal set, use entry
+  uint32_t* tier_hint;            // n_use: smallest search tier known to hold the entry's search (0: none);
+                                  // kept across steps (a search's size depends only on the program)
   int4* ovf_queue;                // general searches that outgrew a small scratch slot
   int64_t queue_cap;
   int32_t* edge_cnt;              // ni + 1 (exclusive scan in place -> offsets)

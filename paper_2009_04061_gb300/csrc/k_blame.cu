@@ -129,9 +129,22 @@ __global__ void k_search_local(Prog P, Arch A) {
           if (counts(q)) scan_pred(P, A, j, r, gj, b0, P.pred[q], S, pj + 1, true);
         continue;
       }
-      const unsigned long long t = atomicAdd(&P.stats[SS_QUEUE_N], 1ull);
-      if (t < (unsigned long long)P.queue_cap) P.queue[t] = make_int4(j, r, (int)S, 0);
-      else set_status(P, ST_CAPACITY);
+      // A search known to outgrow the first tier goes straight to the tier
+      // that held it before (the second tier's queue, or the third tier's
+      // region at the top of the first queue).
+      const uint32_t hint = P.tier_hint[e];
+      const int4 task = make_int4(j, r, (int)S, e);
+      if (hint >= 3) {
+        const unsigned long long t = atomicAdd(&P.stats[SS_HINT3_N], 1ull);
+        if (t < (unsigned long long)P.queue_cap) P.queue[P.queue_cap - 1 - (int64_t)t] = task;
+        else set_status(P, ST_CAPACITY);
+      } else {
+        const int slot = hint == 2 ? SS_OVF_N : SS_QUEUE_N;
+        int4* q = hint == 2 ? P.ovf_queue : P.queue;
+        const unsigned long long t = atomicAdd(&P.stats[slot], 1ull);
+        if (t < (unsigned long long)P.queue_cap) q[t] = task;
+        else set_status(P, ST_CAPACITY);
+      }
     }
   }
 }

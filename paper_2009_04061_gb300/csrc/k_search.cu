@@ -730,17 +730,22 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32) k_search_warp(Prog P, Arch 
   const int h_slot = tier == 1 ? SS_QUEUE_HEAD : tier == 2 ? SS_OVF_HEAD : tier == 3 ? SS_OVF2_HEAD : SS_OVF3_HEAD;
   unsigned long long nq = P.stats[n_slot];
   if (nq > (unsigned long long)P.queue_cap) nq = (unsigned long long)P.queue_cap;
+  // Tier 3 also takes the searches queued for it directly, stored from the
+  // top of the first queue down.
+  unsigned long long nh = tier == 3 ? P.stats[SS_HINT3_N] : 0ull;
+  if (nh > (unsigned long long)P.queue_cap - nq) nh = (unsigned long long)P.queue_cap - nq;
   while (true) {
     unsigned long long t = 0;
     if (lane == 0) t = atomicAdd(&P.stats[h_slot], 1ull);
     t = __shfl_sync(0xffffffffu, t, 0);
-    if (t >= nq) break;
-    const int4 task = q[t];
+    if (t >= nq + nh) break;
+    const int4 task = t < nq ? q[t] : P.queue[P.queue_cap - 1 - (int64_t)(t - nq)];
     const int f = P.block_func[P.instr_block[task.x]];
     const int bound = P.res_maxlat[(size_t)f * kNumRes + task.y];
     const uint16_t live = live_literals(P.res_guards[(size_t)f * kNumRes + task.y], P.guard[task.x]);
     const bool ok = warp_search(P, A, a, task.x, task.y, (uint16_t)task.z, bound, live, tier);
     if (ok || lane != 0) continue;
+    atomicMax(&P.tier_hint[task.w], (unsigned)(tier + 1));  // later steps queue it for a bigger tier
     if (tier < 3 || (tier == 3 && P.t4_nodes > 0)) {
       const int o_slot = tier == 1 ? SS_OVF_N : tier == 2 ? SS_OVF2_N : SS_OVF3_N;
       int4* oq = tier == 2 ? P.queue : P.ovf_queue;

@@ -424,6 +424,7 @@ static gpa_status alloc_program(const gpa_program_desc* d, ProgramRec* R, int ti
   P.queue_cap = (int64_t)d->n_use + 1;
   TRY(dev_alloc(R, &P.queue, (size_t)P.queue_cap));
   TRY(dev_alloc(R, &P.ovf_queue, (size_t)P.queue_cap));
+  TRY(dev_alloc(R, &P.tier_hint, (size_t)std::max<int64_t>(d->n_use, 1)));
   TRY(dev_alloc(R, &P.edge_off, ni + 1));
   P.edge_cnt = P.edge_off;
   P.edge_cap = P.raw_cap;
@@ -505,6 +506,10 @@ gpa_status gpa_load_program(gpa_ctx* ctx, const gpa_program_desc* d, gpa_pid* ou
   if (cudaMemsetAsync(P.cnt, 0, ni * kCnt * sizeof(unsigned long long), st) != cudaSuccess ||
       cudaMemsetAsync(P.stats, 0, SS_N * sizeof(unsigned long long), st) != cudaSuccess ||
       cudaMemsetAsync(P.edge_off, 0, (ni + 1) * sizeof(int32_t), st) != cudaSuccess) {
+    free_program(R);
+    return GPA_ERR_CUDA;
+  }
+  if (cudaMemsetAsync(P.tier_hint, 0, sizeof(uint32_t) * (size_t)std::max<int64_t>(R->n_use, 1), st) != cudaSuccess) {
     free_program(R);
     return GPA_ERR_CUDA;
   }
@@ -724,7 +729,7 @@ gpa_status gpa_sync_status(gpa_ctx* ctx, gpa_pid pid, gpa_stream stream, int64_t
     info[2] = (int64_t)h[SS_MAX_NODES];
     info[3] = (int64_t)h[SS_SWEEPS];
     info[4] = (int64_t)h[SS_OVF_N];
-    info[5] = (int64_t)h[SS_OVF2_N];
+    info[5] = (int64_t)(h[SS_OVF2_N] + h[SS_HINT3_N]);
     info[6] = (int64_t)(h[SS_MAX_TASK] & 0x7FFFFFFFull);     // use of the largest search
     info[7] = (int64_t)((h[SS_MAX_TASK] >> 31) & 0x1FFull);  // its resource
   }

@@ -159,6 +159,36 @@ def test_small_search_slots_overflow_to_large_tier():
         assert_full_parity(r, oracle_run(P, s))
 
 
+def test_tier_hints_on_repeated_steps():
+    """Searches that outgrew a tier are queued straight for the bigger one on later
+    steps of the same program; every step gives the oracle's results."""
+    import paper_2009_04061_gb300 as g
+    with g.Context(ARCH, dict(small_search_nodes=4, mid_search_nodes=16, max_search_nodes=64, search_slots=64)) as c:
+        rng = np.random.default_rng(13)
+        P = synth.make_program(synth.batched_params(16, rng, 13), 1.0)
+        s = P.samples(1_000_000, seed=13)
+        R = oracle_run(P, s)
+        prog = c.load_program(P)
+        try:
+            d = dev(s)
+            tiers = []
+            for step in range(3):
+                prog.reset()
+                prog.ingest(d)
+                prog.blame()
+                adv = prog.advise(fetch=True)
+                st, info = prog.status()
+                cnt, bad = prog.counts()
+                r = dict(status=st, info=info, counts=cnt, invalid=bad, rin=prog.reaching()[0],
+                         rout=prog.reaching()[1], blame=prog.blame_counts(), edges=prog.edges(), advice=adv)
+                assert_full_parity(r, R)
+                tiers.append((info["tier2_searches"], info["tier3_searches"]))
+            # the first step found the big searches by overflow; later steps queue them directly
+            assert tiers[0][0] > 0 and tiers[1] == tiers[2]
+        finally:
+            prog.unload()
+
+
 def test_fourth_tier_program_arena():
     """A third tier of 32 nodes sends the larger searches on to the program's own
     fourth tier (sized from its largest function); results stay exact."""
