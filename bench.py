@@ -367,7 +367,8 @@ def main():
         step()
     st, info = prog.status(stream)
     if st != 0:
-        raise SystemExit(f"device status {st} after warm-up: {info}")
+        raise SystemExit(f"device status {st} after warm-up: {info}; search overflow bits "
+                         f"{prog.search_profile(stream)['overflow_bits']:#x}")
     cnt, bad = prog.counts(stream)
     assert int(cnt.sum()) + bad == n, "counts do not add up to the samples ingested"
 

@@ -100,7 +100,7 @@ typedef struct {
   int32_t max_fixpoint_sweeps;  /* reaching-definitions sweep limit; 0 = 64 */
   int32_t max_search_nodes;     /* (block, predicate-set) nodes of the largest general search; 0 = 32768 */
   int32_t search_slots;         /* warps with a max_search_nodes global-memory arena; 0 = four per SM */
-  int32_t max_sources_per_use;  /* distinct sources merged per stalled use; 0 = 64 (max 64) */
+  int32_t max_sources_per_use;  /* distinct sources merged per stalled use; 0 = 2048 (max 2048) */
   int32_t small_search_nodes;   /* nodes of the shared-memory arena of a first-tier search warp; 0 = 128
                                    (max 1024). A search that outgrows it is redone in the next tier */
   int32_t mid_search_nodes;     /* nodes of the second tier's shared-memory arenas (three warps per SM
@@ -286,7 +286,9 @@ gpa_status gpa_step_launch(gpa_ctx* ctx, gpa_pid pid, gpa_stream stream);
  * graph past the latency bound; out[35] = the slowest search's cycles << 20 |
  * its nodes, out[36] its rule-2 runs, out[37..41] its cycles in the first
  * five phases; out[42..57] the cycles of the searches by floor(log2(nodes)).
- * out must hold 58 values. All zero unless the
+ * out[58] (kept in every build): why searches outgrew their arena in the last
+ * gpa_blame, bit 1 nodes, 2 edges, 3 occurrences, 4 sources, 5 back-edge
+ * layers, 6 hash round limit. out must hold 59 values. The others are zero unless the
  * library was built with -DGPA_PHASE_TIMING (the timers cost a few atomics per
  * search). Synchronizes stream. */
 gpa_status gpa_get_search_profile(gpa_ctx* ctx, gpa_pid pid, uint64_t* out, gpa_stream stream);

@@ -15,7 +15,9 @@ constexpr int kWords = 9;        // 268 bits in 32-bit words
 constexpr int kCnt = 24;         // counters per instruction: class * 2 + latency flag
 constexpr uint16_t kAllLits = 0xFFFF;
 constexpr int kMaxLayers = 8;    // back-edge layers for longest paths (K <= 7)
-constexpr int kMaxSrc = 64;      // merged sources per stalled use (hard upper bound)
+constexpr int kMaxSrc = 64;      // merged sources per stalled use in the thread-per-use kernels
+constexpr int kBigSrc = 2048;    // merged sources per stalled use (hard upper bound; beyond kMaxSrc
+                                 // a CTA per use with shared-memory arrays)
 
 // Bits of the per-program device status word.
 enum : unsigned long long {
@@ -38,7 +40,12 @@ enum {
   SS_OVF3_N = 56, SS_OVF3_HEAD = 57,  // searches handed on to the program's own fourth tier
   SS_SIZE_CYC = 58,  // with -DGPA_PHASE_TIMING: cycles of the searches by log2 of their node count (16)
   SS_HINT3_N = 74,   // searches queued straight for the third tier (from the top of `queue`)
-  SS_N = 75
+  SS_FAILBITS = 75,  // why a step reported GPA_ERR_CAPACITY: the last search tier ran out of
+                     // 1 nodes, 2 edges, 3 occurrences, 4 sources, 5 back-edge layers,
+                     // 6 hash rounds; 8 queue, 9 sources per use, 10 merged edges,
+                     // 11 distance range, 12 raw edges, 13 no path length
+  SS_BIG_N = 76,     // uses with more than kMaxSrc distinct sources (listed in big_use)
+  SS_N = 77
 };
 
 struct Arch {
@@ -105,6 +112,7 @@ struct Prog {
   int4* ovf_queue;                // general searches that outgrew a small scratch slot
   int64_t queue_cap;
   int32_t* edge_cnt;              // ni + 1 (exclusive scan in place -> offsets)
+  int32_t* big_use;               // ni: uses with more than kMaxSrc sources (SS_BIG_N of them)
   int32_t* edge_off;              // ni + 1
   int32_t* e_use;
   int32_t* e_def;
@@ -137,6 +145,11 @@ struct SearchArena {
 
 __device__ __forceinline__ void set_status(const Prog& P, unsigned long long bits) {
   atomicOr(&P.stats[SS_STATUS], bits);
+}
+// GPA_ERR_CAPACITY with its reason (bit `why` of SS_FAILBITS).
+__device__ __forceinline__ void capacity(const Prog& P, int why) {
+  atomicOr(&P.stats[SS_STATUS], (unsigned long long)ST_CAPACITY);
+  atomicOr(&P.stats[SS_FAILBITS], 1ull << why);
 }
 
 // ---------------------------------------------------------------- Sec. 4 predicate literals
@@ -199,9 +212,9 @@ __device__ __forceinline__ void emit_raw(const Prog& P, const Arch& A, int j, in
       if (rr < kPredBase && uses_res(P, i, rr)) { fl |= 1u; break; }
     }
   }
-  if (dmin >= (1 << 24) || dlong >= (1 << 24)) { set_status(P, ST_CAPACITY); return; }
+  if (dmin >= (1 << 24) || dlong >= (1 << 24)) { capacity(P, 11); return; }
   const unsigned long long slot = atomicAdd(&P.stats[SS_RAW_N], 1ull);
-  if (slot >= (unsigned long long)P.raw_cap) { set_status(P, ST_CAPACITY); return; }
+  if (slot >= (unsigned long long)P.raw_cap) { capacity(P, 12); return; }
   const int next = atomicExch(&P.head[j], (int)slot);
   P.raw[slot] = make_int4(i, next, dmin, dlong | (int)(fl << 24));
 }

@@ -137,13 +137,13 @@ __global__ void k_search_local(Prog P, Arch A) {
       if (hint >= 3) {
         const unsigned long long t = atomicAdd(&P.stats[SS_HINT3_N], 1ull);
         if (t < (unsigned long long)P.queue_cap) P.queue[P.queue_cap - 1 - (int64_t)t] = task;
-        else set_status(P, ST_CAPACITY);
+        else capacity(P, 8);
       } else {
         const int slot = hint == 2 ? SS_OVF_N : SS_QUEUE_N;
         int4* q = hint == 2 ? P.ovf_queue : P.queue;
         const unsigned long long t = atomicAdd(&P.stats[slot], 1ull);
         if (t < (unsigned long long)P.queue_cap) q[t] = task;
-        else set_status(P, ST_CAPACITY);
+        else capacity(P, 8);
       }
     }
   }
@@ -160,136 +160,196 @@ __global__ void k_blame_init(Prog P) {
   }
 }
 
-__global__ void k_merge_count(Prog P, int max_src) {
-  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < P.ni; j += gridDim.x * blockDim.x) {
-    int c = 0;
-    int ids[kMaxSrc];
-    for (int t = P.head[j]; t >= 0; t = P.raw[t].y) {
-      const int i = P.raw[t].x;
-      bool seen = false;
-      for (int q = 0; q < c; ++q) seen |= ids[q] == i;
-      if (seen) continue;
-      if (c >= max_src) { set_status(P, ST_CAPACITY); break; }
-      ids[c++] = i;
-    }
-    P.edge_off[j] = c;
-  }
-}
-
 __device__ __forceinline__ void blame_add(unsigned long long* addr, unsigned long long v) {
   cg::coalesced_group g = cg::coalesced_threads();
   cg::coalesced_group grp = cg::labeled_partition(g, (unsigned long long)(uintptr_t)addr);
   const unsigned long long sum = cg::reduce(grp, v, cg::plus<unsigned long long>());
   if (grp.thread_rank() == 0) atomicAdd(addr, sum);
 }
-
 __device__ __forceinline__ bool opcode_keeps(const Arch& A, int cls, int op) {
   if (cls == GPA_MEMORY_DEPENDENCY || cls == GPA_CONSTANT_MEMORY_DEPENDENCY) return (A.flags[op] & GPA_F_MEM) != 0;
   if (cls == GPA_SYNC) return (A.flags[op] & GPA_F_SYNC) != 0;
   return true;
 }
 
-__global__ void k_apportion(Prog P, Arch A, int max_src) {
+// Distinct sources of use j over its raw edge list, using ids[cap] as scratch:
+// the count, or -1 if there are more than cap.
+__device__ int distinct_sources(const Prog& P, int j, int* ids, int cap) {
+  int c = 0;
+  for (int t = P.head[j]; t >= 0; t = P.raw[t].y) {
+    const int i = P.raw[t].x;
+    bool seen = false;
+    for (int q = 0; q < c; ++q) seen |= ids[q] == i;
+    if (seen) continue;
+    if (c >= cap) return -1;
+    ids[c++] = i;
+  }
+  return c;
+}
+
+// Uses with more distinct sources than a thread's arrays hold are listed for
+// k_merge_big / k_apportion_big (shared-memory arrays, one CTA per use).
+__global__ void k_merge_count(Prog P, int max_src) {
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < P.ni; j += gridDim.x * blockDim.x) {
-    const unsigned long long* cj = P.cnt + (size_t)j * kCnt;
-    const int off = P.edge_off[j];
-    int c = P.edge_off[j + 1] - off;
-    if (c == 0 && !stalled(P, j)) continue;
-    if (off + c > P.edge_cap) { set_status(P, ST_CAPACITY); c = 0; }
-    int mi[kMaxSrc], md[kMaxSrc], ml[kMaxSrc];
-    uint32_t mf[kMaxSrc];
-    int m = 0;
-    if (c > 0) {
-      for (int t = P.head[j]; t >= 0; t = P.raw[t].y) {
-        const int4 R = P.raw[t];
-        const int dl = R.w & 0xFFFFFF;
-        const uint32_t fl = (uint32_t)R.w >> 24;
-        int q = 0;
-        while (q < m && mi[q] != R.x) ++q;
-        if (q == m) {
-          if (m >= c) continue;  // capacity already reported by the count pass
-          mi[m] = R.x; md[m] = R.z; ml[m] = dl; mf[m] = fl; ++m;
-        } else {
-          md[q] = min(md[q], R.z); ml[q] = max(ml[q], dl); mf[q] |= fl;
-        }
-      }
-      // ascending def index
-      for (int a = 1; a < m; ++a) {
-        const int xi = mi[a], xd = md[a], xl = ml[a];
-        const uint32_t xf = mf[a];
-        int b = a - 1;
-        while (b >= 0 && mi[b] > xi) { mi[b + 1] = mi[b]; md[b + 1] = md[b]; ml[b + 1] = ml[b]; mf[b + 1] = mf[b]; --b; }
-        mi[b + 1] = xi; md[b + 1] = xd; ml[b + 1] = xl; mf[b + 1] = xf;
-      }
-      for (int t = 0; t < m; ++t) {
-        const int64_t e = off + t;
-        P.e_use[e] = j; P.e_def[e] = mi[t]; P.e_dmin[e] = md[t]; P.e_dlong[e] = ml[t]; P.e_flags[e] = mf[t];
-#pragma unroll
-        for (int q = 0; q < 8; ++q) P.e_share[e * 8 + q] = 0ull;
+    int ids[kMaxSrc];
+    int c = distinct_sources(P, j, ids, min(max_src, kMaxSrc));
+    if (c < 0 && max_src > kMaxSrc) {
+      const unsigned long long k = atomicAdd(&P.stats[SS_BIG_N], 1ull);
+      P.big_use[k] = j;  // k < ni: each use is listed at most once
+      c = 0;             // k_merge_big writes the count
+    } else if (c < 0) {
+      capacity(P, 9);
+      c = 0;
+    }
+    P.edge_off[j] = c;
+  }
+}
+
+__global__ void k_merge_big(Prog P, int max_src) {
+  __shared__ int ids[kBigSrc];
+  const unsigned long long nbig = P.stats[SS_BIG_N];
+  for (unsigned long long k = blockIdx.x; k < nbig; k += gridDim.x) {
+    if (threadIdx.x == 0) {
+      const int j = P.big_use[k];
+      int c = distinct_sources(P, j, ids, min(max_src, kBigSrc));
+      if (c < 0) { capacity(P, 9); c = 0; }
+      P.edge_off[j] = c;
+    }
+    __syncthreads();
+  }
+}
+
+// Merged edges of use j (ascending def index) and Eq. 1 shares of each of its
+// dependency classes and latency flags, with arrays of capacity cap.
+__device__ void apportion_use(const Prog& P, const Arch& A, int j, int off, int c, int* mi, int* md, int* ml,
+                              uint32_t* mf, int* sel, unsigned long long* wt, unsigned __int128* rem,
+                              unsigned long long* sh) {
+  const unsigned long long* cj = P.cnt + (size_t)j * kCnt;
+  int m = 0;
+  if (c > 0) {
+    for (int t = P.head[j]; t >= 0; t = P.raw[t].y) {
+      const int4 R = P.raw[t];
+      const int dl = R.w & 0xFFFFFF;
+      const uint32_t fl = (uint32_t)R.w >> 24;
+      int q = 0;
+      while (q < m && mi[q] != R.x) ++q;
+      if (q == m) {
+        if (m >= c) continue;  // capacity already reported by the count pass
+        mi[m] = R.x; md[m] = R.z; ml[m] = dl; mf[m] = fl; ++m;
+      } else {
+        md[q] = min(md[q], R.z); ml[q] = max(ml[q], dl); mf[q] |= fl;
       }
     }
-    for (int ci = 0; ci < 4; ++ci) {
-      const int cls = dep_class(ci);
-      for (int lat = 0; lat < 2; ++lat) {
-        const unsigned long long S = cj[cls * 2 + lat];
-        if (!S) continue;
-        int sel[kMaxSrc];
-        int ns = 0;
-        for (int t = 0; t < m; ++t)
-          if (opcode_keeps(A, cls, P.opclass[mi[t]])) sel[ns++] = t;
-        if (ns == 0) {  // no surviving source: the samples stay on j
-          blame_add(P.blame + (size_t)j * kCnt + cls * 2 + lat, S);
-          continue;
-        }
-        // Eq. 1: weight = issued samples / longest path, in units of 2^-20.
-        unsigned long long wt[kMaxSrc];
-        unsigned __int128 W = 0;
+    // ascending def index
+    for (int a = 1; a < m; ++a) {
+      const int xi = mi[a], xd = md[a], xl = ml[a];
+      const uint32_t xf = mf[a];
+      int b = a - 1;
+      while (b >= 0 && mi[b] > xi) { mi[b + 1] = mi[b]; md[b + 1] = md[b]; ml[b + 1] = ml[b]; mf[b + 1] = mf[b]; --b; }
+      mi[b + 1] = xi; md[b + 1] = xd; ml[b + 1] = xl; mf[b + 1] = xf;
+    }
+    for (int t = 0; t < m; ++t) {
+      const int64_t e = off + t;
+      P.e_use[e] = j; P.e_def[e] = mi[t]; P.e_dmin[e] = md[t]; P.e_dlong[e] = ml[t]; P.e_flags[e] = mf[t];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) P.e_share[e * 8 + q] = 0ull;
+    }
+  }
+  for (int ci = 0; ci < 4; ++ci) {
+    const int cls = dep_class(ci);
+    for (int lat = 0; lat < 2; ++lat) {
+      const unsigned long long S = cj[cls * 2 + lat];
+      if (!S) continue;
+      int ns = 0;
+      for (int t = 0; t < m; ++t)
+        if (opcode_keeps(A, cls, P.opclass[mi[t]])) sel[ns++] = t;
+      if (ns == 0) {  // no surviving source: the samples stay on j
+        blame_add(P.blame + (size_t)j * kCnt + cls * 2 + lat, S);
+        continue;
+      }
+      // Eq. 1: weight = issued samples / longest path, in units of 2^-20.
+      unsigned __int128 W = 0;
+      for (int q = 0; q < ns; ++q) {
+        const unsigned long long issue = P.cnt[(size_t)mi[sel[q]] * kCnt];
+        const unsigned long long len = (unsigned long long)max(ml[sel[q]], 1);
+        if (issue >> 43) set_status(P, ST_OVERFLOW);
+        wt[q] = (unsigned long long)(((unsigned __int128)issue << 20) / len);
+        W += wt[q];
+      }
+      if (W == 0) {
         for (int q = 0; q < ns; ++q) {
-          const unsigned long long issue = P.cnt[(size_t)mi[sel[q]] * kCnt];
-          const unsigned long long len = (unsigned long long)max(ml[sel[q]], 1);
-          if (issue >> 43) set_status(P, ST_OVERFLOW);
-          wt[q] = (unsigned long long)(((unsigned __int128)issue << 20) / len);
+          wt[q] = (1ull << 20) / (unsigned long long)max(ml[sel[q]], 1);
           W += wt[q];
         }
-        if (W == 0) {
-          for (int q = 0; q < ns; ++q) {
-            wt[q] = (1ull << 20) / (unsigned long long)max(ml[sel[q]], 1);
-            W += wt[q];
-          }
-        }
-        if (W == 0) {
-          for (int q = 0; q < ns; ++q) wt[q] = 1ull;
-          W = (unsigned __int128)ns;
-        }
-        unsigned __int128 rem[kMaxSrc];
-        unsigned long long sh[kMaxSrc];
-        unsigned long long given = 0;
+      }
+      if (W == 0) {
+        for (int q = 0; q < ns; ++q) wt[q] = 1ull;
+        W = (unsigned __int128)ns;
+      }
+      unsigned long long given = 0;
+      for (int q = 0; q < ns; ++q) {
+        const unsigned __int128 num = (unsigned __int128)S * wt[q];
+        sh[q] = (unsigned long long)(num / W);
+        rem[q] = num % W;
+        given += sh[q];
+      }
+      // Largest remainders get the leftover units; ties go to the lower def index.
+      unsigned long long left = S - given;
+      while (left > 0) {
+        int best = -1;
         for (int q = 0; q < ns; ++q) {
-          const unsigned __int128 num = (unsigned __int128)S * wt[q];
-          sh[q] = (unsigned long long)(num / W);
-          rem[q] = num % W;
-          given += sh[q];
+          if (rem[q] == (unsigned __int128)-1) continue;
+          if (best < 0 || rem[q] > rem[best]) best = q;  // sel is in ascending def order
         }
-        // Largest remainders get the leftover units; ties go to the lower def index.
-        unsigned long long left = S - given;
-        while (left > 0) {
-          int best = -1;
-          for (int q = 0; q < ns; ++q) {
-            if (rem[q] == (unsigned __int128)-1) continue;
-            if (best < 0 || rem[q] > rem[best]) best = q;  // sel is in ascending def order
-          }
-          if (best < 0) break;  // cannot happen: fewer leftover units than sources
-          sh[best] += 1;
-          rem[best] = (unsigned __int128)-1;
-          --left;
-        }
-        for (int q = 0; q < ns; ++q) {
-          const int t = sel[q];
-          P.e_share[(int64_t)(off + t) * 8 + ci * 2 + lat] = sh[q];
-          if (sh[q]) blame_add(P.blame + (size_t)mi[t] * kCnt + cls * 2 + lat, sh[q]);
-        }
+        if (best < 0) break;  // cannot happen: fewer leftover units than sources
+        sh[best] += 1;
+        rem[best] = (unsigned __int128)-1;
+        --left;
+      }
+      for (int q = 0; q < ns; ++q) {
+        const int t = sel[q];
+        P.e_share[(int64_t)(off + t) * 8 + ci * 2 + lat] = sh[q];
+        if (sh[q]) blame_add(P.blame + (size_t)mi[t] * kCnt + cls * 2 + lat, sh[q]);
       }
     }
+  }
+}
+
+__global__ void k_apportion(Prog P, Arch A, int max_src) {
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < P.ni; j += gridDim.x * blockDim.x) {
+    const int off = P.edge_off[j];
+    int c = P.edge_off[j + 1] - off;
+    if (c > kMaxSrc) continue;  // k_apportion_big
+    if (c == 0 && !stalled(P, j)) continue;
+    if (off + c > P.edge_cap) { capacity(P, 10); c = 0; }
+    int mi[kMaxSrc], md[kMaxSrc], ml[kMaxSrc], sel[kMaxSrc];
+    uint32_t mf[kMaxSrc];
+    unsigned long long wt[kMaxSrc], sh[kMaxSrc];
+    unsigned __int128 rem[kMaxSrc];
+    apportion_use(P, A, j, off, c, mi, md, ml, mf, sel, wt, rem, sh);
+  }
+}
+
+__global__ void k_apportion_big(Prog P, Arch A) {
+  extern __shared__ __align__(16) unsigned char big_sm[];
+  unsigned __int128* rem = reinterpret_cast<unsigned __int128*>(big_sm);
+  unsigned long long* wt = reinterpret_cast<unsigned long long*>(rem + kBigSrc);
+  unsigned long long* sh = wt + kBigSrc;
+  int* mi = reinterpret_cast<int*>(sh + kBigSrc);
+  int* md = mi + kBigSrc;
+  int* ml = md + kBigSrc;
+  int* sel = ml + kBigSrc;
+  uint32_t* mf = reinterpret_cast<uint32_t*>(sel + kBigSrc);
+  const unsigned long long nbig = P.stats[SS_BIG_N];
+  for (unsigned long long k = blockIdx.x; k < nbig; k += gridDim.x) {
+    if (threadIdx.x == 0) {
+      const int j = P.big_use[k];
+      const int off = P.edge_off[j];
+      int c = P.edge_off[j + 1] - off;
+      if (off + c > P.edge_cap) { capacity(P, 10); c = 0; }
+      if (c > kMaxSrc) apportion_use(P, A, j, off, c, mi, md, ml, mf, sel, wt, rem, sh);
+    }
+    __syncthreads();
   }
 }
 
@@ -305,10 +365,14 @@ void launch_blame(const Prog& P, const Arch& A, const SearchArena* tiers, int ma
   *launches += 2;
   launch_search(P, A, tiers, st, launches);
   k_merge_count<<<g_instr, threads, 0, st>>>(P, max_src);
-  ++*launches;
+  k_merge_big<<<sms, 32, 0, st>>>(P, max_src);
+  *launches += 2;
   scan_exclusive_inplace(P.edge_off, P.ni, scan_tmp, st, launches);
   k_apportion<<<g_instr, threads, 0, st>>>(P, A, max_src);
-  ++*launches;
+  const size_t big_smem = (size_t)kBigSrc * (16 + 8 + 8 + 4 * 5);
+  allow_max_smem(k_apportion_big);
+  k_apportion_big<<<sms, 32, big_smem, st>>>(P, A);
+  *launches += 2;
 }
 
 }  // namespace gpa

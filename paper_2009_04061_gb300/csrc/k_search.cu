@@ -184,7 +184,7 @@ __device__ bool warp_search(const Prog& P, const Arch& A, const Arena& a, int j,
               last_def_pos = pos;
               if (!contains(S, gj) && !(B == b0 && x < j)) {  // sources above j in its block are settled
                 const int o = atomicAdd((int*)&a.ctr[2], 1);
-                if (o < a.O) { a.on[o] = u; a.ox[o] = x; } else { a.ctr[4] = 1; }
+                if (o < a.O) { a.on[o] = u; a.ox[o] = x; } else { a.ctr[4] = 3; }
               }
               S = add_literal(S, (int)((ev >> 12) & 0xFu));
               if (contains(S, gj)) { stop = true; cov = x; }
@@ -224,7 +224,7 @@ __device__ bool warp_search(const Prog& P, const Arch& A, const Arena& a, int j,
     }
     const int total = __shfl_sync(0xffffffffu, incl, 31);
     const int ne = ctr[1];
-    if (ne + total > a.E) { if (lane == 0) ctr[4] = 1; __syncwarp(); return; }
+    if (ne + total > a.E) { if (lane == 0) ctr[4] = 2; __syncwarp(); return; }
     if (mine) { a.e0[u] = ne + incl - deg; a.e1[u] = ne + incl; }
     int maxdeg = deg;
     for (int o = 16; o > 0; o >>= 1) maxdeg = max(maxdeg, __shfl_xor_sync(0xffffffffu, maxdeg, o));
@@ -265,7 +265,7 @@ __device__ bool warp_search(const Prog& P, const Arch& A, const Arena& a, int j,
         }
         __syncwarp();
       }
-      if (pending) a.ctr[4] = 1;  // the round limit is a bound, not expected to be reached
+      if (pending) a.ctr[4] = 6;  // the round limit is a bound, not expected to be reached
       if (kk < deg && v >= 0) a.eto[a.e0[u] + kk] = v | (p >= B ? (int)kBackBit : 0);
     }
     __syncwarp();
@@ -415,7 +415,11 @@ __device__ bool warp_search(const Prog& P, const Arch& A, const Arena& a, int j,
 #endif
   }
   phase(0);
-  if (ctr[4]) return false;
+  if (ctr[4]) {
+    if (lane == 0) ctr[7] = ctr[4];
+    __syncwarp();
+    return false;
+  }
   if (!cand) return true;
 
   // Shortest distance with parents, and fewest back edges, over the whole graph.
@@ -454,7 +458,7 @@ __device__ bool warp_search(const Prog& P, const Arch& A, const Arena& a, int j,
           if (atomicCAS(&a.ht[h], -1, -2 - lane) == -1) {
             const int nm = atomicAdd((int*)&a.ctr[5], 1);
             if (nm >= a.SRC) {
-              a.ctr[4] = 1; a.ht[h] = -1; pending = false;
+              a.ctr[4] = 4; a.ht[h] = -1; pending = false;
             } else {
               a.si[nm] = x; a.sk[nm] = kInf; a.shead[nm] = -1; a.sp[nm] = 0;
               a.sdb[nm] = ~0ull;
@@ -468,7 +472,7 @@ __device__ bool warp_search(const Prog& P, const Arch& A, const Arena& a, int j,
       }
       __syncwarp();
     }
-    if (pending) a.ctr[4] = 1;
+    if (pending) a.ctr[4] = 6;
     if (m >= 0) {
       const int u = a.on[o];
       const int dist = dist_of(a, u) + (last_of(u) - x);
@@ -483,7 +487,11 @@ __device__ bool warp_search(const Prog& P, const Arch& A, const Arena& a, int j,
     for (int t = lane; t < nh2; t += 32) a.ht[a.hused[t]] = -1;
   }
   __syncwarp();
-  if (ctr[4]) return false;
+  if (ctr[4]) {
+    if (lane == 0) ctr[7] = ctr[4];
+    __syncwarp();
+    return false;
+  }
   const int nsrc = ctr[5];
   int alive = 0;
   for (int m = lane; m < nsrc; m += 32) {
@@ -526,7 +534,7 @@ __device__ bool warp_search(const Prog& P, const Arch& A, const Arena& a, int j,
       }
       __syncwarp();
     }
-    if (pending) a.ctr[4] = 1;
+    if (pending) a.ctr[4] = 6;
     if (u < n) a.grp[u] = g;
     if (g >= 0) atomicMax(&a.wpos[g], a.wall[u]);
     __syncwarp();
@@ -536,7 +544,11 @@ __device__ bool warp_search(const Prog& P, const Arch& A, const Arena& a, int j,
     for (int t = lane; t < nh2; t += 32) a.ht[a.hused[t]] = -1;
   }
   __syncwarp();
-  if (ctr[4]) return false;
+  if (ctr[4]) {
+    if (lane == 0) ctr[7] = ctr[4];
+    __syncwarp();
+    return false;
+  }
   const int nw = ctr[5];
   for (int m = lane; m < nsrc; m += 32) {
     if (a.sp[m]) continue;
@@ -640,7 +652,11 @@ __device__ bool warp_search(const Prog& P, const Arch& A, const Arena& a, int j,
   int maxK = 0;
   for (int m = lane; m < nsrc; m += 32) if (!a.sp[m]) maxK = max(maxK, a.sk[m]);
   for (int o = 16; o > 0; o >>= 1) maxK = max(maxK, __shfl_xor_sync(0xffffffffu, maxK, o));
-  if (maxK >= a.L) return false;
+  if (maxK >= a.L) {
+    if (lane == 0) ctr[7] = 5;
+    __syncwarp();
+    return false;
+  }
   for (int t = lane; t < (maxK + 1) * n; t += 32) a.dl[(t / n) * a.N + (t % n)] = -1;
   for (int u = lane; u < n; u += 32) a.ord[u] = 0;
   __syncwarp();
@@ -699,7 +715,7 @@ __device__ bool warp_search(const Prog& P, const Arch& A, const Arena& a, int j,
       const int dlu = a.dl[(int64_t)K * a.N + u];
       if (dlu >= 0) best = max(best, dlu + last_of(u) - a.ox[o]);
     }
-    if (best < 1) { set_status(P, ST_CAPACITY); continue; }
+    if (best < 1) { capacity(P, 13); continue; }
     emit_raw(P, A, j, a.si[m], r, def_kind(P, a.si[m], r), (int)(a.sdb[m] >> 32), best);
   }
   __syncwarp();
@@ -750,9 +766,9 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32) k_search_warp(Prog P, Arch 
       const int o_slot = tier == 1 ? SS_OVF_N : tier == 2 ? SS_OVF2_N : SS_OVF3_N;
       int4* oq = tier == 2 ? P.queue : P.ovf_queue;
       const unsigned long long o = atomicAdd(&P.stats[o_slot], 1ull);
-      if (o < (unsigned long long)P.queue_cap) oq[o] = task; else set_status(P, ST_CAPACITY);
+      if (o < (unsigned long long)P.queue_cap) oq[o] = task; else capacity(P, 8);
     } else {
-      set_status(P, ST_CAPACITY);
+      capacity(P, s_ctr[wid][7] > 0 ? s_ctr[wid][7] : 1);  // the last tier: why it ran out
     }
   }
 }

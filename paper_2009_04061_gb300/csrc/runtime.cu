@@ -258,7 +258,7 @@ gpa_status gpa_create(const gpa_arch_desc* arch, const gpa_options* opts, gpa_ct
     for (int r : o.reserved)
       if (r) return GPA_ERR_INVALID_ARG;
     if (o.max_fixpoint_sweeps < 0 || o.max_search_nodes < 0 || o.search_slots < 0 || o.max_sources_per_use < 0 ||
-        o.max_sources_per_use > kMaxSrc || o.small_search_nodes < 0 || o.mid_search_nodes < 0 ||
+        o.max_sources_per_use > kBigSrc || o.small_search_nodes < 0 || o.mid_search_nodes < 0 ||
         o.hist_variant < 0 || o.hist_variant > 3)
       return GPA_ERR_INVALID_ARG;
   }
@@ -274,7 +274,7 @@ gpa_status gpa_create(const gpa_arch_desc* arch, const gpa_options* opts, gpa_ct
   if (o.max_fixpoint_sweeps == 0) o.max_fixpoint_sweeps = 64;
   if (o.max_search_nodes == 0) o.max_search_nodes = 32768;
   if (o.search_slots == 0) o.search_slots = 4 * c->sms;
-  if (o.max_sources_per_use == 0) o.max_sources_per_use = kMaxSrc;
+  if (o.max_sources_per_use == 0) o.max_sources_per_use = kBigSrc;
   if (o.small_search_nodes == 0) o.small_search_nodes = 128;
   c->opts = o;
   // Tier 1: four warps per CTA with small shared-memory arenas, three CTAs per
@@ -426,6 +426,7 @@ static gpa_status alloc_program(const gpa_program_desc* d, ProgramRec* R, int ti
   TRY(dev_alloc(R, &P.ovf_queue, (size_t)P.queue_cap));
   TRY(dev_alloc(R, &P.tier_hint, (size_t)std::max<int64_t>(d->n_use, 1)));
   TRY(dev_alloc(R, &P.edge_off, ni + 1));
+  TRY(dev_alloc(R, &P.big_use, ni));
   P.edge_cnt = P.edge_off;
   P.edge_cap = P.raw_cap;
   TRY(dev_alloc(R, &P.e_use, (size_t)P.edge_cap));
@@ -446,18 +447,19 @@ static gpa_status alloc_program(const gpa_program_desc* d, ProgramRec* R, int ti
   TRY(dev_alloc(R, &P.a_loop_speedup, nl));
   TRY(dev_alloc(R, &P.a_line_stall, (size_t)P.n_lines));
   TRY(dev_alloc(R, &P.a_line_lat, (size_t)P.n_lines));
-  // Fourth search tier: room for 16 literal sets per block of the largest
-  // function, when that is more than the context's third tier holds.
+  // Fourth search tier: room for 64 literal sets per block of the largest
+  // function (at most 2^22 nodes), when that is more than the context's
+  // third tier holds; fewer warps for bigger arenas (about 2 GB at most).
   {
     int64_t mb = 1;
     for (int f = 0; f < d->n_functions; ++f) mb = std::max<int64_t>(mb, d->func_block_off[f + 1] - d->func_block_off[f]);
     int64_t n4 = 2;
-    while (n4 < 16 * mb && n4 < ((int64_t)1 << 20)) n4 <<= 1;
+    while (n4 < 64 * mb && n4 < ((int64_t)1 << 22)) n4 <<= 1;
     P.t4_nodes = 0; P.t4_arena = nullptr; P.t4_bytes = 0; P.t4_warps = 0; P.t4_src = 0;
     if (n4 > tier3_nodes) {
       P.t4_nodes = (int32_t)n4;
       P.t4_src = (int32_t)std::min<int64_t>(n4, 4096);
-      P.t4_warps = 16;
+      P.t4_warps = n4 <= ((int64_t)1 << 18) ? 16 : n4 <= ((int64_t)1 << 20) ? 8 : 4;
       P.t4_bytes = search_arena_bytes(P.t4_nodes, P.t4_src, kMaxLayers);
       TRY(dev_alloc(R, &P.t4_arena, (size_t)P.t4_bytes * P.t4_warps));
     }
@@ -743,6 +745,7 @@ gpa_status gpa_get_search_profile(gpa_ctx* ctx, gpa_pid pid, uint64_t* out, gpa_
   CK(cudaStreamSynchronize((cudaStream_t)stream));
   CK(cudaMemcpy(out, R->P.stats + SS_PHASE, 42 * sizeof(uint64_t), cudaMemcpyDeviceToHost));
   CK(cudaMemcpy(out + 42, R->P.stats + SS_SIZE_CYC, 16 * sizeof(uint64_t), cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(out + 58, R->P.stats + SS_FAILBITS, sizeof(uint64_t), cudaMemcpyDeviceToHost));
   return GPA_OK;
 }
 

@@ -294,12 +294,12 @@ def gpa_step_launch(ctx, pid, stream=None):
 def gpa_get_search_profile(ctx, pid, stream=None) -> np.ndarray:
     """Search diagnostics (zeros unless built with -DGPA_PHASE_TIMING): per-tier phase
     cycles, shape (3, 6); searches by log2 of their node count (16); searches past the bound."""
-    out = np.zeros(58, np.uint64)
+    out = np.zeros(59, np.uint64)
     _check(library().gpa_get_search_profile(ctx, pid, _p(out), _stream(stream)), "gpa_get_search_profile")
     return dict(phases=out[:18].reshape(3, 6), sizes=out[18:34], pass_b=int(out[34]),
                 slowest=dict(cycles=int(out[35]) >> 20, nodes=int(out[35]) & 0xFFFFF, rule2_runs=int(out[36]),
                              phase_cycles=[int(x) for x in out[37:42]]),
-                size_cycles=out[42:58])
+                size_cycles=out[42:58], overflow_bits=int(out[58]))
 
 
 def gpa_get_counts(ctx, pid, n_instr: int, stream=None):

@@ -189,6 +189,24 @@ def test_tier_hints_on_repeated_steps():
             prog.unload()
 
 
+def test_use_with_many_sources(ctx):
+    """A use with 70 surviving sources (past the thread-per-use arrays) is merged and
+    apportioned by the shared-memory path, bit for bit like the oracle."""
+    import test_oracle as T
+    body = [I("ISETP", ["P0"], ["R9"]), I("ISETP", ["P1"], ["R9"])]
+    body += [I("LDG", ["R1"], ["R2", "R3"], guard="P0") for _ in range(70)]
+    body += [I("IADD", ["R4"], ["R1", "R5"], guard="P1")]
+    prog = T.one_block(body)
+    j = len(body) - 1
+    ss = [(j << 24) | (3 << 20)] * 1000 + [(j << 24) | (3 << 20) | (1 << 19)] * 777
+    ss += [((2 + k) << 24) for k in range(70) for _ in range(k + 1)]   # issued samples of the loads
+    s = np.array(ss, dtype=np.uint64)
+    g = gpu_run(ctx, prog, dev(s))
+    R = oracle_run(prog, s)
+    assert len(R["edges"]["j"]) == 70
+    assert_full_parity(g, R)
+
+
 def test_fourth_tier_program_arena():
     """A third tier of 32 nodes sends the larger searches on to the program's own
     fourth tier (sized from its largest function); results stay exact."""
