@@ -52,6 +52,7 @@ def _L():
         lib.oracle_histogram.argtypes = [vp, vp, i64, vp, vp]
         lib.oracle_reaching.argtypes = [vp, i32, i32, vp, vp]
         lib.oracle_search.argtypes = [vp, i32, i32, i32, vp, vp, vp, vp, vp]
+        lib.oracle_coverage.argtypes = [vp, vp, vp, i32, i32, vp]
         lib.oracle_check_loops.argtypes = [vp, i32]
         lib.oracle_analyze.argtypes = [vp, vp, vp, i32, i32]
         lib.oracle_analyze.restype = vp
@@ -128,6 +129,18 @@ def reaching(prog, f_lo: int = 0, f_hi: int | None = None):
     rout = np.zeros(nb * 9, dtype=np.uint32)
     _L().oracle_reaching(b.ref, f_lo, f_hi, _p(rin), _p(rout))
     return rin.reshape(-1, 9), rout.reshape(-1, 9)
+
+
+def coverage(prog, arch, cnt: np.ndarray, f_lo: int = 0, f_hi: int | None = None) -> tuple[int, int, int]:
+    """Single dependency coverage (Sec. 6): (stalled uses, single-dependency uses before
+    pruning, after pruning) over functions [f_lo, f_hi)."""
+    prog = _arrays(prog)
+    f_hi = int(prog["n_functions"]) if f_hi is None else f_hi
+    b = _Bound(prog, arch)
+    c = np.ascontiguousarray(cnt, dtype=np.uint64).reshape(-1)
+    out = np.zeros(3, np.int64)
+    _L().oracle_coverage(b.ref, ctypes.byref(b.a), _p(c), f_lo, f_hi, _p(out))
+    return int(out[0]), int(out[1]), int(out[2])
 
 
 def search(prog, j: int, r: int):

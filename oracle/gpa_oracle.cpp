@@ -751,6 +751,48 @@ int oracle_search(const OProg* P, int32_t j, int32_t r, int32_t max_out, int32_t
   return (int)v.size();
 }
 
+// Single dependency coverage (Sec. 6, "Single Dependency Coverage"). The nodes
+// of the dependency graph are the stalled uses (instructions with samples of a
+// dependency class); a node is a single dependency node if no resource it
+// reads has more than one incoming edge. Counted over the immediate sources of
+// the backward slice (before pruning) and over the sources that survive the
+// three rules: dominator, latency, and opcode for at least one of the use's
+// stalled classes (after). out: nodes, single before, single after.
+int oracle_coverage(const OProg* P, const OArch* arch, const uint64_t* cnt, int32_t f_lo, int32_t f_hi,
+                    int64_t* out) {
+  out[0] = out[1] = out[2] = 0;
+  for (int f = f_lo; f < f_hi; ++f) {
+    Fn F(*P, f);
+    const int i0 = F.i0, n = F.i1 - F.i0;
+    auto C = [&](int x, int c, int lat) { return cnt[(size_t)(i0 + x) * 24 + c * 2 + lat]; };
+    for (int j = 0; j < n; ++j) {
+      bool stalled = false;
+      for (int c : kDepClass) stalled = stalled || C(j, c, 0) || C(j, c, 1);
+      if (!stalled) continue;
+      ++out[0];
+      size_t most_all = 0, most_kept = 0;
+      for (int e = P->use_off[i0 + j]; e < P->use_off[i0 + j + 1]; ++e) {
+        const int r = P->use_res[e] & 0x1FF;
+        const std::vector<SrcRes> v = search(F, j, r, arch->latency);
+        size_t kept = 0;
+        for (const SrcRes& s : v) {
+          const int op = P->opclass[i0 + s.i];
+          if (s.dom || s.dmin > arch->latency[op]) continue;  // dominator and latency pruning
+          bool any_class = false;                            // opcode pruning
+          for (int c : kDepClass)
+            if ((C(j, c, 0) || C(j, c, 1)) && opcode_keeps(*arch, c, op)) any_class = true;
+          if (any_class) ++kept;
+        }
+        most_all = std::max(most_all, v.size());
+        most_kept = std::max(most_kept, kept);
+      }
+      if (most_all <= 1) ++out[1];
+      if (most_kept <= 1) ++out[2];
+    }
+  }
+  return 0;
+}
+
 // Checks the loop-nest input of function f against natural loops derived from
 // dominators and back edges. Returns 0 when they agree; otherwise a code.
 int oracle_check_loops(const OProg* P, int32_t f) {

@@ -327,3 +327,64 @@ def test_blame_invariants(name, nfun, ns):
     # sorted by (use, def)
     key = e["j"].astype(np.int64) * (1 << 32) + e["i"]
     assert (np.diff(key) > 0).all()
+
+
+# ---------------------------------------------------------------- Sec. 6, single dependency coverage
+def _keeps(flags, cls, op):
+    if cls in (3, 6):
+        return bool(flags[op] & 1)      # memory dependencies: memory instructions only
+    if cls == 5:
+        return bool(flags[op] & 2)      # synchronization: barriers only
+    return True
+
+
+def _bf_coverage(P, arch, cnt):
+    """Coverage from the brute-force sources: nodes are the stalled uses; a node is
+    single if every resource it reads has at most one source (before pruning) or at most
+    one source that survives rules 2, 3 and 1 for one of its stalled classes (after)."""
+    lat, flags = arch
+    F = Fn(P, 0)
+    c3 = np.asarray(cnt).reshape(-1, 12, 2)
+    nodes = before = after = 0
+    for j in range(P.n_instr):
+        stalled = [c for c in (2, 3, 5, 6) if c3[j, c].sum() > 0]
+        if not stalled:
+            continue
+        nodes += 1
+        most_all = most_kept = 0
+        for r in sorted(set(F.uses(j))):
+            src = bf_sources(F, j, r)
+            kept = sum(1 for i, d in src.items()
+                       if not d["dom"] and d["dmin"] <= lat[F.a["opclass"][i]]
+                       and any(_keeps(flags, c, F.a["opclass"][i]) for c in stalled))
+            most_all, most_kept = max(most_all, len(src)), max(most_kept, kept)
+        before += most_all <= 1
+        after += most_kept <= 1
+    return nodes, before, after
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_coverage_matches_bruteforce(seed):
+    P = tiny_program(300 + seed, n_instr=24 + seed % 12, n_loops=seed % 3, guard_pct=25 + 5 * (seed % 5))
+    arch = synth.default_arch()
+    cnt, _ = oracle.histogram(P, P.samples(30_000, seed=seed))
+    got = oracle.coverage(P, arch, cnt)
+    assert got == _bf_coverage(P, arch, cnt)
+    assert got[0] > 0 and got[1] <= got[2] <= got[0]
+
+
+def test_coverage_diamond_opcode_rule():
+    """Two defs of R1 reach the use: not single before pruning. With memory stalls only,
+    the IMAD cannot cause them (rule 1) and the node becomes single; with execution
+    stalls as well, both stay."""
+    b0 = [I("ISETP", ["P0"], ["R5", "R6"]), I("BRA", [], [], guard="P0")]
+    b1 = [I("LDG", ["R1"], ["R2", "R3"])]
+    b2 = [I("IMAD", ["R1"], ["R5", "R6", "R7"])]
+    b3 = [I("IADD", ["R4"], ["R1", "R5"]), I("EXIT")]
+    p = program([([b0, b1, b2, b3], [[1, 2], [3], [3], []], [])])
+    j = int(p["block_instr_off"][3])
+    arch = synth.default_arch()
+    mem = counts(len(p["opclass"]), {(j, 3, 0): 50})
+    assert oracle.coverage(p, arch, mem) == (1, 0, 1)
+    both = counts(len(p["opclass"]), {(j, 3, 0): 50, (j, 2, 1): 7})
+    assert oracle.coverage(p, arch, both) == (1, 0, 0)
