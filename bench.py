@@ -457,6 +457,11 @@ def main():
                "sample": f"functions 0..{k_funcs - 1} ({int(P.func_instr_off[k_funcs])} instructions) with their "
                          f"the first {sub.size} samples of their launch runs; {t:.1f} s single-threaded"}
 
+    # Single dependency coverage (Sec. 6) of this workload, before and after pruning.
+    nodes, single_before, single_after = prog.coverage(stream)
+    coverage = {"stalled_uses": nodes, "before_pruning": single_before / max(nodes, 1),
+                "after_pruning": single_after / max(nodes, 1)}
+
     bvp = None
     if rank == 0 and world == 1 and a.plain_workload:
         bvp = plain_vs_batched(gpa, a.plain_workload, a.seed, dev, stream)
@@ -476,7 +481,7 @@ def main():
                 info["general_searches"], info["tier2_searches"], info["tier3_searches"]],
             "largest_search_nodes": info["max_nodes"], "gpu_launches": launches,
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
-            "batched_vs_plain": bvp, "autotune": tuned, "options": opts,
+            "batched_vs_plain": bvp, "autotune": tuned, "options": opts, "dependency_coverage": coverage,
         }
         print(json.dumps(line), flush=True)
     prog.unload()

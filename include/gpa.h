@@ -263,6 +263,19 @@ gpa_status gpa_advise(gpa_ctx* ctx, gpa_pid pid, const gpa_advice* out, gpa_stre
  * the largest search. */
 gpa_status gpa_sync_status(gpa_ctx* ctx, gpa_pid pid, gpa_stream stream, int64_t* info);
 
+/* Single dependency coverage (Sec. 6) of the program's current counts: out[0]
+ * = stalled uses (instructions with dependency-class samples, the nodes of the
+ * dependency graph), out[1] = those with at most one source through every
+ * resource they read before pruning (all immediate sources of the backward
+ * slice), out[2] = the same after pruning (sources that survive the dominator
+ * and latency rules, and the opcode rule for one of the use's stalled
+ * classes). A diagnostic: it runs unbounded searches (slower than gpa_blame),
+ * leaves blame, edges and advice as they were, and overwrites the search
+ * statistics of gpa_sync_status. out must hold 3 values; synchronizes stream.
+ * The paper reports the ratios out[1] / out[0] and out[2] / out[0] (Sec. 6,
+ * "Single Dependency Coverage"). */
+gpa_status gpa_dependency_coverage(gpa_ctx* ctx, gpa_pid pid, gpa_stream stream, int64_t* out);
+
 /* Captures one whole step of the program into a CUDA graph owned by the
  * program (replacing any earlier one): zero the counters, ingest n samples
  * from dev_samples (device pointer, 8-byte aligned, which must stay valid

@@ -45,7 +45,8 @@ enum {
                      // 6 hash rounds; 8 queue, 9 sources per use, 10 merged edges,
                      // 11 distance range, 12 raw edges, 13 no path length
   SS_BIG_N = 76,     // uses with more than kMaxSrc distinct sources (listed in big_use)
-  SS_N = 77
+  SS_COV = 77,       // gpa_dependency_coverage: stalled uses, single before, single after pruning
+  SS_N = 80
 };
 
 struct Arch {
@@ -57,6 +58,9 @@ struct Arch {
 // Device view of one loaded program and its per-step buffers.
 struct Prog {
   int32_t nf, ni, nb, nl, n_lines;
+  int32_t diag;                   // 1 while gpa_dependency_coverage searches: count sources, emit nothing
+  uint32_t* cov_cnt;              // n_use: that run's sources per use entry, before pruning (low 16 bits)
+                                  // and kept after pruning (high 16 bits)
   int32_t reach_smem;             // shared memory of the staged fixpoint: the largest need that fits
                                   // (functions needing more use the global-memory fixpoint)
   // Fourth search tier, sized for this program's largest function (0 nodes:
@@ -179,6 +183,26 @@ __device__ __forceinline__ bool contains(uint16_t S, int g) {
   return (S >> (g - 1)) & 1u;
 }
 
+// Rule 1, opcode pruning: can instruction class op cause stalls of class cls?
+__device__ __forceinline__ bool opcode_keeps(const Arch& A, int cls, int op) {
+  if (cls == GPA_MEMORY_DEPENDENCY || cls == GPA_CONSTANT_MEMORY_DEPENDENCY) return (A.flags[op] & GPA_F_MEM) != 0;
+  if (cls == GPA_SYNC) return (A.flags[op] & GPA_F_SYNC) != 0;
+  return true;
+}
+// Rule 1 for the coverage count: does op survive for some dependency class stalled at j?
+__device__ __forceinline__ bool keeps_any(const Prog& P, const Arch& A, int j, int op) {
+  const unsigned long long* c = P.cnt + (size_t)j * kCnt;
+  return ((c[2 * GPA_EXEC_DEPENDENCY] | c[2 * GPA_EXEC_DEPENDENCY + 1]) && opcode_keeps(A, GPA_EXEC_DEPENDENCY, op)) ||
+         ((c[2 * GPA_MEMORY_DEPENDENCY] | c[2 * GPA_MEMORY_DEPENDENCY + 1]) && opcode_keeps(A, GPA_MEMORY_DEPENDENCY, op)) ||
+         ((c[2 * GPA_SYNC] | c[2 * GPA_SYNC + 1]) && opcode_keeps(A, GPA_SYNC, op)) ||
+         ((c[2 * GPA_CONSTANT_MEMORY_DEPENDENCY] | c[2 * GPA_CONSTANT_MEMORY_DEPENDENCY + 1]) &&
+          opcode_keeps(A, GPA_CONSTANT_MEMORY_DEPENDENCY, op));
+}
+// Adds a (use entry) contribution to the coverage count.
+__device__ __forceinline__ void cov_add(const Prog& P, int e, int n_all, int n_kept) {
+  atomicAdd(&P.cov_cnt[e], (uint32_t)min(n_all, 0xFFFF) | ((uint32_t)min(n_kept, 0xFFFF) << 16));
+}
+
 // Def kind of resource r at instruction x: -1 not defined, else 0/1/2.
 __device__ __forceinline__ int def_kind(const Prog& P, int x, int r) {
   const int e1 = P.def_off[x + 1];
@@ -251,6 +275,8 @@ constexpr int64_t kReachSmemCap = 200 * 1024;
 void launch_blame(const Prog& P, const Arch& A, const SearchArena* tiers, int max_src, int32_t* scan_tmp,
                   cudaStream_t st, int sms, int64_t* launches);
 void launch_search(const Prog& P, const Arch& A, const SearchArena* tiers, cudaStream_t st, int64_t* launches);
+void launch_coverage(const Prog& P, const Arch& A, const SearchArena* tiers, cudaStream_t st, int sms,
+                     int64_t* launches);
 int64_t search_arena_bytes(int nodes, int src, int layers);
 void launch_build_meta(const Prog& P, int4* meta, cudaStream_t st, int sms, int64_t* launches);
 void launch_build_events(const Prog& P, int32_t* ev_off, uint32_t* events, int32_t* tmp, cudaStream_t st, int sms,

@@ -49,7 +49,7 @@ __device__ __forceinline__ int dep_class(int ci) {
 // rule 2 reduces to an unguarded reader of r below it in p (met first in the
 // bottom-up scan). Defs above j in b0 are settled by the in-block scan.
 __device__ bool scan_pred(const Prog& P, const Arch& A, int j, int r, int gj, int b0, int p, uint16_t S, int d0,
-                          bool emit) {
+                          bool emit, int* n_all = nullptr, int* n_kept = nullptr, bool blocked = false) {
   const int first = P.block_instr_off[p], last = P.block_instr_off[p + 1] - 1;
   bool wall = false;
   int last_def_pos = -1;
@@ -60,9 +60,14 @@ __device__ bool scan_pred(const Prog& P, const Arch& A, int j, int r, int gj, in
     const int pos = (int)(ev >> 16), x = first + pos;
     if (ev & 0x200u) {
       last_def_pos = pos;
-      if (emit && !contains(S, gj) && !(p == b0 && x < j)) {
+      if (!contains(S, gj) && !(p == b0 && x < j)) {
         const int d = d0 + (last - x);
-        if (!wall && d <= A.lat[P.opclass[x]]) emit_raw(P, A, j, x, r, (int)((ev >> 10) & 3u), d, d);
+        const bool keep = !wall && d <= A.lat[P.opclass[x]];
+        if (emit && keep) emit_raw(P, A, j, x, r, (int)((ev >> 10) & 3u), d, d);
+        if (n_all) {  // coverage count
+          ++*n_all;
+          if (keep && !blocked && keeps_any(P, A, j, P.opclass[x])) ++*n_kept;
+        }
       }
       S = add_literal(S, (int)((ev >> 12) & 0xFu));
       if (contains(S, gj)) return true;
@@ -84,8 +89,9 @@ __global__ void k_search_local(Prog P, Arch A) {
     for (int e = P.use_off[j]; e < P.use_off[j + 1]; ++e) {
       const int r = P.use_res[e] & 0x1FF;
       uint16_t S = 0;
-      bool blocked = false;
+      bool blocked = false, covered = false;
       int last_def_pos = -1;
+      int n_all = 0, n_kept = 0;  // coverage count (P.diag)
       for (int t = ev0; t < ev1; ++t) {  // bottom-up
         const uint32_t ev = P.events[t];
         const int pos = (int)(ev >> 16);
@@ -95,16 +101,24 @@ __global__ void k_search_local(Prog P, Arch A) {
           last_def_pos = pos;
           if (!contains(S, gj)) {
             const int d = pj - pos;
-            if (d <= A.lat[P.opclass[x]]) emit_raw(P, A, j, x, r, (int)((ev >> 10) & 3u), d, d);
+            if (!P.diag) {
+              if (d <= A.lat[P.opclass[x]]) emit_raw(P, A, j, x, r, (int)((ev >> 10) & 3u), d, d);
+            } else {
+              ++n_all;
+              if (!blocked && d <= A.lat[P.opclass[x]] && keeps_any(P, A, j, P.opclass[x])) ++n_kept;
+            }
           }
           S = add_literal(S, (int)((ev >> 12) & 0xFu));
-          if (contains(S, gj)) { blocked = true; break; }
-        } else if (pos != last_def_pos) {
-          blocked = true;  // unguarded reader on every path beyond this point
-          break;
+          if (contains(S, gj)) { covered = true; break; }
+        } else if (pos != last_def_pos && !blocked) {
+          // An unguarded reader on every path beyond this point: nothing
+          // further survives rule 2 (the coverage count still counts it).
+          blocked = true;
+          if (!P.diag) break;
         }
       }
-      if (blocked) continue;
+      if (P.diag && covered) { cov_add(P, e, n_all, n_kept); continue; }
+      if (covered || (blocked && !P.diag)) continue;
       // Predecessors through which a def of r reaches b0 (distinct blocks).
       // If each covers j's guard inside itself, resolve here; otherwise queue
       // the general search.
@@ -123,17 +137,23 @@ __global__ void k_search_local(Prog P, Arch A) {
         any = true;
         all_cover = scan_pred(P, A, j, r, gj, b0, P.pred[q], S, pj + 1, false);
       }
-      if (!any) continue;
-      if (all_cover) {
-        for (int q = q0; q < q1; ++q)
-          if (counts(q)) scan_pred(P, A, j, r, gj, b0, P.pred[q], S, pj + 1, true);
+      if (!any) {
+        if (P.diag) cov_add(P, e, n_all, n_kept);
         continue;
       }
+      if (all_cover) {
+        for (int q = q0; q < q1; ++q)
+          if (counts(q))
+            scan_pred(P, A, j, r, gj, b0, P.pred[q], S, pj + 1, !P.diag, P.diag ? &n_all : nullptr, &n_kept, blocked);
+        if (P.diag) cov_add(P, e, n_all, n_kept);
+        continue;
+      }
+      if (P.diag) cov_add(P, e, n_all, n_kept);  // the in-block part; the search adds the rest
       // A search known to outgrow the first tier goes straight to the tier
       // that held it before (the second tier's queue, or the third tier's
       // region at the top of the first queue).
       const uint32_t hint = P.tier_hint[e];
-      const int4 task = make_int4(j, r, (int)S, e);
+      const int4 task = make_int4(j, r, (int)S | (blocked ? 1 << 20 : 0), e);
       if (hint >= 3) {
         const unsigned long long t = atomicAdd(&P.stats[SS_HINT3_N], 1ull);
         if (t < (unsigned long long)P.queue_cap) P.queue[P.queue_cap - 1 - (int64_t)t] = task;
@@ -165,11 +185,6 @@ __device__ __forceinline__ void blame_add(unsigned long long* addr, unsigned lon
   cg::coalesced_group grp = cg::labeled_partition(g, (unsigned long long)(uintptr_t)addr);
   const unsigned long long sum = cg::reduce(grp, v, cg::plus<unsigned long long>());
   if (grp.thread_rank() == 0) atomicAdd(addr, sum);
-}
-__device__ __forceinline__ bool opcode_keeps(const Arch& A, int cls, int op) {
-  if (cls == GPA_MEMORY_DEPENDENCY || cls == GPA_CONSTANT_MEMORY_DEPENDENCY) return (A.flags[op] & GPA_F_MEM) != 0;
-  if (cls == GPA_SYNC) return (A.flags[op] & GPA_F_SYNC) != 0;
-  return true;
 }
 
 // Distinct sources of use j over its raw edge list, using ids[cap] as scratch:
@@ -353,7 +368,47 @@ __global__ void k_apportion_big(Prog P, Arch A) {
   }
 }
 
+// Single dependency coverage: a stalled use is a single dependency node when
+// no resource it reads has more than one source (before pruning) or more than
+// one kept source (after).
+__global__ void k_coverage(Prog P) {
+  unsigned long long nodes = 0, before = 0, after = 0;
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < P.ni; j += gridDim.x * blockDim.x) {
+    if (!stalled(P, j)) continue;
+    uint32_t most_all = 0, most_kept = 0;
+    for (int e = P.use_off[j]; e < P.use_off[j + 1]; ++e) {
+      const uint32_t c = P.cov_cnt[e];
+      most_all = max(most_all, c & 0xFFFFu);
+      most_kept = max(most_kept, c >> 16);
+    }
+    ++nodes;
+    before += most_all <= 1u;
+    after += most_kept <= 1u;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    nodes += __shfl_xor_sync(0xffffffffu, nodes, o);
+    before += __shfl_xor_sync(0xffffffffu, before, o);
+    after += __shfl_xor_sync(0xffffffffu, after, o);
+  }
+  if ((threadIdx.x & 31) == 0 && nodes) {
+    atomicAdd(&P.stats[SS_COV], nodes);
+    atomicAdd(&P.stats[SS_COV + 1], before);
+    atomicAdd(&P.stats[SS_COV + 2], after);
+  }
+}
+
 }  // namespace
+
+void launch_coverage(const Prog& P, const Arch& A, const SearchArena* tiers, cudaStream_t st, int sms,
+                     int64_t* launches) {
+  const int threads = 128;
+  const int g_instr = grid_for(P.ni, threads, sms);
+  k_search_local<<<g_instr, threads, 0, st>>>(P, A);
+  ++*launches;
+  launch_search(P, A, tiers, st, launches);
+  k_coverage<<<g_instr, threads, 0, st>>>(P);
+  ++*launches;
+}
 
 void launch_blame(const Prog& P, const Arch& A, const SearchArena* tiers, int max_src, int32_t* scan_tmp,
                   cudaStream_t st, int sms, int64_t* launches) {

@@ -82,8 +82,11 @@ __device__ __forceinline__ int warp_slot(bool pred, int* total) {
 }
 
 // Returns false when the search outgrew the arena (nothing emitted).
+// With P.diag, the search counts the sources of (j, r) before and after
+// pruning into use entry e (`blocked`: an unguarded reader above j in its
+// block prunes them all by rule 2) and emits nothing.
 __device__ bool warp_search(const Prog& P, const Arch& A, const Arena& a, int j, int r, uint16_t S0, int bound,
-                            uint16_t live, int tier) {
+                            uint16_t live, int tier, int e = 0, bool blocked = false) {
   const int lane = threadIdx.x & 31;
 #ifdef GPA_PHASE_TIMING
   long long t_prev = clock64();
@@ -420,7 +423,7 @@ __device__ bool warp_search(const Prog& P, const Arch& A, const Arena& a, int j,
     __syncwarp();
     return false;
   }
-  if (!cand) return true;
+  if (!cand && !P.diag) return true;
 
   // Shortest distance with parents, and fewest back edges, over the whole graph.
   for (int u = lane; u < n; u += 32) {
@@ -496,12 +499,16 @@ __device__ bool warp_search(const Prog& P, const Arch& A, const Arena& a, int j,
   int alive = 0;
   for (int m = lane; m < nsrc; m += 32) {
     a.sp[m] = (int)(a.sdb[m] >> 32) > A.lat[P.opclass[a.si[m]]] ? 1 : 0;  // rule 3
+    if (P.diag && (blocked || !keeps_any(P, A, j, P.opclass[a.si[m]]))) a.sp[m] = 1;  // rule 2 above j, rule 1
     alive += a.sp[m] ? 0 : 1;
   }
   for (int o = 16; o > 0; o >>= 1) alive += __shfl_xor_sync(0xffffffffu, alive, o);
   __syncwarp();
   phase(2);
-  if (alive == 0) return true;
+  if (alive == 0) {
+    if (P.diag && lane == 0) cov_add(P, e, nsrc, 0);
+    return true;
+  }
 
   // Rule 2. Wall groups, one per block: a hash keyed by block with atomicMax
   // of the positions (the unguarded reader met first from the bottom truncates
@@ -644,6 +651,10 @@ __device__ bool warp_search(const Prog& P, const Arch& A, const Arena& a, int j,
     __syncwarp();
   }
   phase(3);
+  if (P.diag) {
+    if (lane == 0) cov_add(P, e, nsrc, alive);
+    return true;
+  }
   if (alive == 0) return true;
 
   // Longest path with exactly K back edges: layer = back edges used. Each
@@ -757,11 +768,13 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32) k_search_warp(Prog P, Arch 
     if (t >= nq + nh) break;
     const int4 task = t < nq ? q[t] : P.queue[P.queue_cap - 1 - (int64_t)(t - nq)];
     const int f = P.block_func[P.instr_block[task.x]];
-    const int bound = P.res_maxlat[(size_t)f * kNumRes + task.y];
+    // The coverage count needs every source: no latency bound.
+    const int bound = P.diag ? kInf - 1 : P.res_maxlat[(size_t)f * kNumRes + task.y];
     const uint16_t live = live_literals(P.res_guards[(size_t)f * kNumRes + task.y], P.guard[task.x]);
-    const bool ok = warp_search(P, A, a, task.x, task.y, (uint16_t)task.z, bound, live, tier);
+    const bool ok = warp_search(P, A, a, task.x, task.y, (uint16_t)task.z, bound, live, tier, task.w,
+                                (task.z >> 20) & 1);
     if (ok || lane != 0) continue;
-    atomicMax(&P.tier_hint[task.w], (unsigned)(tier + 1));  // later steps queue it for a bigger tier
+    if (!P.diag) atomicMax(&P.tier_hint[task.w], (unsigned)(tier + 1));  // later steps queue it for a bigger tier
     if (tier < 3 || (tier == 3 && P.t4_nodes > 0)) {
       const int o_slot = tier == 1 ? SS_OVF_N : tier == 2 ? SS_OVF2_N : SS_OVF3_N;
       int4* oq = tier == 2 ? P.queue : P.ovf_queue;

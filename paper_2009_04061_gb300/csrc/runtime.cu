@@ -425,6 +425,8 @@ static gpa_status alloc_program(const gpa_program_desc* d, ProgramRec* R, int ti
   TRY(dev_alloc(R, &P.queue, (size_t)P.queue_cap));
   TRY(dev_alloc(R, &P.ovf_queue, (size_t)P.queue_cap));
   TRY(dev_alloc(R, &P.tier_hint, (size_t)std::max<int64_t>(d->n_use, 1)));
+  TRY(dev_alloc(R, &P.cov_cnt, (size_t)std::max<int64_t>(d->n_use, 1)));
+  P.diag = 0;
   TRY(dev_alloc(R, &P.edge_off, ni + 1));
   TRY(dev_alloc(R, &P.big_use, ni));
   P.edge_cnt = P.edge_off;
@@ -632,6 +634,30 @@ gpa_status gpa_blame(gpa_ctx* ctx, gpa_pid pid, gpa_stream stream) {
   ProgramRec* R = find(ctx, pid);
   if (!R) return GPA_ERR_NO_PROGRAM;
   return blame_body(ctx, R, (cudaStream_t)stream, true);
+}
+
+gpa_status gpa_dependency_coverage(gpa_ctx* ctx, gpa_pid pid, gpa_stream stream, int64_t* out) {
+  ProgramRec* R = find(ctx, pid);
+  if (!R) return GPA_ERR_NO_PROGRAM;
+  if (!out) return GPA_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  Prog D = R->P;
+  D.diag = 1;
+  CK(cudaMemsetAsync(D.cov_cnt, 0, sizeof(uint32_t) * (size_t)std::max(R->n_use, 1), st));
+  CK(cudaMemsetAsync(D.stats + SS_GENERAL, 0, sizeof(unsigned long long) * 3, st));
+  CK(cudaMemsetAsync(D.stats + SS_RAW_N, 0, sizeof(unsigned long long) * (SS_N - SS_RAW_N), st));
+  launch_dataflow(D, ctx->arch, ctx->opts.max_fixpoint_sweeps, st, ctx->sms, &ctx->launches);
+  CK(cudaStreamWaitEvent(st, ctx->scratch_ev, 0));
+  launch_coverage(D, ctx->arch, ctx->tier, st, ctx->sms, &ctx->launches);
+  CK(cudaEventRecord(ctx->scratch_ev, st));
+  CK(cudaGetLastError());
+  unsigned long long h[SS_N];
+  CK(cudaStreamSynchronize(st));
+  CK(cudaMemcpy(h, D.stats, sizeof h, cudaMemcpyDeviceToHost));
+  out[0] = (int64_t)h[SS_COV];
+  out[1] = (int64_t)h[SS_COV + 1];
+  out[2] = (int64_t)h[SS_COV + 2];
+  return status_from(h[SS_STATUS]);
 }
 
 gpa_status gpa_step_capture(gpa_ctx* ctx, gpa_pid pid, const uint64_t* dev_samples, size_t n) {

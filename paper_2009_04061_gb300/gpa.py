@@ -94,6 +94,7 @@ def library() -> ctypes.CDLL:
         "gpa_program_footprint": ([vp, vp, vp], i32),
         "gpa_program_bytes": ([vp, u32, vp], i32),
         "gpa_unload_program_async": ([vp, u32, vp], i32),
+        "gpa_dependency_coverage": ([vp, u32, vp, vp], i32),
         "gpa_step_launch": ([vp, u32, vp], i32),
         "gpa_get_reaching": ([vp, u32, vp, vp, vp], i32),
         "gpa_get_blame": ([vp, u32, vp, vp], i32),
@@ -280,6 +281,13 @@ def gpa_sync_status(ctx, pid, stream=None):
                     largest_use=int(info[6]), largest_resource=int(info[7]))
 
 
+def gpa_dependency_coverage(ctx, pid, stream=None) -> tuple[int, int, int]:
+    """(stalled uses, single dependency uses before pruning, after pruning)."""
+    out = np.zeros(3, np.int64)
+    _check(library().gpa_dependency_coverage(ctx, pid, _stream(stream), _p(out)), "gpa_dependency_coverage")
+    return int(out[0]), int(out[1]), int(out[2])
+
+
 def gpa_step_capture(ctx, pid, dev_samples, n: int | None = None):
     """Capture reset + ingest + blame + advise of the program into a CUDA graph."""
     if n is None:
@@ -409,6 +417,9 @@ class Program:
 
     def counts(self, stream=None):
         return gpa_get_counts(self.h, self.pid, self.n_instr, stream)
+
+    def coverage(self, stream=None):
+        return gpa_dependency_coverage(self.h, self.pid, stream)
 
     def device_bytes(self) -> int:
         return gpa_program_bytes(self.h, self.pid)

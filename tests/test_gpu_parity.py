@@ -306,3 +306,36 @@ def test_autotune_picks_a_timed_candidate():
              dict(hist_variant=1, small_search_nodes=128, mid_search_nodes=512, search_slots=304)]
     best, table = autotune.tune(ARCH, P.arrays, d, torch.cuda.current_stream(), cands=cands, reps=1)
     assert best in [t[0] for t in table] and all(ms > 0 for _, ms in table)
+
+
+@pytest.mark.parametrize("which", ["rodinia", "tiny", "batched_subset"])
+def test_dependency_coverage(ctx, which):
+    """Single dependency coverage (Sec. 6) from the unbounded GPU searches equals the
+    oracle's; blame and edges of the program are left as they were."""
+    if which == "rodinia":
+        ps, ns, kz = synth.workload("rodinia")
+        P = synth.make_program(ps, kz)
+        s = P.samples(2_000_000, seed=21)
+    elif which == "tiny":
+        P = tiny_program(21, n_instr=36, n_loops=2, guard_pct=40)
+        s = P.samples(30_000, seed=21)
+    else:
+        P = synth.make_program(synth.batched_params(24, np.random.default_rng(21), 21), 1.0)
+        s = P.samples(2_000_000, seed=21)
+    cnt, _ = oracle.histogram(P, s)
+    want = oracle.coverage(P, ARCH, cnt)
+    prog = ctx.load_program(P)
+    try:
+        prog.reset()
+        prog.ingest(dev(s))
+        prog.blame()
+        e1, b1 = prog.edges(), prog.blame_counts()
+        got = prog.coverage()
+        assert got == want
+        assert got[0] > 0 and got[1] <= got[2]
+        assert np.array_equal(prog.blame_counts(), b1)
+        e2 = prog.edges()
+        for k in e1:
+            assert np.array_equal(e1[k], e2[k]), k
+    finally:
+        prog.unload()
