@@ -276,6 +276,24 @@ gpa_status gpa_sync_status(gpa_ctx* ctx, gpa_pid pid, gpa_stream stream, int64_t
  * "Single Dependency Coverage"). */
 gpa_status gpa_dependency_coverage(gpa_ctx* ctx, gpa_pid pid, gpa_stream stream, int64_t* out);
 
+/* The dependency graph before pruning (Sec. 4, "construct a dependency
+ * graph"): every immediate source of every (stalled use, resource) of the
+ * current counts, with its shortest distance, fewest back edges, the longest
+ * distance with exactly that many back edges, and whether the dominator rule
+ * cuts it (an unguarded reader of the resource on all its source paths; the
+ * latency and opcode rules are left to the caller, from dmin and the def's
+ * opcode class). Runs the unbounded searches twice (a counting pass sizes the
+ * program-owned export buffer); *n_edges receives the edge count. Blame, edges
+ * and advice stay as they were. Synchronizes stream. */
+gpa_status gpa_export_unpruned_edges(gpa_ctx* ctx, gpa_pid pid, gpa_stream stream, int64_t* n_edges);
+
+/* Copies the last export, ordered by (use, resource, def), into arrays of
+ * n_edges entries (NULL pointers are skipped): global use and def instruction
+ * indices, resource id, dmin, back edges, dlong, dom (0/1). */
+gpa_status gpa_get_unpruned_edges(gpa_ctx* ctx, gpa_pid pid, int32_t* use, int32_t* def, int32_t* res,
+                                  int32_t* dmin, int32_t* back_edges, int32_t* dlong, uint8_t* dom,
+                                  gpa_stream stream);
+
 /* Captures one whole step of the program into a CUDA graph owned by the
  * program (replacing any earlier one): zero the counters, ingest n samples
  * from dev_samples (device pointer, 8-byte aligned, which must stay valid

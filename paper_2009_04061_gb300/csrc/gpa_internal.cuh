@@ -46,7 +46,9 @@ enum {
                      // 11 distance range, 12 raw edges, 13 no path length
   SS_BIG_N = 76,     // uses with more than kMaxSrc distinct sources (listed in big_use)
   SS_COV = 77,       // gpa_dependency_coverage: stalled uses, single before, single after pruning
-  SS_N = 80
+  SS_COV_ALL = 80,   // the counting pass's total of sources before pruning
+  SS_XN = 81,        // unpruned edges written by the export pass
+  SS_N = 82
 };
 
 struct Arch {
@@ -58,7 +60,10 @@ struct Arch {
 // Device view of one loaded program and its per-step buffers.
 struct Prog {
   int32_t nf, ni, nb, nl, n_lines;
-  int32_t diag;                   // 1 while gpa_dependency_coverage searches: count sources, emit nothing
+  int32_t diag;                   // 1: the searches count sources (gpa_dependency_coverage), 2: they export
+                                  // every source (gpa_export_unpruned_edges); both emit no raw edges
+  int4* xedges;                   // export: 2 per edge, {use, def, resource, dmin}, {K, dlong, dom, 0}
+  int64_t xcap;                   // edges the export buffer holds
   uint32_t* cov_cnt;              // n_use: that run's sources per use entry, before pruning (low 16 bits)
                                   // and kept after pruning (high 16 bits)
   int32_t reach_smem;             // shared memory of the staged fixpoint: the largest need that fits
@@ -197,6 +202,16 @@ __device__ __forceinline__ bool keeps_any(const Prog& P, const Arch& A, int j, i
          ((c[2 * GPA_SYNC] | c[2 * GPA_SYNC + 1]) && opcode_keeps(A, GPA_SYNC, op)) ||
          ((c[2 * GPA_CONSTANT_MEMORY_DEPENDENCY] | c[2 * GPA_CONSTANT_MEMORY_DEPENDENCY + 1]) &&
           opcode_keeps(A, GPA_CONSTANT_MEMORY_DEPENDENCY, op));
+}
+// One unpruned edge for the export (GPA_ERR_CAPACITY if the buffer is full).
+__device__ __forceinline__ void xemit(const Prog& P, int j, int i, int r, int dmin, int K, int dlong, bool dom) {
+  const unsigned long long k = atomicAdd(&P.stats[SS_XN], 1ull);
+  if (k >= (unsigned long long)P.xcap) {
+    atomicOr(&P.stats[SS_STATUS], (unsigned long long)ST_CAPACITY);
+    return;
+  }
+  P.xedges[2 * k] = make_int4(j, i, r, dmin);
+  P.xedges[2 * k + 1] = make_int4(K, dlong, dom ? 1 : 0, 0);
 }
 // Adds a (use entry) contribution to the coverage count.
 __device__ __forceinline__ void cov_add(const Prog& P, int e, int n_all, int n_kept) {

@@ -68,6 +68,7 @@ __device__ bool scan_pred(const Prog& P, const Arch& A, int j, int r, int gj, in
           ++*n_all;
           if (keep && !blocked && keeps_any(P, A, j, P.opclass[x])) ++*n_kept;
         }
+        if (P.diag == 2 && n_all) xemit(P, j, x, r, d, p >= b0 ? 1 : 0, d, wall || blocked);
       }
       S = add_literal(S, (int)((ev >> 12) & 0xFu));
       if (contains(S, gj)) return true;
@@ -106,6 +107,7 @@ __global__ void k_search_local(Prog P, Arch A) {
             } else {
               ++n_all;
               if (!blocked && d <= A.lat[P.opclass[x]] && keeps_any(P, A, j, P.opclass[x])) ++n_kept;
+              if (P.diag == 2) xemit(P, j, x, r, d, 0, d, blocked);
             }
           }
           S = add_literal(S, (int)((ev >> 12) & 0xFu));
@@ -372,7 +374,7 @@ __global__ void k_apportion_big(Prog P, Arch A) {
 // no resource it reads has more than one source (before pruning) or more than
 // one kept source (after).
 __global__ void k_coverage(Prog P) {
-  unsigned long long nodes = 0, before = 0, after = 0;
+  unsigned long long nodes = 0, before = 0, after = 0, total = 0;
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < P.ni; j += gridDim.x * blockDim.x) {
     if (!stalled(P, j)) continue;
     uint32_t most_all = 0, most_kept = 0;
@@ -380,6 +382,7 @@ __global__ void k_coverage(Prog P) {
       const uint32_t c = P.cov_cnt[e];
       most_all = max(most_all, c & 0xFFFFu);
       most_kept = max(most_kept, c >> 16);
+      total += c & 0xFFFFu;
     }
     ++nodes;
     before += most_all <= 1u;
@@ -389,11 +392,13 @@ __global__ void k_coverage(Prog P) {
     nodes += __shfl_xor_sync(0xffffffffu, nodes, o);
     before += __shfl_xor_sync(0xffffffffu, before, o);
     after += __shfl_xor_sync(0xffffffffu, after, o);
+    total += __shfl_xor_sync(0xffffffffu, total, o);
   }
   if ((threadIdx.x & 31) == 0 && nodes) {
     atomicAdd(&P.stats[SS_COV], nodes);
     atomicAdd(&P.stats[SS_COV + 1], before);
     atomicAdd(&P.stats[SS_COV + 2], after);
+    atomicAdd(&P.stats[SS_COV_ALL], total);
   }
 }
 

@@ -499,14 +499,15 @@ __device__ bool warp_search(const Prog& P, const Arch& A, const Arena& a, int j,
   int alive = 0;
   for (int m = lane; m < nsrc; m += 32) {
     a.sp[m] = (int)(a.sdb[m] >> 32) > A.lat[P.opclass[a.si[m]]] ? 1 : 0;  // rule 3
-    if (P.diag && (blocked || !keeps_any(P, A, j, P.opclass[a.si[m]]))) a.sp[m] = 1;  // rule 2 above j, rule 1
+    if (P.diag == 1 && (blocked || !keeps_any(P, A, j, P.opclass[a.si[m]]))) a.sp[m] = 1;  // rule 2 above j, rule 1
+    if (P.diag == 2) a.sp[m] = 0;  // export: rule 2 for every source
     alive += a.sp[m] ? 0 : 1;
   }
   for (int o = 16; o > 0; o >>= 1) alive += __shfl_xor_sync(0xffffffffu, alive, o);
   __syncwarp();
   phase(2);
   if (alive == 0) {
-    if (P.diag && lane == 0) cov_add(P, e, nsrc, 0);
+    if (P.diag == 1 && lane == 0) cov_add(P, e, nsrc, 0);
     return true;
   }
 
@@ -651,17 +652,19 @@ __device__ bool warp_search(const Prog& P, const Arch& A, const Arena& a, int j,
     __syncwarp();
   }
   phase(3);
-  if (P.diag) {
+  if (P.diag == 1) {
     if (lane == 0) cov_add(P, e, nsrc, alive);
     return true;
   }
-  if (alive == 0) return true;
+  // The export keeps every source: sp marks the rule-2 cuts (its dom flag).
+  const bool every = P.diag == 2;
+  if (alive == 0 && !every) return true;
 
   // Longest path with exactly K back edges: layer = back edges used. Each
   // layer is a DAG over the forward edges, processed in topological order by
   // level-synchronous Kahn frontiers; back edges feed the next layer.
   int maxK = 0;
-  for (int m = lane; m < nsrc; m += 32) if (!a.sp[m]) maxK = max(maxK, a.sk[m]);
+  for (int m = lane; m < nsrc; m += 32) if (!a.sp[m] || every) maxK = max(maxK, a.sk[m]);
   for (int o = 16; o > 0; o >>= 1) maxK = max(maxK, __shfl_xor_sync(0xffffffffu, maxK, o));
   if (maxK >= a.L) {
     if (lane == 0) ctr[7] = 5;
@@ -718,7 +721,7 @@ __device__ bool warp_search(const Prog& P, const Arch& A, const Arena& a, int j,
     }
   }
   for (int m = lane; m < nsrc; m += 32) {
-    if (a.sp[m]) continue;
+    if (a.sp[m] && !every) continue;
     const int K = a.sk[m];
     int best = -1;
     for (int o = a.shead[m]; o >= 0; o = a.onext[o]) {
@@ -727,7 +730,8 @@ __device__ bool warp_search(const Prog& P, const Arch& A, const Arena& a, int j,
       if (dlu >= 0) best = max(best, dlu + last_of(u) - a.ox[o]);
     }
     if (best < 1) { capacity(P, 13); continue; }
-    emit_raw(P, A, j, a.si[m], r, def_kind(P, a.si[m], r), (int)(a.sdb[m] >> 32), best);
+    if (every) xemit(P, j, a.si[m], r, (int)(a.sdb[m] >> 32), K, best, a.sp[m] || blocked);
+    else emit_raw(P, A, j, a.si[m], r, def_kind(P, a.si[m], r), (int)(a.sdb[m] >> 32), best);
   }
   __syncwarp();
   phase(4);

@@ -19,6 +19,8 @@ namespace {
 struct ProgramRec {
   Prog P{};
   bool dry = false;                     // count bytes only (gpa_program_footprint)
+  int4* xbuf = nullptr;                 // export buffer of gpa_export_unpruned_edges (grown on demand)
+  int64_t xbuf_cap = 0, x_n = 0;
   cudaStream_t build = nullptr;         // stream of the stream-ordered allocations and copies
   int64_t bytes = 0;                    // device bytes requested for the program
   cudaGraphExec_t step_exec = nullptr;  // captured step (gpa_step_capture)
@@ -89,6 +91,7 @@ gpa_status dev_copy(ProgramRec* R, const T** dst, const T* src, size_t n) {
 // Frees a program whose work has finished (the callers synchronize first).
 void free_program(ProgramRec* R) {
   if (R->step_exec) cudaGraphExecDestroy(R->step_exec);
+  if (R->xbuf) cudaFree(R->xbuf);
   if (R->build) cudaStreamSynchronize(R->build);
   for (void* p : R->allocs) cudaFree(p);
   delete R;
@@ -636,13 +639,13 @@ gpa_status gpa_blame(gpa_ctx* ctx, gpa_pid pid, gpa_stream stream) {
   return blame_body(ctx, R, (cudaStream_t)stream, true);
 }
 
-gpa_status gpa_dependency_coverage(gpa_ctx* ctx, gpa_pid pid, gpa_stream stream, int64_t* out) {
-  ProgramRec* R = find(ctx, pid);
-  if (!R) return GPA_ERR_NO_PROGRAM;
-  if (!out) return GPA_ERR_INVALID_ARG;
-  cudaStream_t st = (cudaStream_t)stream;
+// The counting run of the searches (P.diag = 1) behind gpa_dependency_coverage
+// and gpa_export_unpruned_edges; h receives the stats words.
+static gpa_status coverage_run(gpa_ctx* ctx, ProgramRec* R, cudaStream_t st, int diag, unsigned long long* h) {
   Prog D = R->P;
-  D.diag = 1;
+  D.diag = diag;
+  D.xedges = R->xbuf;
+  D.xcap = diag == 2 ? R->xbuf_cap : 0;
   CK(cudaMemsetAsync(D.cov_cnt, 0, sizeof(uint32_t) * (size_t)std::max(R->n_use, 1), st));
   CK(cudaMemsetAsync(D.stats + SS_GENERAL, 0, sizeof(unsigned long long) * 3, st));
   CK(cudaMemsetAsync(D.stats + SS_RAW_N, 0, sizeof(unsigned long long) * (SS_N - SS_RAW_N), st));
@@ -651,13 +654,72 @@ gpa_status gpa_dependency_coverage(gpa_ctx* ctx, gpa_pid pid, gpa_stream stream,
   launch_coverage(D, ctx->arch, ctx->tier, st, ctx->sms, &ctx->launches);
   CK(cudaEventRecord(ctx->scratch_ev, st));
   CK(cudaGetLastError());
-  unsigned long long h[SS_N];
   CK(cudaStreamSynchronize(st));
-  CK(cudaMemcpy(h, D.stats, sizeof h, cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(h, D.stats, sizeof(unsigned long long) * SS_N, cudaMemcpyDeviceToHost));
+  return status_from(h[SS_STATUS]);
+}
+
+gpa_status gpa_dependency_coverage(gpa_ctx* ctx, gpa_pid pid, gpa_stream stream, int64_t* out) {
+  ProgramRec* R = find(ctx, pid);
+  if (!R) return GPA_ERR_NO_PROGRAM;
+  if (!out) return GPA_ERR_INVALID_ARG;
+  unsigned long long h[SS_N];
+  const gpa_status s = coverage_run(ctx, R, (cudaStream_t)stream, 1, h);
   out[0] = (int64_t)h[SS_COV];
   out[1] = (int64_t)h[SS_COV + 1];
   out[2] = (int64_t)h[SS_COV + 2];
-  return status_from(h[SS_STATUS]);
+  return s;
+}
+
+gpa_status gpa_export_unpruned_edges(gpa_ctx* ctx, gpa_pid pid, gpa_stream stream, int64_t* n_edges) {
+  ProgramRec* R = find(ctx, pid);
+  if (!R) return GPA_ERR_NO_PROGRAM;
+  if (!n_edges) return GPA_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  unsigned long long h[SS_N];
+  gpa_status s = coverage_run(ctx, R, st, 1, h);  // sizes the export
+  if (s) return s;
+  const int64_t need = (int64_t)h[SS_COV_ALL];
+  if (need > R->xbuf_cap) {
+    if (R->xbuf) cudaFree(R->xbuf);
+    R->xbuf = nullptr;
+    R->xbuf_cap = 0;
+    if (cudaMalloc(&R->xbuf, sizeof(int4) * 2 * (size_t)std::max<int64_t>(need, 1)) != cudaSuccess) return GPA_ERR_OOM;
+    R->xbuf_cap = std::max<int64_t>(need, 1);
+  }
+  s = coverage_run(ctx, R, st, 2, h);
+  R->x_n = std::min<int64_t>((int64_t)h[SS_XN], R->xbuf_cap);
+  *n_edges = R->x_n;
+  return s;
+}
+
+gpa_status gpa_get_unpruned_edges(gpa_ctx* ctx, gpa_pid pid, int32_t* use, int32_t* def, int32_t* res,
+                                  int32_t* dmin, int32_t* back_edges, int32_t* dlong, uint8_t* dom, gpa_stream stream) {
+  ProgramRec* R = find(ctx, pid);
+  if (!R) return GPA_ERR_NO_PROGRAM;
+  CK(cudaStreamSynchronize((cudaStream_t)stream));
+  const int64_t n = R->x_n;
+  std::vector<int4> x(2 * (size_t)n);
+  if (n) CK(cudaMemcpy(x.data(), R->xbuf, sizeof(int4) * 2 * (size_t)n, cudaMemcpyDeviceToHost));
+  std::vector<int64_t> order(n);
+  for (int64_t k = 0; k < n; ++k) order[k] = k;
+  std::sort(order.begin(), order.end(), [&](int64_t a, int64_t b) {
+    const int4 &p = x[2 * a], &q = x[2 * b];
+    if (p.x != q.x) return p.x < q.x;
+    if (p.z != q.z) return p.z < q.z;
+    return p.y < q.y;
+  });
+  for (int64_t t = 0; t < n; ++t) {
+    const int4 a = x[2 * order[t]], b = x[2 * order[t] + 1];
+    if (use) use[t] = a.x;
+    if (def) def[t] = a.y;
+    if (res) res[t] = a.z;
+    if (dmin) dmin[t] = a.w;
+    if (back_edges) back_edges[t] = b.x;
+    if (dlong) dlong[t] = b.y;
+    if (dom) dom[t] = (uint8_t)b.z;
+  }
+  return GPA_OK;
 }
 
 gpa_status gpa_step_capture(gpa_ctx* ctx, gpa_pid pid, const uint64_t* dev_samples, size_t n) {

@@ -95,6 +95,8 @@ def library() -> ctypes.CDLL:
         "gpa_program_bytes": ([vp, u32, vp], i32),
         "gpa_unload_program_async": ([vp, u32, vp], i32),
         "gpa_dependency_coverage": ([vp, u32, vp, vp], i32),
+        "gpa_export_unpruned_edges": ([vp, u32, vp, vp], i32),
+        "gpa_get_unpruned_edges": ([vp, u32, vp, vp, vp, vp, vp, vp, vp, vp], i32),
         "gpa_step_launch": ([vp, u32, vp], i32),
         "gpa_get_reaching": ([vp, u32, vp, vp, vp], i32),
         "gpa_get_blame": ([vp, u32, vp, vp], i32),
@@ -288,6 +290,20 @@ def gpa_dependency_coverage(ctx, pid, stream=None) -> tuple[int, int, int]:
     return int(out[0]), int(out[1]), int(out[2])
 
 
+def gpa_unpruned_edges(ctx, pid, stream=None) -> dict:
+    """Every immediate source before pruning: use, def, res, dmin, K, dlong, dom (ordered)."""
+    n = ctypes.c_int64()
+    _check(library().gpa_export_unpruned_edges(ctx, pid, _stream(stream), ctypes.byref(n)),
+           "gpa_export_unpruned_edges")
+    m = max(n.value, 1)
+    out = {k: np.zeros(m, np.int32) for k in ("use", "def", "res", "dmin", "K", "dlong")}
+    out["dom"] = np.zeros(m, np.uint8)
+    _check(library().gpa_get_unpruned_edges(ctx, pid, *[_p(out[k]) for k in ("use", "def", "res", "dmin", "K",
+                                                                              "dlong", "dom")], _stream(stream)),
+           "gpa_get_unpruned_edges")
+    return {k: v[:n.value] for k, v in out.items()}
+
+
 def gpa_step_capture(ctx, pid, dev_samples, n: int | None = None):
     """Capture reset + ingest + blame + advise of the program into a CUDA graph."""
     if n is None:
@@ -420,6 +436,9 @@ class Program:
 
     def coverage(self, stream=None):
         return gpa_dependency_coverage(self.h, self.pid, stream)
+
+    def unpruned_edges(self, stream=None):
+        return gpa_unpruned_edges(self.h, self.pid, stream)
 
     def device_bytes(self) -> int:
         return gpa_program_bytes(self.h, self.pid)

@@ -339,3 +339,39 @@ def test_dependency_coverage(ctx, which):
             assert np.array_equal(e1[k], e2[k]), k
     finally:
         prog.unload()
+
+
+@pytest.mark.parametrize("which", ["tiny", "guarded", "rodinia"])
+def test_unpruned_edge_export(ctx, which):
+    """The exported dependency graph before pruning equals the oracle's search, source by
+    source, for every stalled use and resource (the dominator rule evaluated for all)."""
+    if which == "rodinia":
+        ps, ns, kz = synth.workload("rodinia")
+        P = synth.make_program(ps[:6], kz)
+        s = P.samples(400_000, seed=22)
+    else:
+        P = tiny_program(22 if which == "tiny" else 23, n_instr=40, n_loops=2,
+                         guard_pct=20 if which == "tiny" else 45)
+        s = P.samples(40_000, seed=22)
+    cnt, _ = oracle.histogram(P, s)
+    prog = ctx.load_program(P)
+    try:
+        prog.reset()
+        prog.ingest(dev(s))
+        prog.blame()
+        x = prog.unpruned_edges()
+    finally:
+        prog.unload()
+    c3 = cnt.reshape(-1, 12, 2)
+    want = []
+    uo, ur = P.use_off, P.use_res
+    for j in range(P.n_instr):
+        if c3[j, [2, 3, 5, 6]].sum() == 0:
+            continue
+        for r in sorted(set(int(v) & 0x1FF for v in ur[uo[j]:uo[j + 1]])):
+            for src in oracle.search(P, j, r):
+                want.append((j, r, src["i"], src["dmin"], src["K"], src["dlong"], int(src["dom"])))
+    want.sort()
+    got = sorted(zip(*(x[k].tolist() for k in ("use", "res", "def", "dmin", "K", "dlong", "dom"))))
+    assert len(want) > 0
+    assert got == want
