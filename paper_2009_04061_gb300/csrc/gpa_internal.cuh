@@ -48,7 +48,8 @@ enum {
   SS_COV = 77,       // gpa_dependency_coverage: stalled uses, single before, single after pruning
   SS_COV_ALL = 80,   // the counting pass's total of sources before pruning
   SS_XN = 81,        // unpruned edges written by the export pass
-  SS_N = 82
+  SS_HIST_HEAD = 82, // next chunk of the run-aware aggregation kernel (reset before each launch)
+  SS_N = 83
 };
 
 struct Arch {

@@ -170,15 +170,15 @@ __global__ void __launch_bounds__(THREADS) k_histogram(Prog P, const uint64_t* _
   if (lane == 0 && bad) atomicAdd(&P.stats[SS_INVALID], (unsigned long long)bad);
 }
 
-// Variant 0 (default), for streams that arrive as kernel-launch runs (a profiler that
-// serializes kernels delivers them so). Each CTA (one per SM, 1,024 threads)
-// takes a contiguous segment of the stream in tiles of 4,096 samples. Its
+// Variant 0 (default), for streams that arrive as kernel-launch runs (a
+// profiler that serializes kernels delivers them so). Each CTA (one per SM,
+// 1,024 threads) claims chunks of 32 consecutive tiles of 4,096 samples. Its
 // main shared-memory region serves the run it is in: as a direct-indexed
 // window over the current kernel's counters when they fit (no hashing, no
 // misses; 16-bit counters, two per word: the increment that brings one to
 // 32,768 moves 32,768 to the global counter), else as a 16,384-entry hash.
-// The first sample of each tile picks
-// the mode; switching flushes the region to the 64-bit global counters.
+// The first sample of each tile picks the mode; switching flushes the region
+// to the 64-bit global counters.
 // Samples of another kernel inside a window tile (a run boundary) go through
 // a small side hash. Both hashes send keys they cannot place to the global
 // counters, and are flushed when half full and at the end.
@@ -190,6 +190,7 @@ constexpr uint32_t kWinCounters = 2u * kMainWords;      // 16-bit window counter
 constexpr int kMainHashLog2 = 14;                     // 16,384 key/value pairs in hash mode
 constexpr int kSideLog2 = 11;                         // 2,048-entry side hash
 constexpr int kRunFlushTiles = 1 << 16;               // keeps 32-bit counts far from overflow
+constexpr int kRunChunk = 32;                         // tiles per claimed chunk
 
 template <int LOG2, int PROBES>
 __device__ __forceinline__ bool table_add(uint32_t* key, uint32_t* val, uint32_t k, uint32_t c, uint32_t& inserts) {
@@ -221,7 +222,7 @@ __device__ void table_flush(uint32_t* key, uint32_t* val, unsigned long long* cn
 }
 
 __global__ void __launch_bounds__(kRunThreads, 1) k_histogram_runs(Prog P, const uint64_t* __restrict__ s,
-                                                                   int64_t n, int head, int64_t per_cta) {
+                                                                   int64_t n, int head) {
   extern __shared__ __align__(16) uint32_t sm[];
   uint32_t* mainr = sm;                                   // kMainWords
   uint32_t* skey = sm + kMainWords;                       // side hash
@@ -272,27 +273,41 @@ __global__ void __launch_bounds__(kRunThreads, 1) k_histogram_runs(Prog P, const
     }
   };
 
+  // Tiles are handed out in chunks of kRunChunk consecutive tiles from a
+  // counter (one chunk ahead, so the last tile of a chunk can prefetch the
+  // first of the next): an SM that meets cheap runs takes more of them.
   const ulonglong2* v2 = reinterpret_cast<const ulonglong2*>(s + head);
-  const int64_t v0 = (int64_t)blockIdx.x * per_cta;
-  const int64_t v1 = min(v0 + per_cta, n2);
-  const int64_t tiles = v1 > v0 ? (v1 - v0 + kRunTile - 1) / kRunTile : 0;
+  const int64_t n_tiles = (n2 + kRunTile - 1) / kRunTile;
+  const int64_t n_chunks = (n_tiles + kRunChunk - 1) / kRunChunk;
+  __shared__ long long s_claim;
+  auto claim = [&]() -> int64_t {
+    if (threadIdx.x == 0) s_claim = (long long)atomicAdd(&P.stats[SS_HIST_HEAD], 1ull);
+    __syncthreads();
+    const int64_t c = s_claim;
+    __syncthreads();
+    return c < n_chunks ? c : n_chunks;
+  };
   ulonglong2 cur[kRunVec], nxt[kRunVec];
   bool in_cur[kRunVec], in_nxt[kRunVec];
-  auto load_tile = [&](int64_t t, ulonglong2* v, bool* in) {
+  auto load_tile = [&](int64_t g, ulonglong2* v, bool* in) {
 #pragma unroll
     for (int u = 0; u < kRunVec; ++u) {
-      const int64_t idx = v0 + t * kRunTile + u * kRunThreads + threadIdx.x;
-      in[u] = idx < v1;
+      const int64_t idx = g * kRunTile + u * kRunThreads + threadIdx.x;
+      in[u] = idx < n2;
       v[u] = in[u] ? load_stream(v2 + idx) : make_ulonglong2(0ull, 0ull);
     }
   };
-  if (tiles) load_tile(0, cur, in_cur);
+  int64_t chunk = claim();
+  int64_t upcoming = chunk < n_chunks ? claim() : n_chunks;
+  int64_t g = chunk * kRunChunk, g_end = min(g + kRunChunk, n_tiles);
+  if (chunk < n_chunks) load_tile(g, cur, in_cur);
   int since = 0;
-  for (int64_t t = 0; t < tiles; ++t) {
-    if (t + 1 < tiles) load_tile(t + 1, nxt, in_nxt);
+  for (int64_t t = 0; chunk < n_chunks; ++t) {
+    const int64_t g_next = g + 1 < g_end ? g + 1 : (upcoming < n_chunks ? upcoming * kRunChunk : -1);
+    if (g_next >= 0) load_tile(g_next, nxt, in_nxt);
     // The tile's first sample picks the mode; every thread reads it (one
     // broadcast load), so all reach the same decision without a barrier.
-    const uint32_t k0 = (uint32_t)(__ldg(reinterpret_cast<const unsigned long long*>(v2 + v0 + t * kRunTile)) >> 48);
+    const uint32_t k0 = (uint32_t)(__ldg(reinterpret_cast<const unsigned long long*>(v2 + g * kRunTile)) >> 48);
     const int want = (k0 < (uint32_t)P.nf && (uint32_t)(foff[k0 + 1] - foff[k0]) * 24u <= kWinCounters)
                          ? (int)k0 : -1;
     if (want != mode || ++since >= kRunFlushTiles) {
@@ -361,6 +376,16 @@ __global__ void __launch_bounds__(kRunThreads, 1) k_histogram_runs(Prog P, const
     }
 #pragma unroll
     for (int u = 0; u < kRunVec; ++u) { cur[u] = nxt[u]; in_cur[u] = in_nxt[u]; }
+    if (g + 1 < g_end) {
+      ++g;
+    } else {
+      chunk = upcoming;
+      if (chunk < n_chunks) {
+        g = chunk * kRunChunk;
+        g_end = min(g + kRunChunk, n_tiles);
+        upcoming = claim();
+      }
+    }
     // every 32 tiles: flush a hash that is half full
     if ((t & 31) == 31) {
       if (main_ins) atomicAdd(&ctl[0], (int)main_ins);
@@ -416,14 +441,14 @@ void launch_histogram(const Prog& P, const uint64_t* samples, size_t n, cudaStre
   if (variant == 0) {
     const int head = (reinterpret_cast<uintptr_t>(samples) & 15u) ? 1 : 0;
     const int64_t vecs = ((int64_t)n - head) / 2;
-    int64_t grid = (vecs + kRunTile - 1) / kRunTile;
+    int64_t grid = (vecs + (int64_t)kRunTile * kRunChunk - 1) / ((int64_t)kRunTile * kRunChunk);
     if (grid > sms) grid = sms;
     if (grid < 1) grid = 1;
-    const int64_t per = (vecs + grid - 1) / grid;
+    cudaMemsetAsync(&P.stats[SS_HIST_HEAD], 0, sizeof(unsigned long long), st);
     const size_t smem = sizeof(uint32_t) * ((size_t)kMainWords + 2 * ((size_t)1 << kSideLog2) + 8) +
                         (P.nf <= kSmemFuncs ? sizeof(int32_t) * (size_t)(P.nf + 1) : 0);
     allow_max_smem(k_histogram_runs);
-    k_histogram_runs<<<(int)grid, kRunThreads, smem, st>>>(P, samples, (int64_t)n, head, per);
+    k_histogram_runs<<<(int)grid, kRunThreads, smem, st>>>(P, samples, (int64_t)n, head);
     ++*launches;
     return;
   }
