@@ -172,7 +172,7 @@ __global__ void __launch_bounds__(THREADS) k_histogram(Prog P, const uint64_t* _
 
 // Variant 0 (default), for streams that arrive as kernel-launch runs (a
 // profiler that serializes kernels delivers them so). Each CTA (one per SM,
-// 1,024 threads) claims chunks of 32 consecutive tiles of 4,096 samples. Its
+// 1,024 threads) claims chunks of 16 consecutive tiles of 8,192 samples. Its
 // main shared-memory region serves the run it is in: as a direct-indexed
 // window over the current kernel's counters when they fit (no hashing, no
 // misses; 16-bit counters, two per word: the increment that brings one to
@@ -183,14 +183,20 @@ __global__ void __launch_bounds__(THREADS) k_histogram(Prog P, const uint64_t* _
 // a small side hash. Both hashes send keys they cannot place to the global
 // counters, and are flushed when half full and at the end.
 constexpr int kRunThreads = 1024;
-constexpr int kRunVec = 2;                            // 16-byte vectors per thread per tile
-constexpr int kRunTile = kRunThreads * kRunVec;       // vectors per tile (4,096 samples)
+#ifndef GPA_RUN_VEC
+#define GPA_RUN_VEC 4
+#endif
+#ifndef GPA_RUN_CHUNK
+#define GPA_RUN_CHUNK 16
+#endif
+constexpr int kRunVec = GPA_RUN_VEC;                  // 16-byte vectors per thread per tile
+constexpr int kRunTile = kRunThreads * kRunVec;       // vectors per tile (8,192 samples)
 constexpr int kMainWords = 40960;                     // 160 KB: window counters or hash pairs
 constexpr uint32_t kWinCounters = 2u * kMainWords;      // 16-bit window counters, two per word
 constexpr int kMainHashLog2 = 14;                     // 16,384 key/value pairs in hash mode
 constexpr int kSideLog2 = 11;                         // 2,048-entry side hash
 constexpr int kRunFlushTiles = 1 << 16;               // keeps 32-bit counts far from overflow
-constexpr int kRunChunk = 32;                         // tiles per claimed chunk
+constexpr int kRunChunk = GPA_RUN_CHUNK;              // tiles per claimed chunk
 
 template <int LOG2, int PROBES>
 __device__ __forceinline__ bool table_add(uint32_t* key, uint32_t* val, uint32_t k, uint32_t c, uint32_t& inserts) {
