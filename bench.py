@@ -52,6 +52,7 @@ def parse():
     ap.add_argument("--cpu-functions", type=int, default=250, help="functions in the CPU-baseline sample")
     ap.add_argument("--cpu-samples", type=int, default=8_000_000, help="sample cap of the CPU-baseline sample")
     ap.add_argument("--hist-variant", type=int, default=None, help="aggregation kernel variant (gpa_options)")
+    ap.add_argument("--options", default="", help="gpa_options fields as JSON, e.g. '{\"search_slots\": 1216}'")
     ap.add_argument("--autotune", action="store_true",
                     help="tune the launch schedule on the workload first and time the tuned one")
     ap.add_argument("--serving", action="store_true", help="run the serving workload instead")
@@ -335,6 +336,8 @@ def main():
     opts = {"search_slots": a.search_slots} if a.search_slots else {}
     if a.hist_variant is not None:
         opts["hist_variant"] = a.hist_variant
+    if a.options:
+        opts.update(json.loads(a.options))
     tuned = None
     if a.autotune:
         from paper_2009_04061_gb300 import autotune

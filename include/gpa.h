@@ -99,12 +99,16 @@ typedef struct {
 typedef struct {
   int32_t max_fixpoint_sweeps;  /* reaching-definitions sweep limit; 0 = 64 */
   int32_t max_search_nodes;     /* (block, predicate-set) nodes of the largest general search; 0 = 32768 */
-  int32_t search_slots;         /* warps with a max_search_nodes global-memory arena; 0 = four per SM */
+  int32_t search_slots;         /* warps with a max_search_nodes global-memory arena; 0 = as many as the
+                                   search kernel keeps resident (21 per SM on GB300, about 14 GB of arenas
+                                   at the default max_search_nodes) */
   int32_t max_sources_per_use;  /* distinct sources merged per stalled use; 0 = 2048 (max 2048) */
   int32_t small_search_nodes;   /* nodes of the shared-memory arena of a first-tier search warp; 0 = 128
                                    (max 1024). A search that outgrows it is redone in the next tier */
   int32_t mid_search_nodes;     /* nodes of the second tier's shared-memory arenas (three warps per SM
-                                   up to 512 nodes, one up to 1024); 0 = min(512, max_search_nodes) */
+                                   up to 512 nodes, one up to 1024); 0 = small_search_nodes (searches that
+                                   outgrow the first tier go on to the global-memory warps, which are
+                                   faster than few large shared-memory arenas) */
   int32_t hist_variant;         /* aggregation kernel: 0 (default) = one CTA per SM over a contiguous
                                    segment, shared memory used per kernel-launch run as a direct-indexed
                                    window of that kernel's counters or as a hash; grid-strided with a

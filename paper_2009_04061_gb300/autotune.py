@@ -19,7 +19,7 @@ DEFAULT = {}
 
 def candidates(sms: int) -> list[dict]:
     out = []
-    for hv, small, mid, slots in itertools.product((0, 1, 2, 3), (64, 128), (256, 512), (2, 4)):
+    for hv, small, mid, slots in itertools.product((0, 1, 2, 3), (64, 128), (128, 512), (4, 21)):
         out.append(dict(hist_variant=hv, small_search_nodes=small, mid_search_nodes=mid, search_slots=slots * sms))
     return out
 

@@ -294,6 +294,7 @@ void launch_search(const Prog& P, const Arch& A, const SearchArena* tiers, cudaS
 void launch_coverage(const Prog& P, const Arch& A, const SearchArena* tiers, cudaStream_t st, int sms,
                      int64_t* launches);
 int64_t search_arena_bytes(int nodes, int src, int layers);
+int search_warps_per_sm();  // resident one-warp CTAs of the search kernel per SM (global-memory tiers)
 void launch_build_meta(const Prog& P, int4* meta, cudaStream_t st, int sms, int64_t* launches);
 void launch_build_events(const Prog& P, int32_t* ev_off, uint32_t* events, int32_t* tmp, cudaStream_t st, int sms,
                          int64_t* launches);

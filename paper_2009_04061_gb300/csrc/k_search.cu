@@ -794,6 +794,12 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32) k_search_warp(Prog P, Arch 
 
 int64_t search_arena_bytes(int nodes, int src, int layers) { return arena_bytes(nodes, src, layers); }
 
+int search_warps_per_sm() {
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_search_warp, 32, 0) != cudaSuccess || n < 1) n = 4;
+  return n;
+}
+
 void launch_search(const Prog& P, const Arch& A, const SearchArena* tiers, cudaStream_t st, int64_t* launches) {
   // Each launch requests its own tier's arena size.
   const size_t smem1 = (size_t)tiers[0].bytes * kWarpsPerCta;

@@ -276,7 +276,10 @@ gpa_status gpa_create(const gpa_arch_desc* arch, const gpa_options* opts, gpa_ct
   for (int k = 0; k < arch->n_opclasses; ++k) { c->arch.lat[k] = arch->latency[k]; c->arch.flags[k] = arch->flags[k]; }
   if (o.max_fixpoint_sweeps == 0) o.max_fixpoint_sweeps = 64;
   if (o.max_search_nodes == 0) o.max_search_nodes = 32768;
-  if (o.search_slots == 0) o.search_slots = 4 * c->sms;
+  // Global-memory search warps: as many as the search kernel keeps resident
+  // (its registers allow 21 one-warp CTAs per SM on GB300). Many warps on
+  // global-memory arenas hide latency better than few on shared memory.
+  if (o.search_slots == 0) o.search_slots = search_warps_per_sm() * c->sms;
   if (o.max_sources_per_use == 0) o.max_sources_per_use = kBigSrc;
   if (o.small_search_nodes == 0) o.small_search_nodes = 128;
   c->opts = o;
@@ -289,7 +292,7 @@ gpa_status gpa_create(const gpa_arch_desc* arch, const gpa_options* opts, gpa_ct
   while (n1 < o.small_search_nodes && n1 < 1024) n1 <<= 1;
   while (n3 < o.max_search_nodes) n3 <<= 1;
   int n2 = 2;
-  const int want2 = o.mid_search_nodes ? o.mid_search_nodes : std::min(512, n3);
+  const int want2 = o.mid_search_nodes ? o.mid_search_nodes : n1;
   while (n2 < want2 && n2 < 1024) n2 <<= 1;
   n2 = std::max(n1, n2);
   SearchArena* T = c->tier;

@@ -69,6 +69,11 @@ class Server:
                  keep_results: bool = False):
         import torch
         self._torch = torch
+        if options is None:
+            # Slots run side by side: four global-memory search warps per SM each
+            # (about 2.6 GB of search scratch per slot) instead of a whole GPU's worth.
+            sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+            options = {"search_slots": 4 * sms}
         self.slots = [_Slot(gpa.Context(arch, options), torch.cuda.Stream()) for _ in range(slots)]
         self.budget = int(budget_bytes)
         self.used = 0
