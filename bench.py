@@ -243,7 +243,8 @@ def serving_bench(a, gpa, dev):
         sessions.append(Session(i, P.arrays, host.numpy().view(np.uint64)))
     arrivals = [d["t_arrival"] for d in specs]
     budget = int(a.budget_gb * (1 << 30))
-    srv = Server(arch, slots=a.slots, budget_bytes=budget)
+    opts = json.loads(a.options) if a.options else None
+    srv = Server(arch, slots=a.slots, budget_bytes=budget, options=opts)
     try:
         # warm each slot (lazy staging buffers, first-launch costs) with a small session
         small = min(range(len(sessions)), key=lambda i: sessions[i].samples.size)
@@ -254,7 +255,7 @@ def serving_bench(a, gpa, dev):
     finally:
         srv.close()
     mix = latency_summary(res)
-    t_seq, res1 = one_at_a_time(arch, sessions)
+    t_seq, res1 = one_at_a_time(arch, sessions, options=opts)
     seq = latency_summary(res1)
     n = sum(s.samples.size for s in sessions)
     print(json.dumps({
@@ -262,7 +263,7 @@ def serving_bench(a, gpa, dev):
         "warmup": 1, "ms_per_step": mix["span_s"] * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "int64", "data": "synthetic",
         "config": {"workload": "serving", "sessions": len(sessions), "rate_per_s": a.rate, "slots": a.slots,
-                   "budget_gb": a.budget_gb, "samples": n,
+                   "budget_gb": a.budget_gb, "samples": n, "options": opts,
                    "instructions": int(sum(int(s.program["n_instr"]) for s in sessions))},
         "latency_ms": {"p50": mix["p50_ms"], "p99": mix["p99_ms"], "mean": mix["mean_ms"], "max": mix["max_ms"]},
         "one_at_a_time": {"value": n / t_seq, "unit": UNIT, "seconds": t_seq,

@@ -173,15 +173,22 @@ __global__ void __launch_bounds__(THREADS) k_histogram(Prog P, const uint64_t* _
 // Variant 0 (default), for streams that arrive as kernel-launch runs (a
 // profiler that serializes kernels delivers them so). Each CTA (one per SM,
 // 1,024 threads) claims chunks of 16 consecutive tiles of 8,192 samples. Its
-// main shared-memory region serves the run it is in: as a direct-indexed
-// window over the current kernel's counters when they fit (no hashing, no
-// misses; 16-bit counters, two per word: the increment that brings one to
-// 32,768 moves 32,768 to the global counter), else as a 16,384-entry hash.
-// The first sample of each tile picks the mode; switching flushes the region
-// to the 64-bit global counters.
-// Samples of another kernel inside a window tile (a run boundary) go through
-// a small side hash. Both hashes send keys they cannot place to the global
-// counters, and are flushed when half full and at the end.
+// shared memory holds a window of 16-bit counters (two per word) over up to
+// 4,156 consecutive instructions of the run's kernel, and a 4,096-entry hash.
+// A kernel that fits is windowed whole; for a larger one the window is placed
+// where most of the tile's first 32 samples fall. The first sample of each
+// tile names the kernel; a new kernel flushes the window to the 64-bit global
+// counters and places it again.
+// A sample inside the window is one shared-memory atomic on its counter;
+// any other valid sample (another kernel at a run boundary, or a pc outside
+// a partial window) goes to the hash, and a key that finds no slot within
+// four probes to its global counter. The hash is flushed when half full and
+// at the end.
+// The increment that brings a 16-bit counter to 32,768 moves 32,768 to the
+// global counter. A tile's window atomics are all issued before their return
+// values are examined, and a barrier every four tiles bounds the increments
+// between two barriers to 32,768: a counter below 32,768 at a barrier stays
+// at most 32,767 + 32,768 = 65,535 until the next one, whatever the order.
 constexpr int kRunThreads = 1024;
 #ifndef GPA_RUN_VEC
 #define GPA_RUN_VEC 4
@@ -191,12 +198,21 @@ constexpr int kRunThreads = 1024;
 #endif
 constexpr int kRunVec = GPA_RUN_VEC;                  // 16-byte vectors per thread per tile
 constexpr int kRunTile = kRunThreads * kRunVec;       // vectors per tile (8,192 samples)
-constexpr int kMainWords = 40960;                     // 160 KB: window counters or hash pairs
-constexpr uint32_t kWinCounters = 2u * kMainWords;      // 16-bit window counters, two per word
-constexpr int kMainHashLog2 = 14;                     // 16,384 key/value pairs in hash mode
-constexpr int kSideLog2 = 11;                         // 2,048-entry side hash
-constexpr int kRunFlushTiles = 1 << 16;               // keeps 32-bit counts far from overflow
+constexpr int kMainWords = 49872;                     // 195 KB of window counters (12 words per instruction)
+constexpr uint32_t kWinCounters = 2u * kMainWords;    // 16-bit window counters, two per word
+constexpr uint32_t kWinInstr = kWinCounters / 24u;    // 4,156 instructions
+constexpr int kSideLog2 = 12;                         // 4,096-entry hash
+constexpr int kRunFlushTiles = 1 << 16;               // forced flush: keeps 32-bit hash counts below 2^30
 constexpr int kRunChunk = GPA_RUN_CHUNK;              // tiles per claimed chunk
+#ifndef GPA_WIN_SYNC
+#define GPA_WIN_SYNC 4
+#endif
+constexpr int kWinSyncTiles = GPA_WIN_SYNC;           // tiles between window barriers
+static_assert(32767 + kWinSyncTiles * 2 * kRunTile < 65536, "window counters could wrap between barriers");
+static_assert(kMainWords % 12 == 0, "the window holds whole instructions (12 words each)");
+// Bit f of kValid5 is set when the 5-bit (class, latency) field f names a
+// counter: class < 12, and not SELECTED with the latency flag.
+constexpr uint32_t kValid5 = 0x00FFFFFDu;
 
 template <int LOG2, int PROBES>
 __device__ __forceinline__ bool table_add(uint32_t* key, uint32_t* val, uint32_t k, uint32_t c, uint32_t& inserts) {
@@ -227,63 +243,105 @@ __device__ void table_flush(uint32_t* key, uint32_t* val, unsigned long long* cn
   }
 }
 
+// Start of the window over a kernel of n instructions: 0 when it fits,
+// else the start, among windows centred on the first 8 of the tile's first 32
+// samples of that kernel, that holds most of those 32 (`x`, this lane's;
+// lanes past the stream pass have ok == false). Every warp reads the same 32
+// samples and reaches the same answer.
+__device__ __forceinline__ uint32_t window_start(uint64_t x, bool ok, uint32_t kernel, uint32_t n) {
+  if (n <= kWinInstr) return 0u;
+  const uint32_t pc = (uint32_t)(x >> 24) & 0xFFFFFFu;
+  const bool mine = ok && (uint32_t)(x >> 48) == kernel && pc < n;
+  uint32_t lo = pc > kWinInstr / 2u ? pc - kWinInstr / 2u : 0u;
+  if (lo > n - kWinInstr) lo = n - kWinInstr;
+  uint32_t best = 0u, best_lo = 0u;
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    const uint32_t lo_c = __shfl_sync(0xffffffffu, lo, c);
+    const bool cand = __shfl_sync(0xffffffffu, mine, c);
+    const uint32_t hits = (uint32_t)__popc(__ballot_sync(0xffffffffu, mine && pc - lo_c < kWinInstr));
+    if (cand && hits > best) { best = hits; best_lo = lo_c; }
+  }
+  return best_lo;
+}
+
 __global__ void __launch_bounds__(kRunThreads, 1) k_histogram_runs(Prog P, const uint64_t* __restrict__ s,
                                                                    int64_t n, int head) {
   extern __shared__ __align__(16) uint32_t sm[];
-  uint32_t* mainr = sm;                                   // kMainWords
-  uint32_t* skey = sm + kMainWords;                       // side hash
+  uint32_t* win = sm;                                     // kMainWords window words, then one word per lane
+  uint32_t* skey = sm + kMainWords + 32;                  // hash
   uint32_t* sval = skey + (1 << kSideLog2);
-  int* ctl = reinterpret_cast<int*>(sval + (1 << kSideLog2));  // 0 main fill, 1 side fill, 2 next mode
-  int32_t* s_off = ctl + 8;
-  const bool smem_off = P.nf <= kSmemFuncs;
+  int* ctl = reinterpret_cast<int*>(sval + (1 << kSideLog2));  // 1: hash fill
   for (int t = threadIdx.x; t < (1 << kSideLog2); t += kRunThreads) { skey[t] = kNoKey; sval[t] = 0u; }
-  for (int t = threadIdx.x; t < (1 << kMainHashLog2); t += kRunThreads) {
-    mainr[t] = kNoKey;
-    mainr[(1 << kMainHashLog2) + t] = 0u;
-  }
+  if (threadIdx.x < 32) win[kMainWords + threadIdx.x] = 0u;
   if (threadIdx.x < 8) ctl[threadIdx.x] = 0;
-  if (smem_off)
-    for (int i = threadIdx.x; i <= P.nf; i += kRunThreads) s_off[i] = P.func_instr_off[i];
   __syncthreads();
-  const int32_t* foff = smem_off ? s_off : P.func_instr_off;
-  uint32_t* hkey = mainr;
-  uint32_t* hval = mainr + (1 << kMainHashLog2);
+  const int32_t* foff = P.func_instr_off;  // read through the cache: the window takes the shared memory
   const int lane = threadIdx.x & 31;
-  uint32_t bad = 0, main_ins = 0, side_ins = 0;
-
-  // Scalar head (an 8-byte-aligned start) and tail (odd count): global atomics.
-  const int64_t n2 = (n - head) / 2;
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    for (int64_t t = 0; t < head; ++t) {
-      const uint32_t k = sample_key(s[t], foff, P.nf);
-      if (k == kNoKey) ++bad; else atomicAdd(P.cnt + k, 1ull);
+  uint32_t bad = 0, side_ins = 0;
+  // The windowed kernel's first instruction and size (kept in registers: a
+  // miss of that kernel needs no offset lookup).
+  uint32_t mode_first = 0, mode_n = 0;
+  int mode = -1;
+  // A sample that is not in the window: the hash, else its global counter.
+  auto count_other = [&](uint64_t x) {
+    uint32_t key;
+    if ((int)(x >> 48) == mode) {
+      const uint32_t pc = (uint32_t)(x >> 24) & 0xFFFFFFu, f5 = (uint32_t)(x >> 19) & 31u;
+      key = (pc < mode_n && ((kValid5 >> f5) & 1u) && (x & 0x7FFull) == 0ull) ? (mode_first + pc) * 24u + f5
+                                                                                : kNoKey;
+    } else {
+      key = sample_key(x, foff, P.nf);
     }
-    for (int64_t t = head + 2 * n2; t < n; ++t) {
-      const uint32_t k = sample_key(s[t], foff, P.nf);
-      if (k == kNoKey) ++bad; else atomicAdd(P.cnt + k, 1ull);
+    if (key == kNoKey) ++bad;
+    else if (!table_add<kSideLog2, 4>(skey, sval, key, 1u, side_ins)) atomicAdd(P.cnt + key, 1ull);
+  };
+
+  // Whole tiles go through the window; what is left (an 8-byte-aligned first
+  // sample, the vectors after the last whole tile, an odd last sample) is
+  // counted by the first CTA through the hash.
+  const ulonglong2* v2 = reinterpret_cast<const ulonglong2*>(s + head);
+  const uint64_t* s2 = s + head;
+  const int64_t n2 = (n - head) / 2;
+  const int64_t n_tiles = n2 / kRunTile;
+  if (blockIdx.x == 0) {
+    if (threadIdx.x == 0) {
+      for (int64_t t = 0; t < head; ++t) count_other(s[t]);
+      for (int64_t t = head + 2 * n2; t < n; ++t) count_other(s[t]);
+    }
+    for (int64_t v = n_tiles * kRunTile + threadIdx.x; v < n2; v += kRunThreads) {
+      const ulonglong2 x = load_stream(v2 + v);
+      count_other(x.x);
+      count_other(x.y);
     }
   }
 
-  // Mode of the main region: the kernel whose window it holds, or -1 (hash).
-  int mode = -1;
-  uint32_t base = 0, range = 0;
-  auto flush_main = [&]() {
-    if (mode >= 0) {
-      for (uint32_t w = threadIdx.x; 2u * w < range; w += kRunThreads) {
-        const uint32_t c = mainr[w], lo = c & 0xFFFFu, hi = c >> 16;
-        if (lo) atomicAdd(P.cnt + base + 2u * w, (unsigned long long)lo);
-        if (hi) atomicAdd(P.cnt + base + 2u * w + 1u, (unsigned long long)hi);
+  // The window: kernel `mode` (-1: none), instructions [lo, lo + wn), whose
+  // counters start at global index base; the counter of (pc, f5), f5 the
+  // 5-bit (class, latency) field, is half f5 & 1 of word ((pc - lo) * 24 + f5) / 2.
+  // With r = bits 19..50 of a sample (f5 | pc << 5 | low 3 kernel bits << 29),
+  // a sample of kernel `mode` is in the window when r - first5 < span5,
+  // first5 = (mode << 29) | (lo << 5), span5 = wn << 5.
+  uint32_t lo = 0, wn = 0, base = 0, mode_hi = 0, first5 = 0, span5 = 0;
+  // The window holds wn * 12 words (a multiple of 4: read and cleared as 16-byte vectors).
+  auto flush_win = [&]() {
+    const uint32_t quads = wn * 3u;
+    for (uint32_t q = threadIdx.x; q < quads; q += kRunThreads) {
+      const uint4 v = reinterpret_cast<const uint4*>(win)[q];
+      const uint32_t c[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        if (!c[e]) continue;
+        unsigned long long* d = P.cnt + base + 8u * q + 2u * e;
+        if (c[e] & 0xFFFFu) atomicAdd(d, (unsigned long long)(c[e] & 0xFFFFu));
+        if (c[e] >> 16) atomicAdd(d + 1, (unsigned long long)(c[e] >> 16));
       }
-    } else {
-      table_flush<kMainHashLog2>(hkey, hval, P.cnt);
     }
   };
 
   // Tiles are handed out in chunks of kRunChunk consecutive tiles from a
   // counter (one chunk ahead, so the last tile of a chunk can prefetch the
   // first of the next): an SM that meets cheap runs takes more of them.
-  const ulonglong2* v2 = reinterpret_cast<const ulonglong2*>(s + head);
-  const int64_t n_tiles = (n2 + kRunTile - 1) / kRunTile;
   const int64_t n_chunks = (n_tiles + kRunChunk - 1) / kRunChunk;
   __shared__ long long s_claim;
   auto claim = [&]() -> int64_t {
@@ -293,95 +351,13 @@ __global__ void __launch_bounds__(kRunThreads, 1) k_histogram_runs(Prog P, const
     __syncthreads();
     return c < n_chunks ? c : n_chunks;
   };
-  ulonglong2 cur[kRunVec], nxt[kRunVec];
-  bool in_cur[kRunVec], in_nxt[kRunVec];
-  auto load_tile = [&](int64_t g, ulonglong2* v, bool* in) {
-#pragma unroll
-    for (int u = 0; u < kRunVec; ++u) {
-      const int64_t idx = g * kRunTile + u * kRunThreads + threadIdx.x;
-      in[u] = idx < n2;
-      v[u] = in[u] ? load_stream(v2 + idx) : make_ulonglong2(0ull, 0ull);
-    }
-  };
   int64_t chunk = claim();
   int64_t upcoming = chunk < n_chunks ? claim() : n_chunks;
   int64_t g = chunk * kRunChunk, g_end = min(g + kRunChunk, n_tiles);
-  if (chunk < n_chunks) load_tile(g, cur, in_cur);
-  int since = 0;
-  for (int64_t t = 0; chunk < n_chunks; ++t) {
-    const int64_t g_next = g + 1 < g_end ? g + 1 : (upcoming < n_chunks ? upcoming * kRunChunk : -1);
-    if (g_next >= 0) load_tile(g_next, nxt, in_nxt);
-    // The tile's first sample picks the mode; every thread reads it (one
-    // broadcast load), so all reach the same decision without a barrier.
-    const uint32_t k0 = (uint32_t)(__ldg(reinterpret_cast<const unsigned long long*>(v2 + g * kRunTile)) >> 48);
-    const int want = (k0 < (uint32_t)P.nf && (uint32_t)(foff[k0 + 1] - foff[k0]) * 24u <= kWinCounters)
-                         ? (int)k0 : -1;
-    if (want != mode || ++since >= kRunFlushTiles) {
-      since = 0;
-      __syncthreads();
-      flush_main();
-      __syncthreads();
-      mode = want;
-      if (mode >= 0) {
-        base = (uint32_t)foff[mode] * 24u;
-        range = (uint32_t)(foff[mode + 1] - foff[mode]) * 24u;
-        for (uint32_t q = threadIdx.x; 2u * q < range; q += kRunThreads) mainr[q] = 0u;
-      } else {
-        for (int q = threadIdx.x; q < (1 << kMainHashLog2); q += kRunThreads) { hkey[q] = kNoKey; hval[q] = 0u; }
-      }
-      if (threadIdx.x == 0) ctl[0] = 0;
-      main_ins = 0;
-      __syncthreads();
-    }
-    if (mode >= 0) {
-      // Window tile: a sample of the window's kernel indexes it directly.
-      const uint32_t n_instr = range / 24u;
-#pragma unroll
-      for (int u = 0; u < kRunVec; ++u) {
-        if (!in_cur[u]) continue;
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          const uint64_t x = h ? cur[u].y : cur[u].x;
-          if ((int)(x >> 48) == mode) {
-            const uint32_t pc = (uint32_t)(x >> 24) & 0xFFFFFFu;
-            const uint32_t cls = (uint32_t)(x >> 20) & 0xFu;
-            const uint32_t lat = (uint32_t)(x >> 19) & 1u;
-            if (pc < n_instr && cls < 12u && !(cls == 0u && lat) && (x & 0x7FFull) == 0ull) {
-              const uint32_t idx = pc * 24u + cls * 2u + lat, sh = (idx & 1u) << 4;
-              const uint32_t old = atomicAdd(&mainr[idx >> 1], 1u << sh);
-              if (((old >> sh) & 0xFFFFu) == 32767u) {  // this increment made it 32,768
-                atomicAdd(P.cnt + base + idx, 32768ull);
-                atomicSub(&mainr[idx >> 1], 32768u << sh);
-              }
-            } else {
-              ++bad;
-            }
-          } else {
-            const uint32_t key = sample_key(x, foff, P.nf);
-            if (key == kNoKey) ++bad;
-            else if (!table_add<kSideLog2, 4>(skey, sval, key, 1u, side_ins)) atomicAdd(P.cnt + key, 1ull);
-          }
-        }
-      }
-    } else {
-      // Hash tile: lanes holding the same counter merge first.
-#pragma unroll
-      for (int u = 0; u < kRunVec; ++u) {
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          const uint64_t x = h ? cur[u].y : cur[u].x;
-          const bool in = in_cur[u];
-          const uint32_t key = in ? sample_key(x, foff, P.nf) : kNoKey;
-          if (in && key == kNoKey) ++bad;
-          const unsigned peers = __match_any_sync(0xffffffffu, key);
-          if (key == kNoKey || lane != __ffs(peers) - 1) continue;
-          const uint32_t c = (uint32_t)__popc(peers);
-          if (!table_add<kMainHashLog2, 4>(hkey, hval, key, c, main_ins)) atomicAdd(P.cnt + key, (unsigned long long)c);
-        }
-      }
-    }
-#pragma unroll
-    for (int u = 0; u < kRunVec; ++u) { cur[u] = nxt[u]; in_cur[u] = in_nxt[u]; }
+  auto next_tile = [&]() -> int64_t {
+    return g + 1 < g_end ? g + 1 : (upcoming < n_chunks ? upcoming * kRunChunk : -1);
+  };
+  auto advance = [&]() {
     if (g + 1 < g_end) {
       ++g;
     } else {
@@ -392,28 +368,127 @@ __global__ void __launch_bounds__(kRunThreads, 1) k_histogram_runs(Prog P, const
         upcoming = claim();
       }
     }
-    // every 32 tiles: flush a hash that is half full
-    if ((t & 31) == 31) {
-      if (main_ins) atomicAdd(&ctl[0], (int)main_ins);
-      if (side_ins) atomicAdd(&ctl[1], (int)side_ins);
-      main_ins = side_ins = 0;
+  };
+  // A tile's vectors, and its first sample's kernel (every thread loads that
+  // word: one broadcast load per warp, issued with the tile's own loads).
+  auto load_tile = [&](int64_t t, ulonglong2* v, uint32_t& k0) {
+#pragma unroll
+    for (int u = 0; u < kRunVec; ++u) v[u] = load_stream(v2 + t * kRunTile + u * kRunThreads + threadIdx.x);
+    k0 = __ldg(reinterpret_cast<const unsigned int*>(s2 + 2 * t * kRunTile) + 1) >> 16;
+  };
+
+  int since = 0, sync_t = 0;
+  int64_t t_count = 0;
+  auto process = [&](const ulonglong2* v, uint32_t k0) {
+    const int want = k0 < (uint32_t)P.nf ? (int)k0 : -1;
+    const bool periodic = ++since >= kRunFlushTiles;  // keeps the hash's 32-bit counts small
+    if (want != mode || periodic) {
+      since = 0;
       __syncthreads();
-      const bool main_full = mode < 0 && ctl[0] > (1 << kMainHashLog2) / 2;
-      const bool side_full = ctl[1] > (1 << kSideLog2) / 2;
+      flush_win();
+      if (periodic) table_flush<kSideLog2>(skey, sval, P.cnt);
       __syncthreads();
-      if (main_full) table_flush<kMainHashLog2>(hkey, hval, P.cnt);
-      if (side_full) table_flush<kSideLog2>(skey, sval, P.cnt);
-      if (main_full || side_full) {
-        __syncthreads();
-        if (threadIdx.x == 0) {
-          if (main_full) ctl[0] = 0;
-          if (side_full) ctl[1] = 0;
+      if (periodic && threadIdx.x == 0) ctl[1] = 0;
+      mode = want;
+      lo = wn = 0;
+      mode_first = mode_n = 0;
+      if (mode >= 0) {
+        const uint32_t n_instr = (uint32_t)(foff[mode + 1] - foff[mode]);
+        mode_first = (uint32_t)foff[mode];
+        mode_n = n_instr;
+        lo = window_start(__ldg(reinterpret_cast<const unsigned long long*>(s2 + 2 * g * kRunTile + lane)), true,
+                          (uint32_t)mode, n_instr);
+        wn = min(n_instr, kWinInstr);
+        base = ((uint32_t)foff[mode] + lo) * 24u;
+        for (uint32_t q = threadIdx.x; q < wn * 3u; q += kRunThreads)
+          reinterpret_cast<uint4*>(win)[q] = make_uint4(0u, 0u, 0u, 0u);
+      }
+      mode_hi = (uint32_t)max(mode, 0) << 16;
+      first5 = ((uint32_t)max(mode, 0) << 29) | (lo << 5);
+      span5 = wn << 5;
+      __syncthreads();
+    }
+    // One shared-memory atomic per sample, without branches: a sample outside
+    // the window adds 0 to this lane's own spare word.
+    uint32_t ovf = 0, slow = 0;
+#pragma unroll
+    for (int u = 0; u < kRunVec; ++u) {
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const uint64_t x = h ? v[u].y : v[u].x;
+        const uint32_t xl = (uint32_t)x, xh = (uint32_t)(x >> 32);
+        const uint32_t rel = __funnelshift_r(xl, xh, 19) - first5;
+        const bool hit = rel < span5 && ((xh ^ mode_hi) >> 16) == 0u && ((kValid5 >> (rel & 31u)) & 1u) &&
+                         (xl & 0x7FFu) == 0u;
+        const uint32_t idx = rel - ((rel >> 5) << 3);  // (pc - lo) * 24 + f5
+        const uint32_t inc = hit ? 1u << ((idx & 1u) << 4) : 0u;
+        const uint32_t old = atomicAdd(&win[hit ? idx >> 1 : kMainWords + lane], inc);
+        // this increment took the 16-bit counter from 32,767 to 32,768
+        if (((old + inc) ^ old) & (inc << 15)) ovf |= 1u << (2 * u + h);
+        if (!hit) slow |= 1u << (2 * u + h);
+      }
+    }
+    // Each lane walks its own missed samples: a warp takes as many rounds as
+    // its busiest lane has misses (scattered misses cost one round).
+    while (slow) {
+      const int i = __ffs(slow) - 1;
+      slow &= slow - 1u;
+      uint64_t x = v[0].x;
+#pragma unroll
+      for (int q = 1; q < 2 * kRunVec; ++q)
+        if (i == q) x = (q & 1) ? v[q >> 1].y : v[q >> 1].x;
+      count_other(x);
+    }
+    if (ovf) {
+#pragma unroll
+      for (int u = 0; u < kRunVec; ++u) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          if (!((ovf >> (2 * u + h)) & 1u)) continue;
+          const uint64_t x = h ? v[u].y : v[u].x;
+          const uint32_t rel = __funnelshift_r((uint32_t)x, (uint32_t)(x >> 32), 19) - first5;
+          const uint32_t idx = rel - ((rel >> 5) << 3);
+          atomicAdd(P.cnt + base + idx, 32768ull);
+          atomicSub(&win[idx >> 1], 32768u << ((idx & 1u) << 4));
         }
       }
     }
+    if (++sync_t == kWinSyncTiles) {
+      sync_t = 0;
+      __syncthreads();
+    }
+    // every 32 tiles: flush the hash if half full
+    if ((++t_count & 31) == 0) {
+      if (side_ins) atomicAdd(&ctl[1], (int)side_ins);
+      side_ins = 0;
+      __syncthreads();
+      const bool side_full = ctl[1] > (1 << kSideLog2) / 2;
+      __syncthreads();
+      if (side_full) {
+        table_flush<kSideLog2>(skey, sval, P.cnt);
+        __syncthreads();
+        if (threadIdx.x == 0) ctl[1] = 0;
+      }
+    }
+  };
+
+  // Two register sets in turn: one tile is counted while the next is loaded.
+  ulonglong2 va[kRunVec], vb[kRunVec];
+  uint32_t ka = 0, kb = 0;
+  if (chunk < n_chunks) load_tile(g, va, ka);
+  while (chunk < n_chunks) {
+    int64_t nx = next_tile();
+    if (nx >= 0) load_tile(nx, vb, kb);
+    process(va, ka);
+    advance();
+    if (chunk >= n_chunks) break;
+    nx = next_tile();
+    if (nx >= 0) load_tile(nx, va, ka);
+    process(vb, kb);
+    advance();
   }
   __syncthreads();
-  flush_main();
+  flush_win();
   table_flush<kSideLog2>(skey, sval, P.cnt);
   for (int o = 16; o > 0; o >>= 1) bad += __shfl_xor_sync(0xffffffffu, bad, o);
   if (lane == 0 && bad) atomicAdd(&P.stats[SS_INVALID], (unsigned long long)bad);
@@ -451,8 +526,7 @@ void launch_histogram(const Prog& P, const uint64_t* samples, size_t n, cudaStre
     if (grid > sms) grid = sms;
     if (grid < 1) grid = 1;
     cudaMemsetAsync(&P.stats[SS_HIST_HEAD], 0, sizeof(unsigned long long), st);
-    const size_t smem = sizeof(uint32_t) * ((size_t)kMainWords + 2 * ((size_t)1 << kSideLog2) + 8) +
-                        (P.nf <= kSmemFuncs ? sizeof(int32_t) * (size_t)(P.nf + 1) : 0);
+    const size_t smem = sizeof(uint32_t) * ((size_t)kMainWords + 32 + 2 * ((size_t)1 << kSideLog2) + 8);
     allow_max_smem(k_histogram_runs);
     k_histogram_runs<<<(int)grid, kRunThreads, smem, st>>>(P, samples, (int64_t)n, head);
     ++*launches;

@@ -296,6 +296,44 @@ def test_histogram_variants_agree():
         assert np.array_equal(r["counts"], ci) and r["invalid"] == bi
 
 
+def test_histogram_partial_window():
+    """Kernels larger than the aggregation window (4,156 instructions): samples
+    inside the window placed for the run, samples outside it, hot counters in
+    both far past 65,536, and malformed samples of the windowed kernel."""
+    # (n_instr, n_loops, seed) of the generator; the two middle functions come out
+    # at exactly 4,156 and 4,157 instructions, the window's size and one more
+    shapes = [(500, 1, 40), (4122, 10, 40), (4127, 10, 59), (5000, 12, 43), (12000, 30, 44), (20000, 50, 45)]
+    ps = [dict(n_instr=n, n_loops=nl, max_depth=5, n_regs=128, zipf_s=1.1, seed=sd) for n, nl, sd in shapes]
+    P = synth.make_program(ps, 1.0, 3)
+    n_instr = np.diff(P.func_instr_off)
+    assert list(n_instr[1:3]) == [4156, 4157]
+    s = P.samples(3_000_001, invalid_ppm=2000, seed=7)
+    cnt, bad = oracle.histogram(P, s)
+    with g_context() as c:
+        r = gpu_run(c, P, dev(s), advise=False)
+        assert np.array_equal(r["counts"], cnt) and r["invalid"] == bad
+
+        def pack(k, pc, cls, lat, low=0):
+            return np.uint64((k << 48) | (pc << 24) | (cls << 20) | (lat << 19) | low)
+        k = 5  # about 20,000 instructions
+        a, b = pack(k, 100, 2, 1), pack(k, 15000, 3, 0)
+        crafted = np.empty(400_006, dtype=np.uint64)
+        crafted[0::2], crafted[1::2] = a, b
+        junk = [pack(k, 101, 12, 0), pack(k, 102, 0, 1), pack(k, 103, 2, 0, low=1 << 3),
+                pack(k, int(n_instr[k]), 2, 0), pack(k, 3000, 15, 1), pack(6, 0, 0, 0)]
+        crafted[1000:1000 + len(junk)] = junk
+        crafted[300_000:300_000 + len(junk)] = junk
+        ch, bh = oracle.histogram(P, crafted)
+        assert bh == 2 * len(junk)
+        r = gpu_run(c, P, dev(crafted), advise=False)
+        assert np.array_equal(r["counts"], ch) and r["invalid"] == bh
+
+
+def g_context(**opts):
+    import paper_2009_04061_gb300 as g
+    return g.Context(ARCH, dict(hist_variant=0, **opts))
+
+
 def test_autotune_picks_a_timed_candidate():
     import torch
     from paper_2009_04061_gb300 import autotune
