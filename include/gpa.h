@@ -109,13 +109,15 @@ typedef struct {
                                    up to 512 nodes, one up to 1024); 0 = small_search_nodes (searches that
                                    outgrow the first tier go on to the global-memory warps, which are
                                    faster than few large shared-memory arenas) */
-  int32_t hist_variant;         /* aggregation kernel: 0 (default) = one CTA per SM over a contiguous
-                                   segment, shared memory used per kernel-launch run as a direct-indexed
-                                   window of that kernel's counters or as a hash; grid-strided with a
-                                   shared-memory hash: 1 = 8,192 entries, 512 threads, 2 CTAs per SM;
-                                   2 = 16,384 entries, 1,024 threads, 1 CTA per SM; 3 = 8,192 entries,
-                                   256 threads, 3 CTAs per SM */
-  int32_t reserved[1];          /* must be 0 */
+  int32_t hist_variant;         /* aggregation kernel: 0 (default) = one CTA per SM taking chunks of
+                                   tiles from a counter, shared memory used per kernel-launch run as a
+                                   direct-indexed window over up to 4,156 instructions of that kernel's
+                                   counters plus a hash for the rest; grid-strided with a shared-memory
+                                   hash: 1 = 8,192 entries, 512 threads, 2 CTAs per SM; 2 = 16,384
+                                   entries, 1,024 threads, 1 CTA per SM; 3 = 8,192 entries, 256 threads,
+                                   3 CTAs per SM */
+  int32_t large_search_nodes;   /* a global-memory search that reached this many nodes is started
+                                   before the others on later steps of its program; 0 = 1024 */
 } gpa_options;
 
 /* A program: n_functions functions laid out one after another. All arrays are

@@ -49,7 +49,10 @@ enum {
   SS_COV_ALL = 80,   // the counting pass's total of sources before pruning
   SS_XN = 81,        // unpruned edges written by the export pass
   SS_HIST_HEAD = 82, // next chunk of the run-aware aggregation kernel (reset before each launch)
-  SS_N = 83
+  SS_HINT3_HEAD = 83,  // next of the searches queued straight for the third tier
+  SS_OVF3H_N = 84,     // searches for the fourth tier stored from the top of `ovf_queue`
+  SS_LARGE_N = 85,     // entries of large_queue
+  SS_N = 86
 };
 
 struct Arch {
@@ -117,6 +120,9 @@ struct Prog {
   int4* raw;                      // raw edges: def, next, dmin, dlong | flags << 24
   int64_t raw_cap;
   int4* queue;                    // general searches: use, resource, start literal set, use entry
+  int32_t large_nodes;            // node count from which a third-tier search is started early
+  uint8_t* large_hint;            // n_use: 1 when the entry's last third-tier search had large_nodes nodes or more
+  int4* large_queue;              // kLargeQueue: such searches, started before the other third-tier ones
   uint32_t* tier_hint;            // n_use: smallest search tier known to hold the entry's search (0: none);
                                   // kept across steps (a search's size depends only on the program)
   int4* ovf_queue;                // general searches that outgrew a small scratch slot
@@ -288,11 +294,20 @@ __host__ __device__ inline int64_t reach_smem_need(int64_t nbf, int64_t ne) {
   return 4 * kWords * nbf + 4 * (nbf + 1) + 4 * ne;
 }
 constexpr int64_t kReachSmemCap = 200 * 1024;
-void launch_blame(const Prog& P, const Arch& A, const SearchArena* tiers, int max_src, int32_t* scan_tmp,
-                  cudaStream_t st, int sms, int64_t* launches);
-void launch_search(const Prog& P, const Arch& A, const SearchArena* tiers, cudaStream_t st, int64_t* launches);
-void launch_coverage(const Prog& P, const Arch& A, const SearchArena* tiers, cudaStream_t st, int sms,
-                     int64_t* launches);
+// A second stream (and two events) on which the searches queued straight for
+// the third tier run beside the first two tiers.
+struct SearchFork {
+  cudaStream_t side;
+  cudaEvent_t fork, join;
+};
+constexpr int kLargeQueue = 4096;  // capacity of large_queue
+constexpr int kLargeNodes = 1024;  // default of large_nodes
+void launch_blame(const Prog& P, const Arch& A, const SearchArena* tiers, const SearchFork* fork, int max_src,
+                  int32_t* scan_tmp, cudaStream_t st, int sms, int64_t* launches);
+void launch_search(const Prog& P, const Arch& A, const SearchArena* tiers, const SearchFork* fork, cudaStream_t st,
+                   int64_t* launches);
+void launch_coverage(const Prog& P, const Arch& A, const SearchArena* tiers, const SearchFork* fork, cudaStream_t st,
+                     int sms, int64_t* launches);
 int64_t search_arena_bytes(int nodes, int src, int layers);
 int search_warps_per_sm();  // resident one-warp CTAs of the search kernel per SM (global-memory tiers)
 void launch_build_meta(const Prog& P, int4* meta, cudaStream_t st, int sms, int64_t* launches);

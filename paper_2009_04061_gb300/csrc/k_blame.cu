@@ -152,14 +152,30 @@ __global__ void k_search_local(Prog P, Arch A) {
       }
       if (P.diag) cov_add(P, e, n_all, n_kept);  // the in-block part; the search adds the rest
       // A search known to outgrow the first tier goes straight to the tier
-      // that held it before (the second tier's queue, or the third tier's
-      // region at the top of the first queue).
+      // that held it before: the second tier's queue; the third tier's large
+      // list (searches that had large_nodes nodes or more, started first) or
+      // its region at the top of the first queue; or the fourth tier's region
+      // at the top of the overflow queue.
       const uint32_t hint = P.tier_hint[e];
       const int4 task = make_int4(j, r, (int)S | (blocked ? 1 << 20 : 0), e);
-      if (hint >= 3) {
-        const unsigned long long t = atomicAdd(&P.stats[SS_HINT3_N], 1ull);
-        if (t < (unsigned long long)P.queue_cap) P.queue[P.queue_cap - 1 - (int64_t)t] = task;
+      if (hint >= 4 && P.t4_nodes > 0) {
+        const unsigned long long t = atomicAdd(&P.stats[SS_OVF3H_N], 1ull);
+        if (t < (unsigned long long)P.queue_cap) P.ovf_queue[P.queue_cap - 1 - (int64_t)t] = task;
         else capacity(P, 8);
+      } else if (hint >= 3) {
+        bool placed = false;
+        if (P.large_hint[e]) {
+          const unsigned long long t = atomicAdd(&P.stats[SS_LARGE_N], 1ull);
+          if (t < (unsigned long long)kLargeQueue) {
+            P.large_queue[t] = task;
+            placed = true;
+          }
+        }
+        if (!placed) {
+          const unsigned long long t = atomicAdd(&P.stats[SS_HINT3_N], 1ull);
+          if (t < (unsigned long long)P.queue_cap) P.queue[P.queue_cap - 1 - (int64_t)t] = task;
+          else capacity(P, 8);
+        }
       } else {
         const int slot = hint == 2 ? SS_OVF_N : SS_QUEUE_N;
         int4* q = hint == 2 ? P.ovf_queue : P.queue;
@@ -404,26 +420,26 @@ __global__ void k_coverage(Prog P) {
 
 }  // namespace
 
-void launch_coverage(const Prog& P, const Arch& A, const SearchArena* tiers, cudaStream_t st, int sms,
-                     int64_t* launches) {
+void launch_coverage(const Prog& P, const Arch& A, const SearchArena* tiers, const SearchFork* fork, cudaStream_t st,
+                     int sms, int64_t* launches) {
   const int threads = 128;
   const int g_instr = grid_for(P.ni, threads, sms);
   k_search_local<<<g_instr, threads, 0, st>>>(P, A);
   ++*launches;
-  launch_search(P, A, tiers, st, launches);
+  launch_search(P, A, tiers, fork, st, launches);
   k_coverage<<<g_instr, threads, 0, st>>>(P);
   ++*launches;
 }
 
-void launch_blame(const Prog& P, const Arch& A, const SearchArena* tiers, int max_src, int32_t* scan_tmp,
-                  cudaStream_t st, int sms, int64_t* launches) {
+void launch_blame(const Prog& P, const Arch& A, const SearchArena* tiers, const SearchFork* fork, int max_src,
+                  int32_t* scan_tmp, cudaStream_t st, int sms, int64_t* launches) {
   const int threads = 128;
   const int g_instr = grid_for(P.ni, threads, sms);
   cudaMemsetAsync(P.head, 0xFF, sizeof(int32_t) * (size_t)P.ni, st);
   k_blame_init<<<grid_for((int64_t)P.ni * kCnt, 256, sms), 256, 0, st>>>(P);
   k_search_local<<<g_instr, threads, 0, st>>>(P, A);
   *launches += 2;
-  launch_search(P, A, tiers, st, launches);
+  launch_search(P, A, tiers, fork, st, launches);
   k_merge_count<<<g_instr, threads, 0, st>>>(P, max_src);
   k_merge_big<<<sms, 32, 0, st>>>(P, max_src);
   *launches += 2;

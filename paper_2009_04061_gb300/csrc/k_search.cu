@@ -741,8 +741,11 @@ __device__ bool warp_search(const Prog& P, const Arch& A, const Arena& a, int j,
 // Persistent work-stealing warps over one queue. Tiers 1 and 2 keep the arena
 // in shared memory (tier 1: several warps per CTA, small arenas; tier 2: one
 // warp per CTA, a large arena); tier 3 uses global-memory arenas. A search that
-// outgrows its tier is queued for the next one.
-__global__ void __launch_bounds__(kWarpsPerCta * 32) k_search_warp(Prog P, Arch A, SearchArena SA, int tier) {
+// outgrows its tier is queued for the next one. Tier 3 runs in two parts:
+// part 1 takes the searches queued straight for it (the large list first)
+// and may run beside tiers 1 and 2; part 2 takes the second tier's overflow.
+__global__ void __launch_bounds__(kWarpsPerCta * 32) k_search_warp(Prog P, Arch A, SearchArena SA, int tier,
+                                                                   int part) {
   extern __shared__ __align__(16) char smem[];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int gw = blockIdx.x * (blockDim.x >> 5) + wid;
@@ -753,37 +756,62 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32) k_search_warp(Prog P, Arch 
   const Arena a = carve(base, SA.nodes, SA.src, SA.layers, s_ctr[wid]);
   for (int t = lane; t < 2 * SA.nodes; t += 32) a.ht[t] = -1;
   __syncwarp();
-  // tier 1 reads the local pass's queue, tier 2 the first overflow queue,
-  // tier 3 the second, which reuses the first queue's storage, and tier 4
-  // the third, which reuses the first overflow queue's.
-  const int4* q = (tier == 2 || tier == 4) ? P.ovf_queue : P.queue;
-  const int n_slot = tier == 1 ? SS_QUEUE_N : tier == 2 ? SS_OVF_N : tier == 3 ? SS_OVF2_N : SS_OVF3_N;
-  const int h_slot = tier == 1 ? SS_QUEUE_HEAD : tier == 2 ? SS_OVF_HEAD : tier == 3 ? SS_OVF2_HEAD : SS_OVF3_HEAD;
-  unsigned long long nq = P.stats[n_slot];
-  if (nq > (unsigned long long)P.queue_cap) nq = (unsigned long long)P.queue_cap;
-  // Tier 3 also takes the searches queued for it directly, stored from the
-  // top of the first queue down.
-  unsigned long long nh = tier == 3 ? P.stats[SS_HINT3_N] : 0ull;
-  if (nh > (unsigned long long)P.queue_cap - nq) nh = (unsigned long long)P.queue_cap - nq;
+  // The tasks of this launch, in order: nl of the large list, n0 read up
+  // from the bottom of q0, n1 read down from the top of q1.
+  // Tier 1 reads the local pass's queue; tier 2 the first overflow queue;
+  // tier 3 part 1 the large list and the region at the top of the first
+  // queue, part 2 the second overflow, which reuses the first queue's
+  // storage; tier 4 the third overflow (bottom of the first overflow queue's
+  // storage) and its top region.
+  const unsigned long long cap = (unsigned long long)P.queue_cap;
+  const int4* q0 = P.queue;
+  const int4* q1 = P.queue;
+  unsigned long long nl = 0, n0 = 0, n1 = 0;
+  int h_slot = SS_QUEUE_HEAD;
+  if (tier == 1) {
+    n0 = P.stats[SS_QUEUE_N];
+  } else if (tier == 2) {
+    q0 = P.ovf_queue, n0 = P.stats[SS_OVF_N], h_slot = SS_OVF_HEAD;
+  } else if (tier == 3 && part == 1) {
+    nl = min(P.stats[SS_LARGE_N], (unsigned long long)kLargeQueue);
+    n1 = P.stats[SS_HINT3_N], h_slot = SS_HINT3_HEAD;
+  } else if (tier == 3) {
+    n0 = P.stats[SS_OVF2_N], h_slot = SS_OVF2_HEAD;
+  } else {
+    q0 = q1 = P.ovf_queue, n0 = P.stats[SS_OVF3_N], n1 = P.stats[SS_OVF3H_N], h_slot = SS_OVF3_HEAD;
+  }
+  n0 = min(n0, cap);
+  n1 = min(n1, cap - n0);
   while (true) {
     unsigned long long t = 0;
     if (lane == 0) t = atomicAdd(&P.stats[h_slot], 1ull);
     t = __shfl_sync(0xffffffffu, t, 0);
-    if (t >= nq + nh) break;
-    const int4 task = t < nq ? q[t] : P.queue[P.queue_cap - 1 - (int64_t)(t - nq)];
+    if (t >= nl + n0 + n1) break;
+    const int4 task = t < nl        ? P.large_queue[t]
+                      : t < nl + n0 ? q0[t - nl]
+                                    : q1[cap - 1 - (t - nl - n0)];
     const int f = P.block_func[P.instr_block[task.x]];
     // The coverage count needs every source: no latency bound.
     const int bound = P.diag ? kInf - 1 : P.res_maxlat[(size_t)f * kNumRes + task.y];
     const uint16_t live = live_literals(P.res_guards[(size_t)f * kNumRes + task.y], P.guard[task.x]);
     const bool ok = warp_search(P, A, a, task.x, task.y, (uint16_t)task.z, bound, live, tier, task.w,
                                 (task.z >> 20) & 1);
-    if (ok || lane != 0) continue;
+    if (ok) {
+      // later steps start a large third-tier search before the others
+      if (lane == 0 && tier >= 3 && !P.diag && ((volatile int*)a.ctr)[0] >= P.large_nodes) P.large_hint[task.w] = 1;
+      continue;
+    }
+    if (lane != 0) continue;
     if (!P.diag) atomicMax(&P.tier_hint[task.w], (unsigned)(tier + 1));  // later steps queue it for a bigger tier
     if (tier < 3 || (tier == 3 && P.t4_nodes > 0)) {
-      const int o_slot = tier == 1 ? SS_OVF_N : tier == 2 ? SS_OVF2_N : SS_OVF3_N;
+      // tier 1 -> bottom of ovf_queue; tier 2 -> bottom of queue; tier 3 part 2
+      // -> bottom of ovf_queue (after tier 2 read it); part 1, which may run
+      // beside tier 1, -> top of ovf_queue
+      const bool top = tier == 3 && part == 1;
+      const int o_slot = tier == 1 ? SS_OVF_N : tier == 2 ? SS_OVF2_N : top ? SS_OVF3H_N : SS_OVF3_N;
       int4* oq = tier == 2 ? P.queue : P.ovf_queue;
       const unsigned long long o = atomicAdd(&P.stats[o_slot], 1ull);
-      if (o < (unsigned long long)P.queue_cap) oq[o] = task; else capacity(P, 8);
+      if (o < cap) oq[top ? cap - 1 - o : o] = task; else capacity(P, 8);
     } else {
       capacity(P, s_ctr[wid][7] > 0 ? s_ctr[wid][7] : 1);  // the last tier: why it ran out
     }
@@ -800,18 +828,32 @@ int search_warps_per_sm() {
   return n;
 }
 
-void launch_search(const Prog& P, const Arch& A, const SearchArena* tiers, cudaStream_t st, int64_t* launches) {
+void launch_search(const Prog& P, const Arch& A, const SearchArena* tiers, const SearchFork* fork, cudaStream_t st,
+                   int64_t* launches) {
   // Each launch requests its own tier's arena size.
   const size_t smem1 = (size_t)tiers[0].bytes * kWarpsPerCta;
-  allow_max_smem(k_search_warp);
-  k_search_warp<<<tiers[0].warps / kWarpsPerCta, kWarpsPerCta * 32, smem1, st>>>(P, A, tiers[0], 1);
   const size_t smem2 = (size_t)tiers[1].bytes;
-  k_search_warp<<<tiers[1].warps, 32, smem2, st>>>(P, A, tiers[1], 2);
-  k_search_warp<<<tiers[2].warps, 32, 0, st>>>(P, A, tiers[2], 3);
-  *launches += 3;
+  allow_max_smem(k_search_warp);
+  // The searches queued straight for the third tier depend on nothing the
+  // first two tiers do: with a second stream they run beside them (no kernel
+  // waits on another; the join only orders the third tier's second part,
+  // which shares its arenas, after them).
+  cudaStream_t s3 = st;
+  if (fork) {
+    cudaEventRecord(fork->fork, st);
+    cudaStreamWaitEvent(fork->side, fork->fork, 0);
+    s3 = fork->side;
+  }
+  k_search_warp<<<tiers[2].warps, 32, 0, s3>>>(P, A, tiers[2], 3, 1);
+  if (fork) cudaEventRecord(fork->join, fork->side);
+  k_search_warp<<<tiers[0].warps / kWarpsPerCta, kWarpsPerCta * 32, smem1, st>>>(P, A, tiers[0], 1, 0);
+  k_search_warp<<<tiers[1].warps, 32, smem2, st>>>(P, A, tiers[1], 2, 0);
+  if (fork) cudaStreamWaitEvent(st, fork->join, 0);
+  k_search_warp<<<tiers[2].warps, 32, 0, st>>>(P, A, tiers[2], 3, 2);
+  *launches += 4;
   if (P.t4_nodes > 0) {
     SearchArena t4{P.t4_nodes, P.t4_src, kMaxLayers, P.t4_warps, P.t4_bytes, P.t4_arena};
-    k_search_warp<<<P.t4_warps, 32, 0, st>>>(P, A, t4, 4);
+    k_search_warp<<<P.t4_warps, 32, 0, st>>>(P, A, t4, 4, 0);
     ++*launches;
   }
 }

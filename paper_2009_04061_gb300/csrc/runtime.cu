@@ -52,6 +52,7 @@ struct gpa_ctx {
   cudaStream_t capture_stream = nullptr;  // private stream for gpa_step_capture
   cudaStream_t build_stream = nullptr;    // program allocation, copies and layout builds
   cudaEvent_t ev_copied[2] = {nullptr, nullptr}, ev_used[2] = {nullptr, nullptr};
+  gpa::SearchFork fork{nullptr, nullptr, nullptr};  // third-tier searches beside tiers 1-2
 };
 
 namespace {
@@ -258,11 +259,9 @@ gpa_status gpa_create(const gpa_arch_desc* arch, const gpa_options* opts, gpa_ct
   gpa_options o{};
   if (opts) {
     o = *opts;
-    for (int r : o.reserved)
-      if (r) return GPA_ERR_INVALID_ARG;
     if (o.max_fixpoint_sweeps < 0 || o.max_search_nodes < 0 || o.search_slots < 0 || o.max_sources_per_use < 0 ||
         o.max_sources_per_use > kBigSrc || o.small_search_nodes < 0 || o.mid_search_nodes < 0 ||
-        o.hist_variant < 0 || o.hist_variant > 3)
+        o.hist_variant < 0 || o.hist_variant > 3 || o.large_search_nodes < 0)
       return GPA_ERR_INVALID_ARG;
   }
   auto* c = new (std::nothrow) gpa_ctx();
@@ -281,6 +280,7 @@ gpa_status gpa_create(const gpa_arch_desc* arch, const gpa_options* opts, gpa_ct
   // global-memory arenas hide latency better than few on shared memory.
   if (o.search_slots == 0) o.search_slots = search_warps_per_sm() * c->sms;
   if (o.max_sources_per_use == 0) o.max_sources_per_use = kBigSrc;
+  if (o.large_search_nodes == 0) o.large_search_nodes = kLargeNodes;
   if (o.small_search_nodes == 0) o.small_search_nodes = 128;
   c->opts = o;
   // Tier 1: four warps per CTA with small shared-memory arenas, three CTAs per
@@ -312,9 +312,16 @@ gpa_status gpa_create(const gpa_arch_desc* arch, const gpa_options* opts, gpa_ct
   if (!s && cudaMemset(T[2].global, 0, (size_t)T[2].bytes * T[2].warps) != cudaSuccess) s = GPA_ERR_CUDA;
   if (!s && cudaEventCreateWithFlags(&c->scratch_ev, cudaEventDisableTiming) != cudaSuccess) s = GPA_ERR_CUDA;
   if (!s && cudaStreamCreateWithFlags(&c->build_stream, cudaStreamNonBlocking) != cudaSuccess) s = GPA_ERR_CUDA;
+  if (!s && cudaStreamCreateWithFlags(&c->fork.side, cudaStreamNonBlocking) != cudaSuccess) s = GPA_ERR_CUDA;
+  if (!s && cudaEventCreateWithFlags(&c->fork.fork, cudaEventDisableTiming) != cudaSuccess) s = GPA_ERR_CUDA;
+  if (!s && cudaEventCreateWithFlags(&c->fork.join, cudaEventDisableTiming) != cudaSuccess) s = GPA_ERR_CUDA;
   if (s) {
     if (c->tier[2].global) cudaFree(c->tier[2].global);
     if (c->scratch_ev) cudaEventDestroy(c->scratch_ev);
+    if (c->build_stream) cudaStreamDestroy(c->build_stream);
+    if (c->fork.side) cudaStreamDestroy(c->fork.side);
+    if (c->fork.fork) cudaEventDestroy(c->fork.fork);
+    if (c->fork.join) cudaEventDestroy(c->fork.join);
     delete c;
     return s;
   }
@@ -336,6 +343,9 @@ gpa_status gpa_destroy(gpa_ctx* ctx) {
   if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
   if (ctx->build_stream) cudaStreamDestroy(ctx->build_stream);
   if (ctx->scratch_ev) cudaEventDestroy(ctx->scratch_ev);
+  if (ctx->fork.side) cudaStreamDestroy(ctx->fork.side);
+  if (ctx->fork.fork) cudaEventDestroy(ctx->fork.fork);
+  if (ctx->fork.join) cudaEventDestroy(ctx->fork.join);
   delete ctx;
   return GPA_OK;
 }
@@ -431,6 +441,8 @@ static gpa_status alloc_program(const gpa_program_desc* d, ProgramRec* R, int ti
   TRY(dev_alloc(R, &P.queue, (size_t)P.queue_cap));
   TRY(dev_alloc(R, &P.ovf_queue, (size_t)P.queue_cap));
   TRY(dev_alloc(R, &P.tier_hint, (size_t)std::max<int64_t>(d->n_use, 1)));
+  TRY(dev_alloc(R, &P.large_hint, (size_t)std::max<int64_t>(d->n_use, 1)));
+  TRY(dev_alloc(R, &P.large_queue, (size_t)kLargeQueue));
   TRY(dev_alloc(R, &P.cov_cnt, (size_t)std::max<int64_t>(d->n_use, 1)));
   P.diag = 0;
   TRY(dev_alloc(R, &P.edge_off, ni + 1));
@@ -507,6 +519,7 @@ gpa_status gpa_load_program(gpa_ctx* ctx, const gpa_program_desc* d, gpa_pid* ou
   s = alloc_program(d, R, ctx->tier[2].nodes);
   if (s) { free_program(R); return s; }
   Prog& P = R->P;
+  P.large_nodes = ctx->opts.large_search_nodes;
   const size_t ni = P.ni;
   int32_t *pred_off = R->pred_off, *cursor = R->cursor, *ev_off = R->ev_off;
   uint32_t* events = R->events;
@@ -519,7 +532,8 @@ gpa_status gpa_load_program(gpa_ctx* ctx, const gpa_program_desc* d, gpa_pid* ou
     free_program(R);
     return GPA_ERR_CUDA;
   }
-  if (cudaMemsetAsync(P.tier_hint, 0, sizeof(uint32_t) * (size_t)std::max<int64_t>(R->n_use, 1), st) != cudaSuccess) {
+  if (cudaMemsetAsync(P.tier_hint, 0, sizeof(uint32_t) * (size_t)std::max<int64_t>(R->n_use, 1), st) != cudaSuccess ||
+      cudaMemsetAsync(P.large_hint, 0, (size_t)std::max<int64_t>(R->n_use, 1), st) != cudaSuccess) {
     free_program(R);
     return GPA_ERR_CUDA;
   }
@@ -630,7 +644,8 @@ static gpa_status blame_body(gpa_ctx* ctx, ProgramRec* R, cudaStream_t st, bool 
   launch_dataflow(R->P, ctx->arch, ctx->opts.max_fixpoint_sweeps, st, ctx->sms, &ctx->launches);
   // The search scratch is shared by the context's programs: order its users.
   if (order_scratch) CK(cudaStreamWaitEvent(st, ctx->scratch_ev, 0));
-  launch_blame(R->P, ctx->arch, ctx->tier, ctx->opts.max_sources_per_use, R->scan_tmp, st, ctx->sms, &ctx->launches);
+  launch_blame(R->P, ctx->arch, ctx->tier, &ctx->fork, ctx->opts.max_sources_per_use, R->scan_tmp, st, ctx->sms,
+               &ctx->launches);
   if (order_scratch) CK(cudaEventRecord(ctx->scratch_ev, st));
   CK(cudaGetLastError());
   return GPA_OK;
@@ -654,7 +669,7 @@ static gpa_status coverage_run(gpa_ctx* ctx, ProgramRec* R, cudaStream_t st, int
   CK(cudaMemsetAsync(D.stats + SS_RAW_N, 0, sizeof(unsigned long long) * (SS_N - SS_RAW_N), st));
   launch_dataflow(D, ctx->arch, ctx->opts.max_fixpoint_sweeps, st, ctx->sms, &ctx->launches);
   CK(cudaStreamWaitEvent(st, ctx->scratch_ev, 0));
-  launch_coverage(D, ctx->arch, ctx->tier, st, ctx->sms, &ctx->launches);
+  launch_coverage(D, ctx->arch, ctx->tier, &ctx->fork, st, ctx->sms, &ctx->launches);
   CK(cudaEventRecord(ctx->scratch_ev, st));
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(st));
@@ -822,7 +837,7 @@ gpa_status gpa_sync_status(gpa_ctx* ctx, gpa_pid pid, gpa_stream stream, int64_t
     info[2] = (int64_t)h[SS_MAX_NODES];
     info[3] = (int64_t)h[SS_SWEEPS];
     info[4] = (int64_t)h[SS_OVF_N];
-    info[5] = (int64_t)(h[SS_OVF2_N] + h[SS_HINT3_N]);
+    info[5] = (int64_t)(h[SS_OVF2_N] + h[SS_HINT3_N] + std::min<unsigned long long>(h[SS_LARGE_N], kLargeQueue));
     info[6] = (int64_t)(h[SS_MAX_TASK] & 0x7FFFFFFFull);     // use of the largest search
     info[7] = (int64_t)((h[SS_MAX_TASK] >> 31) & 0x1FFull);  // its resource
   }

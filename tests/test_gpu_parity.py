@@ -189,6 +189,47 @@ def test_tier_hints_on_repeated_steps():
             prog.unload()
 
 
+def test_large_and_fourth_tier_hints_on_repeated_steps():
+    """Later steps start the third-tier searches that were large (here: 8 nodes or more)
+    before the others, beside the first two tiers, and send the searches that outgrew
+    the third tier straight to the program's own fourth tier; eager steps and CUDA-graph
+    launches of the same program give the oracle's results every time."""
+    import paper_2009_04061_gb300 as g
+    opts = dict(small_search_nodes=4, mid_search_nodes=8, max_search_nodes=32, search_slots=32,
+                large_search_nodes=8)
+    with g.Context(ARCH, opts) as c:
+        rng = np.random.default_rng(12)
+        P = synth.make_program(synth.batched_params(12, rng, 12), 1.0)
+        s = P.samples(1_000_000, seed=12)
+        R = oracle_run(P, s)
+        prog = c.load_program(P)
+        d = dev(s)
+
+        def results(adv):
+            st, info = prog.status()
+            cnt, bad = prog.counts()
+            rin, rout = prog.reaching()
+            return dict(status=st, info=info, counts=cnt, invalid=bad, rin=rin, rout=rout,
+                        blame=prog.blame_counts(), edges=prog.edges(), advice=adv)
+        try:
+            infos = []
+            for step in range(3):
+                prog.reset()
+                prog.ingest(d)
+                prog.blame()
+                r = results(prog.advise(fetch=True))
+                assert_full_parity(r, R)
+                infos.append(r["info"])
+            assert infos[0]["max_nodes"] > 32 and infos[0]["tier3_searches"] > 0
+            assert infos[1]["tier3_searches"] == infos[2]["tier3_searches"]
+            prog.capture_step(d)
+            for _ in range(2):
+                prog.launch_step()
+            assert_full_parity(results(prog.get_advice()), R)
+        finally:
+            prog.unload()
+
+
 def test_use_with_many_sources(ctx):
     """A use with 70 surviving sources (past the thread-per-use arrays) is merged and
     apportioned by the shared-memory path, bit for bit like the oracle."""
