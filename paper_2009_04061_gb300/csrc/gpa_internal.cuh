@@ -102,7 +102,8 @@ struct Prog {
   const int32_t* reach_order;     // nf: functions by block count, largest first
   const int32_t* block_minreach;  // nb: smallest block reachable from the block (itself included)
   const int4* block_meta;         // 2 per block: {first instr, end instr, first event, end event},
-                                  // {first pred, end pred, 0, 0} (one 32-byte line for the searches)
+                                  // {first pred, end pred, first two predecessors or -1} (one
+                                  // 32-byte line for the searches)
   const int32_t* ev_off;          // nb + 1: per-block event lists
   const uint32_t* events;         // defs and unguarded reads, bottom-up: resource | def << 9 |
                                   // kind << 10 | guard << 12 | position in block << 16

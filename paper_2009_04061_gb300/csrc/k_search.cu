@@ -209,17 +209,28 @@ __device__ bool warp_search(const Prog& P, const Arch& A, const Arena& a, int j,
   // added with a warp-synchronous insert: a lane claims an empty slot with
   // atomicCAS, allocates and publishes the node in the same round, and lanes
   // that met a claim in progress retry the slot in the next round.
-  auto link_chunk = [&](const int* lst, int cnt) {
+  // pm: the node's predecessor record (range, first two predecessors);
+  // ro0 / ro1: the reach words of those two (loaded before the scan).
+  auto link_chunk = [&](const int* lst, int cnt, int4 pm, uint32_t ro0, uint32_t ro1) {
     const bool mine = lane < cnt;
     const int u = mine ? lst[lane] : 0;
     const int B = mine ? a.blk[u] : 0;
     const int Sout = mine ? ((a.S[u] >> 16) & 0xFFFF) : 0;
     const bool open = mine && !(a.fl[u] & 4);
+    if (!open) pm = make_int4(0, 0, -1, -1);
+    // whether a def of r reaches out of the predecessor at q, and that predecessor
+    auto reaches = [&](int q) -> bool {
+      const int k = q - pm.x;
+      if (k == 0) return ro0 & bit;
+      if (k == 1) return ro1 & bit;
+      return P.rout[(size_t)__ldg(&P.pred[q]) * kWords + w] & bit;
+    };
+    auto pred_at = [&](int q) -> int {
+      const int k = q - pm.x;
+      return k == 0 ? pm.z : k == 1 ? pm.w : __ldg(&P.pred[q]);
+    };
     int deg = 0;
-    const int4 pm = open ? P.block_meta[2 * (size_t)B + 1] : make_int4(0, 0, 0, 0);
-    if (open)
-      for (int q = pm.x; q < pm.y; ++q)
-        deg += (P.rout[(size_t)__ldg(&P.pred[q]) * kWords + w] & bit) ? 1 : 0;
+    for (int q = pm.x; q < pm.y; ++q) deg += reaches(q) ? 1 : 0;
     int incl = deg;
     for (int o = 1; o < 32; o <<= 1) {
       const int y = __shfl_up_sync(0xffffffffu, incl, o);
@@ -236,8 +247,8 @@ __device__ bool warp_search(const Prog& P, const Arch& A, const Arena& a, int j,
       bool pending = kk < deg;
       int p = -1;
       if (pending) {
-        while (!(P.rout[(size_t)P.pred[qp] * kWords + w] & bit)) ++qp;
-        p = P.pred[qp++];
+        while (!reaches(qp)) ++qp;
+        p = pred_at(qp++);
       }
       uint32_t h = pending ? (node_hash(p, Sout) & hmask) : 0;
       int v = -1;
@@ -279,10 +290,20 @@ __device__ bool warp_search(const Prog& P, const Arch& A, const Arena& a, int j,
   // Expand every listed node: parallel scans, then parallel linking.
   auto expand_list = [&](const int* list, int cnt) {
     for (int c0 = 0; c0 < cnt; c0 += 32) {
-      if (c0 + lane < cnt) scan(list[c0 + lane]);
+      int4 pm = make_int4(0, 0, -1, -1);
+      uint32_t ro0 = 0u, ro1 = 0u;
+      if (c0 + lane < cnt) {
+        const int u = list[c0 + lane];
+        // The predecessor record and the reach words of the first two
+        // predecessors are loaded first: their latency overlaps the scan.
+        pm = P.block_meta[2 * (size_t)a.blk[u] + 1];
+        if (pm.z >= 0) ro0 = P.rout[(size_t)pm.z * kWords + w];
+        if (pm.w >= 0) ro1 = P.rout[(size_t)pm.w * kWords + w];
+        scan(u);
+      }
       __syncwarp();
       if (ctr[4]) return;
-      link_chunk(list + c0, min(32, cnt - c0));
+      link_chunk(list + c0, min(32, cnt - c0), pm, ro0, ro1);
       if (ctr[4]) return;
     }
   };

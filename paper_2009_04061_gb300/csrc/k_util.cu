@@ -147,7 +147,8 @@ void launch_build_events(const Prog& P, int32_t* ev_off, uint32_t* events, int32
 __global__ void k_block_meta(Prog P, int4* meta) {
   for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < P.nb; b += gridDim.x * blockDim.x) {
     meta[2 * (size_t)b] = make_int4(P.block_instr_off[b], P.block_instr_off[b + 1], P.ev_off[b], P.ev_off[b + 1]);
-    meta[2 * (size_t)b + 1] = make_int4(P.pred_off[b], P.pred_off[b + 1], 0, 0);
+    const int q0 = P.pred_off[b], q1 = P.pred_off[b + 1];
+    meta[2 * (size_t)b + 1] = make_int4(q0, q1, q1 > q0 ? P.pred[q0] : -1, q1 > q0 + 1 ? P.pred[q0 + 1] : -1);
   }
 }
 
