@@ -859,15 +859,17 @@ void launch_search(const Prog& P, const Arch& A, const SearchArena* tiers, const
   // first two tiers do: with a second stream they run beside them (no kernel
   // waits on another; the join only orders the third tier's second part,
   // which shares its arenas, after them).
+  // Tier 1 is submitted first, so its CTAs take their share of each SM and the
+  // third tier's warps fill the registers left beside them.
   cudaStream_t s3 = st;
   if (fork) {
     cudaEventRecord(fork->fork, st);
     cudaStreamWaitEvent(fork->side, fork->fork, 0);
     s3 = fork->side;
   }
+  k_search_warp<<<tiers[0].warps / kWarpsPerCta, kWarpsPerCta * 32, smem1, st>>>(P, A, tiers[0], 1, 0);
   k_search_warp<<<tiers[2].warps, 32, 0, s3>>>(P, A, tiers[2], 3, 1);
   if (fork) cudaEventRecord(fork->join, fork->side);
-  k_search_warp<<<tiers[0].warps / kWarpsPerCta, kWarpsPerCta * 32, smem1, st>>>(P, A, tiers[0], 1, 0);
   k_search_warp<<<tiers[1].warps, 32, smem2, st>>>(P, A, tiers[1], 2, 0);
   if (fork) cudaStreamWaitEvent(st, fork->join, 0);
   k_search_warp<<<tiers[2].warps, 32, 0, st>>>(P, A, tiers[2], 3, 2);
