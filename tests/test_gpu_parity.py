@@ -230,6 +230,17 @@ def test_large_and_fourth_tier_hints_on_repeated_steps():
             prog.unload()
 
 
+def test_search_of_thousands_of_nodes(ctx):
+    """One 20,034-instruction function of the batched workload whose largest search
+    (a global-memory search) has more than 4,096 nodes; results equal the oracle's."""
+    ps, _, _ = synth.workload("batched")
+    P = synth.make_program([ps[1544]], 1.0)
+    s = P.samples(2_000_000, seed=3)
+    g = gpu_run(ctx, P, dev(s))
+    assert g["status"] == 0 and g["info"]["max_nodes"] > 4096, g["info"]
+    assert_full_parity(g, oracle_run(P, s))
+
+
 def test_use_with_many_sources(ctx):
     """A use with 70 surviving sources (past the thread-per-use arrays) is merged and
     apportioned by the shared-memory path, bit for bit like the oracle."""
