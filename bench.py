@@ -458,13 +458,18 @@ def main():
         sub, m = cpu_sample(P, n, k_funcs, a.seed, a.cpu_samples)
         t = run_oracle_once(P, sub, k_funcs)
         cpu = {"value": sub.size / t, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"functions 0..{k_funcs - 1} ({int(P.func_instr_off[k_funcs])} instructions) with their "
+               "sample": f"functions 0..{k_funcs - 1} ({int(P.func_instr_off[k_funcs])} instructions) with "
                          f"the first {sub.size} samples of their launch runs; {t:.1f} s single-threaded"}
 
     # Single dependency coverage (Sec. 6) of this workload, before and after pruning.
-    nodes, single_before, single_after = prog.coverage(stream)
-    coverage = {"stalled_uses": nodes, "before_pruning": single_before / max(nodes, 1),
-                "after_pruning": single_after / max(nodes, 1)}
+    # Its searches have no latency bound, so on a very large function they can
+    # outgrow the largest arena; the diagnostic then says so.
+    try:
+        nodes, single_before, single_after = prog.coverage(stream)
+        coverage = {"stalled_uses": nodes, "before_pruning": single_before / max(nodes, 1),
+                    "after_pruning": single_after / max(nodes, 1)}
+    except gpa.GpaError as e:
+        coverage = {"unavailable": str(e)}
 
     bvp = None
     if rank == 0 and world == 1 and a.plain_workload:

@@ -241,10 +241,12 @@ gpa_status gpa_reset_counts(gpa_ctx* ctx, gpa_pid pid, gpa_stream stream);
 gpa_status gpa_ingest_samples(gpa_ctx* ctx, gpa_pid pid, const uint64_t* dev_samples, size_t n,
                               gpa_stream stream);
 
-/* Step (a) from host memory: copies n samples in chunks through library
- * staging buffers (pinned host memory makes the copies overlap the
- * aggregation) and aggregates them. Returns when the copies are enqueued;
- * host_samples must stay valid until stream completes this call. */
+/* Step (a) from host memory (8-byte aligned). Pinned host memory that the
+ * current device can address is read by the aggregation kernel directly over
+ * the host link; other memory is copied in chunks through library staging
+ * buffers, the copy of one chunk overlapping the aggregation of the last.
+ * Returns when the work is enqueued; host_samples must stay valid and
+ * unchanged until stream completes this call. */
 gpa_status gpa_ingest_host_samples(gpa_ctx* ctx, gpa_pid pid, const uint64_t* host_samples, size_t n,
                                    gpa_stream stream);
 

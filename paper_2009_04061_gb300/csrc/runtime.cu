@@ -605,6 +605,20 @@ gpa_status gpa_ingest_host_samples(gpa_ctx* ctx, gpa_pid pid, const uint64_t* ho
   if (n == 0) return GPA_OK;
   if (!host) return GPA_ERR_INVALID_ARG;
   cudaStream_t st = (cudaStream_t)stream;
+  // Pinned host memory that this device can address (page-locked allocations
+  // are mapped under unified addressing) is read by the aggregation kernel
+  // itself over the host link: no staging buffer, no copy engine. Other
+  // memory goes through the staging buffers.
+  cudaPointerAttributes at{};
+  int dev = -1;
+  if (cudaPointerGetAttributes(&at, host) == cudaSuccess && at.type == cudaMemoryTypeHost && at.devicePointer &&
+      cudaGetDevice(&dev) == cudaSuccess && dev == ctx->device) {
+    launch_histogram(R->P, static_cast<const uint64_t*>(at.devicePointer), n, st, ctx->sms, &ctx->launches,
+                     ctx->opts.hist_variant);
+    CK(cudaGetLastError());
+    return GPA_OK;
+  }
+  cudaGetLastError();  // a failed query is not an error here
   if (!ctx->stage[0]) {
     ctx->stage_n = kStageSamples;
     for (int k = 0; k < 2; ++k) {

@@ -99,15 +99,23 @@ def test_batched_subset_of_uneven_functions(ctx):
     assert_full_parity(g, oracle_run(P, s))
 
 
-def test_host_ingest_equals_device_ingest(ctx):
+def test_host_ingest_pinned_and_pageable(ctx):
+    """Host samples: pinned memory read by the aggregation kernel over the host link
+    (also from an interior pointer that is not 16-byte aligned), pageable memory
+    through the staging buffers; all give the oracle's counts and the device path's blame."""
     ps, _, kz = synth.workload("rodinia")
     P = synth.make_program(ps, kz)
-    s = P.samples(1_000_000, seed=3)
+    s = P.samples(1_000_001, invalid_ppm=1000, seed=3)
     import torch
-    h = torch.from_numpy(s.view(np.int64)).pin_memory()
-    g1 = gpu_run(ctx, P, None, host=h)
     g2 = gpu_run(ctx, P, dev(s))
-    assert np.array_equal(g1["counts"], g2["counts"]) and np.array_equal(g1["blame"], g2["blame"])
+    cnt, bad = oracle.histogram(P, s)
+    assert np.array_equal(g2["counts"], cnt) and g2["invalid"] == bad
+    h = torch.from_numpy(s.view(np.int64)).pin_memory()
+    for host, (c, b) in [(h, (cnt, bad)), (h[1:], oracle.histogram(P, s[1:])), (s.copy(), (cnt, bad))]:
+        g1 = gpu_run(ctx, P, None, host=host)
+        assert np.array_equal(g1["counts"], c) and g1["invalid"] == b
+    g1 = gpu_run(ctx, P, None, host=h)
+    assert np.array_equal(g1["blame"], g2["blame"])
 
 
 def test_plain_per_function_equals_batched(ctx):
