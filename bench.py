@@ -351,6 +351,10 @@ def main():
         opts = best
     ctx = gpa.Context(synth.default_arch(), opts or None)
     prog = ctx.load_program(P)
+    # Seeded launch statistics of the workload's kernels on this GPU's SM model:
+    # the advice step also runs the parallel optimizers (Table 2, Eqs. 6-10).
+    prog.set_launch_stats(synth.launch_stats(P.n_functions, a.seed),
+                          gpa.gpa_sm_model_of_device(torch.cuda.current_device()))
     stream = torch.cuda.current_stream(dev)
 
     def step(ev=None):
@@ -470,6 +474,10 @@ def main():
                     "after_pruning": single_after / max(nodes, 1)}
     except gpa.GpaError as e:
         coverage = {"unavailable": str(e)}
+    adv = prog.get_advice(stream)
+    parallel = {"block_increase_matched": int(adv["par_match"][:, 0].sum()),
+                "thread_increase_matched": int(adv["par_match"][:, 1].sum()),
+                "largest_speedup": float(adv["par_speedup"].max())}
 
     bvp = None
     if rank == 0 and world == 1 and a.plain_workload:
@@ -491,6 +499,7 @@ def main():
             "largest_search_nodes": info["max_nodes"], "gpu_launches": launches,
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
             "batched_vs_plain": bvp, "autotune": tuned, "options": opts, "dependency_coverage": coverage,
+            "parallel_optimizers": parallel,
         }
         print(json.dumps(line), flush=True)
     prog.unload()

@@ -166,6 +166,32 @@ typedef struct {
   const int32_t* loop_header;
 } gpa_program_desc;
 
+/* Launch statistics of one function (kernel) as the profiler's kernel
+ * records give them, input of the parallel optimizers (Table 2 "Parallel
+ * Optimizers", Sec. 5.2 "Parallel Optimization Estimator"). */
+typedef struct {
+  int64_t blocks;             /* blocks in the grid, >= 1 */
+  int32_t threads_per_block;  /* 1..1024 */
+  int32_t regs_per_thread;    /* 0..255 */
+  int32_t smem_per_block;     /* shared memory per block in bytes (static + dynamic), >= 0 */
+  int32_t reserved;           /* must be 0 */
+} gpa_launch_stats;
+
+/* The SM of the occupancy model behind the parallel estimators (the public
+ * occupancy-calculator rules): blocks per SM = the least of
+ *   max_blocks_per_sm,
+ *   floor(max_warps_per_sm / warps per block),
+ *   floor(schedulers_per_sm * floor(regs_per_sm / schedulers_per_sm / regs per warp) / warps per block)
+ *     with regs per warp = regs_per_thread * 32 rounded up to reg_alloc_unit (no limit if 0),
+ *   floor(smem_per_sm / (smem_per_block + smem_reserved_per_block rounded up to smem_alloc_unit))
+ *     (no limit if smem_per_block is 0).
+ * All fields > 0 except smem_reserved_per_block (>= 0). */
+typedef struct {
+  int32_t n_sms, schedulers_per_sm, max_warps_per_sm, max_blocks_per_sm;
+  int32_t regs_per_sm, reg_alloc_unit;
+  int32_t smem_per_sm, smem_alloc_unit, smem_reserved_per_block;
+} gpa_sm_model;
+
 /* Advice destination (host memory); any NULL field is skipped.
  *  totals[n_functions*4]           T, A (active), L (latency), issued samples (Sec. 2.1, 5.2).
  *  matched[n_functions*8]          matched samples M (Eq. 2) or M^L (Eq. 4) per optimizer.
@@ -177,7 +203,19 @@ typedef struct {
  *                                  distance (shortest path), matched samples; -1 when unused.
  *  loop_active[n_loops], loop_matched[n_loops], loop_speedup[n_loops]  Eq. 5 per loop scope.
  *  line_stall[n_lines], line_latency[n_lines]  blamed stall samples per source line and their
- *                                  latency-sample part. */
+ *                                  latency-sample part.
+ *  par_match[n_functions*2] (int32)  parallel optimizers (0 Block Increase, 1 Thread Increase):
+ *                                  1 when Table 2's condition holds (fewer blocks than SMs; the
+ *                                  per-SM block limit binds before the warp, register and
+ *                                  shared-memory limits, with blocks enough to reach it).
+ *  par_speedup[n_functions*2]      Eq. 10 with f = 1 when matched, else 1.0 (also without launch
+ *                                  statistics). Not part of rank (kept apart from the code
+ *                                  optimizers).
+ *  par_warps[n_functions*4]        per optimizer: resident warps per scheduler before and after
+ *                                  (W of Eq. 8 and W_new of Eq. 9); 0 without launch statistics.
+ *  par_limit[n_functions] (int32)  the binding occupancy limit: 0 warps, 1 registers, 2 shared
+ *                                  memory, 3 blocks per SM (lowest id on ties); -1 without
+ *                                  launch statistics. */
 typedef struct {
   uint64_t* totals;
   uint64_t* matched;
@@ -190,6 +228,10 @@ typedef struct {
   double* loop_speedup;
   uint64_t* line_stall;
   uint64_t* line_latency;
+  int32_t* par_match;
+  double* par_speedup;
+  double* par_warps;
+  int32_t* par_limit;
 } gpa_advice;
 
 const char* gpa_status_string(gpa_status s);
@@ -349,6 +391,17 @@ gpa_status gpa_get_edges(gpa_ctx* ctx, gpa_pid pid, int64_t* n_edges, int64_t ca
                          int32_t* dmin, int32_t* dlong, uint32_t* flags, uint64_t* share, gpa_stream stream);
 /* Copies the advice computed by the last gpa_advise (see gpa_advice). */
 gpa_status gpa_get_advice(gpa_ctx* ctx, gpa_pid pid, const gpa_advice* out, gpa_stream stream);
+
+/* Sets the launch statistics of the program's functions (stats[n_functions],
+ * host, copied) and the SM they ran on, for the parallel optimizers of later
+ * gpa_advise calls; stats == NULL clears them. Synchronous. Returns
+ * GPA_ERR_INVALID_ARG for a field out of its range. */
+gpa_status gpa_set_launch_stats(gpa_ctx* ctx, gpa_pid pid, const gpa_launch_stats* stats, const gpa_sm_model* sm);
+
+/* The SM model of a CUDA device: counts and sizes from the device properties;
+ * register allocation in units of 256 per warp, shared memory in units of 128
+ * bytes (the allocation granularities of this GPU generation). */
+gpa_status gpa_sm_model_of_device(int device, gpa_sm_model* out);
 
 /* Kernel launches issued by this context since creation (for accounting). */
 int64_t gpa_launch_count(gpa_ctx* ctx);

@@ -14,6 +14,8 @@ import subprocess
 
 import numpy as np
 
+from .parallel import parallel  # noqa: E402,F401  (Table 2 parallel optimizers, Eqs. 6-10)
+
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB = os.path.join(_HERE, "libgpa_oracle.so")
 N_OPT = 8

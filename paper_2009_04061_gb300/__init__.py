@@ -6,4 +6,5 @@ from .gpa import (Context, GpaError, Program, gpa_advise, gpa_arch_default, gpa_
                   gpa_exclusive_scan_noalloc,
                   gpa_get_advice, gpa_get_blame, gpa_get_counts, gpa_get_edges, gpa_get_reaching,
                   gpa_ingest_host_samples, gpa_ingest_samples, gpa_launch_count, gpa_load_program,
-                  gpa_reset_counts, gpa_sync_status, gpa_unload_program, header_functions, library, OPT_NAMES)
+                  gpa_reset_counts, gpa_set_launch_stats, gpa_sm_model_of_device, gpa_sync_status,
+                  gpa_unload_program, header_functions, library, LAUNCH_DTYPE, OPT_NAMES)

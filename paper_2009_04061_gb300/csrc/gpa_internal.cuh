@@ -62,6 +62,16 @@ struct Arch {
 };
 
 // Device view of one loaded program and its per-step buffers.
+// One function's launch statistics (the layout of gpa_launch_stats) and the
+// SM of the occupancy model (the fields of gpa_sm_model).
+struct LaunchRec {
+  long long blocks;
+  int32_t threads, regs, smem, reserved;
+};
+struct SmModel {
+  int32_t n_sms, schedulers, max_warps, max_blocks, regs, reg_unit, smem, smem_unit, smem_reserved;
+};
+
 struct Prog {
   int32_t nf, ni, nb, nl, n_lines;
   int32_t diag;                   // 1: the searches count sources (gpa_dependency_coverage), 2: they export
@@ -151,6 +161,14 @@ struct Prog {
   double* a_loop_speedup;
   unsigned long long* a_line_stall;
   unsigned long long* a_line_lat;
+  // parallel optimizers (Table 2, Eqs. 6-10): launch statistics per function
+  // (nullptr: none set) and the SM they ran on
+  const LaunchRec* launch;
+  SmModel sm;
+  int32_t* a_par_match;           // nf * 2
+  double* a_par_speedup;          // nf * 2
+  double* a_par_warps;            // nf * 4
+  int32_t* a_par_limit;           // nf
 };
 
 // Per-warp arenas of the general (multi-block) search.

@@ -1,7 +1,8 @@
 // Step (d), Sec. 5: roll blame up to lines, loops and functions, match the
 // code optimizers of Table 2, estimate their speedups (Eq. 2 for stall
 // elimination, Eq. 4 for latency hiding, Eq. 5 per loop scope), rank them and
-// pick each optimizer's top five hotspots (def, use, distance).
+// pick each optimizer's top five hotspots (def, use, distance); with launch
+// statistics, the parallel optimizers (Eqs. 6-10).
 //
 // One CTA per function: threads stride over the function's instructions and
 // its merged edges (contiguous, since edges are ordered by use), reduce the
@@ -62,6 +63,85 @@ __device__ __forceinline__ EdgeMatch edge_match(const Prog& P, const Arch& A, in
   m.cr = sh[1] + (global_mem ? sh[3] : 0ull);                                 // latency samples
   m.lu = lca_loop(P, innermost_loop(P, P.e_def[e]), innermost_loop(P, P.e_use[e])) >= 0 ? m.cr : 0ull;
   return m;
+}
+
+// Parallel optimizers of function f (Table 2; Sec. 5.2, Eqs. 6-10 with f = 1),
+// from its launch statistics, the SM model and its totals (T samples, issued).
+// Occupancy: blocks per SM is the least of the warp, register, shared-memory
+// and block-count limits (the binding one is reported, lowest id on ties).
+// W = resident blocks per SM * warps per block / schedulers; R_I = issued / T;
+// I(W) = 1 - (1 - R_I)^W (Eqs. 8-9).
+//  Block Increase (fewer blocks than SMs): the same threads in one block per
+//  SM, W_new = W * blocks / SMs; every SM runs one wave, so a scheduler's
+//  warps over the run are its resident warps: C_W = W_new / W (Eq. 6).
+//  Thread Increase (the block-count limit binds, and the grid reaches it): the
+//  same threads in larger blocks, W_new = the warps per SM the warp, register
+//  and shared-memory limits (per warp) and the grid allow, / schedulers; a
+//  scheduler's warps over the run are unchanged: C_W = 1.
+//  S = (1 / C_W) * C_I (Eq. 10), C_I = I(W_new) / I(W) (Eq. 7).
+__device__ void parallel_advice(const Prog& P, int f, unsigned long long T, unsigned long long issued) {
+  int match[2] = {0, 0}, limit = -1;
+  double sp[2] = {1.0, 1.0}, w[4] = {0.0, 0.0, 0.0, 0.0};
+  if (P.launch) {
+    const LaunchRec L = P.launch[f];
+    const SmModel& M = P.sm;
+    const long long big = 1ll << 40;
+    const long long wpb = (L.threads + 31) / 32;
+    long long lim[4];
+    lim[0] = M.max_warps / wpb;
+    long long warps_by_regs = M.max_warps;  // warps per SM the registers allow
+    if (L.regs > 0) {
+      const long long rpw = ((long long)L.regs * 32 + M.reg_unit - 1) / M.reg_unit * M.reg_unit;
+      warps_by_regs = (long long)M.schedulers * ((M.regs / M.schedulers) / rpw);
+      lim[1] = warps_by_regs / wpb;
+    } else {
+      lim[1] = big;
+    }
+    long long warps_by_smem = big;          // warps per SM the shared memory allows
+    if (L.smem > 0) {
+      const long long per = ((long long)L.smem + M.smem_reserved + M.smem_unit - 1) / M.smem_unit * M.smem_unit;
+      lim[2] = M.smem / per;
+      warps_by_smem = lim[2] * wpb;
+    } else {
+      lim[2] = big;
+    }
+    lim[3] = M.max_blocks;
+    long long bps = lim[0];
+    limit = 0;
+    for (int q = 1; q < 4; ++q)
+      if (lim[q] < bps) { bps = lim[q]; limit = q; }
+    const long long per_sm = (L.blocks + M.n_sms - 1) / M.n_sms;  // blocks per SM the grid gives
+    const long long rb = bps < per_sm ? bps : per_sm;
+    const double W = (double)(rb * wpb) / (double)M.schedulers;
+    match[0] = L.blocks < M.n_sms;
+    match[1] = limit == 3 && per_sm >= bps;
+    double Wn[2] = {0.0, 0.0};
+    Wn[0] = W * (double)L.blocks / (double)M.n_sms;
+    long long wn = M.max_warps;
+    if (warps_by_regs < wn) wn = warps_by_regs;
+    if (warps_by_smem < wn) wn = warps_by_smem;
+    const long long grid_warps = (L.blocks * wpb + M.n_sms - 1) / M.n_sms;
+    if (grid_warps < wn) wn = grid_warps;
+    Wn[1] = (double)wn / (double)M.schedulers;
+    // an estimate needs a resident warp and an issue rate above zero
+    const bool est_ok = bps > 0 && T > 0 && issued > 0;
+    const double R = T ? (double)issued / (double)T : 0.0;
+    const double I = 1.0 - pow(1.0 - R, W);
+    for (int k = 0; k < 2; ++k) {
+      if (!match[k]) continue;
+      w[2 * k] = W;
+      w[2 * k + 1] = Wn[k];
+      if (!est_ok) continue;
+      const double cw = k == 0 ? Wn[0] / W : 1.0, ci = (1.0 - pow(1.0 - R, Wn[k])) / I;
+      sp[k] = (1.0 / cw) * ci;
+    }
+  }
+  for (int k = 0; k < 2; ++k) {
+    P.a_par_match[(size_t)f * 2 + k] = match[k];
+    P.a_par_speedup[(size_t)f * 2 + k] = sp[k];
+  }
+  for (int k = 0; k < 4; ++k) P.a_par_warps[(size_t)f * 4 + k] = w[k];
+  P.a_par_limit[f] = limit;
 }
 
 __global__ void __launch_bounds__(kThreads) k_advise(Prog P, Arch A) {
@@ -143,6 +223,7 @@ __global__ void __launch_bounds__(kThreads) k_advise(Prog P, Arch A) {
       }
       for (int o = 0; o < N_O; ++o) P.a_rank[(size_t)f * N_O + o] = ord[o];
       for (int q = 0; q < 4; ++q) P.a_totals[(size_t)f * 4 + q] = tot[q];
+      parallel_advice(P, f, T, tot[3]);
     }
     // Hotspots, one optimizer at a time: thread-local top five, then thread 0 merges.
     for (int o = 0; o < N_O; ++o) {

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstddef>
 #include <cstdio>
 #include <cstring>
 #include <map>
@@ -24,6 +25,7 @@ struct ProgramRec {
   cudaStream_t build = nullptr;         // stream of the stream-ordered allocations and copies
   int64_t bytes = 0;                    // device bytes requested for the program
   cudaGraphExec_t step_exec = nullptr;  // captured step (gpa_step_capture)
+  LaunchRec* launch = nullptr;          // launch statistics (gpa_set_launch_stats)
   int64_t step_launches = 0;            // kernels in it
   int32_t *pred_off = nullptr, *cursor = nullptr, *ev_off = nullptr;  // build scratch kept from allocation
   uint32_t* events = nullptr;
@@ -93,6 +95,7 @@ gpa_status dev_copy(ProgramRec* R, const T** dst, const T* src, size_t n) {
 void free_program(ProgramRec* R) {
   if (R->step_exec) cudaGraphExecDestroy(R->step_exec);
   if (R->xbuf) cudaFree(R->xbuf);
+  if (R->launch) cudaFree(R->launch);
   if (R->build) cudaStreamSynchronize(R->build);
   for (void* p : R->allocs) cudaFree(p);
   delete R;
@@ -467,6 +470,12 @@ static gpa_status alloc_program(const gpa_program_desc* d, ProgramRec* R, int ti
   TRY(dev_alloc(R, &P.a_loop_speedup, nl));
   TRY(dev_alloc(R, &P.a_line_stall, (size_t)P.n_lines));
   TRY(dev_alloc(R, &P.a_line_lat, (size_t)P.n_lines));
+  TRY(dev_alloc(R, &P.a_par_match, nf * 2));
+  TRY(dev_alloc(R, &P.a_par_speedup, nf * 2));
+  TRY(dev_alloc(R, &P.a_par_warps, nf * 4));
+  TRY(dev_alloc(R, &P.a_par_limit, nf));
+  P.launch = nullptr;
+  P.sm = SmModel{};
   // Fourth search tier: room for 64 literal sets per block of the largest
   // function (at most 2^22 nodes), when that is more than the context's
   // third tier holds; fewer warps for bigger arenas (about 2 GB at most).
@@ -817,7 +826,70 @@ static gpa_status copy_advice(ProgramRec* R, const gpa_advice* out, cudaStream_t
   CK(cp(out->loop_speedup, P.a_loop_speedup, (size_t)P.nl * 8));
   CK(cp(out->line_stall, P.a_line_stall, (size_t)P.n_lines * 8));
   CK(cp(out->line_latency, P.a_line_lat, (size_t)P.n_lines * 8));
+  CK(cp(out->par_match, P.a_par_match, nf * 2 * 4));
+  CK(cp(out->par_speedup, P.a_par_speedup, nf * 2 * 8));
+  CK(cp(out->par_warps, P.a_par_warps, nf * 4 * 8));
+  CK(cp(out->par_limit, P.a_par_limit, nf * 4));
   CK(cudaStreamSynchronize(st));
+  return GPA_OK;
+}
+
+static_assert(sizeof(LaunchRec) == sizeof(gpa_launch_stats) && offsetof(gpa_launch_stats, threads_per_block) == 8 &&
+                  offsetof(LaunchRec, threads) == 8 && offsetof(gpa_launch_stats, smem_per_block) == 16 &&
+                  offsetof(LaunchRec, smem) == 16,
+              "LaunchRec mirrors gpa_launch_stats");
+
+gpa_status gpa_set_launch_stats(gpa_ctx* ctx, gpa_pid pid, const gpa_launch_stats* stats, const gpa_sm_model* sm) {
+  ProgramRec* R = find(ctx, pid);
+  if (!R) return GPA_ERR_NO_PROGRAM;
+  Prog& P = R->P;
+  if (stats) {
+    if (!sm || sm->n_sms < 1 || sm->schedulers_per_sm < 1 || sm->max_warps_per_sm < 1 || sm->max_blocks_per_sm < 1 ||
+        sm->regs_per_sm < 1 || sm->reg_alloc_unit < 1 || sm->smem_per_sm < 1 || sm->smem_alloc_unit < 1 ||
+        sm->smem_reserved_per_block < 0)
+      return GPA_ERR_INVALID_ARG;
+    for (int f = 0; f < P.nf; ++f) {
+      const gpa_launch_stats& L = stats[f];
+      if (L.blocks < 1 || L.threads_per_block < 1 || L.threads_per_block > 1024 || L.regs_per_thread < 0 ||
+          L.regs_per_thread > 255 || L.smem_per_block < 0 || L.reserved != 0)
+        return GPA_ERR_INVALID_ARG;
+    }
+  }
+  // Kernels of earlier calls may read the old statistics; a captured step
+  // holds the old ones and is dropped (capture it again).
+  CK(cudaDeviceSynchronize());
+  if (R->step_exec) {
+    cudaGraphExecDestroy(R->step_exec);
+    R->step_exec = nullptr;
+  }
+  if (!stats) {
+    P.launch = nullptr;
+    return GPA_OK;
+  }
+  if (!R->launch && cudaMalloc(&R->launch, sizeof(LaunchRec) * (size_t)std::max(P.nf, 1)) != cudaSuccess) {
+    R->launch = nullptr;
+    return GPA_ERR_OOM;
+  }
+  CK(cudaMemcpy(R->launch, stats, sizeof(LaunchRec) * (size_t)P.nf, cudaMemcpyHostToDevice));
+  P.launch = R->launch;
+  P.sm = SmModel{sm->n_sms, sm->schedulers_per_sm, sm->max_warps_per_sm, sm->max_blocks_per_sm, sm->regs_per_sm,
+                 sm->reg_alloc_unit, sm->smem_per_sm, sm->smem_alloc_unit, sm->smem_reserved_per_block};
+  return GPA_OK;
+}
+
+gpa_status gpa_sm_model_of_device(int device, gpa_sm_model* out) {
+  if (!out) return GPA_ERR_INVALID_ARG;
+  cudaDeviceProp d{};
+  CK(cudaGetDeviceProperties(&d, device));
+  out->n_sms = d.multiProcessorCount;
+  out->schedulers_per_sm = 4;
+  out->max_warps_per_sm = d.maxThreadsPerMultiProcessor / 32;
+  out->max_blocks_per_sm = d.maxBlocksPerMultiProcessor;
+  out->regs_per_sm = d.regsPerMultiprocessor;
+  out->reg_alloc_unit = 256;
+  out->smem_per_sm = (int32_t)d.sharedMemPerMultiprocessor;
+  out->smem_alloc_unit = 128;
+  out->smem_reserved_per_block = (int32_t)d.reservedSharedMemPerBlock;
   return GPA_OK;
 }
 

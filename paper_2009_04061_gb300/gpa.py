@@ -56,11 +56,22 @@ class gpa_program_desc(ctypes.Structure):
 
 
 _ADV = ["totals", "matched", "speedup", "rank", "n_hot", "hot", "loop_active", "loop_matched", "loop_speedup",
-        "line_stall", "line_latency"]
+        "line_stall", "line_latency", "par_match", "par_speedup", "par_warps", "par_limit"]
 
 
 class gpa_advice(ctypes.Structure):
     _fields_ = [(k, ctypes.c_void_p) for k in _ADV]
+
+
+# One function's launch statistics (gpa_launch_stats) as a numpy record.
+LAUNCH_DTYPE = np.dtype([("blocks", np.int64), ("threads_per_block", np.int32), ("regs_per_thread", np.int32),
+                         ("smem_per_block", np.int32), ("reserved", np.int32)])
+_SM_FIELDS = ["n_sms", "schedulers_per_sm", "max_warps_per_sm", "max_blocks_per_sm", "regs_per_sm", "reg_alloc_unit",
+              "smem_per_sm", "smem_alloc_unit", "smem_reserved_per_block"]
+
+
+class gpa_sm_model(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_int32) for k in _SM_FIELDS]
 
 
 _lib = None
@@ -102,6 +113,8 @@ def library() -> ctypes.CDLL:
         "gpa_get_blame": ([vp, u32, vp, vp], i32),
         "gpa_get_edges": ([vp, u32, vp, i64, vp, vp, vp, vp, vp, vp, vp], i32),
         "gpa_get_advice": ([vp, u32, vp, vp], i32),
+        "gpa_set_launch_stats": ([vp, u32, vp, vp], i32),
+        "gpa_sm_model_of_device": ([ctypes.c_int, vp], i32),
         "gpa_launch_count": ([vp], i64),
         "gpa_exclusive_scan_noalloc": ([vp, i64, vp, vp], i32),
     }
@@ -245,7 +258,9 @@ def _advice_buffers(shape):
                 n_hot=np.zeros((nf, NUM_OPT), np.int32), hot=np.zeros((nf, NUM_OPT, 5, 6), np.int64),
                 loop_active=np.zeros(max(nl, 1), np.uint64), loop_matched=np.zeros(max(nl, 1), np.uint64),
                 loop_speedup=np.zeros(max(nl, 1), np.float64), line_stall=np.zeros(max(nlines, 1), np.uint64),
-                line_latency=np.zeros(max(nlines, 1), np.uint64))
+                line_latency=np.zeros(max(nlines, 1), np.uint64), par_match=np.zeros((nf, 2), np.int32),
+                par_speedup=np.zeros((nf, 2), np.float64), par_warps=np.zeros((nf, 2, 2), np.float64),
+                par_limit=np.zeros(nf, np.int32))
 
 
 def _trim(b, shape):
@@ -266,6 +281,28 @@ def gpa_advise(ctx, pid, shape=None, stream=None):
     adv = gpa_advice(*[_p(b[k]) for k in _ADV])
     _check(library().gpa_advise(ctx, pid, ctypes.byref(adv), _stream(stream)), "gpa_advise")
     return _trim(b, shape)
+
+
+def gpa_set_launch_stats(ctx, pid, stats, sm: dict | None = None):
+    """stats: LAUNCH_DTYPE records (or a dict of equal-length arrays), one per
+    function, or None to clear; sm: the gpa_sm_model fields as a dict."""
+    if stats is None:
+        _check(library().gpa_set_launch_stats(ctx, pid, None, None), "gpa_set_launch_stats")
+        return
+    if isinstance(stats, dict):
+        rec = np.zeros(len(stats["blocks"]), LAUNCH_DTYPE)
+        for k in ("blocks", "threads_per_block", "regs_per_thread", "smem_per_block"):
+            rec[k] = stats[k]
+        stats = rec
+    stats = np.ascontiguousarray(stats, dtype=LAUNCH_DTYPE)
+    m = gpa_sm_model(*[int(sm[k]) for k in _SM_FIELDS])
+    _check(library().gpa_set_launch_stats(ctx, pid, _p(stats), ctypes.byref(m)), "gpa_set_launch_stats")
+
+
+def gpa_sm_model_of_device(device: int = 0) -> dict:
+    m = gpa_sm_model()
+    _check(library().gpa_sm_model_of_device(device, ctypes.byref(m)), "gpa_sm_model_of_device")
+    return {k: int(getattr(m, k)) for k in _SM_FIELDS}
 
 
 def gpa_get_advice(ctx, pid, shape, stream=None):
@@ -421,6 +458,9 @@ class Program:
 
     def ingest_host(self, host_samples, n=None, stream=None):
         gpa_ingest_host_samples(self.h, self.pid, host_samples, n, stream)
+
+    def set_launch_stats(self, stats, sm: dict | None = None):
+        gpa_set_launch_stats(self.h, self.pid, stats, sm)
 
     def blame(self, stream=None):
         gpa_blame(self.h, self.pid, stream)

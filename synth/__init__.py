@@ -289,6 +289,22 @@ def serving_sessions(n_sessions: int, seed: int = 0, rate_per_s: float = 200.0, 
     return out
 
 
+# ---------------------------------------------------------------- launch statistics
+def launch_stats(n_functions: int, seed: int = 0) -> dict:
+    """Seeded launch statistics, one kernel launch per function (the inputs of
+    the parallel optimizers): blocks log-uniform over 1..2^17 (some grids
+    smaller than the GPU), threads per block from small (16, 32: the per-SM
+    block cap binds) to 1,024, registers per thread 16..255, shared memory per
+    block 0 for half of the kernels, else up to 96 KB."""
+    rng = np.random.default_rng(seed + 15485863)
+    blocks = np.maximum(1, _loguniform_int(rng, 1, 2 ** 17 + 1, n_functions))
+    threads = rng.choice(np.array([16, 32, 32, 64, 96, 128, 192, 256, 256, 512, 640, 1024]), n_functions)
+    regs = rng.integers(16, 256, n_functions)
+    smem = np.where(rng.random(n_functions) < 0.5, 0, rng.integers(1, 96 * 1024 + 1, n_functions))
+    return dict(blocks=blocks.astype(np.int64), threads_per_block=threads.astype(np.int32),
+                regs_per_thread=regs.astype(np.int32), smem_per_block=smem.astype(np.int32))
+
+
 # ---------------------------------------------------------------- slicing
 def subprogram(arrays: dict, f_lo: int, f_hi: int) -> dict:
     """The arrays of functions [f_lo, f_hi) as a program of their own (all

@@ -7,7 +7,7 @@ import pytest
 import oracle
 import synth
 from bruteforce import tiny_program
-from parity import ARCH, assert_advice_equal, assert_edges_equal, assert_full_parity, gpu_run, oracle_run
+from parity import ARCH, RTOL, assert_advice_equal, assert_edges_equal, assert_full_parity, gpu_run, oracle_run
 from progbuild import I, counts, program
 
 pytestmark = pytest.mark.gpu
@@ -247,6 +247,47 @@ def test_search_of_thousands_of_nodes(ctx):
     g = gpu_run(ctx, P, dev(s))
     assert g["status"] == 0 and g["info"]["max_nodes"] > 4096, g["info"]
     assert_full_parity(g, oracle_run(P, s))
+
+
+def test_parallel_optimizers_match_oracle(ctx):
+    """Parallel optimizers (Table 2, Eqs. 6-10) from launch statistics: generated ones
+    plus launches made to match each rule, on this device's SM model and on a 4-SM
+    model. Match flags and binding limits equal the oracle's exactly, warps and
+    speedups within 1e-12; clearing the statistics resets the outputs."""
+    import paper_2009_04061_gb300 as g
+    import torch
+    rng = np.random.default_rng(31)
+    P = synth.make_program(synth.batched_params(40, rng, 31), 1.0)
+    s = P.samples(2_000_000, seed=31)
+    R = oracle_run(P, s)
+    st = synth.launch_stats(40, seed=31)
+    st["blocks"][:5] = [10 ** 5, 3, 10 ** 5, 7, 500]
+    st["threads_per_block"][:5] = [32, 256, 16, 1024, 32]
+    st["regs_per_thread"][:5] = [32, 64, 0, 40, 24]
+    st["smem_per_block"][:5] = [0, 48 * 1024, 0, 200 * 1024, 0]
+    dev_sm = g.gpa_sm_model_of_device(torch.cuda.current_device())
+    small_sm = dict(dev_sm, n_sms=4)
+    prog = ctx.load_program(P)
+    try:
+        d = dev(s)
+        prog.reset()
+        prog.ingest(d)
+        prog.blame()
+        for sm in (dev_sm, small_sm):
+            prog.set_launch_stats(st, sm)
+            adv = prog.advise(fetch=True)
+            exp = oracle.parallel(st, sm, R["totals"])
+            assert np.array_equal(adv["totals"], R["totals"])
+            assert np.array_equal(adv["par_match"], exp["par_match"]), sm
+            assert np.array_equal(adv["par_limit"], exp["par_limit"]), sm
+            assert np.allclose(adv["par_speedup"], exp["par_speedup"], rtol=RTOL, atol=0), sm
+            assert np.allclose(adv["par_warps"], exp["par_warps"], rtol=RTOL, atol=0), sm
+            assert exp["par_match"][:, 0].sum() > 0 and exp["par_match"][:, 1].sum() > 0
+        prog.set_launch_stats(None)
+        adv = prog.advise(fetch=True)
+        assert np.all(adv["par_limit"] == -1) and np.all(adv["par_speedup"] == 1.0) and not adv["par_match"].any()
+    finally:
+        prog.unload()
 
 
 def test_use_with_many_sources(ctx):

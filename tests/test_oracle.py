@@ -388,3 +388,74 @@ def test_coverage_diamond_opcode_rule():
     assert oracle.coverage(p, arch, mem) == (1, 0, 1)
     both = counts(len(p["opclass"]), {(j, 3, 0): 50, (j, 2, 1): 7})
     assert oracle.coverage(p, arch, both) == (1, 0, 0)
+
+
+# ---------------------------------------------------------------- parallel optimizers (Table 2, Eqs. 6-10)
+GB_SM = dict(n_sms=152, schedulers_per_sm=4, max_warps_per_sm=64, max_blocks_per_sm=32, regs_per_sm=65536,
+             reg_alloc_unit=256, smem_per_sm=233472, smem_alloc_unit=128, smem_reserved_per_block=1024)
+SMALL_SM = dict(GB_SM, n_sms=4)
+
+
+def _par(sm, blocks, threads, regs, smem, T, issued):
+    st = dict(blocks=[blocks], threads_per_block=[threads], regs_per_thread=[regs], smem_per_block=[smem])
+    tot = np.array([[T, 0, 0, issued]], dtype=np.uint64)
+    return oracle.parallel(st, sm, tot)
+
+
+def test_occupancy_worked_cases():
+    """Blocks per SM by hand: 256 threads, 64 registers, 48 KB -> registers allow
+    4 x floor(16384 / 2048) = 32 warps = 4 blocks, shared memory floor(233472 /
+    50176) = 4 blocks (the tie reports registers); 32 threads with 96 registers ->
+    4 x floor(16384 / 3072) = 20 warps (20 blocks); 32 threads, 32 registers, no
+    shared memory -> the 32-block cap binds; 1,024 threads -> 2 blocks by warp slots."""
+    from oracle.parallel import occupancy
+    o = occupancy(256, 64, 48 * 1024, GB_SM)
+    assert (o["blocks_per_sm"], o["limit"], o["limits"][2]) == (4, 1, 4)
+    o = occupancy(32, 96, 0, GB_SM)
+    assert (o["blocks_per_sm"], o["limit"], o["warps_by_regs"]) == (20, 1, 20)
+    o = occupancy(32, 32, 0, GB_SM)
+    assert (o["blocks_per_sm"], o["limit"]) == (32, 3)
+    o = occupancy(1024, 0, 0, GB_SM)
+    assert (o["blocks_per_sm"], o["limit"]) == (2, 0)
+    o = occupancy(64, 32, 200 * 1024, GB_SM)   # one 201 KB block fits
+    assert (o["blocks_per_sm"], o["limit"]) == (1, 2)
+
+
+def test_block_increase_closed_form():
+    """2 blocks of 8 warps on 4 SMs: W = 8 / 4 = 2 warps per scheduler, W_new = 2 * 2 / 4 = 1;
+    Eq. 10 gives (W / W_new) * (1 - (1-R)) / (1 - (1-R)^2) = 2 / (2 - R)."""
+    for R, T in [(0.5, 1000), (0.25, 4000), (0.1, 10)]:
+        r = _par(SMALL_SM, 2, 256, 32, 0, T, int(R * T))
+        assert r["par_match"][0].tolist() == [1, 0]
+        assert math.isclose(r["par_speedup"][0, 0], 2 / (2 - R), rel_tol=1e-14)
+        assert r["par_warps"][0, 0].tolist() == [2.0, 1.0]
+
+
+def test_thread_increase_closed_form():
+    """1-warp blocks capped at 32 per SM (W = 8), the grid large enough: merging them
+    lets all 64 warp slots fill (W_new = 16) and C_W = 1, so S = (1 - (1-R)^16) /
+    (1 - (1-R)^8) = 1 + (1-R)^8."""
+    for R in (0.5, 0.2, 0.05):
+        r = _par(SMALL_SM, 4 * 32 * 2, 32, 32, 0, 10 ** 6, int(R * 10 ** 6))
+        assert r["par_match"][0].tolist() == [0, 1] and r["par_limit"][0] == 3
+        assert r["par_warps"][0, 1].tolist() == [8.0, 16.0]
+        assert math.isclose(r["par_speedup"][0, 1], 1 + (1 - R) ** 8, rel_tol=1e-14)
+    # the grid caps W_new: 4 SMs x 40 one-warp blocks give 40 warps per SM (W_new = 10)
+    r = _par(SMALL_SM, 4 * 40, 32, 32, 0, 1000, 500)
+    assert r["par_warps"][0, 1].tolist() == [8.0, 10.0]
+    assert math.isclose(r["par_speedup"][0, 1], (1 - 0.5 ** 10) / (1 - 0.5 ** 8), rel_tol=1e-14)
+
+
+def test_parallel_unmatched_and_degenerate():
+    """Grid of exactly one block per SM, or a limit other than the block cap: no match,
+    speedup 1.0. No issued samples: matched, speedup 1.0. No statistics: limit -1."""
+    r = _par(SMALL_SM, 4, 256, 32, 0, 1000, 100)
+    assert r["par_match"][0].tolist() == [0, 0] and r["par_speedup"][0].tolist() == [1.0, 1.0]
+    r = _par(SMALL_SM, 4 * 32 * 2, 64, 32, 0, 1000, 100)   # 32 blocks x 2 warps = 64: tie, warp slots reported
+    assert r["par_limit"][0] == 0 and r["par_match"][0].tolist() == [0, 0]
+    r = _par(SMALL_SM, 3 * 32, 32, 32, 0, 1000, 100)       # grid gives an SM 24 blocks, below the cap
+    assert r["par_limit"][0] == 3 and r["par_match"][0].tolist() == [0, 0]
+    r = _par(SMALL_SM, 2, 256, 32, 0, 1000, 0)
+    assert r["par_match"][0].tolist() == [1, 0] and r["par_speedup"][0].tolist() == [1.0, 1.0]
+    none = oracle.parallel(None, SMALL_SM, np.zeros((3, 4), np.uint64))
+    assert none["par_limit"].tolist() == [-1, -1, -1] and np.all(none["par_speedup"] == 1.0)
