@@ -173,22 +173,19 @@ __global__ void __launch_bounds__(THREADS) k_histogram(Prog P, const uint64_t* _
 // Variant 0 (default), for streams that arrive as kernel-launch runs (a
 // profiler that serializes kernels delivers them so). Each CTA (one per SM,
 // 1,024 threads) claims chunks of 16 consecutive tiles of 8,192 samples. Its
-// shared memory holds a window of 16-bit counters (two per word) over up to
-// 4,156 consecutive instructions of the run's kernel, and a 4,096-entry hash.
+// shared memory holds a window of 32-bit counters over up to 2,078
+// consecutive instructions of the run's kernel, and a 4,096-entry hash.
 // A kernel that fits is windowed whole; for a larger one the window is placed
 // where most of the tile's first 32 samples fall. The first sample of each
 // tile names the kernel; a new kernel flushes the window to the 64-bit global
 // counters and places it again.
-// A sample inside the window is one shared-memory atomic on its counter;
-// any other valid sample (another kernel at a run boundary, or a pc outside
-// a partial window) goes to the hash, and a key that finds no slot within
-// four probes to its global counter. The hash is flushed when half full and
-// at the end.
-// The increment that brings a 16-bit counter to 32,768 moves 32,768 to the
-// global counter. A tile's window atomics are all issued before their return
-// values are examined, and a barrier every four tiles bounds the increments
-// between two barriers to 32,768: a counter below 32,768 at a barrier stays
-// at most 32,767 + 32,768 = 65,535 until the next one, whatever the order.
+// A sample inside the window is one shared-memory reduction (no return value,
+// predicated on the window test: no branch) on its counter; any other valid
+// sample (another kernel at a run boundary, or a pc outside a partial window)
+// goes to the hash, and a key that finds no slot within four probes to its
+// global counter. The hash is flushed when half full, and window and hash at
+// least every 2^16 tiles (fewer than 2^30 increments: no 32-bit count wraps)
+// and at the end.
 constexpr int kRunThreads = 1024;
 #ifndef GPA_RUN_VEC
 #define GPA_RUN_VEC 4
@@ -198,18 +195,13 @@ constexpr int kRunThreads = 1024;
 #endif
 constexpr int kRunVec = GPA_RUN_VEC;                  // 16-byte vectors per thread per tile
 constexpr int kRunTile = kRunThreads * kRunVec;       // vectors per tile (8,192 samples)
-constexpr int kMainWords = 49872;                     // 195 KB of window counters (12 words per instruction)
-constexpr uint32_t kWinCounters = 2u * kMainWords;    // 16-bit window counters, two per word
-constexpr uint32_t kWinInstr = kWinCounters / 24u;    // 4,156 instructions
+constexpr int kMainWords = 49872;                     // 195 KB of 32-bit window counters, 24 per instruction
+constexpr uint32_t kWinInstr = kMainWords / 24u;      // 2,078 instructions
 constexpr int kSideLog2 = 12;                         // 4,096-entry hash
-constexpr int kRunFlushTiles = 1 << 16;               // forced flush: keeps 32-bit hash counts below 2^30
+constexpr int kRunFlushTiles = 1 << 16;               // forced flush: keeps 32-bit counts below 2^30
 constexpr int kRunChunk = GPA_RUN_CHUNK;              // tiles per claimed chunk
-#ifndef GPA_WIN_SYNC
-#define GPA_WIN_SYNC 4
-#endif
-constexpr int kWinSyncTiles = GPA_WIN_SYNC;           // tiles between window barriers
-static_assert(32767 + kWinSyncTiles * 2 * kRunTile < 65536, "window counters could wrap between barriers");
-static_assert(kMainWords % 12 == 0, "the window holds whole instructions (12 words each)");
+static_assert((long long)kRunFlushTiles * 2 * kRunTile < (1ll << 30), "32-bit counts could wrap between flushes");
+static_assert(kMainWords % 24 == 0, "the window holds whole instructions (24 words each)");
 // Bit f of kValid5 is set when the 5-bit (class, latency) field f names a
 // counter: class < 12, and not SELECTED with the latency flag.
 constexpr uint32_t kValid5 = 0x00FFFFFDu;
@@ -268,12 +260,12 @@ __device__ __forceinline__ uint32_t window_start(uint64_t x, bool ok, uint32_t k
 __global__ void __launch_bounds__(kRunThreads, 1) k_histogram_runs(Prog P, const uint64_t* __restrict__ s,
                                                                    int64_t n, int head) {
   extern __shared__ __align__(16) uint32_t sm[];
-  uint32_t* win = sm;                                     // kMainWords window words, then one word per lane
-  uint32_t* skey = sm + kMainWords + 32;                  // hash
+  uint32_t* win = sm;                                     // kMainWords window counters
+  const uint32_t win_base = (uint32_t)__cvta_generic_to_shared(win);
+  uint32_t* skey = sm + kMainWords;                       // hash
   uint32_t* sval = skey + (1 << kSideLog2);
   int* ctl = reinterpret_cast<int*>(sval + (1 << kSideLog2));  // 1: hash fill
   for (int t = threadIdx.x; t < (1 << kSideLog2); t += kRunThreads) { skey[t] = kNoKey; sval[t] = 0u; }
-  if (threadIdx.x < 32) win[kMainWords + threadIdx.x] = 0u;
   if (threadIdx.x < 8) ctl[threadIdx.x] = 0;
   __syncthreads();
   const int32_t* foff = P.func_instr_off;  // read through the cache: the window takes the shared memory
@@ -318,24 +310,20 @@ __global__ void __launch_bounds__(kRunThreads, 1) k_histogram_runs(Prog P, const
 
   // The window: kernel `mode` (-1: none), instructions [lo, lo + wn), whose
   // counters start at global index base; the counter of (pc, f5), f5 the
-  // 5-bit (class, latency) field, is half f5 & 1 of word ((pc - lo) * 24 + f5) / 2.
+  // 5-bit (class, latency) field, is word (pc - lo) * 24 + f5.
   // With r = bits 19..50 of a sample (f5 | pc << 5 | low 3 kernel bits << 29),
   // a sample of kernel `mode` is in the window when r - first5 < span5,
   // first5 = (mode << 29) | (lo << 5), span5 = wn << 5.
   uint32_t lo = 0, wn = 0, base = 0, mode_hi = 0, first5 = 0, span5 = 0;
-  // The window holds wn * 12 words (a multiple of 4: read and cleared as 16-byte vectors).
+  // The window holds wn * 24 words (a multiple of 4: read and cleared as 16-byte vectors).
   auto flush_win = [&]() {
-    const uint32_t quads = wn * 3u;
+    const uint32_t quads = wn * 6u;
     for (uint32_t q = threadIdx.x; q < quads; q += kRunThreads) {
       const uint4 v = reinterpret_cast<const uint4*>(win)[q];
       const uint32_t c[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        if (!c[e]) continue;
-        unsigned long long* d = P.cnt + base + 8u * q + 2u * e;
-        if (c[e] & 0xFFFFu) atomicAdd(d, (unsigned long long)(c[e] & 0xFFFFu));
-        if (c[e] >> 16) atomicAdd(d + 1, (unsigned long long)(c[e] >> 16));
-      }
+      for (int e = 0; e < 4; ++e)
+        if (c[e]) atomicAdd(P.cnt + base + 4u * q + e, (unsigned long long)c[e]);
     }
   };
 
@@ -377,7 +365,7 @@ __global__ void __launch_bounds__(kRunThreads, 1) k_histogram_runs(Prog P, const
     k0 = __ldg(reinterpret_cast<const unsigned int*>(s2 + 2 * t * kRunTile) + 1) >> 16;
   };
 
-  int since = 0, sync_t = 0;
+  int since = 0;
   int64_t t_count = 0;
   auto process = [&](const ulonglong2* v, uint32_t k0) {
     const int want = k0 < (uint32_t)P.nf ? (int)k0 : -1;
@@ -400,7 +388,7 @@ __global__ void __launch_bounds__(kRunThreads, 1) k_histogram_runs(Prog P, const
                           (uint32_t)mode, n_instr);
         wn = min(n_instr, kWinInstr);
         base = ((uint32_t)foff[mode] + lo) * 24u;
-        for (uint32_t q = threadIdx.x; q < wn * 3u; q += kRunThreads)
+        for (uint32_t q = threadIdx.x; q < wn * 6u; q += kRunThreads)
           reinterpret_cast<uint4*>(win)[q] = make_uint4(0u, 0u, 0u, 0u);
       }
       mode_hi = (uint32_t)max(mode, 0) << 16;
@@ -408,9 +396,9 @@ __global__ void __launch_bounds__(kRunThreads, 1) k_histogram_runs(Prog P, const
       span5 = wn << 5;
       __syncthreads();
     }
-    // One shared-memory atomic per sample, without branches: a sample outside
-    // the window adds 0 to this lane's own spare word.
-    uint32_t ovf = 0, slow = 0;
+    // One predicated shared-memory reduction per window sample (no return
+    // value to wait for, no branch).
+    uint32_t slow = 0;
 #pragma unroll
     for (int u = 0; u < kRunVec; ++u) {
 #pragma unroll
@@ -421,10 +409,9 @@ __global__ void __launch_bounds__(kRunThreads, 1) k_histogram_runs(Prog P, const
         const bool hit = rel < span5 && ((xh ^ mode_hi) >> 16) == 0u && ((kValid5 >> (rel & 31u)) & 1u) &&
                          (xl & 0x7FFu) == 0u;
         const uint32_t idx = rel - ((rel >> 5) << 3);  // (pc - lo) * 24 + f5
-        const uint32_t inc = hit ? 1u << ((idx & 1u) << 4) : 0u;
-        const uint32_t old = atomicAdd(&win[hit ? idx >> 1 : kMainWords + lane], inc);
-        // this increment took the 16-bit counter from 32,767 to 32,768
-        if (((old + inc) ^ old) & (inc << 15)) ovf |= 1u << (2 * u + h);
+        const uint32_t addr = win_base + 4u * idx;
+        asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %1, 0;\n\t@p red.shared.add.u32 [%0], 1;\n\t}"
+                     :: "r"(addr), "r"((uint32_t)hit) : "memory");
         if (!hit) slow |= 1u << (2 * u + h);
       }
     }
@@ -438,24 +425,6 @@ __global__ void __launch_bounds__(kRunThreads, 1) k_histogram_runs(Prog P, const
       for (int q = 1; q < 2 * kRunVec; ++q)
         if (i == q) x = (q & 1) ? v[q >> 1].y : v[q >> 1].x;
       count_other(x);
-    }
-    if (ovf) {
-#pragma unroll
-      for (int u = 0; u < kRunVec; ++u) {
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          if (!((ovf >> (2 * u + h)) & 1u)) continue;
-          const uint64_t x = h ? v[u].y : v[u].x;
-          const uint32_t rel = __funnelshift_r((uint32_t)x, (uint32_t)(x >> 32), 19) - first5;
-          const uint32_t idx = rel - ((rel >> 5) << 3);
-          atomicAdd(P.cnt + base + idx, 32768ull);
-          atomicSub(&win[idx >> 1], 32768u << ((idx & 1u) << 4));
-        }
-      }
-    }
-    if (++sync_t == kWinSyncTiles) {
-      sync_t = 0;
-      __syncthreads();
     }
     // every 32 tiles: flush the hash if half full
     if ((++t_count & 31) == 0) {
@@ -526,7 +495,7 @@ void launch_histogram(const Prog& P, const uint64_t* samples, size_t n, cudaStre
     if (grid > sms) grid = sms;
     if (grid < 1) grid = 1;
     cudaMemsetAsync(&P.stats[SS_HIST_HEAD], 0, sizeof(unsigned long long), st);
-    const size_t smem = sizeof(uint32_t) * ((size_t)kMainWords + 32 + 2 * ((size_t)1 << kSideLog2) + 8);
+    const size_t smem = sizeof(uint32_t) * ((size_t)kMainWords + 2 * ((size_t)1 << kSideLog2) + 8);
     allow_max_smem(k_histogram_runs);
     k_histogram_runs<<<(int)grid, kRunThreads, smem, st>>>(P, samples, (int64_t)n, head);
     ++*launches;

@@ -398,16 +398,16 @@ def test_histogram_variants_agree():
 
 
 def test_histogram_partial_window():
-    """Kernels larger than the aggregation window (4,156 instructions): samples
+    """Kernels larger than the aggregation window (2,078 instructions): samples
     inside the window placed for the run, samples outside it, hot counters in
     both far past 65,536, and malformed samples of the windowed kernel."""
     # (n_instr, n_loops, seed) of the generator; the two middle functions come out
-    # at exactly 4,156 and 4,157 instructions, the window's size and one more
-    shapes = [(500, 1, 40), (4122, 10, 40), (4127, 10, 59), (5000, 12, 43), (12000, 30, 44), (20000, 50, 45)]
+    # at exactly 2,078 and 2,079 instructions, the window's size and one more
+    shapes = [(500, 1, 40), (2051, 5, 75), (2053, 5, 75), (5000, 12, 43), (12000, 30, 44), (20000, 50, 45)]
     ps = [dict(n_instr=n, n_loops=nl, max_depth=5, n_regs=128, zipf_s=1.1, seed=sd) for n, nl, sd in shapes]
     P = synth.make_program(ps, 1.0, 3)
     n_instr = np.diff(P.func_instr_off)
-    assert list(n_instr[1:3]) == [4156, 4157]
+    assert list(n_instr[1:3]) == [2078, 2079]
     s = P.samples(3_000_001, invalid_ppm=2000, seed=7)
     cnt, bad = oracle.histogram(P, s)
     with g_context() as c:
