@@ -111,7 +111,7 @@ typedef struct {
                                    faster than few large shared-memory arenas) */
   int32_t hist_variant;         /* aggregation kernel: 0 (default) = one CTA per SM taking chunks of
                                    tiles from a counter, shared memory used per kernel-launch run as a
-                                   direct-indexed window over up to 4,156 instructions of that kernel's
+                                   direct-indexed window over up to 2,078 instructions of that kernel's
                                    counters plus a hash for the rest; grid-strided with a shared-memory
                                    hash: 1 = 8,192 entries, 512 threads, 2 CTAs per SM; 2 = 16,384
                                    entries, 1,024 threads, 1 CTA per SM; 3 = 8,192 entries, 256 threads,

@@ -383,7 +383,7 @@ def test_histogram_variants_agree():
                 r = gpu_run(c, P, d[lo:hi], advise=False)
                 c2, b2 = oracle.histogram(P, s[lo:hi])
                 assert np.array_equal(r["counts"], c2) and r["invalid"] == b2, (v, lo, hi)
-    # one hot counter far past the 16-bit window counters' spill point
+    # one hot counter far past 2^16
     hot = np.full(1_000_003, s[0], dtype=np.uint64)
     ch, bh = oracle.histogram(P, hot)
     with g.Context(ARCH, dict(hist_variant=0)) as c:
