@@ -147,8 +147,7 @@ __device__ void parallel_advice(const Prog& P, int f, unsigned long long T, unsi
 __global__ void __launch_bounds__(kThreads) k_advise(Prog P, Arch A) {
   __shared__ unsigned long long red[12][kThreads / 32];
   __shared__ unsigned long long tot[12];
-  __shared__ Cand cand[kThreads * kHot];
-  __shared__ int ncand[kThreads];
+  __shared__ Cand wtop[kThreads / 32][kHot];  // each warp's top five (v == 0: none)
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
   for (int f = blockIdx.x; f < P.nf; f += gridDim.x) {
@@ -225,7 +224,8 @@ __global__ void __launch_bounds__(kThreads) k_advise(Prog P, Arch A) {
       for (int q = 0; q < 4; ++q) P.a_totals[(size_t)f * 4 + q] = tot[q];
       parallel_advice(P, f, T, tot[3]);
     }
-    // Hotspots, one optimizer at a time: thread-local top five, then thread 0 merges.
+    // Hotspots, one optimizer at a time: thread-local top five, a warp-level
+    // merge, then thread 0 merges the warps' lists.
     for (int o = 0; o < N_O; ++o) {
       Cand top[kHot];
       int nt = 0;
@@ -247,14 +247,31 @@ __global__ void __launch_bounds__(kThreads) k_advise(Prog P, Arch A) {
           top_insert(top, nt, Cand{v, x - i0, x - i0, 0});
         }
       }
-      for (int h = 0; h < nt; ++h) cand[tid * kHot + h] = top[h];
-      ncand[tid] = nt;
+      // The warp's top five: five rounds of a butterfly maximum over the lanes'
+      // next candidates (candidates are distinct, so the order is total; lanes
+      // out of candidates offer v = 0, ties between those go to the lower lane).
+      int ptr = 0;
+      for (int h = 0; h < kHot; ++h) {
+        Cand b = ptr < nt ? top[ptr] : Cand{0ull, 0, 0, 0};
+        int owner = lane;
+        for (int o = 16; o > 0; o >>= 1) {
+          Cand y;
+          y.v = __shfl_xor_sync(0xffffffffu, b.v, o);
+          y.def = __shfl_xor_sync(0xffffffffu, b.def, o);
+          y.use = __shfl_xor_sync(0xffffffffu, b.use, o);
+          y.dist = __shfl_xor_sync(0xffffffffu, b.dist, o);
+          const int yo = __shfl_xor_sync(0xffffffffu, owner, o);
+          if (better(y, b) || (!better(b, y) && yo < owner)) { b = y; owner = yo; }
+        }
+        if (lane == owner && b.v != 0ull) ++ptr;
+        if (lane == 0) wtop[warp][h] = b;
+      }
       __syncthreads();
       if (tid == 0) {
         Cand best[kHot];
         int nb = 0;
-        for (int t = 0; t < kThreads; ++t)
-          for (int h = 0; h < ncand[t]; ++h) top_insert(best, nb, cand[t * kHot + h]);
+        for (int w = 0; w < kThreads / 32; ++w)
+          for (int h = 0; h < kHot; ++h) top_insert(best, nb, wtop[w][h]);
         long long* out = P.a_hot + ((size_t)f * N_O + o) * kHot * 6;
         for (int h = 0; h < kHot; ++h) {
           if (h < nb) {
