@@ -286,6 +286,17 @@ def test_parallel_optimizers_match_oracle(ctx):
         prog.set_launch_stats(None)
         adv = prog.advise(fetch=True)
         assert np.all(adv["par_limit"] == -1) and np.all(adv["par_speedup"] == 1.0) and not adv["par_match"].any()
+        # out-of-range statistics or a missing SM model are refused and change nothing
+        for k, bad in [("threads_per_block", 0), ("threads_per_block", 1025), ("regs_per_thread", 256),
+                       ("blocks", 0), ("smem_per_block", -1)]:
+            st_bad = {key: v.copy() for key, v in st.items()}
+            st_bad[k][7] = bad
+            with pytest.raises(g.GpaError):
+                prog.set_launch_stats(st_bad, dev_sm)
+        with pytest.raises(g.GpaError):
+            prog.set_launch_stats(st, dict(dev_sm, n_sms=0))
+        assert np.all(prog.advise(fetch=True)["par_limit"] == -1)
+        assert dev_sm["n_sms"] == torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
     finally:
         prog.unload()
 
