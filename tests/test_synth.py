@@ -74,3 +74,18 @@ def test_subprogram_matches_the_batch():
         assert np.array_equal(R["edges"]["i"] - i0, R_f["edges"]["i"])
         assert np.array_equal(R["edges"]["share"], R_f["edges"]["share"])
         assert np.array_equal(R["speedup"], R_f["speedup"])
+
+
+def test_launch_stats_seeded_and_in_range():
+    """Launch statistics are a pure function of (count, seed), stay within the ABI's
+    ranges, and include grids smaller than a GPU and launches where the per-SM block
+    cap binds (both parallel optimizers can match)."""
+    a, b = synth.launch_stats(500, seed=3), synth.launch_stats(500, seed=3)
+    c = synth.launch_stats(500, seed=4)
+    assert all(np.array_equal(a[k], b[k]) for k in a)
+    assert any(not np.array_equal(a[k], c[k]) for k in a)
+    assert a["blocks"].min() >= 1 and a["blocks"].max() <= 2 ** 17
+    assert a["threads_per_block"].min() >= 1 and a["threads_per_block"].max() <= 1024
+    assert a["regs_per_thread"].min() >= 0 and a["regs_per_thread"].max() <= 255
+    assert a["smem_per_block"].min() >= 0
+    assert (a["blocks"] < 152).mean() > 0.2 and (a["threads_per_block"] <= 32).mean() > 0.1
