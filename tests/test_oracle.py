@@ -459,3 +459,54 @@ def test_parallel_unmatched_and_degenerate():
     assert r["par_match"][0].tolist() == [1, 0] and r["par_speedup"][0].tolist() == [1.0, 1.0]
     none = oracle.parallel(None, SMALL_SM, np.zeros((3, 4), np.uint64))
     assert none["par_limit"].tolist() == [-1, -1, -1] and np.all(none["par_speedup"] == 1.0)
+
+
+# ---------------------------------------------------------------- Sec. 2.3, the two motivating examples
+def _loop_program(body):
+    """entry block, one single-block loop `body` (header and latch), exit block."""
+    entry = [I("MOV", ["R10"], ["R11"])]
+    return program([([entry, body, [I("EXIT")]], [[1], [1, 2], []], [(1, [1], -1)])])
+
+
+def test_motivating_conversion_chain_strength_reduction():
+    """Sec. 2.3, first example: execution-dependency stalls on an FMA that consumes a
+    type conversion inside a hot loop are blamed on the conversion, so Strength
+    Reduction (conversions are flagged long-latency arithmetic) matches them, ranks
+    first, and points at the conversion -> FMA pair."""
+    body = [I("LDS", ["R2"], ["R10"]), I("F2F", ["R4"], ["R2"]), I("FFMA", ["R5"], ["R4", "R6", "R7"]),
+            I("STS", [], ["R10", "R5"]), I("IADD", ["R10"], ["R10", "R12"]), I("ISETP", ["P0"], ["R10", "R13"]),
+            I("BRA", [], [], guard="P0")]
+    prog = _loop_program(body)
+    ffma, f2f = 3, 2                                  # global instruction indices (entry block has one)
+    cnt = counts(9, {(ffma, C_EXEC, 1): 60, (ffma, C_EXEC, 0): 20, (f2f, 0, 0): 10, (1, 0, 0): 10,
+                     (4, 0, 0): 10, (6, 9, 0): 5})
+    R = oracle.analyze(prog, ARCH, cnt)
+    T, A, L, _ = (int(x) for x in R["totals"][0])
+    assert (T, L) == (115, 60)
+    assert R["blame"][f2f, C_EXEC].tolist() == [20, 60] and R["blame"][ffma, C_EXEC].sum() == 0
+    assert R["M"][0][1] == 80 and R["speedup"][0][1] == 115 / (115 - 80)    # Eq. 2
+    assert R["rank"][0][0] == 1                                             # Strength Reduction first
+    assert list(R["hot"][0][1][0][[0, 1, 4, 5]]) == [f2f, ffma, 1, 80]      # def, use, distance, samples
+
+
+def test_motivating_short_load_use_in_synchronized_loop():
+    """Sec. 2.3, second example: a global load whose value is consumed by the next
+    instruction in a loop that also synchronizes. The use's memory-dependency latency
+    samples are blamed on the load at distance 1: Code Reordering and Loop Unrolling
+    (def and use share the loop) match them (Eq. 4), and the barrier's sync stalls
+    match Warp Balance (Eq. 2)."""
+    body = [I("LDG", ["R0"], ["R2", "R3"]), I("ISETP", ["P0"], ["R0", "R4"]), I("BAR"),
+            I("IADD", ["R10"], ["R10", "R12"]), I("ISETP", ["P1"], ["R10", "R13"]), I("BRA", [], [], guard="P1")]
+    prog = _loop_program(body)
+    ldg, use, bar = 1, 2, 3
+    cnt = counts(8, {(use, C_MEM, 1): 50, (use, C_MEM, 0): 10, (bar, C_SYNC, 1): 20, (bar, C_SYNC, 0): 10,
+                     (ldg, 0, 0): 15, (4, 0, 0): 15})
+    R = oracle.analyze(prog, ARCH, cnt)
+    T, A, L, _ = (int(x) for x in R["totals"][0])
+    assert (T, A, L) == (120, 50, 70)
+    assert R["blame"][ldg, C_MEM].tolist() == [10, 50]
+    M, sp = R["M"][0], R["speedup"][0]
+    assert M[6] == M[7] == 50 and M[4] == 30
+    assert sp[6] == sp[7] == 120 / (120 - min(50, 50)) and sp[4] == 120 / (120 - 30)
+    assert list(R["rank"][0][:3]) == [6, 7, 4]        # equal speedups: the lower id first
+    assert list(R["hot"][0][7][0][[0, 1, 4, 5]]) == [ldg, use, 1, 50]
