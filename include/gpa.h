@@ -394,8 +394,10 @@ gpa_status gpa_get_advice(gpa_ctx* ctx, gpa_pid pid, const gpa_advice* out, gpa_
 
 /* Sets the launch statistics of the program's functions (stats[n_functions],
  * host, copied) and the SM they ran on, for the parallel optimizers of later
- * gpa_advise calls; stats == NULL clears them. Synchronous. Returns
- * GPA_ERR_INVALID_ARG for a field out of its range. */
+ * gpa_advise calls; stats == NULL clears them. Synchronous (waits for the
+ * device). A step captured with gpa_step_capture is dropped (capture it
+ * again; gpa_step_launch returns GPA_ERR_INVALID_ARG until then). Returns
+ * GPA_ERR_INVALID_ARG, changing nothing, for a field out of its range. */
 gpa_status gpa_set_launch_stats(gpa_ctx* ctx, gpa_pid pid, const gpa_launch_stats* stats, const gpa_sm_model* sm);
 
 /* The SM model of a CUDA device: counts and sizes from the device properties;
