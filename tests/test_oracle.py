@@ -510,3 +510,20 @@ def test_motivating_short_load_use_in_synchronized_loop():
     assert sp[6] == sp[7] == 120 / (120 - min(50, 50)) and sp[4] == 120 / (120 - 30)
     assert list(R["rank"][0][:3]) == [6, 7, 4]        # equal speedups: the lower id first
     assert list(R["hot"][0][7][0][[0, 1, 4, 5]]) == [ldg, use, 1, 50]
+
+
+def test_counts_independent_of_order_and_chunking():
+    """Sec. 2.1: the counters are a multiset statistic of the samples. A permuted
+    stream gives the same counts, and chunks counted apart add up to the whole
+    stream's counts (invalid samples included); the analysis follows the counts."""
+    ps, _, kz = synth.workload("rodinia")
+    P = synth.make_program(ps[:6], kz)
+    s = P.samples(200_000, invalid_ppm=5000, seed=8)
+    cnt, bad = oracle.histogram(P, s)
+    perm = np.random.default_rng(8).permutation(s.size)
+    cnt_p, bad_p = oracle.histogram(P, s[perm])
+    assert np.array_equal(cnt, cnt_p) and bad == bad_p
+    parts = [oracle.histogram(P, c) for c in np.array_split(s[perm], [1, 70_001, 150_000])]
+    assert np.array_equal(sum(p[0] for p in parts), cnt) and sum(p[1] for p in parts) == bad
+    R, Rp = oracle.analyze(P, ARCH, cnt), oracle.analyze(P, ARCH, cnt_p)
+    assert np.array_equal(R["blame"], Rp["blame"]) and np.array_equal(R["rank"], Rp["rank"])
