@@ -44,6 +44,33 @@ def test_paper_examples_blame(ctx):
         assert_full_parity(g, R)
 
 
+def _samples_of(entries):
+    ss = []
+    for (pc, c, l), v in entries.items():
+        ss += [(pc << 24) | (c << 20) | (l << 19)] * v
+    return np.array(ss, dtype=np.uint64)
+
+
+def test_hand_worked_pins(ctx):
+    """The oracle's hand-worked cases (write-after-read, Register Reuse, Memory
+    Transaction Reduction, Fast Math, the two-level Eq. 5 nest, line roll-up) through
+    the CUDA path: every output equals the oracle's, and the hand-derived values hold."""
+    import test_oracle as T
+    cases = [T.war_case("R4"), T.war_case("R9"), T.war_case("R9", uses=("R4", "R7")), T.war_case("R4", kind="wb"),
+             T.register_reuse_case(), T.transaction_case(), T.fast_math_case(), T.nest_case(), T.lines_case()]
+    got = []
+    for prog, ent in cases:
+        s = _samples_of(ent)
+        g = gpu_run(ctx, prog, dev(s))
+        assert_full_parity(g, oracle_run(prog, s))
+        got.append(g)
+    assert [int(g["edges"]["flags"][0]) for g in got[:4]] == [3, 2, 2, 2]
+    assert got[4]["advice"]["matched"][0][0] == 45 and got[5]["advice"]["matched"][0][5] == 16
+    assert got[6]["advice"]["matched"][0][3] == 15
+    assert got[7]["advice"]["loop_active"].tolist() == [45, 17] and got[7]["advice"]["loop_matched"].tolist() == [77, 25]
+    assert got[8]["advice"]["line_stall"].tolist() == [0, 0, 0, 0, 0, 60, 0, 5]
+
+
 @pytest.mark.parametrize("seed", range(16))
 def test_tiny_guarded_programs(ctx, seed):
     P = tiny_program(seed, n_instr=25 + seed, n_loops=seed % 3, guard_pct=20 + 3 * seed)

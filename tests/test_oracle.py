@@ -527,3 +527,163 @@ def test_counts_independent_of_order_and_chunking():
     assert np.array_equal(sum(p[0] for p in parts), cnt) and sum(p[1] for p in parts) == bad
     R, Rp = oracle.analyze(P, ARCH, cnt), oracle.analyze(P, ARCH, cnt_p)
     assert np.array_equal(R["blame"], Rp["blame"]) and np.array_equal(R["rank"], Rp["rank"])
+
+
+# ---------------------------------------------------------------- hand-worked pins of single oracle functions
+def war_case(dst, uses=("R6", "R7"), kind="rb"):
+    st = I("STG", [], ["R2", "R3", "R4"], **{kind: 1})
+    prog = one_block([st, I("MOV", ["R9"], ["R8"]), I("IADD", [dst], list(uses), wait=[1])])
+    return prog, {(0, 0, 0): 5, (2, C_EXEC, 0): 10, (2, C_EXEC, 1): 40}
+
+
+def test_write_after_read_flag():
+    """Sec. 4, Fig. 6: an execution-dependency edge is write-after-read when its
+    resource is a read barrier set by a variable-latency instruction i and the
+    stalled instruction j overwrites a register that i reads. Here a store reads R4
+    and sets read barrier B1; the next writer of R4 waits on B1. Flags: bit 1 (2) =
+    through a barrier, bit 0 (1) = write-after-read. The flag needs all three: a
+    read barrier (not a write barrier), j writing (not merely reading) a register
+    that i reads, and i of variable latency."""
+    def run(dst, uses=("R6", "R7"), kind="rb", arch=ARCH):
+        prog, ent = war_case(dst, uses, kind)
+        R = oracle.analyze(prog, arch, counts(3, ent))
+        e = R["edges"]
+        assert list(e["i"]) == [0] and list(e["j"]) == [2]
+        assert R["blame"][0, C_EXEC].tolist() == [10, 40] and R["blame"][2, C_EXEC].sum() == 0
+        return int(e["flags"][0])
+    assert run("R4") == 2 | 1                      # j overwrites R4, which the store reads
+    assert run("R9") == 2                          # j writes another register
+    assert run("R9", uses=("R4", "R7")) == 2       # j only reads R4: no write after read
+    assert run("R4", kind="wb") == 2               # write barrier: a read-after-write wait
+    lat, fl = ARCH
+    fl = fl.copy()
+    fl[synth.OP["STG"]] &= ~np.uint32(synth.F_VARLAT)
+    assert run("R4", arch=(lat, fl)) == 2          # fixed-latency i: no barrier to wait for
+
+
+def register_reuse_case():
+    ins = [I("LDL", ["R0"], ["R1"]), I("LDG", ["R4"], ["R2", "R3"]), I("MOV", ["R9"], ["R8"]),
+           I("FFMA", ["R5"], ["R0", "R4", "R6"])]
+    return one_block(ins), {(0, 0, 0): 30, (1, 0, 0): 20, (2, 0, 0): 10, (3, C_MEM, 0): 30, (3, C_MEM, 1): 60,
+                            (3, C_EXEC, 1): 8}
+
+
+def test_register_reuse_local_memory_blame():
+    """Table 2 Register Reuse: memory-dependency stalls blamed on local-memory
+    instructions. The FFMA reads R0 from an LDL (3 instructions up) and R4 from an
+    LDG (2 up). Issue/longest path is 30/3 = 20/2 for both, so Eq. 1 splits evenly:
+    memory stalls 30 active + 60 latency -> 15 + 30 to each load, execution stalls
+    8 (latency) -> 4 + 4. Register Reuse takes only the LDL's memory shares: M = 45,
+    Eq. 2 gives T / (T - M) = 158 / 113. Code Reordering takes execution latency
+    samples and global-memory latency samples: 4 + 4 + 30 = 38, min(A = 90, 38)."""
+    prog, ent = register_reuse_case()
+    R = oracle.analyze(prog, ARCH, counts(4, ent))
+    assert R["blame"][0, C_MEM].tolist() == [15, 30] and R["blame"][1, C_MEM].tolist() == [15, 30]
+    assert R["blame"][0, C_EXEC].tolist() == [0, 4] and R["blame"][1, C_EXEC].tolist() == [0, 4]
+    T, A, L, _ = (int(x) for x in R["totals"][0])
+    assert (T, A, L) == (158, 90, 68)
+    assert R["M"][0][0] == 45 and R["speedup"][0][0] == 158 / 113
+    assert R["M"][0][7] == 38 and R["speedup"][0][7] == 158 / 120
+    assert R["n_hot"][0][0] == 1 and list(R["hot"][0][0][0][[0, 1, 4, 5]]) == [0, 3, 3, 45]
+
+
+def transaction_case():
+    ins = [I("LDG", ["R0"], ["R2", "R3"]), I("LDS", ["R4"], ["R5"]), I("STG", [], ["R2", "R3", "R0"]), I("EXIT")]
+    return one_block(ins), {(0, 8, 0): 7, (0, 8, 1): 5, (1, 8, 1): 9, (2, 8, 0): 4, (0, 0, 0): 10, (3, 9, 0): 5}
+
+
+def test_memory_transaction_reduction_global_only():
+    """Table 2 Memory Transaction Reduction: memory-throttle samples at global-memory
+    instructions. Throttling at the LDG (7 + 5) and the STG (4) counts, at the LDS (9)
+    it does not: M = 16 of T = 40, Eq. 2 = 40 / 24; hotspots are the instructions
+    themselves (def = use, distance 0), the larger first."""
+    prog, ent = transaction_case()
+    R = oracle.analyze(prog, ARCH, counts(4, ent))
+    assert int(R["totals"][0][0]) == 40
+    assert R["M"][0][5] == 16 and R["speedup"][0][5] == 40 / 24
+    assert R["n_hot"][0][5] == 2
+    assert R["hot"][0][5][0].tolist() == [0, 0, 0, 0, 0, 12] and R["hot"][0][5][1].tolist() == [2, 2, 0, 0, 0, 4]
+
+
+def fast_math_case():
+    ins = [I("MOV", ["R1"], ["R2"]), I("MUFU", ["R3"], ["R1"], flags=1), I("FFMA", ["R4"], ["R3", "R5", "R6"], flags=1),
+           I("FFMA", ["R7"], ["R4", "R5", "R6"])]
+    return one_block(ins), {(0, 0, 0): 5, (1, 0, 0): 20, (1, C_EXEC, 1): 6, (1, 7, 0): 3, (1, 1, 1): 2,
+                            (2, C_EXEC, 0): 4, (3, C_EXEC, 1): 10}
+
+
+def test_fast_math_stalls_at_math_library_instructions():
+    """Table 2 Fast Math: stall samples observed at instructions of a math-library
+    routine (iflags bit 0). The flagged MUFU has 20 issued samples (not stalls) and
+    6 + 3 + 2 stalls of three reasons; the flagged FFMA after it 4; the unflagged
+    FFMA's 10 do not count. The stalls are taken where they were sampled, before
+    blame moves dependency stalls to their sources: M = 15 of T = 50, Eq. 2 = 50 / 35.
+    (Counted after blame it would be 9 + 10 = 19.)"""
+    prog, ent = fast_math_case()
+    R = oracle.analyze(prog, ARCH, counts(4, ent))
+    assert int(R["totals"][0][0]) == 50
+    assert R["M"][0][3] == 15 and R["speedup"][0][3] == 50 / 35
+    assert R["hot"][0][3][0].tolist() == [1, 1, 0, 0, 0, 11] and R["hot"][0][3][1].tolist() == [2, 2, 0, 0, 0, 4]
+
+
+def _nest_program():
+    """Entry B0; outer loop B1..B3 (header B1, latch B3); inner single-block loop B2
+    inside it; exit B4."""
+    b0 = [I("LDG", ["R0"], ["R2", "R3"])]                                          # 0
+    b1 = [I("LDG", ["R4"], ["R2", "R3"]), I("MOV", ["R9"], ["R8"])]                # 1, 2
+    b2 = [I("IADD", ["R5"], ["R4", "R6"]), I("LDG", ["R10"], ["R2", "R3"]),         # 3, 4
+          I("FFMA", ["R11"], ["R10", "R0", "R6"]), I("ISETP", ["P0"], ["R5", "R6"]),  # 5, 6
+          I("BRA", [], [], guard="P0")]                                             # 7
+    b3 = [I("IMAD", ["R12"], ["R5", "R6"]), I("IADD", ["R13"], ["R12", "R6"]),      # 8, 9
+          I("ISETP", ["P1"], ["R13", "R6"]), I("BRA", [], [], guard="P1")]           # 10, 11
+    b4 = [I("EXIT")]                                                                # 12
+    return program([([b0, b1, b2, b3, b4], [[1], [2], [2, 3], [1, 4], []], [(1, [1, 2, 3], -1), (2, [2], 0)])])
+
+
+def nest_case():
+    return _nest_program(), {(0, 0, 0): 10, (1, 0, 0): 10, (4, 0, 0): 10, (8, 0, 0): 10,
+                             (3, C_MEM, 1): 40, (5, C_MEM, 1): 30, (9, C_EXEC, 1): 12, (9, C_EXEC, 0): 3,
+                             (6, 9, 0): 7, (2, 9, 0): 5, (12, 9, 0): 4, (0, 9, 0): 2}
+
+
+def test_eq5_two_level_loop_nest_by_hand():
+    """Eq. 5 scopes on a two-level nest, every term by hand. Edges with latency
+    samples: LDG@1 -> IADD@3 (memory, 40; innermost common loop: outer), LDG@4 ->
+    FFMA@5 (memory 25 after Eq. 1 gives it 5:1 against LDG@0: issue 10 over paths
+    1 and 5), LDG@0 -> FFMA@5 (memory 5; the def is outside every loop) and
+    IMAD@8 -> IADD@9 (execution, 12; outer). A of a loop sums the active samples of
+    its body with nested loops: inner = 10 + 7 = 17, outer = 10 + 5 + 17 + 10 + 3 =
+    45. M^L of a loop sums edges whose innermost common loop is nested in it: inner
+    = 25, outer = 40 + 25 + 12 = 77. T = 143, so S_inner = 143 / (143 - 17) and
+    S_outer = 143 / (143 - 45). At function scope Loop Unrolling has M^L = 77 and
+    Code Reordering 82 (the edge from outside the loops too), both bounded by A = 61
+    in Eq. 4."""
+    prog, ent = nest_case()
+    R = oracle.analyze(prog, ARCH, counts(13, ent))
+    assert R["blame"][4, C_MEM, 1] == 25 and R["blame"][0, C_MEM, 1] == 5 and R["blame"][1, C_MEM, 1] == 40
+    T, A, L, _ = (int(x) for x in R["totals"][0])
+    assert (T, A, L) == (143, 61, 82)
+    assert R["loop_A"].tolist() == [45, 17]
+    assert R["loop_ML"].tolist() == [77, 25]
+    assert R["loop_S"].tolist() == [143 / 98, 143 / 126]
+    assert R["M"][0][6] == 77 and R["M"][0][7] == 82
+    assert R["speedup"][0][6] == 143 / 82 and R["speedup"][0][7] == 143 / 82
+
+
+def lines_case():
+    ins = [I("LDG", ["R0"], ["R2", "R3"], line=5), I("MOV", ["R9"], ["R8"], line=5),
+           I("FFMA", ["R1"], ["R0", "R6", "R7"], line=7), I("EXIT", line=7)]
+    return one_block(ins), {(0, 0, 0): 10, (1, 1, 0): 6, (1, 1, 1): 4, (2, C_MEM, 0): 20, (2, C_MEM, 1): 30,
+                            (2, 9, 0): 5, (3, 0, 0): 3}
+
+
+def test_line_rollup_after_blame():
+    """Lines sum the stall samples (every reason but SELECTED) that blame leaves on
+    their instructions, and the latency part of them. Line 5 holds the LDG, which
+    takes the FFMA's memory stalls (20 + 30), and a MOV with instruction-fetch
+    stalls (6 + 4): 60 samples, 34 latency. Line 7 keeps the FFMA's own
+    not-selected samples (5, active) and the EXIT's issued samples do not count."""
+    prog, ent = lines_case()
+    R = oracle.analyze(prog, ARCH, counts(4, ent))
+    assert R["line_stall"].tolist() == [0, 0, 0, 0, 0, 60, 0, 5]
+    assert R["line_lat"].tolist() == [0, 0, 0, 0, 0, 34, 0, 0]
