@@ -410,15 +410,17 @@ int64_t gpa_launch_count(gpa_ctx* ctx);
 
 /* In-place exclusive prefix sum of n int32 values on the device: dev_buf[k]
  * becomes the sum of the inputs before k and *dev_total (device memory) the sum
- * of all n. The paper has no counterpart: this is the scan the library uses
- * for its own offsets (edges per use, events per block, predecessors).
+ * of all n. The sums are int32 and wrap silently on overflow: the running
+ * total of the inputs must fit in int32. The paper has no counterpart: this is
+ * the scan the library uses for its own offsets (edges per use, events per
+ * block, predecessors).
  *
  * It allocates nothing, unlike the rest of the library, which owns
  * cudaMalloc'd buffers. It is for callers that cannot call cudaMalloc at the
- * point where they need a scan: code recorded into a CUDA graph (allocation is
- * not allowed during stream capture), code that runs inside another
- * framework's memory pool and must not grow the process's device footprint,
- * or a profiler callback that must not perturb the application it measures.
+ * point where they need a scan: code that runs inside another framework's
+ * memory pool and must not grow the process's device footprint, or a profiler
+ * callback that must not perturb the application it measures (an allocation
+ * there can synchronize the device or change the memory the application sees).
  * Its scratch (the per-tile sums) is a fixed static device array of
  * (4096 + 64) int32 that every device loading the library holds until exit.
  *
@@ -429,7 +431,9 @@ int64_t gpa_launch_count(gpa_ctx* ctx);
  * any stream capture. Every call shares the one scratch array and leaves its
  * contents behind (nothing in it needs to start at zero): calls that overlap on
  * the GPU, on different streams or from different threads, race and give
- * wrong results. The call is asynchronous on stream. */
+ * wrong results. The call is asynchronous on stream. A CUDA error already
+ * pending when it is called (from an earlier, unrelated call) makes it return
+ * GPA_ERR_CUDA without launching, and leaves that error pending. */
 gpa_status gpa_exclusive_scan_noalloc(int32_t* dev_buf, int64_t n, int32_t* dev_total, gpa_stream stream);
 
 #ifdef __cplusplus

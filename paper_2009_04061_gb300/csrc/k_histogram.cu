@@ -365,13 +365,15 @@ __global__ void __launch_bounds__(kRunThreads, 1) k_histogram_runs(Prog P, const
     k0 = __ldg(reinterpret_cast<const unsigned int*>(s2 + 2 * t * kRunTile) + 1) >> 16;
   };
 
+  // Tiles since the hash was last flushed (the window is flushed at every
+  // kernel change as well, so this bounds both).
   int since = 0;
   int64_t t_count = 0;
   auto process = [&](const ulonglong2* v, uint32_t k0) {
     const int want = k0 < (uint32_t)P.nf ? (int)k0 : -1;
-    const bool periodic = ++since >= kRunFlushTiles;  // keeps the hash's 32-bit counts small
+    const bool periodic = ++since >= kRunFlushTiles;  // keeps the 32-bit counts small
     if (want != mode || periodic) {
-      since = 0;
+      if (periodic) since = 0;
       __syncthreads();
       flush_win();
       if (periodic) table_flush<kSideLog2>(skey, sval, P.cnt);
@@ -435,6 +437,7 @@ __global__ void __launch_bounds__(kRunThreads, 1) k_histogram_runs(Prog P, const
       __syncthreads();
       if (side_full) {
         table_flush<kSideLog2>(skey, sval, P.cnt);
+        since = 0;
         __syncthreads();
         if (threadIdx.x == 0) ctl[1] = 0;
       }

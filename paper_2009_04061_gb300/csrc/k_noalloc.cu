@@ -108,11 +108,16 @@ extern "C" gpa_status gpa_exclusive_scan_noalloc(int32_t* dev_buf, int64_t n, in
   int32_t* scratch = nullptr;
   const gpa_status s = scratch_address(&scratch);
   if (s) return s;
+  // An error left pending by an earlier, unrelated call is not ours to clear:
+  // report it (it stays pending for its owner) and launch nothing.
+  if (cudaPeekAtLastError() != cudaSuccess) return GPA_ERR_CUDA;
   cudaStream_t st = (cudaStream_t)stream;
   if (n == 0) return cudaMemsetAsync(dev_total, 0, sizeof(int32_t), st) == cudaSuccess ? GPA_OK : GPA_ERR_CUDA;
   const int tiles = (int)((n + kTile - 1) / kTile);
   k_na_scan_tiles<<<tiles, kThreads, 0, st>>>(dev_buf, (int)n, scratch);
+  if (cudaGetLastError() != cudaSuccess) return GPA_ERR_CUDA;
   k_na_scan_sums<<<1, kThreads, 0, st>>>(scratch, tiles, dev_total);
+  if (cudaGetLastError() != cudaSuccess) return GPA_ERR_CUDA;
   k_na_scan_add<<<tiles, kThreads, 0, st>>>(dev_buf, (int)n, scratch);
   return cudaGetLastError() == cudaSuccess ? GPA_OK : GPA_ERR_CUDA;
 }

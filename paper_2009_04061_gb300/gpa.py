@@ -404,10 +404,25 @@ def gpa_launch_count(ctx) -> int:
 
 
 def gpa_exclusive_scan_noalloc(dev_buf, dev_total, n: int | None = None, stream=None):
-    """In-place exclusive scan of an int32 CUDA tensor; the total goes to dev_total (int32, 1 element).
-    Allocates no device memory (fixed static scratch, see include/gpa.h)."""
+    """In-place exclusive scan of the first n values (default: all) of a contiguous int32
+    CUDA tensor on the current device; the total goes to dev_total[0] (int32, same device).
+    Allocates no device memory (fixed static scratch, see include/gpa.h). Raises ValueError
+    for anything else, before the library sees a pointer: a host array or a tensor of
+    another dtype or device would be read and written on the device as if it were this."""
+    import torch
+    for name, t in (("dev_buf", dev_buf), ("dev_total", dev_total)):
+        if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.int32:
+            raise ValueError(f"{name} must be an int32 CUDA tensor")
+        if t.device.index != torch.cuda.current_device():
+            raise ValueError(f"{name} is on {t.device}, not on the current device")
+    if not dev_buf.is_contiguous():
+        raise ValueError("dev_buf must be contiguous")
+    if dev_total.numel() < 1:
+        raise ValueError("dev_total must hold at least one element")
     if n is None:
         n = dev_buf.numel()
+    if not 0 <= int(n) <= dev_buf.numel():
+        raise ValueError(f"n = {n} outside 0..{dev_buf.numel()} (the elements of dev_buf)")
     _check(library().gpa_exclusive_scan_noalloc(_p(dev_buf), n, _p(dev_total), _stream(stream)),
            "gpa_exclusive_scan_noalloc")
 
