@@ -57,6 +57,8 @@ def parse():
                     help="tune the launch schedule on the workload first and time the tuned one")
     ap.add_argument("--serving", action="store_true", help="run the serving workload instead")
     ap.add_argument("--sessions", type=int, default=200, help="serving: sessions")
+    ap.add_argument("--serving-sessions", type=int, default=100,
+                    help="sessions of the serving record in the default run (0 to skip)")
     ap.add_argument("--rate", type=float, default=200.0, help="serving: mean arrivals per second")
     ap.add_argument("--slots", type=int, default=8, help="serving: concurrent sessions")
     ap.add_argument("--budget-gb", type=float, default=64.0, help="serving: device-memory admission budget")
@@ -227,13 +229,14 @@ def plain_vs_batched(gpa, workload: str, seed: int, dev, stream, reps: int = 3) 
         ctx.close()
 
 
-def serving_bench(a, gpa, dev):
-    """Serving workload: Poisson session arrivals through the continuous-batching
-    server against the same sessions one at a time. Prints one JSON line."""
+def serving_measure(a, gpa, dev, n_sessions: int) -> dict:
+    """Serving workload: Poisson session arrivals (mean a.rate per second) through the
+    continuous-batching server, p50/p99 ingest-to-advice latency and samples/s, against
+    the same sessions one at a time."""
     import torch
     from paper_2009_04061_gb300.serving import Server, Session, latency_summary, one_at_a_time, serve
     arch = synth.default_arch()
-    specs = synth.serving_sessions(a.sessions, seed=a.seed, rate_per_s=a.rate)
+    specs = synth.serving_sessions(n_sessions, seed=a.seed, rate_per_s=a.rate)
     sessions, keep = [], []
     for i, d in enumerate(specs):
         P = synth.make_program(d["params"], 1.0, d["seed"])
@@ -258,10 +261,8 @@ def serving_bench(a, gpa, dev):
     t_seq, res1 = one_at_a_time(arch, sessions, options=opts)
     seq = latency_summary(res1)
     n = sum(s.samples.size for s in sessions)
-    print(json.dumps({
-        "metric": METRIC, "value": mix["samples_per_s"], "unit": UNIT, "n_gpus": 1, "steps": 1,
-        "warmup": 1, "ms_per_step": mix["span_s"] * 1e3, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+    return {
+        "value": mix["samples_per_s"], "unit": UNIT, "span_s": mix["span_s"],
         "config": {"workload": "serving", "sessions": len(sessions), "rate_per_s": a.rate, "slots": a.slots,
                    "budget_gb": a.budget_gb, "samples": n, "options": opts,
                    "instructions": int(sum(int(s.program["n_instr"]) for s in sessions))},
@@ -270,16 +271,67 @@ def serving_bench(a, gpa, dev):
                           "latency_ms_without_queueing": {"p50": seq["p50_ms"], "p99": seq["p99_ms"]}},
         "speedup_vs_one_at_a_time": mix["samples_per_s"] / (n / t_seq),
         "clocks": clk.summary(),
+    }
+
+
+def serving_bench(a, gpa, dev):
+    """The serving workload alone; prints one JSON line."""
+    r = serving_measure(a, gpa, dev, a.sessions)
+    print(json.dumps({
+        "metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": 1, "steps": 1,
+        "warmup": 1, "ms_per_step": r["span_s"] * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int64", "data": "synthetic", "config": r["config"],
+        "latency_ms": r["latency_ms"], "one_at_a_time": r["one_at_a_time"],
+        "speedup_vs_one_at_a_time": r["speedup_vs_one_at_a_time"], "clocks": r["clocks"],
     }), flush=True)
 
 
-def run_oracle_once(P, sub, k_funcs):
+def pinned_h2d_gbs(host, dev, nbytes: int = 1 << 31) -> float:
+    """Best of three plain copies of `nbytes` from pinned host memory to the device (GB/s)."""
+    import torch
+    m = min(host.numel(), nbytes // 8)
+    src = host[:m]
+    dst = torch.empty(m, dtype=torch.int64, device=dev)
+    best = 0.0
+    for _ in range(3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        dst.copy_(src, non_blocking=True)
+        e1.record()
+        torch.cuda.synchronize(dev)
+        best = max(best, 8 * m / (e0.elapsed_time(e1) / 1e3) / 1e9)
+    del dst
+    return best
+
+
+def run_oracle_once(P, sub, k_funcs, threads: int = 1):
+    """Seconds the oracle takes for the bounded sample: the histogram of `sub` and
+    the analysis of functions 0..k_funcs-1, on a program cut to those functions.
+    With threads > 1 the samples are counted in `threads` slices and the functions
+    analyzed one per task on a pool of host threads (the oracle's C++ runs outside
+    the interpreter lock), and the slice counts summed: the same results."""
     import oracle
+    from concurrent.futures import ThreadPoolExecutor
     arch = synth.default_arch()
+    Q = synth.subprogram(P.arrays if hasattr(P, "arrays") else P, 0, k_funcs)
     t0 = time.perf_counter()
-    cnt, _ = oracle.histogram(P, sub)
-    oracle.analyze(P, arch, cnt, 0, k_funcs)
+    if threads <= 1:
+        cnt, _ = oracle.histogram(Q, sub)
+        oracle.analyze(Q, arch, cnt, 0, k_funcs)
+        return time.perf_counter() - t0
+    with ThreadPoolExecutor(threads) as ex:
+        parts = list(ex.map(lambda x: oracle.histogram(Q, x)[0], np.array_split(sub, threads)))
+        cnt = parts[0]
+        for c in parts[1:]:
+            cnt += c
+        sizes = np.diff(np.asarray(Q["func_instr_off"]))
+        order = np.argsort(-sizes, kind="stable")          # largest functions first
+        list(ex.map(lambda f: oracle.analyze(Q, arch, cnt, int(f), int(f) + 1), order))
     return time.perf_counter() - t0
+
+
+def host_threads() -> int:
+    return len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
 
 
 def reference_arm(a):
@@ -287,22 +339,23 @@ def reference_arm(a):
     if rank != 0:
         return
     P, n = make_workload(a.workload, a.seed, a.samples)
+    threads = host_threads()
     k_funcs = min(P.n_functions, max(1, a.cpu_functions // 4))
     sub, m = cpu_sample(P, n, k_funcs, a.seed, max(1, a.cpu_samples // 4))
     for _ in range(a.warmup):
-        run_oracle_once(P, sub, k_funcs)
-    ts = [run_oracle_once(P, sub, k_funcs) for _ in range(a.steps)]
+        run_oracle_once(P, sub, k_funcs, threads)
+    ts = [run_oracle_once(P, sub, k_funcs, threads) for _ in range(a.steps)]
     t = statistics.mean(ts)
     v = sub.size / t
     instr = int(P.func_instr_off[k_funcs])
     sample = (f"functions 0..{k_funcs - 1} of the {a.workload} workload ({instr} instructions) with the "
-              f"first {sub.size} samples of their launch runs")
+              f"first {sub.size} samples of their launch runs; oracle over functions on {threads} host threads")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": a.gpus, "steps": a.steps,
         "warmup": a.warmup, "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "int64", "data": "synthetic",
         "config": {"workload": a.workload, "sample": sample},
-        "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
 
@@ -349,8 +402,12 @@ def main():
         tuned = {"fixed_ms_per_step": fixed_ms, "tuned_ms_per_step": min(t for _, t in table),
                  "options": best, "candidates_tried": len(table)}
         opts = best
+    torch.cuda.synchronize(dev)
+    t_load = time.perf_counter()
     ctx = gpa.Context(synth.default_arch(), opts or None)
     prog = ctx.load_program(P)
+    torch.cuda.synchronize(dev)
+    load_ms = (time.perf_counter() - t_load) * 1e3
     # Seeded launch statistics of the workload's kernels on this GPU's SM model:
     # the advice step also runs the parallel optimizers (Table 2, Eqs. 6-10).
     prog.set_launch_stats(synth.launch_stats(P.n_functions, a.seed),
@@ -371,6 +428,16 @@ def main():
         if ev:
             ev[3].record(stream)
 
+    # The cold step: the first one of the freshly loaded program (kernels load on
+    # first use, and no search knows its tier yet), as a profile analysed once sees it.
+    cold = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    torch.cuda.synchronize(dev)
+    t_cold = time.perf_counter()
+    step(cold)
+    torch.cuda.synchronize(dev)
+    cold_wall_ms = (time.perf_counter() - t_cold) * 1e3
+    cold_step = {"ms": cold[0].elapsed_time(cold[3]), "wall_ms": cold_wall_ms,
+                 "blame_ms": cold[1].elapsed_time(cold[2]), "load_ms": load_ms}
     for _ in range(a.warmup):
         step()
     st, info = prog.status(stream)
@@ -453,17 +520,35 @@ def main():
             adv = prog.advise(fetch=True, stream=stream)  # synchronizes the stream
         te = (time.perf_counter() - t0) / reps
         te = reduce_max(te, world)
+        # The host link: ingest from pinned host memory alone (CUDA events) against a
+        # plain pinned host-to-device copy.
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        prog.reset(stream)
+        e0.record(stream)
+        prog.ingest_host(host, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ingest_gbs = 8 * n / (e0.elapsed_time(e1) / 1e3) / 1e9
+        h2d = pinned_h2d_gbs(host, dev)
         e2e = {"value": weak_value(n, te * 1e3, world), "unit": UNIT, "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": d2h,
-               "ms_per_step": te * 1e3}
+               "ms_per_step": te * 1e3,
+               "host_link": {"ingest_gbs": ingest_gbs, "pinned_h2d_gbs": h2d, "frac": ingest_gbs / h2d}}
 
     cpu = None
-    if rank == 0 and world == 1 and not a.no_cpu_baseline:
+    if rank == 0 and world == 1 and not a.no_cpu_baseline and a.workload == "large":
+        cpu = {"unavailable": "the oracle's analysis of the one 200,000-instruction function does not finish in "
+                              "a bounded sample (its searches take hours on the host); see the batched workload"}
+    elif rank == 0 and world == 1 and not a.no_cpu_baseline:
         k_funcs = min(P.n_functions, a.cpu_functions)
         sub, m = cpu_sample(P, n, k_funcs, a.seed, a.cpu_samples)
-        t = run_oracle_once(P, sub, k_funcs)
-        cpu = {"value": sub.size / t, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"functions 0..{k_funcs - 1} ({int(P.func_instr_off[k_funcs])} instructions) with "
-                         f"the first {sub.size} samples of their launch runs; {t:.1f} s single-threaded"}
+        threads = host_threads()
+        t_all = run_oracle_once(P, sub, k_funcs, threads)
+        t_one = run_oracle_once(P, sub, k_funcs, 1)
+        sample = (f"functions 0..{k_funcs - 1} ({int(P.func_instr_off[k_funcs])} instructions) with the first "
+                  f"{sub.size} samples of their launch runs")
+        cpu = {"value": sub.size / t_all, "unit": UNIT, "cores": threads, "kind": "oracle",
+               "sample": f"{sample}; {t_all:.1f} s on {threads} host threads (functions in parallel)",
+               "single_core": {"value": sub.size / t_one, "unit": UNIT, "cores": 1, "seconds": t_one}}
 
     # Single dependency coverage (Sec. 6) of this workload, before and after pruning.
     # Its searches have no latency bound, so on a very large function they can
@@ -482,6 +567,14 @@ def main():
     bvp = None
     if rank == 0 and world == 1 and a.plain_workload:
         bvp = plain_vs_batched(gpa, a.plain_workload, a.seed, dev, stream)
+    serving = None
+    if rank == 0 and world == 1 and a.serving_sessions > 0:
+        prog.unload()
+        ctx.close()
+        prog = ctx = None
+        del d
+        torch.cuda.empty_cache()
+        serving = serving_measure(a, gpa, dev, a.serving_sessions)
 
     if rank == 0:
         line = {
@@ -499,11 +592,12 @@ def main():
             "largest_search_nodes": info["max_nodes"], "gpu_launches": launches,
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
             "batched_vs_plain": bvp, "autotune": tuned, "options": opts, "dependency_coverage": coverage,
-            "parallel_optimizers": parallel,
+            "parallel_optimizers": parallel, "cold_first_step": cold_step, "serving": serving,
         }
         print(json.dumps(line), flush=True)
-    prog.unload()
-    ctx.close()
+    if prog is not None:
+        prog.unload()
+        ctx.close()
     if world > 1:
         dist.destroy_process_group()
 

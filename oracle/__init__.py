@@ -58,6 +58,8 @@ def _L():
         lib.oracle_check_loops.argtypes = [vp, i32]
         lib.oracle_analyze.argtypes = [vp, vp, vp, i32, i32]
         lib.oracle_analyze.restype = vp
+        lib.oracle_edges_of_uses.argtypes = [vp, vp, vp, i32, vp]
+        lib.oracle_edges_of_uses.restype = vp
         lib.oracle_n_edges.argtypes = [vp]
         lib.oracle_n_edges.restype = i64
         lib.oracle_get_edges.argtypes = [vp] * 7
@@ -164,6 +166,32 @@ def check_loops(prog, f: int) -> int:
     return int(_L().oracle_check_loops(b.ref, f))
 
 
+def _read_edges(lib, h):
+    ne = int(lib.oracle_n_edges(h))
+    m = max(ne, 1)
+    ej, ei, dmin, dlong = (np.zeros(m, np.int32) for _ in range(4))
+    fl = np.zeros(m, np.uint32)
+    share = np.zeros(m * 8, np.uint64)
+    lib.oracle_get_edges(h, _p(ej), _p(ei), _p(dmin), _p(dlong), _p(fl), _p(share))
+    return dict(j=ej[:ne], i=ei[:ne], dmin=dmin[:ne], dlong=dlong[:ne], flags=fl[:ne],
+                share=share[:ne * 8].reshape(ne, 4, 2))
+
+
+def edges_of_uses(prog, arch, cnt: np.ndarray, uses) -> dict:
+    """Surviving merged edges with their Eq. 1 shares of the given uses only (global
+    instruction indices): the rows of analyze()'s edges whose use is listed."""
+    prog = _arrays(prog)
+    b = _Bound(prog, arch)
+    c = np.ascontiguousarray(cnt, dtype=np.uint64).reshape(-1)
+    u = np.ascontiguousarray(np.unique(np.asarray(uses, dtype=np.int64)), dtype=np.int32)
+    lib = _L()
+    h = lib.oracle_edges_of_uses(b.ref, ctypes.byref(b.a), _p(c), int(u.size), _p(u) if u.size else None)
+    try:
+        return _read_edges(lib, h)
+    finally:
+        lib.oracle_free(h)
+
+
 def analyze(prog, arch, cnt: np.ndarray, f_lo: int = 0, f_hi: int | None = None) -> dict:
     """Blame, surviving merged edges and advice for functions [f_lo, f_hi)."""
     prog = _arrays(prog)
@@ -174,12 +202,7 @@ def analyze(prog, arch, cnt: np.ndarray, f_lo: int = 0, f_hi: int | None = None)
     lib = _L()
     h = lib.oracle_analyze(b.ref, ctypes.byref(b.a), _p(c), f_lo, f_hi)
     try:
-        ne = int(lib.oracle_n_edges(h))
-        m = max(ne, 1)
-        ej, ei, dmin, dlong = (np.zeros(m, np.int32) for _ in range(4))
-        fl = np.zeros(m, np.uint32)
-        share = np.zeros(m * 8, np.uint64)
-        lib.oracle_get_edges(h, _p(ej), _p(ei), _p(dmin), _p(dlong), _p(fl), _p(share))
+        edges = _read_edges(lib, h)
         i_lo, i_hi = int(prog["func_instr_off"][f_lo]), int(prog["func_instr_off"][f_hi])
         blame = np.zeros((i_hi - i_lo) * 24, np.uint64)
         lib.oracle_get_blame(h, _p(blame))
@@ -202,8 +225,7 @@ def analyze(prog, arch, cnt: np.ndarray, f_lo: int = 0, f_hi: int | None = None)
     finally:
         lib.oracle_free(h)
     return dict(
-        edges=dict(j=ej[:ne], i=ei[:ne], dmin=dmin[:ne], dlong=dlong[:ne], flags=fl[:ne],
-                   share=share[:ne * 8].reshape(ne, 4, 2)),
+        edges=edges,
         blame=blame.reshape(-1, 12, 2),
         totals=tot.reshape(nfr, 4), M=M.reshape(nfr, N_OPT), speedup=sp.reshape(nfr, N_OPT),
         rank=rank.reshape(nfr, N_OPT), n_hot=nhot.reshape(nfr, N_OPT), hot=hot.reshape(nfr, N_OPT, 5, 6),

@@ -434,6 +434,80 @@ double est(uint64_t T, uint64_t M) {
   return (double)T / (double)(T - M);
 }
 
+// Sec. 4 for one use j (local index) of function F: immediate sources over
+// every resource j reads, the three pruning rules, and Eq. 1 for each
+// dependency class and latency flag. Appends the surviving merged edges (with
+// their shares) to `edges` and hands every share to add(def, class, latency
+// flag, samples), or the samples to j itself when no source survives.
+template <class AddBlame>
+void blame_use(const OProg& P, const OArch& arch, const uint64_t* cnt, const Fn& F, int j, std::vector<Edge>& edges,
+               AddBlame add) {
+  const int i0 = F.i0;
+  auto C = [&](int x, int c, int lat) { return cnt[(size_t)(i0 + x) * 24 + c * 2 + lat]; };
+  bool stalled = false;
+  for (int c : kDepClass) stalled = stalled || C(j, c, 0) || C(j, c, 1);
+  if (!stalled) return;
+  // Immediate sources over every resource j uses; parallel edges (i, j)
+  // through several resources merge into one source i.
+  std::map<int, Edge> m;
+  for (int e = P.use_off[i0 + j]; e < P.use_off[i0 + j + 1]; ++e) {
+    int r = P.use_res[e] & 0x1FF;
+    for (const SrcRes& s : search(F, j, r, arch.latency)) {
+      int op = P.opclass[i0 + s.i];
+      bool survive = !s.dom && s.dmin <= arch.latency[op];  // dominator and latency pruning
+      if (!survive) continue;
+      auto it = m.find(s.i);
+      if (it == m.end()) {
+        Edge E{};
+        E.j = i0 + j; E.i = i0 + s.i; E.dmin = s.dmin; E.dlong = s.dlong; E.flags = 0;
+        it = m.emplace(s.i, E).first;
+      } else {
+        it->second.dmin = std::min(it->second.dmin, s.dmin);
+        it->second.dlong = std::max(it->second.dlong, s.dlong);
+      }
+      Edge& E = it->second;
+      if (r >= kBarBase) E.flags |= 2;
+      else if (r >= kPredBase) E.flags |= 8;
+      else E.flags |= 4;
+      // Write-after-read: a variable-latency def reads a register that the use writes,
+      // linked through a read barrier (Sec. 4, Fig. 6).
+      if (r >= kBarBase && def_kind(P, i0 + s.i, r) == 2 && (arch.flags[op] & F_VARLAT)) {
+        for (int d = P.def_off[i0 + j]; d < P.def_off[i0 + j + 1]; ++d) {
+          int rr = P.def_res[d] & 0x1FF;
+          if (rr < kPredBase && uses(P, i0 + s.i, rr)) E.flags |= 1;
+        }
+      }
+    }
+  }
+  std::vector<Edge> ej;
+  for (auto& kv : m) ej.push_back(kv.second);
+  // Apportion each dependency class and latency flag separately (Eq. 1).
+  for (int ci = 0; ci < 4; ++ci) {
+    int c = kDepClass[ci];
+    for (int lat = 0; lat < 2; ++lat) {
+      uint64_t S = C(j, c, lat);
+      if (!S) continue;
+      std::vector<int> idx, dl, di;
+      std::vector<uint64_t> iss;
+      for (size_t t = 0; t < ej.size(); ++t) {
+        if (!opcode_keeps(arch, c, P.opclass[ej[t].i])) continue;  // opcode pruning
+        idx.push_back((int)t);
+        iss.push_back(cnt[(size_t)ej[t].i * 24 + 0]);
+        dl.push_back(ej[t].dlong);
+        di.push_back(ej[t].i);
+      }
+      if (idx.empty()) { add(j, c, lat, S); continue; }  // no source survives: stays on j
+      std::vector<uint64_t> sh;
+      apportion(S, iss, dl, di, sh);
+      for (size_t t = 0; t < idx.size(); ++t) {
+        ej[idx[t]].share[ci][lat] = sh[t];
+        add(ej[idx[t]].i - i0, c, lat, sh[t]);
+      }
+    }
+  }
+  for (auto& E : ej) edges.push_back(E);
+}
+
 void analyze_function(const OProg& P, const OArch& arch, const uint64_t* cnt, int f, Result& R) {
   Fn F(P, f);
   const int i0 = F.i0, n = F.i1 - F.i0;
@@ -448,70 +522,8 @@ void analyze_function(const OProg& P, const OArch& arch, const uint64_t* cnt, in
       for (int lat = 0; lat < 2; ++lat) Bl(x, c, lat) += C(x, c, lat);
     }
 
-  for (int j = 0; j < n; ++j) {
-    bool stalled = false;
-    for (int c : kDepClass) stalled = stalled || C(j, c, 0) || C(j, c, 1);
-    if (!stalled) continue;
-    // Immediate sources over every resource j uses; parallel edges (i, j)
-    // through several resources merge into one source i.
-    std::map<int, Edge> m;
-    for (int e = P.use_off[i0 + j]; e < P.use_off[i0 + j + 1]; ++e) {
-      int r = P.use_res[e] & 0x1FF;
-      for (const SrcRes& s : search(F, j, r, arch.latency)) {
-        int op = P.opclass[i0 + s.i];
-        bool survive = !s.dom && s.dmin <= arch.latency[op];  // dominator and latency pruning
-        if (!survive) continue;
-        auto it = m.find(s.i);
-        if (it == m.end()) {
-          Edge E{};
-          E.j = i0 + j; E.i = i0 + s.i; E.dmin = s.dmin; E.dlong = s.dlong; E.flags = 0;
-          it = m.emplace(s.i, E).first;
-        } else {
-          it->second.dmin = std::min(it->second.dmin, s.dmin);
-          it->second.dlong = std::max(it->second.dlong, s.dlong);
-        }
-        Edge& E = it->second;
-        if (r >= kBarBase) E.flags |= 2;
-        else if (r >= kPredBase) E.flags |= 8;
-        else E.flags |= 4;
-        // Write-after-read: a variable-latency def reads a register that the use writes,
-        // linked through a read barrier (Sec. 4, Fig. 6).
-        if (r >= kBarBase && def_kind(P, i0 + s.i, r) == 2 && (arch.flags[op] & F_VARLAT)) {
-          for (int d = P.def_off[i0 + j]; d < P.def_off[i0 + j + 1]; ++d) {
-            int rr = P.def_res[d] & 0x1FF;
-            if (rr < kPredBase && uses(P, i0 + s.i, rr)) E.flags |= 1;
-          }
-        }
-      }
-    }
-    std::vector<Edge> ej;
-    for (auto& kv : m) ej.push_back(kv.second);
-    // Apportion each dependency class and latency flag separately (Eq. 1).
-    for (int ci = 0; ci < 4; ++ci) {
-      int c = kDepClass[ci];
-      for (int lat = 0; lat < 2; ++lat) {
-        uint64_t S = C(j, c, lat);
-        if (!S) continue;
-        std::vector<int> idx, dl, di;
-        std::vector<uint64_t> iss;
-        for (size_t t = 0; t < ej.size(); ++t) {
-          if (!opcode_keeps(arch, c, P.opclass[ej[t].i])) continue;  // opcode pruning
-          idx.push_back((int)t);
-          iss.push_back(cnt[(size_t)ej[t].i * 24 + 0]);
-          dl.push_back(ej[t].dlong);
-          di.push_back(ej[t].i);
-        }
-        if (idx.empty()) { Bl(j, c, lat) += S; continue; }  // no source survives: stays on j
-        std::vector<uint64_t> sh;
-        apportion(S, iss, dl, di, sh);
-        for (size_t t = 0; t < idx.size(); ++t) {
-          ej[idx[t]].share[ci][lat] = sh[t];
-          Bl(ej[idx[t]].i - i0, c, lat) += sh[t];
-        }
-      }
-    }
-    for (auto& E : ej) R.edges.push_back(E);
-  }
+  for (int j = 0; j < n; ++j)
+    blame_use(P, arch, cnt, F, j, R.edges, [&](int x, int c, int lat, uint64_t v) { Bl(x, c, lat) += v; });
 
   // ---------------------------------------------------------------- Sec. 5
   Advice A;
@@ -850,6 +862,30 @@ void* oracle_analyze(const OProg* P, const OArch* arch, const uint64_t* cnt, int
   R->line_stall.assign(P->n_lines, 0);
   R->line_lat.assign(P->n_lines, 0);
   for (int f = f_lo; f < f_hi; ++f) analyze_function(*P, *arch, cnt, f, *R);
+  return R;
+}
+
+// Surviving merged edges (with their Eq. 1 shares) of the given stalled uses
+// only (global instruction indices, ascending): what oracle_analyze gives for
+// those uses, without analyzing the others. Read with oracle_n_edges /
+// oracle_get_edges; the handle holds no blame or advice.
+void* oracle_edges_of_uses(const OProg* P, const OArch* arch, const uint64_t* cnt, int32_t n_uses,
+                           const int32_t* uses) {
+  auto* R = new Result();
+  R->f_lo = R->f_hi = R->i_lo = R->i_hi = R->l_lo = R->l_hi = 0;
+  int f = -1;
+  Fn* F = nullptr;
+  for (int t = 0; t < n_uses; ++t) {
+    const int j = uses[t];
+    if (f < 0 || j < P->func_instr_off[f] || j >= P->func_instr_off[f + 1]) {
+      f = 0;
+      while (P->func_instr_off[f + 1] <= j) ++f;
+      delete F;
+      F = new Fn(*P, f);
+    }
+    blame_use(*P, *arch, cnt, *F, j - F->i0, R->edges, [](int, int, int, uint64_t) {});
+  }
+  delete F;
   return R;
 }
 

@@ -42,6 +42,7 @@ class Result:
     device_bytes: int
     counts: np.ndarray | None = None
     blame: np.ndarray | None = None
+    edges: dict | None = None
 
     @property
     def latency(self) -> float:
@@ -62,8 +63,9 @@ class _Slot:
 
 class Server:
     """slots: concurrent sessions; budget_bytes: device memory the admitted
-    sessions' programs may hold together; keep_results: also return counts
-    and blame (for checking results against a session run alone)."""
+    sessions' programs may hold together; keep_results: also return counts,
+    blame and edges (for checking results against the session run alone and
+    against the oracle)."""
 
     def __init__(self, arch, slots: int = 4, budget_bytes: int = 64 << 30, options: dict | None = None,
                  keep_results: bool = False):
@@ -110,11 +112,13 @@ class Server:
         if st_code != 0:
             raise RuntimeError(f"session {s.sid}: device status {st_code} ({info})")
         adv = prog.get_advice(st)
-        counts = blame = None
+        counts = blame = edges = None
         if self.keep_results:
             counts, _ = prog.counts(st)
             blame = prog.blame_counts(st)
-        r = Result(s.sid, adv, int(s.samples.size), s.t_arrival, sl.t_admit, self.now(), sl.bytes, counts, blame)
+            edges = prog.edges(st)
+        r = Result(s.sid, adv, int(s.samples.size), s.t_arrival, sl.t_admit, self.now(), sl.bytes, counts, blame,
+                   edges)
         prog.unload_async(st)
         self.used -= sl.bytes
         sl.session = sl.prog = sl.event = None

@@ -1,10 +1,11 @@
 """Serving: sessions admitted while others run on the device give the same
-results as each session run alone (bit-exact counts, blame and advice)."""
+results as each session run alone and as the oracle on that session
+(bit-exact counts, edges and blame; advice bit-exact, speedups within 1e-12)."""
 import numpy as np
 import pytest
 
 import synth
-from parity import ARCH, gpu_run
+from parity import ARCH, assert_advice_equal, assert_edges_equal, gpu_run, oracle_run
 
 pytestmark = pytest.mark.gpu
 
@@ -45,6 +46,14 @@ def test_sessions_same_alone_and_in_the_mix():
             assert np.array_equal(alone["blame"], r.blame)
             for k in alone["advice"]:
                 assert np.array_equal(alone["advice"][k], r.advice[k]), (r.sid, k)
+            # and the oracle on the same session
+            R = oracle_run(P, s.samples)
+            assert np.array_equal(r.counts, R["counts"]), r.sid
+            assert_edges_equal(r.edges, R["edges"])
+            assert np.array_equal(r.blame, R["blame"]), r.sid
+            assert_advice_equal(r.advice, R)
+            assert np.array_equal(r.advice["line_stall"], R["line_stall"])
+            assert np.array_equal(r.advice["line_latency"], R["line_lat"])
     finally:
         ctx.close()
 

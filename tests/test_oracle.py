@@ -687,3 +687,20 @@ def test_line_rollup_after_blame():
     R = oracle.analyze(prog, ARCH, counts(4, ent))
     assert R["line_stall"].tolist() == [0, 0, 0, 0, 0, 60, 0, 5]
     assert R["line_lat"].tolist() == [0, 0, 0, 0, 0, 34, 0, 0]
+
+
+def test_edges_of_selected_uses_equal_full_analysis():
+    """The oracle's per-use entry (used where the whole analysis is too slow) gives,
+    for any set of uses, exactly the rows of the full analysis's edge list."""
+    ps, _, kz = synth.workload("rodinia")
+    P = synth.make_program(ps[:5], kz)
+    cnt, _ = oracle.histogram(P, P.samples(200_000, seed=3))
+    R = oracle.analyze(P, ARCH, cnt)["edges"]
+    uses = np.unique(R["j"])
+    pick = np.random.default_rng(3).choice(uses, size=len(uses) // 3, replace=False)
+    pick = np.concatenate([pick, [0, P.n_instr - 1]])          # unstalled uses add nothing
+    got = oracle.edges_of_uses(P, ARCH, cnt, pick)
+    keep = np.isin(R["j"], pick)
+    for k in ("j", "i", "dmin", "dlong", "flags", "share"):
+        assert np.array_equal(got[k], R[k][keep]), k
+    assert len(got["j"]) > 0
