@@ -110,14 +110,15 @@ typedef struct {
                                    outgrow the first tier go on to the global-memory warps, which are
                                    faster than few large shared-memory arenas) */
   int32_t hist_variant;         /* aggregation kernel: 0 (default) = one CTA per SM taking chunks of
-                                   tiles from a counter, shared memory used per kernel-launch run as a
-                                   direct-indexed window over up to 2,078 instructions of that kernel's
-                                   counters plus a hash for the rest; grid-strided with a shared-memory
-                                   hash: 1 = 8,192 entries, 512 threads, 2 CTAs per SM; 2 = 16,384
-                                   entries, 1,024 threads, 1 CTA per SM; 3 = 8,192 entries, 256 threads,
-                                   3 CTAs per SM */
+                                   tiles of 8,192 samples from a counter, shared memory used per
+                                   2,048-sample segment as a direct-indexed window over up to 1,558
+                                   instructions of the segment's kernel plus a hash for the rest;
+                                   grid-strided with a shared-memory hash: 1 = 8,192 entries, 512
+                                   threads, 2 CTAs per SM; 2 = 16,384 entries, 1,024 threads, 1 CTA
+                                   per SM; 3 = 8,192 entries, 256 threads, 3 CTAs per SM */
   int32_t large_search_nodes;   /* a global-memory search that reached this many nodes is started
                                    before the others on later steps of its program; 0 = 1024 */
+  int32_t hist_chunk;           /* aggregation variant 0: tiles per claimed chunk, 0 = 24 (max 4096) */
 } gpa_options;
 
 /* A program: n_functions functions laid out one after another. All arrays are

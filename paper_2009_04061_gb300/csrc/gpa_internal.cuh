@@ -290,7 +290,7 @@ void launch_build_layout(const Prog& P, cudaStream_t st, int sms, int64_t* launc
 void launch_build_preds(const Prog& P, int n_succ, int32_t* pred_off, int32_t* cursor, int32_t* tmp, cudaStream_t st,
                         int sms, int64_t* launches);
 void launch_histogram(const Prog& P, const uint64_t* samples, size_t n, cudaStream_t st, int sms, int64_t* launches,
-                      int variant);
+                      int variant, int hist_chunk);
 void launch_dataflow(const Prog& P, const Arch& A, int max_sweeps, cudaStream_t st, int sms, int64_t* launches);
 
 // Lets kernel func take up to the device's opt-in shared memory per block.

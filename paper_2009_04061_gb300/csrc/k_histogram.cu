@@ -11,6 +11,8 @@
 // that finds no slot within a few probes goes straight to its 64-bit global
 // counter. The hash is flushed to the global counters when three quarters
 // full and at the end. With Zipf-skewed hotness most samples stay on chip.
+#include <type_traits>
+
 #include "gpa_internal.cuh"
 
 namespace gpa {
@@ -172,36 +174,37 @@ __global__ void __launch_bounds__(THREADS) k_histogram(Prog P, const uint64_t* _
 
 // Variant 0 (default), for streams that arrive as kernel-launch runs (a
 // profiler that serializes kernels delivers them so). Each CTA (one per SM,
-// 1,024 threads) claims chunks of 16 consecutive tiles of 8,192 samples. Its
-// shared memory holds a window of 32-bit counters over up to 2,078
-// consecutive instructions of the run's kernel, and a 4,096-entry hash.
-// A kernel that fits is windowed whole; for a larger one the window is placed
-// where most of the tile's first 32 samples fall. The first sample of each
-// tile names the kernel; a new kernel flushes the window to the 64-bit global
-// counters and places it again.
-// A sample inside the window is one shared-memory reduction (no return value,
-// predicated on the window test: no branch) on its counter; any other valid
-// sample (another kernel at a run boundary, or a pc outside a partial window)
-// goes to the hash, and a key that finds no slot within four probes to its
+// 1,024 threads) claims chunks of consecutive tiles of 8,192 samples from a
+// counter; a tile is four segments of 2,048 samples, one 16-byte vector per
+// thread each. Shared memory holds a window of 32-bit counters over up to
+// 1,558 consecutive instructions of one kernel, 32 words per instruction
+// indexed by the sample's 5-bit (class, latency) field, and a 4,096-entry
+// hash. The middle sample of each segment names the kernel that segment is
+// counted for: when it differs from the window's, the window is flushed to the
+// 64-bit global counters and placed for the new kernel (whole when it fits,
+// else on the densest span of the 32 samples around that middle sample). A
+// run boundary inside a segment thus costs at most its minority side.
+// A sample inside the window is one shared-memory reduction on its word (no
+// return value, predicated: no branch). The 9 field values that name no
+// counter (SELECTED with the latency flag, class 12 and up) land in words the
+// flush counts as invalid samples. A vector whose two samples do not both carry
+// the window kernel's upper id bits and zero reserved bits, and any other
+// sample (another kernel, a pc outside a partial window), takes the checked
+// path: the hash, and a key that finds no slot within four probes goes to its
 // global counter. The hash is flushed when half full, and window and hash at
 // least every 2^16 tiles (fewer than 2^30 increments: no 32-bit count wraps)
 // and at the end.
 constexpr int kRunThreads = 1024;
-#ifndef GPA_RUN_VEC
-#define GPA_RUN_VEC 4
-#endif
-#ifndef GPA_RUN_CHUNK
-#define GPA_RUN_CHUNK 16
-#endif
-constexpr int kRunVec = GPA_RUN_VEC;                  // 16-byte vectors per thread per tile
+constexpr int kRunVec = 4;                            // segments per tile: vectors per thread per tile
 constexpr int kRunTile = kRunThreads * kRunVec;       // vectors per tile (8,192 samples)
-constexpr int kMainWords = 49872;                     // 195 KB of 32-bit window counters, 24 per instruction
-constexpr uint32_t kWinInstr = kMainWords / 24u;      // 2,078 instructions
+constexpr int kWinStride = 32;                        // window words per instruction
+constexpr uint32_t kWinInstr = 1558;                  // instructions in the window
+constexpr int kMainWords = (int)kWinInstr * kWinStride;  // 199,424 bytes of 32-bit counters
 constexpr int kSideLog2 = 12;                         // 4,096-entry hash
 constexpr int kRunFlushTiles = 1 << 16;               // forced flush: keeps 32-bit counts below 2^30
-constexpr int kRunChunk = GPA_RUN_CHUNK;              // tiles per claimed chunk
 static_assert((long long)kRunFlushTiles * 2 * kRunTile < (1ll << 30), "32-bit counts could wrap between flushes");
-static_assert(kMainWords % 24 == 0, "the window holds whole instructions (24 words each)");
+static_assert(kMainWords % 4 == 0, "the window is read and cleared as 16-byte vectors");
+static_assert(kRunVec == 4, "the per-tile kernel test reads four segment kernels");
 // Bit f of kValid5 is set when the 5-bit (class, latency) field f names a
 // counter: class < 12, and not SELECTED with the latency flag.
 constexpr uint32_t kValid5 = 0x00FFFFFDu;
@@ -235,20 +238,19 @@ __device__ void table_flush(uint32_t* key, uint32_t* val, unsigned long long* cn
   }
 }
 
-// Start of the window over a kernel of n instructions: 0 when it fits,
-// else the start, among windows centred on the first 8 of the tile's first 32
-// samples of that kernel, that holds most of those 32 (`x`, this lane's;
-// lanes past the stream pass have ok == false). Every warp reads the same 32
-// samples and reaches the same answer.
-__device__ __forceinline__ uint32_t window_start(uint64_t x, bool ok, uint32_t kernel, uint32_t n) {
+// Start of the window over a kernel of n instructions: 0 when it fits, else
+// the start, among windows centred on lanes 12-19 of the 32 samples `x` (one
+// per lane) that are of that kernel, that holds most of those 32. Every warp
+// reads the same 32 samples and reaches the same answer.
+__device__ __forceinline__ uint32_t window_start(uint64_t x, uint32_t kernel, uint32_t n) {
   if (n <= kWinInstr) return 0u;
   const uint32_t pc = (uint32_t)(x >> 24) & 0xFFFFFFu;
-  const bool mine = ok && (uint32_t)(x >> 48) == kernel && pc < n;
+  const bool mine = (uint32_t)(x >> 48) == kernel && pc < n;
   uint32_t lo = pc > kWinInstr / 2u ? pc - kWinInstr / 2u : 0u;
   if (lo > n - kWinInstr) lo = n - kWinInstr;
   uint32_t best = 0u, best_lo = 0u;
 #pragma unroll
-  for (int c = 0; c < 8; ++c) {
+  for (int c = 12; c < 20; ++c) {
     const uint32_t lo_c = __shfl_sync(0xffffffffu, lo, c);
     const bool cand = __shfl_sync(0xffffffffu, mine, c);
     const uint32_t hits = (uint32_t)__popc(__ballot_sync(0xffffffffu, mine && pc - lo_c < kWinInstr));
@@ -257,28 +259,50 @@ __device__ __forceinline__ uint32_t window_start(uint64_t x, bool ok, uint32_t k
   return best_lo;
 }
 
+// One window sample: when chk == 0 and r < span, one shared-memory reduction
+// (no return value) on the word at addr; otherwise BIT is set in slow.
+template <uint32_t BIT>
+__device__ __forceinline__ void count_window(uint32_t addr, uint32_t r, uint32_t chk, uint32_t span, uint32_t& slow) {
+  asm volatile("{\n\t.reg .pred ok, p;\n\t"
+               "setp.eq.u32 ok, %3, 0;\n\t"
+               "setp.lt.and.u32 p, %2, %4, ok;\n\t"
+               "@p red.shared.add.u32 [%1], 1;\n\t"
+               "@!p or.b32 %0, %0, %5;\n\t}"
+               : "+r"(slow) : "r"(addr), "r"(r), "r"(chk), "r"(span), "n"(BIT) : "memory");
+}
+
 __global__ void __launch_bounds__(kRunThreads, 1) k_histogram_runs(Prog P, const uint64_t* __restrict__ s,
-                                                                   int64_t n, int head) {
+                                                                   int64_t n, int head, int chunk_tiles) {
   extern __shared__ __align__(16) uint32_t sm[];
   uint32_t* win = sm;                                     // kMainWords window counters
   const uint32_t win_base = (uint32_t)__cvta_generic_to_shared(win);
   uint32_t* skey = sm + kMainWords;                       // hash
   uint32_t* sval = skey + (1 << kSideLog2);
   int* ctl = reinterpret_cast<int*>(sval + (1 << kSideLog2));  // 1: hash fill
+  // Every window word is zero whenever no kernel is being counted into it (the
+  // flush zeroes what it reads), so placing the window needs no clearing.
+  for (int t = threadIdx.x; t < kMainWords / 4; t += kRunThreads)
+    reinterpret_cast<uint4*>(win)[t] = make_uint4(0u, 0u, 0u, 0u);
   for (int t = threadIdx.x; t < (1 << kSideLog2); t += kRunThreads) { skey[t] = kNoKey; sval[t] = 0u; }
   if (threadIdx.x < 8) ctl[threadIdx.x] = 0;
   __syncthreads();
   const int32_t* foff = P.func_instr_off;  // read through the cache: the window takes the shared memory
   const int lane = threadIdx.x & 31;
   uint32_t bad = 0, side_ins = 0;
-  // The windowed kernel's first instruction and size (kept in registers: a
-  // miss of that kernel needs no offset lookup).
-  uint32_t mode_first = 0, mode_n = 0;
-  int mode = -1;
-  // A sample that is not in the window: the hash, else its global counter.
+  // The window: mode_hi = its kernel << 16 (kNoMode: none), instructions
+  // [lo, lo + wn) of it; word (pc - lo) * 32 + f5 counts (pc, f5), f5 the
+  // 5-bit (class, latency) field. With r = bits 19..50 of a sample (f5 | pc << 5
+  // | low 3 kernel bits << 29), a sample whose kernel bits 51..63 match is in the
+  // window when r - first5 < span5, first5 = (kernel << 29) | (lo << 5), span5 =
+  // wn << 5 (so lo and wn need no registers of their own). The kernel's first
+  // instruction and size stay in registers: a miss of that kernel needs no
+  // offset lookup.
+  constexpr uint32_t kNoMode = 0xFFFF0000u;
+  uint32_t mode_hi = kNoMode, first5 = 0, span5 = 0, mode_first = 0, mode_n = 0;
+  // A sample that is not counted in the window: the hash, else its global counter.
   auto count_other = [&](uint64_t x) {
     uint32_t key;
-    if ((int)(x >> 48) == mode) {
+    if (((uint32_t)(x >> 32) & 0xFFFF0000u) == mode_hi) {
       const uint32_t pc = (uint32_t)(x >> 24) & 0xFFFFFFu, f5 = (uint32_t)(x >> 19) & 31u;
       key = (pc < mode_n && ((kValid5 >> f5) & 1u) && (x & 0x7FFull) == 0ull) ? (mode_first + pc) * 24u + f5
                                                                                 : kNoKey;
@@ -295,55 +319,85 @@ __global__ void __launch_bounds__(kRunThreads, 1) k_histogram_runs(Prog P, const
   const ulonglong2* v2 = reinterpret_cast<const ulonglong2*>(s + head);
   const uint64_t* s2 = s + head;
   const int64_t n2 = (n - head) / 2;
-  const int64_t n_tiles = n2 / kRunTile;
+  const int n_tiles = (int)(n2 / kRunTile);
   if (blockIdx.x == 0) {
     if (threadIdx.x == 0) {
       for (int64_t t = 0; t < head; ++t) count_other(s[t]);
       for (int64_t t = head + 2 * n2; t < n; ++t) count_other(s[t]);
     }
-    for (int64_t v = n_tiles * kRunTile + threadIdx.x; v < n2; v += kRunThreads) {
+    for (int64_t v = (int64_t)n_tiles * kRunTile + threadIdx.x; v < n2; v += kRunThreads) {
       const ulonglong2 x = load_stream(v2 + v);
       count_other(x.x);
       count_other(x.y);
     }
   }
 
-  // The window: kernel `mode` (-1: none), instructions [lo, lo + wn), whose
-  // counters start at global index base; the counter of (pc, f5), f5 the
-  // 5-bit (class, latency) field, is word (pc - lo) * 24 + f5.
-  // With r = bits 19..50 of a sample (f5 | pc << 5 | low 3 kernel bits << 29),
-  // a sample of kernel `mode` is in the window when r - first5 < span5,
-  // first5 = (mode << 29) | (lo << 5), span5 = wn << 5.
-  uint32_t lo = 0, wn = 0, base = 0, mode_hi = 0, first5 = 0, span5 = 0;
-  // The window holds wn * 24 words (a multiple of 4: read and cleared as 16-byte vectors).
   auto flush_win = [&]() {
-    const uint32_t quads = wn * 6u;
+    const uint32_t quads = span5 >> 2;                     // wn * 32 words, 4 per quad
+    const uint32_t gfirst = mode_first + ((first5 >> 5) & 0xFFFFFFu);
     for (uint32_t q = threadIdx.x; q < quads; q += kRunThreads) {
-      const uint4 v = reinterpret_cast<const uint4*>(win)[q];
+      uint4* w = reinterpret_cast<uint4*>(win) + q;
+      const uint4 v = *w;
+      if ((v.x | v.y | v.z | v.w) == 0u) continue;
+      *w = make_uint4(0u, 0u, 0u, 0u);
       const uint32_t c[4] = {v.x, v.y, v.z, v.w};
+      const uint32_t f0 = (q % (kWinStride / 4)) * 4u;
+      const uint32_t g = (gfirst + q / (kWinStride / 4)) * 24u;
 #pragma unroll
-      for (int e = 0; e < 4; ++e)
-        if (c[e]) atomicAdd(P.cnt + base + 4u * q + e, (unsigned long long)c[e]);
+      for (int e = 0; e < 4; ++e) {
+        if (!c[e]) continue;
+        const uint32_t f5 = f0 + e;
+        if ((kValid5 >> f5) & 1u) atomicAdd(P.cnt + g + f5, (unsigned long long)c[e]);
+        else bad += c[e];
+      }
+    }
+  };
+  // Flush the window and place it for kernel id `want` (>= nf: none), from the
+  // 32 samples starting at stream index m. CTA-uniform: every thread takes part.
+  auto place = [&](uint32_t want, int64_t m) {
+    __syncthreads();
+    flush_win();
+    __syncthreads();
+    mode_hi = kNoMode;
+    first5 = span5 = mode_first = mode_n = 0;
+    if (want < (uint32_t)P.nf) {
+      const uint32_t n_instr = (uint32_t)(foff[want + 1] - foff[want]);
+      mode_first = (uint32_t)foff[want];
+      mode_n = n_instr;
+      const uint32_t lo = window_start(__ldg(reinterpret_cast<const unsigned long long*>(s2 + m + lane)), want, n_instr);
+      mode_hi = want << 16;
+      first5 = (want << 29) | (lo << 5);
+      span5 = min(n_instr, kWinInstr) << 5;
     }
   };
 
-  // Tiles are handed out in chunks of kRunChunk consecutive tiles from a
+  // Tiles are handed out in chunks of chunk_tiles consecutive tiles from a
   // counter (one chunk ahead, so the last tile of a chunk can prefetch the
   // first of the next): an SM that meets cheap runs takes more of them.
-  const int64_t n_chunks = (n_tiles + kRunChunk - 1) / kRunChunk;
-  __shared__ long long s_claim;
-  auto claim = [&]() -> int64_t {
-    if (threadIdx.x == 0) s_claim = (long long)atomicAdd(&P.stats[SS_HIST_HEAD], 1ull);
+  const int n_chunks = (n_tiles + chunk_tiles - 1) / chunk_tiles;
+  __shared__ int s_claim;
+  // A chunk claim also reports this thread's hash inserts and flushes the hash
+  // when half full (the claim's barriers order both).
+  auto claim = [&]() -> int {
+    if (side_ins) atomicAdd(&ctl[1], (int)side_ins);
+    side_ins = 0;
+    if (threadIdx.x == 0) s_claim = (int)atomicAdd(&P.stats[SS_HIST_HEAD], 1ull);
     __syncthreads();
-    const int64_t c = s_claim;
+    const int c = s_claim;
+    const bool side_full = ctl[1] > (1 << kSideLog2) / 2;
     __syncthreads();
+    if (side_full) {
+      table_flush<kSideLog2>(skey, sval, P.cnt);
+      if (threadIdx.x == 0) ctl[1] = 0;
+      __syncthreads();
+    }
     return c < n_chunks ? c : n_chunks;
   };
-  int64_t chunk = claim();
-  int64_t upcoming = chunk < n_chunks ? claim() : n_chunks;
-  int64_t g = chunk * kRunChunk, g_end = min(g + kRunChunk, n_tiles);
-  auto next_tile = [&]() -> int64_t {
-    return g + 1 < g_end ? g + 1 : (upcoming < n_chunks ? upcoming * kRunChunk : -1);
+  int chunk = claim();
+  int upcoming = chunk < n_chunks ? claim() : n_chunks;
+  int g = chunk * chunk_tiles, g_end = min(g + chunk_tiles, n_tiles);
+  auto next_tile = [&]() -> int {
+    return g + 1 < g_end ? g + 1 : (upcoming < n_chunks ? upcoming * chunk_tiles : -1);
   };
   auto advance = [&]() {
     if (g + 1 < g_end) {
@@ -351,72 +405,71 @@ __global__ void __launch_bounds__(kRunThreads, 1) k_histogram_runs(Prog P, const
     } else {
       chunk = upcoming;
       if (chunk < n_chunks) {
-        g = chunk * kRunChunk;
-        g_end = min(g + kRunChunk, n_tiles);
+        g = chunk * chunk_tiles;
+        g_end = min(g + chunk_tiles, n_tiles);
         upcoming = claim();
       }
     }
   };
-  // A tile's vectors, and its first sample's kernel (every thread loads that
-  // word: one broadcast load per warp, issued with the tile's own loads).
-  auto load_tile = [&](int64_t t, ulonglong2* v, uint32_t& k0) {
+  // The tile after next, when it is in this chunk, is fetched into L2 by one
+  // bulk prefetch from one thread, so the register loads of the next tile
+  // find it there.
+  auto prefetch_after = [&]() {
+    if (threadIdx.x == 0 && g + 2 < g_end) {
+      const ulonglong2* p = v2 + (int64_t)(g + 2) * kRunTile;
+      asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" :: "l"(p), "r"((uint32_t)(kRunTile * 16)) : "memory");
+    }
+  };
+  // A tile's vectors, and the kernel of each segment's middle sample: lane u
+  // of every warp loads segment u's (issued with the tile's own loads).
+  auto load_tile = [&](int t, ulonglong2* v, uint32_t& k) {
+    const int64_t t0 = (int64_t)t * kRunTile;
 #pragma unroll
-    for (int u = 0; u < kRunVec; ++u) v[u] = load_stream(v2 + t * kRunTile + u * kRunThreads + threadIdx.x);
-    k0 = __ldg(reinterpret_cast<const unsigned int*>(s2 + 2 * t * kRunTile) + 1) >> 16;
+    for (int u = 0; u < kRunVec; ++u) v[u] = load_stream(v2 + t0 + u * kRunThreads + threadIdx.x);
+    k = lane < kRunVec ? __ldg(reinterpret_cast<const unsigned int*>(s2 + 2 * (t0 + lane * kRunThreads) +
+                                                                     kRunThreads) + 1) >> 16
+                       : 0u;
   };
 
-  // Tiles since the hash was last flushed (the window is flushed at every
-  // kernel change as well, so this bounds both).
-  int since = 0;
-  int64_t t_count = 0;
-  auto process = [&](const ulonglong2* v, uint32_t k0) {
-    const int want = k0 < (uint32_t)P.nf ? (int)k0 : -1;
-    const bool periodic = ++since >= kRunFlushTiles;  // keeps the 32-bit counts small
-    if (want != mode || periodic) {
-      if (periodic) since = 0;
+  int since = 0;      // tiles since window and hash were last both flushed
+  auto process = [&](const ulonglong2* v, uint32_t k) {
+    if (++since >= kRunFlushTiles) {  // keeps the 32-bit counts small
+      since = 0;
       __syncthreads();
       flush_win();
-      if (periodic) table_flush<kSideLog2>(skey, sval, P.cnt);
-      __syncthreads();
-      if (periodic && threadIdx.x == 0) ctl[1] = 0;
-      mode = want;
-      lo = wn = 0;
-      mode_first = mode_n = 0;
-      if (mode >= 0) {
-        const uint32_t n_instr = (uint32_t)(foff[mode + 1] - foff[mode]);
-        mode_first = (uint32_t)foff[mode];
-        mode_n = n_instr;
-        lo = window_start(__ldg(reinterpret_cast<const unsigned long long*>(s2 + 2 * g * kRunTile + lane)), true,
-                          (uint32_t)mode, n_instr);
-        wn = min(n_instr, kWinInstr);
-        base = ((uint32_t)foff[mode] + lo) * 24u;
-        for (uint32_t q = threadIdx.x; q < wn * 6u; q += kRunThreads)
-          reinterpret_cast<uint4*>(win)[q] = make_uint4(0u, 0u, 0u, 0u);
-      }
-      mode_hi = (uint32_t)max(mode, 0) << 16;
-      first5 = ((uint32_t)max(mode, 0) << 29) | (lo << 5);
-      span5 = wn << 5;
+      table_flush<kSideLog2>(skey, sval, P.cnt);
+      if (threadIdx.x == 0) ctl[1] = 0;
       __syncthreads();
     }
-    // One predicated shared-memory reduction per window sample (no return
-    // value to wait for, no branch).
     uint32_t slow = 0;
-#pragma unroll
-    for (int u = 0; u < kRunVec; ++u) {
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const uint64_t x = h ? v[u].y : v[u].x;
-        const uint32_t xl = (uint32_t)x, xh = (uint32_t)(x >> 32);
-        const uint32_t rel = __funnelshift_r(xl, xh, 19) - first5;
-        const bool hit = rel < span5 && ((xh ^ mode_hi) >> 16) == 0u && ((kValid5 >> (rel & 31u)) & 1u) &&
-                         (xl & 0x7FFu) == 0u;
-        const uint32_t idx = rel - ((rel >> 5) << 3);  // (pc - lo) * 24 + f5
-        const uint32_t addr = win_base + 4u * idx;
-        asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %1, 0;\n\t@p red.shared.add.u32 [%0], 1;\n\t}"
-                     :: "r"(addr), "r"((uint32_t)hit) : "memory");
-        if (!hit) slow |= 1u << (2 * u + h);
+    auto segment = [&](auto U, bool check) {
+      constexpr int u = decltype(U)::value;
+      if (check) {
+        const uint32_t ku = __shfl_sync(0xffffffffu, k, u);
+        if ((ku < (uint32_t)P.nf ? ku << 16 : kNoMode) != mode_hi)
+          place(ku, 2 * ((int64_t)g * kRunTile + u * kRunThreads) + kRunThreads - 16);
       }
-    }
+      // Both samples of the vector carry the window kernel's upper id bits and
+      // zero reserved bits; then each is in the window when its offset is.
+      const uint32_t x0l = (uint32_t)v[u].x, x0h = (uint32_t)(v[u].x >> 32);
+      const uint32_t x1l = (uint32_t)v[u].y, x1h = (uint32_t)(v[u].y >> 32);
+      const uint32_t chk = (((x0h ^ mode_hi) | (x1h ^ mode_hi)) & 0xFFF80000u) | ((x0l | x1l) & 0x7FFu);
+      const uint32_t r0 = __funnelshift_r(x0l, x0h, 19) - first5;
+      const uint32_t r1 = __funnelshift_r(x1l, x1h, 19) - first5;
+      count_window<1u << (2 * u)>(win_base + 4u * r0, r0, chk, span5, slow);
+      count_window<2u << (2 * u)>(win_base + 4u * r1, r1, chk, span5, slow);
+    };
+    // The four segments, with (check) or without a test of each segment's
+    // kernel against the window's: most tiles lie inside one run. (The kernel
+    // ids are the same in every warp, so the choice is uniform over the CTA.)
+    auto segments = [&](bool check) {
+      segment(std::integral_constant<int, 0>{}, check);
+      segment(std::integral_constant<int, 1>{}, check);
+      segment(std::integral_constant<int, 2>{}, check);
+      segment(std::integral_constant<int, 3>{}, check);
+    };
+    if (__all_sync(0xffffffffu, lane >= kRunVec || k == (mode_hi >> 16))) segments(false);
+    else segments(true);
     // Each lane walks its own missed samples: a warp takes as many rounds as
     // its busiest lane has misses (scattered misses cost one round).
     while (slow) {
@@ -428,20 +481,6 @@ __global__ void __launch_bounds__(kRunThreads, 1) k_histogram_runs(Prog P, const
         if (i == q) x = (q & 1) ? v[q >> 1].y : v[q >> 1].x;
       count_other(x);
     }
-    // every 32 tiles: flush the hash if half full
-    if ((++t_count & 31) == 0) {
-      if (side_ins) atomicAdd(&ctl[1], (int)side_ins);
-      side_ins = 0;
-      __syncthreads();
-      const bool side_full = ctl[1] > (1 << kSideLog2) / 2;
-      __syncthreads();
-      if (side_full) {
-        table_flush<kSideLog2>(skey, sval, P.cnt);
-        since = 0;
-        __syncthreads();
-        if (threadIdx.x == 0) ctl[1] = 0;
-      }
-    }
   };
 
   // Two register sets in turn: one tile is counted while the next is loaded.
@@ -449,13 +488,15 @@ __global__ void __launch_bounds__(kRunThreads, 1) k_histogram_runs(Prog P, const
   uint32_t ka = 0, kb = 0;
   if (chunk < n_chunks) load_tile(g, va, ka);
   while (chunk < n_chunks) {
-    int64_t nx = next_tile();
+    int nx = next_tile();
     if (nx >= 0) load_tile(nx, vb, kb);
+    prefetch_after();
     process(va, ka);
     advance();
     if (chunk >= n_chunks) break;
     nx = next_tile();
     if (nx >= 0) load_tile(nx, va, ka);
+    prefetch_after();
     process(vb, kb);
     advance();
   }
@@ -484,23 +525,24 @@ static void launch_variant(const Prog& P, const uint64_t* samples, size_t n, cud
 
 }  // namespace
 
-// variant 0 (default): contiguous segments with a per-run window or hash
-// (k_histogram_runs); 1: grid-strided, 8,192-entry hash, 512 threads, 2 CTAs
+// variant 0 (default): tiles claimed in chunks of hist_chunk (0: 24), a
+// per-segment window plus a hash (k_histogram_runs); 1: grid-strided, 8,192-entry hash, 512 threads, 2 CTAs
 // per SM, 4 probes; 2: 16,384 entries, 1,024 threads, 1 CTA per SM, 4 probes;
 // 3: 8,192 entries, 256 threads, 3 CTAs per SM, 8 probes.
 void launch_histogram(const Prog& P, const uint64_t* samples, size_t n, cudaStream_t st, int sms, int64_t* launches,
-                      int variant) {
+                      int variant, int hist_chunk) {
   if (n == 0) return;
   if (variant == 0) {
     const int head = (reinterpret_cast<uintptr_t>(samples) & 15u) ? 1 : 0;
     const int64_t vecs = ((int64_t)n - head) / 2;
-    int64_t grid = (vecs + (int64_t)kRunTile * kRunChunk - 1) / ((int64_t)kRunTile * kRunChunk);
+    const int chunk_tiles = hist_chunk > 0 ? hist_chunk : 24;
+    int64_t grid = (vecs + (int64_t)kRunTile * chunk_tiles - 1) / ((int64_t)kRunTile * chunk_tiles);
     if (grid > sms) grid = sms;
     if (grid < 1) grid = 1;
     cudaMemsetAsync(&P.stats[SS_HIST_HEAD], 0, sizeof(unsigned long long), st);
     const size_t smem = sizeof(uint32_t) * ((size_t)kMainWords + 2 * ((size_t)1 << kSideLog2) + 8);
     allow_max_smem(k_histogram_runs);
-    k_histogram_runs<<<(int)grid, kRunThreads, smem, st>>>(P, samples, (int64_t)n, head);
+    k_histogram_runs<<<(int)grid, kRunThreads, smem, st>>>(P, samples, (int64_t)n, head, chunk_tiles);
     ++*launches;
     return;
   }

@@ -264,7 +264,8 @@ gpa_status gpa_create(const gpa_arch_desc* arch, const gpa_options* opts, gpa_ct
     o = *opts;
     if (o.max_fixpoint_sweeps < 0 || o.max_search_nodes < 0 || o.search_slots < 0 || o.max_sources_per_use < 0 ||
         o.max_sources_per_use > kBigSrc || o.small_search_nodes < 0 || o.mid_search_nodes < 0 ||
-        o.hist_variant < 0 || o.hist_variant > 3 || o.large_search_nodes < 0)
+        o.hist_variant < 0 || o.hist_variant > 3 || o.large_search_nodes < 0 || o.hist_chunk < 0 ||
+        o.hist_chunk > 4096)
       return GPA_ERR_INVALID_ARG;
   }
   auto* c = new (std::nothrow) gpa_ctx();
@@ -603,7 +604,8 @@ gpa_status gpa_ingest_samples(gpa_ctx* ctx, gpa_pid pid, const uint64_t* dev_sam
   if (!R) return GPA_ERR_NO_PROGRAM;
   if (n == 0) return GPA_OK;
   if (!dev_samples || (reinterpret_cast<uintptr_t>(dev_samples) & 7u)) return GPA_ERR_INVALID_ARG;
-  launch_histogram(R->P, dev_samples, n, (cudaStream_t)stream, ctx->sms, &ctx->launches, ctx->opts.hist_variant);
+  launch_histogram(R->P, dev_samples, n, (cudaStream_t)stream, ctx->sms, &ctx->launches, ctx->opts.hist_variant,
+                   ctx->opts.hist_chunk);
   CK(cudaGetLastError());
   return GPA_OK;
 }
@@ -623,7 +625,7 @@ gpa_status gpa_ingest_host_samples(gpa_ctx* ctx, gpa_pid pid, const uint64_t* ho
   if (cudaPointerGetAttributes(&at, host) == cudaSuccess && at.type == cudaMemoryTypeHost && at.devicePointer &&
       cudaGetDevice(&dev) == cudaSuccess && dev == ctx->device) {
     launch_histogram(R->P, static_cast<const uint64_t*>(at.devicePointer), n, st, ctx->sms, &ctx->launches,
-                     ctx->opts.hist_variant);
+                     ctx->opts.hist_variant, ctx->opts.hist_chunk);
     CK(cudaGetLastError());
     return GPA_OK;
   }
@@ -649,7 +651,8 @@ gpa_status gpa_ingest_host_samples(gpa_ctx* ctx, gpa_pid pid, const uint64_t* ho
     CK(cudaMemcpyAsync(ctx->stage[k], host + off, m * sizeof(uint64_t), cudaMemcpyHostToDevice, ctx->copy_stream));
     CK(cudaEventRecord(ctx->ev_copied[k], ctx->copy_stream));
     CK(cudaStreamWaitEvent(st, ctx->ev_copied[k], 0));
-    launch_histogram(R->P, ctx->stage[k], m, st, ctx->sms, &ctx->launches, ctx->opts.hist_variant);
+    launch_histogram(R->P, ctx->stage[k], m, st, ctx->sms, &ctx->launches, ctx->opts.hist_variant,
+                     ctx->opts.hist_chunk);
     CK(cudaEventRecord(ctx->ev_used[k], st));
     off += m;
   }
@@ -775,7 +778,9 @@ gpa_status gpa_step_capture(gpa_ctx* ctx, gpa_pid pid, const uint64_t* dev_sampl
   if (cudaMemsetAsync(R->P.cnt, 0, (size_t)R->P.ni * kCnt * sizeof(unsigned long long), cs) != cudaSuccess ||
       cudaMemsetAsync(R->P.stats, 0, SS_N * sizeof(unsigned long long), cs) != cudaSuccess)
     s = GPA_ERR_CUDA;
-  if (!s && n) launch_histogram(R->P, dev_samples, n, cs, ctx->sms, &ctx->launches, ctx->opts.hist_variant);
+  if (!s && n)
+    launch_histogram(R->P, dev_samples, n, cs, ctx->sms, &ctx->launches, ctx->opts.hist_variant,
+                     ctx->opts.hist_chunk);
   if (!s) s = blame_body(ctx, R, cs, false);
   if (!s) launch_advise(R->P, ctx->arch, cs, ctx->sms, &ctx->launches);
   cudaGraph_t g = nullptr;
