@@ -144,11 +144,14 @@ class Clocks:
 
 
 def make_workload(name: str, seed: int, n_override: int = 0, functions: int = 0):
+    """The workload's program (with a call table: a tenth of the functions are device
+    functions called from other functions, for Function Inlining) and sample count.
+    Returns (generator handle for the samples, program arrays, samples)."""
     ps, ns, kz = synth.workload(name, seed=seed)
     if functions:
         ps = ps[:functions]
     P = synth.make_program(ps, kz, kseed=seed)
-    return P, (n_override or ns)
+    return P, synth.add_calls(P, 0.1, seed=seed), (n_override or ns)
 
 
 def cpu_sample(P, n_total: int, k_funcs: int, seed: int, cap: int):
@@ -188,14 +191,14 @@ def plain_vs_batched(gpa, workload: str, seed: int, dev, stream, reps: int = 3) 
     program per function (the plain form), each fed its own launch runs; same GPU,
     same samples, eager steps (reset, ingest, blame, advise kept on the device)."""
     import torch
-    P, n = make_workload(workload, seed, 0, 0)
+    P, arrays, n = make_workload(workload, seed, 0, 0)
     s = P.samples(n, seed=seed)
     ctx = gpa.Context(synth.default_arch())
     try:
-        progs, inputs = [ctx.load_program(P)], [torch.from_numpy(s.view(np.int64)).to(dev)]
+        progs, inputs = [ctx.load_program(arrays)], [torch.from_numpy(s.view(np.int64)).to(dev)]
         plain, plain_in = [], []
         for f in range(P.n_functions):
-            plain.append(ctx.load_program(synth.subprogram(P.arrays, f, f + 1)))
+            plain.append(ctx.load_program(synth.subprogram(arrays, f, f + 1)))
             plain_in.append(torch.from_numpy(synth.rebase_samples(s, f, f + 1).view(np.int64)).to(dev))
 
         def run(ps, xs):
@@ -313,7 +316,7 @@ def run_oracle_once(P, sub, k_funcs, threads: int = 1):
     import oracle
     from concurrent.futures import ThreadPoolExecutor
     arch = synth.default_arch()
-    Q = synth.subprogram(P.arrays if hasattr(P, "arrays") else P, 0, k_funcs)
+    Q = synth.subprogram(P, 0, k_funcs)
     t0 = time.perf_counter()
     if threads <= 1:
         cnt, _ = oracle.histogram(Q, sub)
@@ -338,13 +341,13 @@ def reference_arm(a):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    P, n = make_workload(a.workload, a.seed, a.samples)
+    P, arrays, n = make_workload(a.workload, a.seed, a.samples)
     threads = host_threads()
     k_funcs = min(P.n_functions, max(1, a.cpu_functions // 4))
     sub, m = cpu_sample(P, n, k_funcs, a.seed, max(1, a.cpu_samples // 4))
     for _ in range(a.warmup):
-        run_oracle_once(P, sub, k_funcs, threads)
-    ts = [run_oracle_once(P, sub, k_funcs, threads) for _ in range(a.steps)]
+        run_oracle_once(arrays, sub, k_funcs, threads)
+    ts = [run_oracle_once(arrays, sub, k_funcs, threads) for _ in range(a.steps)]
     t = statistics.mean(ts)
     v = sub.size / t
     instr = int(P.func_instr_off[k_funcs])
@@ -383,7 +386,7 @@ def main():
             dist.destroy_process_group()
         return
 
-    P, n = make_workload(a.workload, a.seed + rank, a.samples, a.functions)
+    P, arrays, n = make_workload(a.workload, a.seed + rank, a.samples, a.functions)
     host = torch.empty(n, dtype=torch.int64).pin_memory()
     P.samples(n, seed=a.seed + rank, out=host.numpy().view(np.uint64))
     d = host.to(dev, non_blocking=False)
@@ -397,15 +400,15 @@ def main():
         from paper_2009_04061_gb300 import autotune
         stream0 = torch.cuda.current_stream(dev)
         with gpa.Context(synth.default_arch(), opts or None) as c0:
-            fixed_ms = autotune.time_step(c0, P.arrays, d, stream0)
-        best, table = autotune.tune(synth.default_arch(), P.arrays, d, stream0)
+            fixed_ms = autotune.time_step(c0, arrays, d, stream0)
+        best, table = autotune.tune(synth.default_arch(), arrays, d, stream0)
         tuned = {"fixed_ms_per_step": fixed_ms, "tuned_ms_per_step": min(t for _, t in table),
                  "options": best, "candidates_tried": len(table)}
         opts = best
     torch.cuda.synchronize(dev)
     t_load = time.perf_counter()
     ctx = gpa.Context(synth.default_arch(), opts or None)
-    prog = ctx.load_program(P)
+    prog = ctx.load_program(arrays)
     torch.cuda.synchronize(dev)
     load_ms = (time.perf_counter() - t_load) * 1e3
     # Seeded launch statistics of the workload's kernels on this GPU's SM model:
@@ -542,8 +545,8 @@ def main():
         k_funcs = min(P.n_functions, a.cpu_functions)
         sub, m = cpu_sample(P, n, k_funcs, a.seed, a.cpu_samples)
         threads = host_threads()
-        t_all = run_oracle_once(P, sub, k_funcs, threads)
-        t_one = run_oracle_once(P, sub, k_funcs, 1)
+        t_all = run_oracle_once(arrays, sub, k_funcs, threads)
+        t_one = run_oracle_once(arrays, sub, k_funcs, 1)
         sample = (f"functions 0..{k_funcs - 1} ({int(P.func_instr_off[k_funcs])} instructions) with the first "
                   f"{sub.size} samples of their launch runs")
         cpu = {"value": sub.size / t_all, "unit": UNIT, "cores": threads, "kind": "oracle",
@@ -583,6 +586,8 @@ def main():
             "dtype": "int64", "data": "synthetic",
             "config": {"workload": a.workload, "functions": P.n_functions, "instructions": P.n_instr,
                        "blocks": P.n_blocks, "loops": P.n_loops, "samples_per_gpu": n,
+                       "call_sites": int(arrays["call_site"].size),
+                       "device_functions": int(np.unique(arrays["call_callee"]).size),
                        "sample_bytes_per_gpu": 8 * n, "l2": "inputs (samples) larger than L2, no flush",
                        "parallelism": f"replicas x{world}, no collective on the data path"},
             "analysed_instrs_per_s": instr_per_s, "phases_ms": phase, "eager_ms_per_step": eager_ms,

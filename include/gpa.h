@@ -55,7 +55,7 @@ enum {
 
 #define GPA_NUM_RES 268      /* R0..R254 = 0..254, P0..P6 = 255..261, B0..B5 = 262..267 */
 #define GPA_NUM_CLASSES 12   /* stall reasons, see below */
-#define GPA_NUM_OPT 8        /* optimizers, see below */
+#define GPA_NUM_OPT 9        /* optimizers, see below */
 #define GPA_MAX_OPCLASSES 64
 
 /* Stall reasons (class field of a sample). Sec. 4 names memory dependency,
@@ -67,11 +67,13 @@ enum {
   GPA_MEMORY_THROTTLE = 8, GPA_NOT_SELECTED = 9, GPA_OTHER = 10, GPA_SLEEPING = 11
 };
 
-/* Optimizers of Table 2 (code optimizers), in result order. */
+/* Optimizers of Table 2 (code optimizers), in result order. Function Inlining
+ * (a latency-hiding optimizer, Eq. 4) matches the latency stall samples taken
+ * at instructions of device functions and at call sites. */
 enum {
   GPA_OPT_REGISTER_REUSE = 0, GPA_OPT_STRENGTH_REDUCTION = 1, GPA_OPT_FUNCTION_SPLIT = 2,
   GPA_OPT_FAST_MATH = 3, GPA_OPT_WARP_BALANCE = 4, GPA_OPT_MEMORY_TRANSACTION_REDUCTION = 5,
-  GPA_OPT_LOOP_UNROLLING = 6, GPA_OPT_CODE_REORDERING = 7
+  GPA_OPT_LOOP_UNROLLING = 6, GPA_OPT_CODE_REORDERING = 7, GPA_OPT_FUNCTION_INLINING = 8
 };
 
 /* Opcode-class property bits of gpa_arch_desc.flags. */
@@ -144,6 +146,10 @@ typedef struct {
  *                                 predicate, barriers in the wait mask. No duplicates in a list.
  *  block_loop[n_blocks]           innermost loop containing the block, or -1.
  *  loop_parent[n_loops]           enclosing loop or -1; loop_header[n_loops] its header block.
+ *  call_site[n_calls], call_callee[n_calls]  optional call table (n_calls = 0: none): the
+ *                                 global index of a call instruction, strictly ascending, and
+ *                                 the function it calls. A function that some call site calls
+ *                                 is a device function (Table 2, Function Inlining).
  * Limits: n_functions < 65536, instructions per function < 2^24. */
 typedef struct {
   int32_t n_functions, n_instr, n_blocks, n_loops, n_lines;
@@ -165,6 +171,9 @@ typedef struct {
   const int32_t* block_loop;
   const int32_t* loop_parent;
   const int32_t* loop_header;
+  int32_t n_calls;
+  const int32_t* call_site;
+  const int32_t* call_callee;
 } gpa_program_desc;
 
 /* Launch statistics of one function (kernel) as the profiler's kernel
@@ -195,12 +204,12 @@ typedef struct {
 
 /* Advice destination (host memory); any NULL field is skipped.
  *  totals[n_functions*4]           T, A (active), L (latency), issued samples (Sec. 2.1, 5.2).
- *  matched[n_functions*8]          matched samples M (Eq. 2) or M^L (Eq. 4) per optimizer.
- *  speedup[n_functions*8]          Eq. 2 for optimizers 0-5, Eq. 4 for 6-7; T = 0 gives 1.0,
+ *  matched[n_functions*9]          matched samples M (Eq. 2) or M^L (Eq. 4) per optimizer.
+ *  speedup[n_functions*9]          Eq. 2 for optimizers 0-5, Eq. 4 for 6-8; T = 0 gives 1.0,
  *                                  T = M gives +inf.
- *  rank[n_functions*8]             optimizer ids by speedup, descending (ties: lower id).
- *  n_hot[n_functions*8]            hotspots filled (0..5).
- *  hot[n_functions*8*5*6]          per hotspot: def pc, use pc, def line, use line,
+ *  rank[n_functions*9]             optimizer ids by speedup, descending (ties: lower id).
+ *  n_hot[n_functions*9]            hotspots filled (0..5).
+ *  hot[n_functions*9*5*6]          per hotspot: def pc, use pc, def line, use line,
  *                                  distance (shortest path), matched samples; -1 when unused.
  *  loop_active[n_loops], loop_matched[n_loops], loop_speedup[n_loops]  Eq. 5 per loop scope.
  *  line_stall[n_lines], line_latency[n_lines]  blamed stall samples per source line and their
@@ -239,7 +248,7 @@ const char* gpa_status_string(gpa_status s);
 
 /* Fills *arch with the library's default table (host pointers to static
  * storage): opcode classes IADD, IMAD, FFMA, ISETP, MOV, BRA, BAR, MEMBAR, LDG,
- * STG, LDS, STS, LDL, STL, LDC, ATOM, F2F, MUFU, DFMA, EXIT in that order. */
+ * STG, LDS, STS, LDL, STL, LDC, ATOM, F2F, MUFU, DFMA, EXIT, CALL in that order. */
 gpa_status gpa_arch_default(gpa_arch_desc* arch);
 
 /* Creates a context on the current CUDA device. arch and opts are copied;

@@ -18,9 +18,9 @@ from .parallel import parallel  # noqa: E402,F401  (Table 2 parallel optimizers,
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB = os.path.join(_HERE, "libgpa_oracle.so")
-N_OPT = 8
+N_OPT = 9
 OPT_NAMES = ["REG_REUSE", "STRENGTH_RED", "FUNC_SPLIT", "FAST_MATH", "WARP_BALANCE", "MEM_TXN_RED",
-             "LOOP_UNROLL", "CODE_REORDER"]
+             "LOOP_UNROLL", "CODE_REORDER", "FUNC_INLINE"]
 
 
 def build(force: bool = False) -> str:
@@ -35,7 +35,8 @@ class _OProg(ctypes.Structure):
                 ("n_lines", ctypes.c_int32)] + [(k, ctypes.c_void_p) for k in (
                     "func_instr_off", "func_block_off", "func_loop_off", "block_instr_off", "succ_off", "succ",
                     "opclass", "guard", "iflags", "line", "def_off", "def_res", "use_off", "use_res",
-                    "block_loop", "loop_parent", "loop_header")]
+                    "block_loop", "loop_parent", "loop_header")] + [
+                    ("n_calls", ctypes.c_int32), ("call_site", ctypes.c_void_p), ("call_callee", ctypes.c_void_p)]
 
 
 class _OArch(ctypes.Structure):
@@ -81,7 +82,7 @@ class _Bound:
         keep = {}
 
         def arr(k, dt):
-            a = np.ascontiguousarray(prog[k], dtype=dt)
+            a = np.ascontiguousarray(prog.get(k, np.zeros(0, dt)), dtype=dt)
             if a.size == 0:
                 a = np.zeros(1, dtype=dt)
             keep[k] = a
@@ -95,7 +96,8 @@ class _Bound:
                         arr("guard", np.uint8), arr("iflags", np.uint8), arr("line", np.int32),
                         arr("def_off", np.int32), arr("def_res", np.uint16), arr("use_off", np.int32),
                         arr("use_res", np.uint16), arr("block_loop", np.int32), arr("loop_parent", np.int32),
-                        arr("loop_header", np.int32))
+                        arr("loop_header", np.int32), int(np.asarray(prog.get("call_site", [])).size),
+                        arr("call_site", np.int32), arr("call_callee", np.int32))
         if arch is not None:
             lat = np.ascontiguousarray(arch[0], dtype=np.int32)
             fl = np.ascontiguousarray(arch[1], dtype=np.uint32)

@@ -40,7 +40,7 @@ enum { C_SELECTED = 0, C_INST_FETCH = 1, C_EXEC = 2, C_MEM = 3, C_SYNC = 5, C_CO
        C_MEM_THROTTLE = 8 };
 // Optimizers of Table 2 built here, in this fixed enumeration order.
 enum { O_REG_REUSE, O_STRENGTH_RED, O_FUNC_SPLIT, O_FAST_MATH, O_WARP_BALANCE, O_MEM_TXN_RED,
-       O_LOOP_UNROLL, O_CODE_REORDER, N_OPT };
+       O_LOOP_UNROLL, O_CODE_REORDER, O_FUNC_INLINE, N_OPT };
 constexpr int kDepClass[4] = {C_EXEC, C_MEM, C_SYNC, C_CONST_MEM};
 
 }  // namespace
@@ -58,6 +58,8 @@ struct OProg {
   const int32_t* use_off;
   const uint16_t* use_res;
   const int32_t *block_loop, *loop_parent, *loop_header;
+  int32_t n_calls;                          // call table: call instruction -> called function
+  const int32_t *call_site, *call_callee;
 };
 
 struct OArch {
@@ -569,6 +571,14 @@ void analyze_function(const OProg& P, const OArch& arch, const uint64_t* cnt, in
     }
     return 0;
   };
+  // Function Inlining (Table 2): is f a device function, is local x a call site.
+  bool device_fn = false;
+  for (int c = 0; c < P.n_calls; ++c) device_fn = device_fn || P.call_callee[c] == f;
+  auto is_call_site = [&](int x) {
+    for (int c = 0; c < P.n_calls; ++c)
+      if (P.call_site[c] == i0 + x) return true;
+    return false;
+  };
   auto instr_match = [&](int x, int o) -> uint64_t {
     uint64_t v = 0;
     switch (o) {
@@ -581,10 +591,16 @@ void analyze_function(const OProg& P, const OArch& arch, const uint64_t* cnt, in
       case O_MEM_TXN_RED:
         if (arch.flags[P.opclass[i0 + x]] & F_GLOBAL) v = C(x, C_MEM_THROTTLE, 0) + C(x, C_MEM_THROTTLE, 1);
         return v;
+      case O_FUNC_INLINE:
+        // Latency stall samples sampled in a device function (one that some
+        // call site calls) or at a call instruction.
+        if (device_fn || is_call_site(x))
+          for (int c = 1; c < kNumClass; ++c) v += C(x, c, 1);
+        return v;
     }
     return 0;
   };
-  const bool edge_based[N_OPT] = {true, true, false, false, false, false, true, true};
+  const bool edge_based[N_OPT] = {true, true, false, false, false, false, true, true, false};
   for (int o = 0; o < N_OPT; ++o) {
     std::vector<std::array<int64_t, 6>> cand;
     if (edge_based[o]) {
@@ -610,7 +626,8 @@ void analyze_function(const OProg& P, const OArch& arch, const uint64_t* cnt, in
     for (int h = 0; h < 5; ++h)
       for (int q = 0; q < 6; ++q) A.hot[o][h][q] = h < A.n_hot[o] ? cand[h][q] : -1;
     // Eq. 2 for stall elimination; Eq. 4 for latency hiding.
-    if (o == O_LOOP_UNROLL || o == O_CODE_REORDER) A.speedup[o] = est(A.T, std::min(A.A, A.M[o]));
+    const bool hiding = o == O_LOOP_UNROLL || o == O_CODE_REORDER || o == O_FUNC_INLINE;
+    if (hiding) A.speedup[o] = est(A.T, std::min(A.A, A.M[o]));
     else A.speedup[o] = est(A.T, A.M[o]);
   }
   std::vector<int> ord(N_OPT);

@@ -97,7 +97,7 @@ struct Prog {
   const int32_t* pred;
   const uint8_t* opclass;
   const uint8_t* guard;
-  const uint8_t* iflags;
+  const uint8_t* iflags;          // bit 0 math-library code, 1 call site, 2 in a device function
   const int32_t* line;
   const int32_t* def_off;
   const uint16_t* def_res;

@@ -1,6 +1,7 @@
 // Step (d), Sec. 5: roll blame up to lines, loops and functions, match the
-// code optimizers of Table 2, estimate their speedups (Eq. 2 for stall
-// elimination, Eq. 4 for latency hiding, Eq. 5 per loop scope), rank them and
+// code optimizers of Table 2 (Function Inlining from the program's call
+// table), estimate their speedups (Eq. 2 for stall elimination, Eq. 4 for
+// latency hiding, Eq. 5 per loop scope), rank them and
 // pick each optimizer's top five hotspots (def, use, distance); with launch
 // statistics, the parallel optimizers (Eqs. 6-10).
 //
@@ -15,7 +16,8 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kHot = 5;
-enum { O_RR = 0, O_SR, O_FS, O_FM, O_WB, O_MT, O_LU, O_CR, N_O = 8 };
+enum { O_RR = 0, O_SR, O_FS, O_FM, O_WB, O_MT, O_LU, O_CR, O_FI, N_O = 9 };
+constexpr int kAcc = 13;  // per-function sums, see k_advise
 
 struct Cand { unsigned long long v; int def, use, dist; };
 
@@ -145,8 +147,8 @@ __device__ void parallel_advice(const Prog& P, int f, unsigned long long T, unsi
 }
 
 __global__ void __launch_bounds__(kThreads) k_advise(Prog P, Arch A) {
-  __shared__ unsigned long long red[12][kThreads / 32];
-  __shared__ unsigned long long tot[12];
+  __shared__ unsigned long long red[kAcc][kThreads / 32];
+  __shared__ unsigned long long tot[kAcc];
   __shared__ Cand wtop[kThreads / 32][kHot];  // each warp's top five (v == 0: none)
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
@@ -154,10 +156,10 @@ __global__ void __launch_bounds__(kThreads) k_advise(Prog P, Arch A) {
     const int i0 = P.func_instr_off[f], i1 = P.func_instr_off[f + 1];
     // Edge ranges are clamped to the edge capacity (overflow is reported in the status word).
     const int64_t e0 = min((int64_t)P.edge_off[i0], P.edge_cap), e1 = min((int64_t)P.edge_off[i1], P.edge_cap);
-    unsigned long long acc[12];
+    unsigned long long acc[kAcc];
 #pragma unroll
-    for (int q = 0; q < 12; ++q) acc[q] = 0ull;
-    // acc: 0 T, 1 A, 2 L, 3 issued, 4 FS, 5 FM, 6 WB, 7 MT, 8 RR, 9 SR, 10 LU, 11 CR
+    for (int q = 0; q < kAcc; ++q) acc[q] = 0ull;
+    // acc: 0 T, 1 A, 2 L, 3 issued, 4 FS, 5 FM, 6 WB, 7 MT, 8 RR, 9 SR, 10 LU, 11 CR, 12 FI
     for (int x = i0 + tid; x < i1; x += kThreads) {
       const unsigned long long* c = P.cnt + (size_t)x * kCnt;
       unsigned long long a = 0, l = 0, stall = 0;
@@ -171,6 +173,7 @@ __global__ void __launch_bounds__(kThreads) k_advise(Prog P, Arch A) {
       if (P.iflags[x] & 1) acc[5] += stall;
       acc[6] += c[10] + c[11];
       if (A.flags[P.opclass[x]] & GPA_F_GLOBAL) acc[7] += c[16] + c[17];
+      if (P.iflags[x] & 6) acc[12] += l;  // latency stalls in a device function or at a call site
       for (int lp = innermost_loop(P, x); lp >= 0; lp = P.loop_parent[lp])
         if (a) atomicAdd(&P.a_loop_active[lp], a);
       const unsigned long long* b = P.blame + (size_t)x * kCnt;
@@ -189,13 +192,13 @@ __global__ void __launch_bounds__(kThreads) k_advise(Prog P, Arch A) {
       }
     }
 #pragma unroll
-    for (int q = 0; q < 12; ++q) {
+    for (int q = 0; q < kAcc; ++q) {
       unsigned long long v = acc[q];
       for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
       if (lane == 0) red[q][warp] = v;
     }
     __syncthreads();
-    if (tid < 12) {
+    if (tid < kAcc) {
       unsigned long long v = 0;
       for (int w = 0; w < kThreads / 32; ++w) v += red[tid][w];
       tot[tid] = v;
@@ -205,10 +208,10 @@ __global__ void __launch_bounds__(kThreads) k_advise(Prog P, Arch A) {
     if (tid == 0) {
       unsigned long long M[N_O];
       M[O_RR] = tot[8]; M[O_SR] = tot[9]; M[O_FS] = tot[4]; M[O_FM] = tot[5];
-      M[O_WB] = tot[6]; M[O_MT] = tot[7]; M[O_LU] = tot[10]; M[O_CR] = tot[11];
+      M[O_WB] = tot[6]; M[O_MT] = tot[7]; M[O_LU] = tot[10]; M[O_CR] = tot[11]; M[O_FI] = tot[12];
       double sp[N_O];
       for (int o = 0; o < N_O; ++o) {
-        const bool hide = (o == O_LU || o == O_CR);
+        const bool hide = (o == O_LU || o == O_CR || o == O_FI);
         sp[o] = est(T, hide ? min(Aact, M[o]) : M[o]);
         P.a_matched[(size_t)f * N_O + o] = M[o];
         P.a_speedup[(size_t)f * N_O + o] = sp[o];
@@ -243,6 +246,7 @@ __global__ void __launch_bounds__(kThreads) k_advise(Prog P, Arch A) {
           if (o == O_FS) v = c[2] + c[3];
           else if (o == O_FM) { if (P.iflags[x] & 1) for (int e = 2; e < kCnt; ++e) v += c[e]; }
           else if (o == O_WB) v = c[10] + c[11];
+          else if (o == O_FI) { if (P.iflags[x] & 6) for (int e = 3; e < kCnt; e += 2) v += c[e]; }
           else if (A.flags[P.opclass[x]] & GPA_F_GLOBAL) v = c[16] + c[17];
           top_insert(top, nt, Cand{v, x - i0, x - i0, 0});
         }

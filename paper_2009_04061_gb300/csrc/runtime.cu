@@ -118,8 +118,13 @@ gpa_status validate(const gpa_program_desc* d, const Arch& A) {
       !d->opclass || !d->guard || !d->iflags || !d->line || !d->def_off || !d->use_off || !d->block_loop)
     return GPA_ERR_INVALID_ARG;
   if ((d->n_succ && !d->succ) || (d->n_def && !d->def_res) || (d->n_use && !d->use_res) ||
-      (nl && (!d->loop_parent || !d->loop_header)))
+      (nl && (!d->loop_parent || !d->loop_header)) || d->n_calls < 0 ||
+      (d->n_calls && (!d->call_site || !d->call_callee)))
     return GPA_ERR_INVALID_ARG;
+  for (int c = 0; c < d->n_calls; ++c)
+    if (d->call_site[c] < 0 || d->call_site[c] >= ni || (c && d->call_site[c] <= d->call_site[c - 1]) ||
+        d->call_callee[c] < 0 || d->call_callee[c] >= nf)
+      return GPA_ERR_INVALID_PROGRAM;
   auto mono = [](const int32_t* a, int n, int last, bool strict) {
     if (a[0] != 0 || a[n] != last) return false;
     for (int i = 0; i < n; ++i)
@@ -217,14 +222,14 @@ gpa_status status_from(unsigned long long st) {
 }
 
 // Default opcode classes (order documented in gpa.h).
-const int32_t kDefLat[20] = {4, 5, 4, 4, 2, 0, 32, 32, 1024, 1024, 32, 32, 1024, 1024, 64, 1024, 16, 16, 8, 0};
-const uint32_t kDefFlags[20] = {
+const int32_t kDefLat[21] = {4, 5, 4, 4, 2, 0, 32, 32, 1024, 1024, 32, 32, 1024, 1024, 64, 1024, 16, 16, 8, 0, 1024};
+const uint32_t kDefFlags[21] = {
     0, 0, 0, 0, 0, 0, GPA_F_SYNC, GPA_F_SYNC,
     GPA_F_MEM | GPA_F_GLOBAL | GPA_F_VARLAT, GPA_F_MEM | GPA_F_GLOBAL | GPA_F_VARLAT,
     GPA_F_SHARED | GPA_F_VARLAT, GPA_F_SHARED | GPA_F_VARLAT,
     GPA_F_MEM | GPA_F_LOCAL | GPA_F_VARLAT, GPA_F_MEM | GPA_F_LOCAL | GPA_F_VARLAT,
     GPA_F_MEM | GPA_F_CONST | GPA_F_VARLAT, GPA_F_MEM | GPA_F_GLOBAL | GPA_F_VARLAT,
-    GPA_F_LONG_ARITH | GPA_F_VARLAT, GPA_F_LONG_ARITH | GPA_F_VARLAT, 0, 0};
+    GPA_F_LONG_ARITH | GPA_F_VARLAT, GPA_F_LONG_ARITH | GPA_F_VARLAT, 0, 0, 0};
 
 }  // namespace
 
@@ -247,7 +252,7 @@ const char* gpa_status_string(gpa_status s) {
 
 gpa_status gpa_arch_default(gpa_arch_desc* arch) {
   if (!arch) return GPA_ERR_INVALID_ARG;
-  arch->n_opclasses = 20;
+  arch->n_opclasses = 21;
   arch->latency = kDefLat;
   arch->flags = kDefFlags;
   return GPA_OK;
@@ -403,7 +408,19 @@ static gpa_status alloc_program(const gpa_program_desc* d, ProgramRec* R, int ti
   TRY(dev_copy(R, &P.succ, d->succ, (size_t)d->n_succ));
   TRY(dev_copy(R, &P.opclass, d->opclass, ni));
   TRY(dev_copy(R, &P.guard, d->guard, ni));
-  TRY(dev_copy(R, &P.iflags, d->iflags, ni));
+  {
+    // Instruction flags on the device: bit 0 math-library code (the caller's
+    // bit 0), bit 1 call site, bit 2 in a device function (a function some call
+    // site calls): Function Inlining matches bits 1-2.
+    std::vector<uint8_t> fl(ni);
+    std::vector<char> dev(nf, 0);
+    for (int c = 0; c < d->n_calls; ++c) dev[d->call_callee[c]] = 1;
+    for (size_t f = 0; f < nf; ++f)
+      for (int x = d->func_instr_off[f]; x < d->func_instr_off[f + 1]; ++x)
+        fl[x] = (uint8_t)((d->iflags[x] & 1) | (dev[f] ? 4 : 0));
+    for (int c = 0; c < d->n_calls; ++c) fl[d->call_site[c]] |= 2;
+    TRY(dev_copy(R, &P.iflags, fl.data(), ni));
+  }
   TRY(dev_copy(R, &P.line, d->line, ni));
   TRY(dev_copy(R, &P.def_off, d->def_off, ni + 1));
   TRY(dev_copy(R, &P.def_res, d->def_res, (size_t)d->n_def));

@@ -22,9 +22,9 @@ GPA_OK = 0
 STATUS = {0: "GPA_OK", -1: "GPA_ERR_INVALID_ARG", -2: "GPA_ERR_INVALID_PROGRAM", -3: "GPA_ERR_CUDA",
           -4: "GPA_ERR_NOT_CONVERGED", -5: "GPA_ERR_CAPACITY", -6: "GPA_ERR_TIMEOUT", -7: "GPA_ERR_NO_PROGRAM",
           -8: "GPA_ERR_OOM"}
-NUM_OPT = 8
+NUM_OPT = 9
 OPT_NAMES = ["REGISTER_REUSE", "STRENGTH_REDUCTION", "FUNCTION_SPLIT", "FAST_MATH", "WARP_BALANCE",
-             "MEMORY_TRANSACTION_REDUCTION", "LOOP_UNROLLING", "CODE_REORDERING"]
+             "MEMORY_TRANSACTION_REDUCTION", "LOOP_UNROLLING", "CODE_REORDERING", "FUNCTION_INLINING"]
 
 
 class GpaError(RuntimeError):
@@ -53,7 +53,8 @@ _PROG_DTYPES = dict(opclass=np.uint8, guard=np.uint8, iflags=np.uint8, def_res=n
 
 class gpa_program_desc(ctypes.Structure):
     _fields_ = [(k, ctypes.c_int32) for k in ("n_functions", "n_instr", "n_blocks", "n_loops", "n_lines", "n_succ",
-                                             "n_def", "n_use")] + [(k, ctypes.c_void_p) for k in _PROG_ARRAYS]
+                                             "n_def", "n_use")] + [(k, ctypes.c_void_p) for k in _PROG_ARRAYS] + [
+                   ("n_calls", ctypes.c_int32), ("call_site", ctypes.c_void_p), ("call_callee", ctypes.c_void_p)]
 
 
 _ADV = ["totals", "matched", "speedup", "rank", "n_hot", "hot", "loop_active", "loop_matched", "loop_speedup",
@@ -185,15 +186,18 @@ def gpa_destroy(ctx):
 
 
 def program_desc(arrays: dict):
-    """gpa_program_desc over host arrays (kept alive in the returned tuple)."""
+    """gpa_program_desc over host arrays (kept alive in the returned tuple). The call
+    table (call_site, call_callee) is optional."""
     keep = {}
-    for k in _PROG_ARRAYS:
-        a = np.ascontiguousarray(arrays[k], dtype=_PROG_DTYPES.get(k, np.int32))
+    for k in _PROG_ARRAYS + ["call_site", "call_callee"]:
+        a = np.ascontiguousarray(arrays.get(k, np.zeros(0, np.int32)), dtype=_PROG_DTYPES.get(k, np.int32))
         keep[k] = a if a.size else np.zeros(1, dtype=a.dtype)
+    n_calls = int(np.asarray(arrays.get("call_site", np.zeros(0))).size)
     d = gpa_program_desc(int(arrays["n_functions"]), int(arrays["n_instr"]), int(arrays["n_blocks"]),
                          int(arrays["n_loops"]), int(arrays["n_lines"]), int(np.asarray(arrays["succ"]).size),
                          int(np.asarray(arrays["def_res"]).size), int(np.asarray(arrays["use_res"]).size),
-                         *[_p(keep[k]) for k in _PROG_ARRAYS])
+                         *[_p(keep[k]) for k in _PROG_ARRAYS], n_calls, _p(keep["call_site"]),
+                         _p(keep["call_callee"]))
     return d, keep
 
 

@@ -39,7 +39,7 @@ R_BASE, P_BASE, B_BASE = 0, 255, 262
 KIND_WRITE, KIND_READ = 1, 2
 
 OPS = ["IADD", "IMAD", "FFMA", "ISETP", "MOV", "BRA", "BAR", "MEMBAR", "LDG", "STG",
-       "LDS", "STS", "LDL", "STL", "LDC", "ATOM", "F2F", "MUFU", "DFMA", "EXIT"]
+       "LDS", "STS", "LDL", "STL", "LDC", "ATOM", "F2F", "MUFU", "DFMA", "EXIT", "CALL"]
 OP = {n: i for i, n in enumerate(OPS)}
 
 # Stall reasons (modelled on the public CUPTI PC-sampling reason list, Sec. 4).
@@ -58,11 +58,14 @@ def default_arch():
 
     The paper prints no latency values (Sec. 4, "Instruction latency based
     pruning" takes microbenchmarked fixed latencies and upper bounds for
-    variable-latency memory operations); these are stand-ins of that shape.
+    variable-latency memory operations); these are stand-ins of that shape. A
+    call's results are ready when the callee returns: the same upper bound as
+    a global load.
     """
     lat = {"IADD": 4, "IMAD": 5, "FFMA": 4, "ISETP": 4, "MOV": 2, "BRA": 0, "BAR": 32,
            "MEMBAR": 32, "LDG": 1024, "STG": 1024, "LDS": 32, "STS": 32, "LDL": 1024,
-           "STL": 1024, "LDC": 64, "ATOM": 1024, "F2F": 16, "MUFU": 16, "DFMA": 8, "EXIT": 0}
+           "STL": 1024, "LDC": 64, "ATOM": 1024, "F2F": 16, "MUFU": 16, "DFMA": 8, "EXIT": 0,
+           "CALL": 1024}
     flags = {"BAR": F_SYNC, "MEMBAR": F_SYNC,
              "LDG": F_MEM | F_GLOBAL | F_VARLAT, "STG": F_MEM | F_GLOBAL | F_VARLAT,
              "ATOM": F_MEM | F_GLOBAL | F_VARLAT,
@@ -339,6 +342,12 @@ def subprogram(arrays: dict, f_lo: int, f_hi: int) -> dict:
     )
     for k in ("opclass", "guard", "iflags", "prof"):
         out[k] = np.asarray(a[k])[i0:i1].copy()
+    # calls whose site and callee both lie in the range (a function whose callers
+    # are all outside it is no longer a device function of the slice)
+    cs, cc = np.asarray(a.get("call_site", [])), np.asarray(a.get("call_callee", []))
+    keep = (cs >= i0) & (cs < i1) & (cc >= f_lo) & (cc < f_hi)
+    out["call_site"] = (cs[keep] - i0).astype(np.int32)
+    out["call_callee"] = (cc[keep] - f_lo).astype(np.int32)
     return out
 
 
@@ -348,3 +357,40 @@ def rebase_samples(samples: np.ndarray, f_lo: int, f_hi: int) -> np.ndarray:
     k = s >> np.uint64(48)
     keep = (k >= np.uint64(f_lo)) & (k < np.uint64(f_hi))
     return (s[keep] - (np.uint64(f_lo) << np.uint64(48))).astype(np.uint64)
+
+
+# ---------------------------------------------------------------- calls (Function Inlining)
+def add_calls(arrays, device_frac: float = 0.1, seed: int = 0, max_sites: int = 3) -> dict:
+    """A copy of the program's arrays with a call table: a seeded `device_frac` of
+    the functions become device functions, each called from 1..max_sites call
+    sites in other functions. A call site is a MOV (one register in, one out)
+    turned into a CALL: argument and result pass through those registers, so the
+    dataflow is unchanged and only the opcode class (its latency) differs.
+    Returns the arrays with call_site (ascending) and call_callee added."""
+    a = dict(arrays.arrays if hasattr(arrays, "arrays") else arrays)
+    nf = int(a["n_functions"])
+    fio = np.asarray(a["func_instr_off"], dtype=np.int64)
+    op = np.asarray(a["opclass"]).copy()
+    rng = np.random.default_rng(seed + 2654435761)
+    sites, callees = [], []
+    if nf >= 2:
+        n_dev = max(1, int(round(device_frac * nf)))
+        devs = rng.choice(nf, size=min(n_dev, nf - 1), replace=False)
+        movs = np.flatnonzero(op == OP["MOV"])
+        taken = set()
+        for d in devs:
+            cands = movs[(movs < fio[d]) | (movs >= fio[d + 1])]
+            cands = np.array([x for x in cands if int(x) not in taken], dtype=np.int64)
+            if cands.size == 0:
+                continue
+            k = int(rng.integers(1, max_sites + 1))
+            for x in rng.choice(cands, size=min(k, cands.size), replace=False):
+                taken.add(int(x))
+                sites.append(int(x))
+                callees.append(int(d))
+    order = np.argsort(np.asarray(sites, dtype=np.int64), kind="stable")
+    cs = np.asarray(sites, dtype=np.int32)[order]
+    cc = np.asarray(callees, dtype=np.int32)[order]
+    op[cs] = OP["CALL"]
+    a.update(opclass=op, call_site=cs, call_callee=cc)
+    return a

@@ -34,10 +34,11 @@ def I(op, defs=(), uses=(), guard=None, wb=None, rb=None, wait=(), line=0, flags
     return dict(op=synth.OP[op], guard=guard_lit(guard), defs=d, uses=u, line=line, flags=flags)
 
 
-def program(functions):
+def program(functions, calls=()):
     """functions: list of (blocks, succ, loops); blocks = list of instruction
     lists, succ = list of successor lists (local block ids), loops = list of
-    (header, body_blocks, parent_loop_local_or_-1)."""
+    (header, body_blocks, parent_loop_local_or_-1). calls: (global instruction
+    index of a call site, called function) pairs."""
     a = {k: [] for k in ("block_instr_off", "succ_off", "succ", "opclass", "guard", "iflags", "line",
                          "def_off", "def_res", "use_off", "use_res", "block_loop", "loop_parent",
                          "loop_header", "func_instr_off", "func_block_off", "func_loop_off", "func_line_off")}
@@ -73,6 +74,9 @@ def program(functions):
     dt = dict(opclass=np.uint8, guard=np.uint8, iflags=np.uint8, def_res=np.uint16, use_res=np.uint16)
     out = {k: np.array(v, dtype=dt.get(k, np.int32)) for k, v in a.items()}
     out.update(n_functions=len(functions), n_instr=ni, n_blocks=nb, n_loops=nl, n_lines=max_line + 1)
+    calls = sorted(calls)
+    out.update(call_site=np.array([c[0] for c in calls], dtype=np.int32),
+               call_callee=np.array([c[1] for c in calls], dtype=np.int32))
     return out
 
 

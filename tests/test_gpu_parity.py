@@ -71,6 +71,39 @@ def test_hand_worked_pins(ctx):
     assert got[8]["advice"]["line_stall"].tolist() == [0, 0, 0, 0, 0, 60, 0, 5]
 
 
+def test_function_inlining(ctx):
+    """Function Inlining from the call table (Table 2): the hand-worked three-function
+    case and a generated program whose MOVs partly became calls; everything equals the
+    oracle, and call tables that break the format are refused."""
+    import test_oracle as T
+    import paper_2009_04061_gb300 as g
+    prog, ent = T.inlining_case()
+    fio, ss = prog["func_instr_off"], []
+    for (x, c, l), v in ent.items():       # global instruction index -> (kernel, pc)
+        k = int(np.searchsorted(fio, x, side="right")) - 1
+        ss += [(k << 48) | ((x - int(fio[k])) << 24) | (c << 20) | (l << 19)] * v
+    s = np.array(ss, dtype=np.uint64)
+    gr = gpu_run(ctx, prog, dev(s))
+    R = oracle_run(prog, s)
+    assert_full_parity(gr, R)
+    assert gr["advice"]["matched"][:, 8].tolist() == [25, 14, 0]
+    ps, _, kz = synth.workload("rodinia")
+    P = synth.make_program(ps, kz)
+    a = synth.add_calls(P, 0.2, seed=3)
+    s = P.samples(2_000_000, seed=3)
+    gr = gpu_run(ctx, a, dev(s))
+    R = oracle_run(a, s)
+    assert_full_parity(gr, R)
+    assert (gr["advice"]["matched"][:, 8] > 0).sum() >= 4
+    bad = [dict(a, call_site=a["call_site"][::-1].copy(), call_callee=a["call_callee"][::-1].copy()),
+           dict(a, call_site=np.array([a["n_instr"]], np.int32), call_callee=np.array([0], np.int32)),
+           dict(a, call_site=np.array([0], np.int32), call_callee=np.array([a["n_functions"]], np.int32))]
+    for b in bad:
+        with pytest.raises(g.GpaError) as e:
+            ctx.load_program(b)
+        assert e.value.status == -2
+
+
 @pytest.mark.parametrize("seed", range(16))
 def test_tiny_guarded_programs(ctx, seed):
     P = tiny_program(seed, n_instr=25 + seed, n_loops=seed % 3, guard_pct=20 + 3 * seed)

@@ -704,3 +704,60 @@ def test_edges_of_selected_uses_equal_full_analysis():
     for k in ("j", "i", "dmin", "dlong", "flags", "share"):
         assert np.array_equal(got[k], R[k][keep]), k
     assert len(got["j"]) > 0
+
+
+def inlining_case(with_calls=True):
+    """f0 calls device function f1 at instruction 2; f2 is unrelated."""
+    f0 = [I("LDG", ["R0"], ["R2", "R3"]), I("MOV", ["R1"], ["R4"]), I("CALL", ["R5"], ["R0"]),
+          I("FFMA", ["R6"], ["R5", "R7", "R8"]), I("EXIT")]
+    f1 = [I("IADD", ["R1"], ["R2", "R3"]), I("FFMA", ["R4"], ["R1", "R5", "R6"]), I("EXIT")]
+    f2 = [I("LDG", ["R0"], ["R2", "R3"]), I("FFMA", ["R1"], ["R0", "R4", "R5"]), I("EXIT")]
+    prog = program([([f0], [[]], []), ([f1], [[]], []), ([f2], [[]], [])], calls=[(2, 1)] if with_calls else [])
+    ent = {(0, 0, 0): 10, (1, 0, 0): 5, (2, C_MEM, 1): 20, (2, 9, 1): 5, (2, 9, 0): 3, (3, C_EXEC, 1): 7,
+           (5, 0, 0): 4, (6, C_EXEC, 1): 12, (6, C_EXEC, 0): 6, (7, 1, 1): 2,
+           (8, 0, 0): 3, (9, C_MEM, 1): 9}
+    return prog, ent
+
+
+def test_function_inlining_device_functions_and_call_sites():
+    """Table 2 Function Inlining, a latency-hiding optimizer (Eq. 4): the latency
+    stall samples sampled in device functions and at their call sites. f0 (T = 50,
+    A = 18) has 20 memory + 5 not-selected latency samples at its call instruction
+    (the 3 active ones and the FFMA's 7 after the call do not count): M^L = 25,
+    S = 50 / (50 - min(18, 25)) = 50 / 32. f1 is the device function (T = 24, A =
+    10): its latency stalls 12 + 2, S = 24 / (24 - 10). f2 takes no part: M = 0,
+    S = 1. The call-site stalls count where they were sampled (blame moves the
+    memory stall to the load). Without the call table nothing matches."""
+    prog, ent = inlining_case()
+    R = oracle.analyze(prog, ARCH, counts(11, ent))
+    assert R["blame"][0, C_MEM, 1] == 20                          # the call's memory stall goes to the load
+    assert [list(map(int, t[:2])) for t in R["totals"]] == [[50, 18], [24, 10], [12, 3]]
+    assert R["M"][:, 8].tolist() == [25, 14, 0]
+    assert R["speedup"][:, 8].tolist() == [50 / 32, 24 / 14, 1.0]
+    assert R["hot"][0][8][0].tolist() == [2, 2, 0, 0, 0, 25]
+    assert R["hot"][1][8][:2].tolist() == [[1, 1, 0, 0, 0, 12], [2, 2, 0, 0, 0, 2]]
+    assert R["n_hot"][:, 8].tolist() == [1, 2, 0]
+    # in f1 the FFMA's execution latency stalls are blamed on the IADD one up, so Code
+    # Reordering also has M^L = 12 and the same 24 / 14: equal speedups rank the lower id first
+    assert R["speedup"][1][7] == 24 / 14 and R["rank"][1][:2].tolist() == [7, 8]
+    prog, ent = inlining_case(with_calls=False)
+    R = oracle.analyze(prog, ARCH, counts(11, ent))
+    assert R["M"][:, 8].tolist() == [0, 0, 0] and R["speedup"][:, 8].tolist() == [1.0, 1.0, 1.0]
+
+
+def test_add_calls_keeps_dataflow():
+    """The generator's call tables turn MOVs into CALLs: ascending distinct sites in
+    functions other than their callee, the same defs and uses, and the oracle's
+    edges change only through the call's latency."""
+    ps, _, kz = synth.workload("rodinia")
+    P = synth.make_program(ps[:8], kz)
+    a = synth.add_calls(P, 0.25, seed=1)
+    cs, cc = a["call_site"], a["call_callee"]
+    assert cs.size > 0 and np.all(np.diff(cs) > 0)
+    fio = P.func_instr_off
+    for x, d in zip(cs, cc):
+        assert not (fio[d] <= x < fio[d + 1])
+        assert a["opclass"][x] == synth.OP["CALL"] and P.opclass[x] == synth.OP["MOV"]
+    assert np.array_equal(np.delete(a["opclass"], cs), np.delete(P.opclass, cs))
+    sub = synth.subprogram(a, 0, 8)
+    assert np.array_equal(sub["call_site"], cs) and np.array_equal(sub["call_callee"], cc)
