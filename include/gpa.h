@@ -147,9 +147,12 @@ typedef struct {
  *  block_loop[n_blocks]           innermost loop containing the block, or -1.
  *  loop_parent[n_loops]           enclosing loop or -1; loop_header[n_loops] its header block.
  *  call_site[n_calls], call_callee[n_calls]  optional call table (n_calls = 0: none): the
- *                                 global index of a call instruction, strictly ascending, and
- *                                 the function it calls. A function that some call site calls
- *                                 is a device function (Table 2, Function Inlining).
+ *                                 global index of a call instruction and the function it
+ *                                 calls. A function that some call site calls is a device
+ *                                 function (Table 2, Function Inlining). A call into or out of
+ *                                 the program (as in one shard of a larger one) has site -1
+ *                                 (called from elsewhere) or callee -1 (calls elsewhere), not
+ *                                 both. Sites ascend: -1 entries first, the others distinct.
  * Limits: n_functions < 65536, instructions per function < 2^24. */
 typedef struct {
   int32_t n_functions, n_instr, n_blocks, n_loops, n_lines;
@@ -301,6 +304,21 @@ gpa_status gpa_ingest_samples(gpa_ctx* ctx, gpa_pid pid, const uint64_t* dev_sam
  * unchanged until stream completes this call. */
 gpa_status gpa_ingest_host_samples(gpa_ctx* ctx, gpa_pid pid, const uint64_t* host_samples, size_t n,
                                    gpa_stream stream);
+
+/* The program's counters (n_instr*24 uint64, the layout of gpa_get_counts) as
+ * device data, for a batch sharded over several GPUs (Sec. 2.1 aggregation is a
+ * sum over samples, so counts of disjoint sample chunks add up): every rank
+ * aggregates its chunk of the samples over the whole program and copies the
+ * counters out with gpa_copy_counts (dev_dst: device memory of the current
+ * device, 8-byte aligned, n_instr*24 entries); the owner of a function receives
+ * the sum of the ranks' counts of that function in one exchange, and loads them
+ * into its own program of the functions it owns with gpa_set_counts, which
+ * replaces the counters, sets the invalid-sample count and clears the status
+ * word (as gpa_reset_counts plus an ingest would). Both are asynchronous on
+ * stream; dev_counts must stay valid until stream passes the call. */
+gpa_status gpa_copy_counts(gpa_ctx* ctx, gpa_pid pid, uint64_t* dev_dst, gpa_stream stream);
+gpa_status gpa_set_counts(gpa_ctx* ctx, gpa_pid pid, const uint64_t* dev_counts, uint64_t invalid,
+                          gpa_stream stream);
 
 /* Steps (b)-(c), Sec. 4: reaching definitions, backward slicing, pruning and
  * apportioning over the counters ingested so far. Replaces any previous blame. */

@@ -571,7 +571,8 @@ void analyze_function(const OProg& P, const OArch& arch, const uint64_t* cnt, in
     }
     return 0;
   };
-  // Function Inlining (Table 2): is f a device function, is local x a call site.
+  // Function Inlining (Table 2): is f a device function, is local x a call site
+  // (a site or callee of -1 stands for one outside the program: it matches nothing).
   bool device_fn = false;
   for (int c = 0; c < P.n_calls; ++c) device_fn = device_fn || P.call_callee[c] == f;
   auto is_call_site = [&](int x) {

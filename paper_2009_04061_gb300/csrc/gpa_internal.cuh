@@ -287,6 +287,7 @@ __device__ __forceinline__ void emit_raw(const Prog& P, const Arch& A, int j, in
 // ---------------------------------------------------------------- launchers
 int grid_for(int64_t n, int threads, int sms);
 void launch_build_layout(const Prog& P, cudaStream_t st, int sms, int64_t* launches);
+void launch_store_u64(unsigned long long* p, unsigned long long v, cudaStream_t st, int64_t* launches);
 void launch_build_preds(const Prog& P, int n_succ, int32_t* pred_off, int32_t* cursor, int32_t* tmp, cudaStream_t st,
                         int sms, int64_t* launches);
 void launch_histogram(const Prog& P, const uint64_t* samples, size_t n, cudaStream_t st, int sms, int64_t* launches,

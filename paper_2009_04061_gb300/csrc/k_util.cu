@@ -157,6 +157,15 @@ void launch_build_meta(const Prog& P, int4* meta, cudaStream_t st, int sms, int6
   ++*launches;
 }
 
+namespace {
+__global__ void k_store_u64(unsigned long long* p, unsigned long long v) { *p = v; }
+}  // namespace
+
+void launch_store_u64(unsigned long long* p, unsigned long long v, cudaStream_t st, int64_t* launches) {
+  k_store_u64<<<1, 1, 0, st>>>(p, v);
+  ++*launches;
+}
+
 int grid_for(int64_t n, int threads, int sms) {
   int64_t g = (n + threads - 1) / threads;
   int64_t cap = (int64_t)sms * 8;

@@ -121,10 +121,11 @@ gpa_status validate(const gpa_program_desc* d, const Arch& A) {
       (nl && (!d->loop_parent || !d->loop_header)) || d->n_calls < 0 ||
       (d->n_calls && (!d->call_site || !d->call_callee)))
     return GPA_ERR_INVALID_ARG;
-  for (int c = 0; c < d->n_calls; ++c)
-    if (d->call_site[c] < 0 || d->call_site[c] >= ni || (c && d->call_site[c] <= d->call_site[c - 1]) ||
-        d->call_callee[c] < 0 || d->call_callee[c] >= nf)
-      return GPA_ERR_INVALID_PROGRAM;
+  for (int c = 0; c < d->n_calls; ++c) {
+    const int x = d->call_site[c], g = d->call_callee[c];
+    if (x < -1 || x >= ni || g < -1 || g >= nf || (x < 0 && g < 0)) return GPA_ERR_INVALID_PROGRAM;
+    if (c && (x < d->call_site[c - 1] || (x >= 0 && x == d->call_site[c - 1]))) return GPA_ERR_INVALID_PROGRAM;
+  }
   auto mono = [](const int32_t* a, int n, int last, bool strict) {
     if (a[0] != 0 || a[n] != last) return false;
     for (int i = 0; i < n; ++i)
@@ -414,11 +415,13 @@ static gpa_status alloc_program(const gpa_program_desc* d, ProgramRec* R, int ti
     // site calls): Function Inlining matches bits 1-2.
     std::vector<uint8_t> fl(ni);
     std::vector<char> dev(nf, 0);
-    for (int c = 0; c < d->n_calls; ++c) dev[d->call_callee[c]] = 1;
+    for (int c = 0; c < d->n_calls; ++c)
+      if (d->call_callee[c] >= 0) dev[d->call_callee[c]] = 1;
     for (size_t f = 0; f < nf; ++f)
       for (int x = d->func_instr_off[f]; x < d->func_instr_off[f + 1]; ++x)
         fl[x] = (uint8_t)((d->iflags[x] & 1) | (dev[f] ? 4 : 0));
-    for (int c = 0; c < d->n_calls; ++c) fl[d->call_site[c]] |= 2;
+    for (int c = 0; c < d->n_calls; ++c)
+      if (d->call_site[c] >= 0) fl[d->call_site[c]] |= 2;
     TRY(dev_copy(R, &P.iflags, fl.data(), ni));
   }
   TRY(dev_copy(R, &P.line, d->line, ni));
@@ -613,6 +616,29 @@ gpa_status gpa_reset_counts(gpa_ctx* ctx, gpa_pid pid, gpa_stream stream) {
   cudaStream_t st = (cudaStream_t)stream;
   CK(cudaMemsetAsync(R->P.cnt, 0, (size_t)R->P.ni * kCnt * sizeof(unsigned long long), st));
   CK(cudaMemsetAsync(R->P.stats, 0, SS_N * sizeof(unsigned long long), st));
+  return GPA_OK;
+}
+
+gpa_status gpa_copy_counts(gpa_ctx* ctx, gpa_pid pid, uint64_t* dev_dst, gpa_stream stream) {
+  ProgramRec* R = find(ctx, pid);
+  if (!R) return GPA_ERR_NO_PROGRAM;
+  if (!dev_dst || (reinterpret_cast<uintptr_t>(dev_dst) & 7u)) return GPA_ERR_INVALID_ARG;
+  CK(cudaMemcpyAsync(dev_dst, R->P.cnt, (size_t)R->P.ni * kCnt * sizeof(unsigned long long),
+                     cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
+  return GPA_OK;
+}
+
+gpa_status gpa_set_counts(gpa_ctx* ctx, gpa_pid pid, const uint64_t* dev_counts, uint64_t invalid,
+                          gpa_stream stream) {
+  ProgramRec* R = find(ctx, pid);
+  if (!R) return GPA_ERR_NO_PROGRAM;
+  if (!dev_counts || (reinterpret_cast<uintptr_t>(dev_counts) & 7u)) return GPA_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  CK(cudaMemsetAsync(R->P.stats, 0, SS_N * sizeof(unsigned long long), st));
+  CK(cudaMemcpyAsync(R->P.cnt, dev_counts, (size_t)R->P.ni * kCnt * sizeof(unsigned long long),
+                     cudaMemcpyDeviceToDevice, st));
+  launch_store_u64(&R->P.stats[SS_INVALID], (unsigned long long)invalid, st, &ctx->launches);
+  CK(cudaGetLastError());
   return GPA_OK;
 }
 

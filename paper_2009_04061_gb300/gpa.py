@@ -119,6 +119,8 @@ def library() -> ctypes.CDLL:
         "gpa_sm_model_of_device": ([ctypes.c_int, vp], i32),
         "gpa_launch_count": ([vp], i64),
         "gpa_exclusive_scan_noalloc": ([vp, i64, vp, vp], i32),
+        "gpa_copy_counts": ([vp, u32, vp, vp], i32),
+        "gpa_set_counts": ([vp, u32, vp, ctypes.c_uint64, vp], i32),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -250,6 +252,25 @@ def gpa_ingest_host_samples(ctx, pid, host_samples, n: int | None = None, stream
         n = host_samples.numel() if hasattr(host_samples, "numel") else host_samples.size
     _check(library().gpa_ingest_host_samples(ctx, pid, _p(host_samples), n, _stream(stream)),
            "gpa_ingest_host_samples")
+
+
+def _dev_u64(t, n: int, what: str):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype not in (torch.int64, torch.uint64) \
+            or not t.is_contiguous() or t.numel() < n:
+        raise ValueError(f"{what} must be a contiguous 64-bit CUDA tensor of at least {n} elements")
+
+
+def gpa_copy_counts(ctx, pid, dev_dst, n_instr: int, stream=None):
+    """Copies the program's counters into dev_dst (a 64-bit CUDA tensor of n_instr * 24 elements)."""
+    _dev_u64(dev_dst, n_instr * 24, "dev_dst")
+    _check(library().gpa_copy_counts(ctx, pid, _p(dev_dst), _stream(stream)), "gpa_copy_counts")
+
+
+def gpa_set_counts(ctx, pid, dev_counts, n_instr: int, invalid: int = 0, stream=None):
+    """Replaces the program's counters with dev_counts (a 64-bit CUDA tensor of n_instr * 24 elements)."""
+    _dev_u64(dev_counts, n_instr * 24, "dev_counts")
+    _check(library().gpa_set_counts(ctx, pid, _p(dev_counts), int(invalid), _stream(stream)), "gpa_set_counts")
 
 
 def gpa_blame(ctx, pid, stream=None):
@@ -481,6 +502,12 @@ class Program:
 
     def set_launch_stats(self, stats, sm: dict | None = None):
         gpa_set_launch_stats(self.h, self.pid, stats, sm)
+
+    def copy_counts(self, dev_dst, stream=None):
+        gpa_copy_counts(self.h, self.pid, dev_dst, self.n_instr, stream)
+
+    def set_counts(self, dev_counts, invalid: int = 0, stream=None):
+        gpa_set_counts(self.h, self.pid, dev_counts, self.n_instr, invalid, stream)
 
     def blame(self, stream=None):
         gpa_blame(self.h, self.pid, stream)
