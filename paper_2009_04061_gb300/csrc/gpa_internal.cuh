@@ -36,7 +36,7 @@ enum {
   // And the slowest search: (cycles << 20 | nodes), its rule-2 runs and the
   // cycles of its five phases.
   SS_PHASE = 13, SS_SIZES = 31, SS_PASSB = 47, SS_SLOW = 48,
-  SS_REACH_HEAD = 55,  // next entry of reach_order for the staged fixpoint
+  // 55: unused
   SS_OVF3_N = 56, SS_OVF3_HEAD = 57,  // searches handed on to the program's own fourth tier
   SS_SIZE_CYC = 58,  // with -DGPA_PHASE_TIMING: cycles of the searches by log2 of their node count (16)
   SS_HINT3_N = 74,   // searches queued straight for the third tier (from the top of `queue`)
@@ -52,7 +52,8 @@ enum {
   SS_HINT3_HEAD = 83,  // next of the searches queued straight for the third tier
   SS_OVF3H_N = 84,     // searches for the fourth tier stored from the top of `ovf_queue`
   SS_LARGE_N = 85,     // entries of large_queue
-  SS_N = 86
+  SS_REACH_CLS = 86,   // next entry of reach_order for each of the staged fixpoint's 4 launches
+  SS_N = 90
 };
 
 struct Arch {
@@ -81,6 +82,9 @@ struct Prog {
   uint32_t* cov_cnt;              // n_use: that run's sources per use entry, before pruning (low 16 bits)
                                   // and kept after pruning (high 16 bits)
   int32_t reach_smem;             // shared memory of the staged fixpoint: the largest need that fits
+  int32_t reach_cls[5];           // the staged fixpoint's launches: reach_order[reach_cls[c], reach_cls[c + 1])
+  int32_t reach_cls_smem[4];      // and the largest need among them (0: no launch)
+  const uint8_t* func_natural;    // nf: 1 when every loop body of the function is a natural loop
                                   // (functions needing more use the global-memory fixpoint)
   // Fourth search tier, sized for this program's largest function (0 nodes:
   // none): searches that outgrow the context's third tier.
@@ -109,7 +113,7 @@ struct Prog {
   const int32_t* loop_depth;
   const int32_t* instr_block;
   const int32_t* block_func;
-  const int32_t* reach_order;     // nf: functions by block count, largest first
+  const int32_t* reach_order;     // nf: functions by the staged fixpoint's shared memory need, largest first
   const int32_t* block_minreach;  // nb: smallest block reachable from the block (itself included)
   const int4* block_meta;         // 2 per block: {first instr, end instr, first event, end event},
                                   // {first pred, end pred, first two predecessors or -1} (one
@@ -310,9 +314,17 @@ inline void allow_max_smem(F func) {
 
 // Shared memory the staged reaching-definitions fixpoint needs for a function
 // of nbf blocks and ne predecessor entries, and the most it may use.
-__host__ __device__ inline int64_t reach_smem_need(int64_t nbf, int64_t ne) {
-  return 4 * kWords * nbf + 4 * (nbf + 1) + 4 * ne;
+// Shared memory of the staged fixpoint for a function of nbf blocks, ne
+// predecessor entries and nlf loops: ROUT (9 words a block), a 16-byte record
+// per block (16-byte aligned: up to 12 bytes of padding), the predecessor CSR,
+// each block's innermost loop, and per loop its parent and two 9-word masks (the
+// definitions in its body; those of its body and enclosing loops).
+__host__ __device__ inline int64_t reach_smem_need(int64_t nbf, int64_t ne, int64_t nlf) {
+  return 4 * kWords * nbf + 12 + 16 * nbf + 4 * (nbf + 1) + 4 * ne + 4 * nbf + 4 * nlf + 2 * 4 * kWords * nlf;
 }
+// Size classes of the staged fixpoint's launches (upper bounds of the need):
+// the larger a function, the fewer warps per SM its launch runs.
+constexpr int64_t kReachClassCap[4] = {200 * 1024, 64 * 1024, 28 * 1024, 12 * 1024};
 constexpr int64_t kReachSmemCap = 200 * 1024;
 // A second stream (and two events) on which the searches queued straight for
 // the third tier run beside the first two tiers.

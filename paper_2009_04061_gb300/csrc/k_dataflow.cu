@@ -74,58 +74,131 @@ __global__ void k_res_maxlat(Prog P, Arch A) {
 }
 
 // One warp per function, the function staged in shared memory: ROUT (9
-// words per block, starting at DEF) and the predecessor lists as local block
-// indices. ROUT only grows, so ROUT[b] = ROUT[b] | OR of the predecessors'
-// ROUT needs no separate DEF. Each sweep visits the blocks one after another
-// in layout order (a topological order of the forward edges, so one sweep
-// carries a def along any forward path), lanes 0-8 over the 9 words, with the
-// previous block's ROUT kept in a register (the fall-through predecessor);
-// sweeps repeat until one changes nothing (back edges). Then RIN = OR of the
-// predecessors' ROUT and both go to global memory. Functions needing more
-// than P.reach_smem bytes are left to k_reaching.
-__global__ void __launch_bounds__(32) k_reaching_smem(Prog P, int max_sweeps) {
-  extern __shared__ uint32_t sm[];
+// words per block, starting at DEF), and per block a record of its first two
+// predecessors other than the block before it, its innermost loop, and flags
+// (the block before it is a predecessor; more predecessors in the CSR). ROUT
+// only grows, so ROUT[b] = ROUT[b] | OR of the predecessors' ROUT needs no
+// separate DEF. A sweep visits the blocks one after another in layout order (a
+// topological order of the forward edges, so one sweep carries a def along any
+// forward path), lanes 0-8 over the 9 words, with the previous block's ROUT in
+// a register and the next block's record and ROUT loaded a block ahead.
+// When every loop body of the function is a natural loop (or it has none),
+// each block also takes in, from the start, the defs of the bodies of the loops
+// around it: every block of a natural loop reaches every other one through the
+// back edge, and a def from outside a loop enters it through its header, which
+// precedes the body in layout order. With that, the first sweep gives every
+// block all the defs that reach it: the least fixpoint, in one sweep. Other
+// functions sweep until a sweep changes nothing (max_sweeps at most). Then RIN
+// = OR of the predecessors' ROUT and both go to global memory. The launch
+// takes reach_order[q_lo, q_hi) from the counter at `head`; functions needing
+// more than `cap` bytes are left to another launch.
+__device__ __forceinline__ void cp_async4(void* smem_dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((uint32_t)__cvta_generic_to_shared(smem_dst)),
+               "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+__global__ void __launch_bounds__(32) k_reaching_smem(Prog P, int max_sweeps, int q_lo, int q_hi, int head, int cap) {
+  extern __shared__ __align__(16) uint32_t sm[];
   const int lane = threadIdx.x;
   while (true) {
     // Functions are taken largest first, so the long ones start early.
     unsigned long long q = 0;
-    if (lane == 0) q = atomicAdd(&P.stats[SS_REACH_HEAD], 1ull);
-    q = __shfl_sync(0xffffffffu, q, 0);
-    if (q >= (unsigned long long)P.nf) break;
+    if (lane == 0) q = atomicAdd(&P.stats[head], 1ull);
+    q = __shfl_sync(0xffffffffu, q, 0) + (unsigned long long)q_lo;
+    if (q >= (unsigned long long)q_hi) break;
     const int f = P.reach_order[q];
     const int b0 = P.func_block_off[f], b1 = P.func_block_off[f + 1], nbf = b1 - b0;
     const int e0 = P.pred_off[b0], ne = P.pred_off[b1] - e0;
-    if (nbf == 0 || reach_smem_need(nbf, ne) > P.reach_smem) continue;
+    const int l0 = P.func_loop_off[f], nlf = P.func_loop_off[f + 1] - l0;
+    if (nbf == 0 || reach_smem_need(nbf, ne, nlf) > cap) continue;
+    const bool exact = P.func_natural[f];  // one seeded sweep is the fixpoint
+    const bool seed = exact && nlf > 0;
     uint32_t* so = sm;
-    int* spo = reinterpret_cast<int*>(so + (size_t)nbf * kWords);
+    int4* rec = reinterpret_cast<int4*>(so + (size_t)nbf * kWords + ((nbf * kWords) & 3 ? 4 - ((nbf * kWords) & 3) : 0));
+    int* spo = reinterpret_cast<int*>(rec + nbf);
     int* sp = spo + nbf + 1;
-    for (int t = lane; t < nbf * kWords; t += 32) so[t] = P.def_mask[(size_t)b0 * kWords + t];
-    for (int t = lane; t <= nbf; t += 32) spo[t] = P.pred_off[b0 + t] - e0;
-    for (int t = lane; t < ne; t += 32) sp[t] = P.pred[e0 + t] - b0;
+    int* sloop = sp + ne;
+    int* spar = sloop + nbf;
+    uint32_t* ldef = reinterpret_cast<uint32_t*>(spar + nlf);
+    uint32_t* lin = ldef + (size_t)nlf * kWords;
+    // Staging: asynchronous 4-byte copies, all in flight together, then the
+    // global indices rebased to the function in place.
+    for (int t = lane; t < nbf * kWords; t += 32) cp_async4(so + t, P.def_mask + (size_t)b0 * kWords + t);
+    for (int t = lane; t <= nbf; t += 32) cp_async4(spo + t, P.pred_off + b0 + t);
+    for (int t = lane; t < ne; t += 32) cp_async4(sp + t, P.pred + e0 + t);
+    if (seed) {
+      for (int t = lane; t < nbf; t += 32) cp_async4(sloop + t, P.block_loop + b0 + t);
+      for (int t = lane; t < nlf; t += 32) cp_async4(spar + t, P.loop_parent + l0 + t);
+    }
+    cp_async_wait_all();
+    __syncwarp();
+    for (int t = lane; t <= nbf; t += 32) spo[t] -= e0;
+    for (int t = lane; t < ne; t += 32) sp[t] -= b0;
+    if (seed) {
+      for (int t = lane; t < nbf; t += 32) sloop[t] = sloop[t] >= 0 ? sloop[t] - l0 : -1;
+      for (int t = lane; t < nlf; t += 32) spar[t] = spar[t] >= 0 ? spar[t] - l0 : -1;
+      for (int t = lane; t < nlf * kWords; t += 32) ldef[t] = 0u;
+    }
+    __syncwarp();
+    for (int b = lane; b < nbf; b += 32) {
+      int p1 = -1, p2 = -1, fl = 0;
+      for (int e = spo[b]; e < spo[b + 1]; ++e) {
+        const int p = sp[e];
+        if (p == b - 1) fl |= 1;
+        else if (p1 < 0) p1 = p;
+        else if (p2 < 0) p2 = p;
+        else fl |= 2;
+      }
+      rec[b] = make_int4(p1, p2, seed ? sloop[b] : -1, fl);
+    }
+    if (seed) {
+      // the defs of each loop's body, nested loops included
+      for (int t = lane; t < nbf * kWords; t += 32) {
+        const uint32_t v = so[t];
+        if (!v) continue;
+        const int w = t % kWords;
+        for (int l = sloop[t / kWords]; l >= 0; l = spar[l]) atomicOr(&ldef[l * kWords + w], v);
+      }
+      __syncwarp();
+      // and of the enclosing loops' bodies
+      for (int t = lane; t < nlf * kWords; t += 32) {
+        const int w = t % kWords;
+        uint32_t v = 0u;
+        for (int l = t / kWords; l >= 0; l = spar[l]) v |= ldef[l * kWords + w];
+        lin[t] = v;
+      }
+    }
     __syncwarp();
     bool converged = false;
     int sweep = 0;
-    for (; sweep < max_sweeps && !converged; ++sweep) {
+    const int limit = exact ? 1 : max_sweeps;
+    for (; sweep < limit && !converged; ++sweep) {
       bool ch = false;
       if (lane < kWords) {
         uint32_t prev = 0u;
-        int e_lo = spo[0];
+        int4 r = rec[0];
+        uint32_t old = so[lane];
         for (int b = 0; b < nbf; ++b) {
-          const int e_hi = spo[b + 1];
-          const uint32_t old = so[b * kWords + lane];
-          uint32_t in = 0u;
-          for (int e = e_lo; e < e_hi; ++e) {
-            const int p = sp[e];
-            in |= p == b - 1 ? prev : so[p * kWords + lane];
-          }
+          const bool more = b + 1 < nbf;
+          const int4 rn = more ? rec[b + 1] : r;
+          const uint32_t oldn = more ? so[(b + 1) * kWords + lane] : 0u;
+          uint32_t in = r.z >= 0 ? lin[r.z * kWords + lane] : 0u;
+          if (r.w & 1) in |= prev;
+          if (r.x >= 0) in |= so[r.x * kWords + lane];
+          if (r.y >= 0) in |= so[r.y * kWords + lane];
+          if (r.w & 2)
+            for (int e = spo[b]; e < spo[b + 1]; ++e) in |= so[sp[e] * kWords + lane];
           const uint32_t o = old | in;
           ch |= o != old;
           so[b * kWords + lane] = o;
           prev = o;
-          e_lo = e_hi;
+          r = rn;
+          old = oldn;
         }
       }
-      converged = !__any_sync(0xffffffffu, ch);
+      converged = exact || !__any_sync(0xffffffffu, ch);
     }
     __syncwarp();
     for (int t = lane; t < nbf * kWords; t += 32) {
@@ -155,7 +228,10 @@ __global__ void k_reaching(Prog P, int max_sweeps) {
   const int n_warps = (gridDim.x * blockDim.x) >> 5;
   for (int f = warp; f < P.nf; f += n_warps) {
     const int b0 = P.func_block_off[f], b1 = P.func_block_off[f + 1];
-    if (b1 > b0 && reach_smem_need(b1 - b0, P.pred_off[b1] - P.pred_off[b0]) <= P.reach_smem) continue;
+    if (b1 > b0 &&
+        reach_smem_need(b1 - b0, P.pred_off[b1] - P.pred_off[b0], P.func_loop_off[f + 1] - P.func_loop_off[f]) <=
+            P.reach_smem)
+      continue;
     bool converged = false;
     int sweep = 0;
     for (; sweep < max_sweeps && !converged; ++sweep) {
@@ -209,13 +285,19 @@ void launch_dataflow(const Prog& P, const Arch& A, int max_sweeps, cudaStream_t 
   if (blocks < 1) blocks = 1;
   k_block_masks<<<blocks, threads, 0, st>>>(P);
   if (P.reach_smem > 0) {
+    // One launch per size class: the larger the functions, the more shared
+    // memory each warp stages and the fewer warps per SM.
     allow_max_smem(k_reaching_smem);
-    int per_sm = (int)((200 * 1024) / (P.reach_smem + 1024));
-    if (per_sm < 1) per_sm = 1;
-    if (per_sm > 16) per_sm = 16;
-    const int g = std::min(P.nf, sms * per_sm);
-    k_reaching_smem<<<g, 32, P.reach_smem, st>>>(P, max_sweeps);
-    ++*launches;
+    cudaMemsetAsync(&P.stats[SS_REACH_CLS], 0, 4 * sizeof(unsigned long long), st);
+    for (int c = 0; c < 4; ++c) {
+      const int n = P.reach_cls[c + 1] - P.reach_cls[c];
+      if (n <= 0 || P.reach_cls_smem[c] <= 0) continue;
+      const int smem = P.reach_cls_smem[c];
+      const int per_sm = std::max(1, std::min(32, (int)((200 * 1024) / (smem + 1024))));
+      const int g = std::min(n, sms * per_sm);
+      k_reaching_smem<<<g, 32, smem, st>>>(P, max_sweeps, P.reach_cls[c], P.reach_cls[c + 1], SS_REACH_CLS + c, smem);
+      ++*launches;
+    }
   }
   int fblocks = (P.nf * 32 + 127) / 128;
   if (fblocks > sms * 16) fblocks = sms * 16;

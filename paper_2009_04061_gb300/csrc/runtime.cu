@@ -368,11 +368,17 @@ static gpa_status alloc_program(const gpa_program_desc* d, ProgramRec* R, int ti
   // Staged fixpoint: the largest per-function need within the cap (edges stay
   // inside their function, so a function's predecessor entries are its
   // blocks' successor entries).
+  auto reach_need = [&](int f) {
+    const int b0 = d->func_block_off[f], b1 = d->func_block_off[f + 1];
+    return reach_smem_need(b1 - b0, (int64_t)d->succ_off[b1] - d->succ_off[b0],
+                           (int64_t)d->func_loop_off[f + 1] - d->func_loop_off[f]);
+  };
+  // Staged fixpoint: functions needing at most this much shared memory (the
+  // others take the windowed global-memory kernel).
   P.reach_smem = 0;
   for (int f = 0; f < d->n_functions; ++f) {
-    const int b0 = d->func_block_off[f], b1 = d->func_block_off[f + 1];
-    const int64_t need = reach_smem_need(b1 - b0, (int64_t)d->succ_off[b1] - d->succ_off[b0]);
-    if (b1 > b0 && need <= kReachSmemCap && need > P.reach_smem) P.reach_smem = (int32_t)need;
+    const int64_t need = reach_need(f);
+    if (need <= kReachClassCap[0] && need > P.reach_smem) P.reach_smem = (int32_t)need;
   }
   R->n_succ = d->n_succ; R->n_def = d->n_def; R->n_use = d->n_use;
   const size_t ni = P.ni, nb = P.nb, nl = P.nl, nf = P.nf;
@@ -383,12 +389,68 @@ static gpa_status alloc_program(const gpa_program_desc* d, ProgramRec* R, int ti
   } while (0)
   TRY(dev_copy(R, &P.func_instr_off, d->func_instr_off, nf + 1));
   {
+    // The staged fixpoint takes the functions by shared memory need, largest
+    // first, in four launches by size class (kReachClassCap): class c holds the
+    // needs in (cap[c + 1], cap[c]], and its launch sizes its stage for the
+    // largest of them. Functions beyond cap[0] are left to the windowed kernel.
+    std::vector<int64_t> need(nf);
+    for (size_t f = 0; f < nf; ++f) need[f] = reach_need((int)f);
     std::vector<int32_t> order(nf);
     for (size_t f = 0; f < nf; ++f) order[f] = (int32_t)f;
-    std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
-      return d->func_block_off[a + 1] - d->func_block_off[a] > d->func_block_off[b + 1] - d->func_block_off[b];
-    });
+    std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return need[a] > need[b]; });
     TRY(dev_copy(R, &P.reach_order, order.data(), nf));
+    int q = 0;
+    while (q < (int)nf && need[order[q]] > kReachClassCap[0]) ++q;
+    for (int c = 0; c < 4; ++c) {
+      P.reach_cls[c] = q;
+      P.reach_cls_smem[c] = 0;
+      const int64_t lo = c < 3 ? kReachClassCap[c + 1] : -1;
+      while (q < (int)nf && need[order[q]] > lo) {
+        P.reach_cls_smem[c] = std::max<int32_t>(P.reach_cls_smem[c], (int32_t)need[order[q]]);
+        ++q;
+      }
+    }
+    P.reach_cls[4] = q;
+    // Natural loops: a loop body is the header and the blocks that reach one of
+    // its latches (a body block with an edge to the header) without passing the
+    // header. Then every body block reaches every other one, which lets the
+    // fixpoint seed a block with the definitions of its enclosing loops.
+    std::vector<uint8_t> natural(nf, 1);
+    if (!R->dry) {  // (a footprint needs only the sizes)
+      std::vector<int32_t> pcnt(nb + 1, 0), pl((size_t)d->n_succ);
+      for (size_t u = 0; u < nb; ++u)
+        for (int e = d->succ_off[u]; e < d->succ_off[u + 1]; ++e) ++pcnt[d->succ[e] + 1];
+      for (size_t b = 0; b < nb; ++b) pcnt[b + 1] += pcnt[b];
+      std::vector<int32_t> fill(pcnt.begin(), pcnt.end() - 1);
+      for (size_t u = 0; u < nb; ++u)
+        for (int e = d->succ_off[u]; e < d->succ_off[u + 1]; ++e) pl[fill[d->succ[e]]++] = (int32_t)u;
+      auto in_body = [&](int b, int l) {
+        for (int q = d->block_loop[b]; q >= 0; q = d->loop_parent[q])
+          if (q == l) return true;
+        return false;
+      };
+      std::vector<int32_t> body_n(nl, 0), stamp(nb, -1), st;
+      for (size_t b = 0; b < nb; ++b)
+        for (int q = d->block_loop[b]; q >= 0; q = d->loop_parent[q]) ++body_n[q];
+      for (size_t f = 0; f < nf; ++f)
+        for (int l = d->func_loop_off[f]; l < d->func_loop_off[f + 1] && natural[f]; ++l) {
+          const int h = d->loop_header[l];
+          int seen = 1;
+          stamp[h] = l;
+          st.clear();
+          for (int e = pcnt[h]; e < pcnt[h + 1]; ++e)
+            if (in_body(pl[e], l) && stamp[pl[e]] != l) { stamp[pl[e]] = l; ++seen; st.push_back(pl[e]); }
+          while (!st.empty() && natural[f]) {
+            const int x = st.back();
+            st.pop_back();
+            if (!in_body(x, l)) { natural[f] = 0; break; }
+            for (int e = pcnt[x]; e < pcnt[x + 1]; ++e)
+              if (stamp[pl[e]] != l) { stamp[pl[e]] = l; ++seen; st.push_back(pl[e]); }
+          }
+          if (seen != body_n[l]) natural[f] = 0;
+        }
+    }
+    TRY(dev_copy(R, &P.func_natural, natural.data(), nf));
     // Smallest block reachable from each block: a min fixpoint over
     // successors, swept in descending block order (forward edges point up, so
     // each sweep settles every forward path; back edges need a few more).

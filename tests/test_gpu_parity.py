@@ -197,13 +197,35 @@ def test_plain_per_function_equals_batched(ctx):
         assert np.array_equal(gf["advice"]["hot"][0][..., [0, 1, 4, 5]], gb["advice"]["hot"][f][..., [0, 1, 4, 5]])
 
 
+def _unnatural_loop_program():
+    """A loop whose listed body holds an exit block that cannot reach the latch
+    (not a natural loop): carrying the latch's def back to the header takes a
+    sweep of the fixpoint that the seeded single sweep of natural loops skips."""
+    b0 = [I("MOV", ["R1"], ["R2"])]
+    b1 = [I("IADD", ["R3"], ["R1", "R4"])]
+    b2 = [I("MOV", ["R1"], ["R5"]), I("ISETP", ["P0"], ["R3", "R6"]), I("BRA", [], [], guard="P0")]
+    b3 = [I("FFMA", ["R7"], ["R1", "R3", "R5"]), I("EXIT")]
+    return program([([b0, b1, b2, b3], [[1], [2], [1, 3], []], [(1, [1, 2, 3], -1)])])
+
+
 def test_fixpoint_sweep_limit_reports_not_converged():
+    """The sweep limit applies to functions whose loop bodies are not natural loops
+    (the others take one sweep that is exact): one sweep leaves such a function
+    unconverged and reports it, while the natural plain workload converges within the
+    same limit. Without the limit both equal the oracle's fixpoint."""
     import paper_2009_04061_gb300 as g
+    odd = _unnatural_loop_program()
+    s_odd = np.array([(3 << 24) | (2 << 20)] * 20 + [(1 << 24) | (2 << 20) | (1 << 19)] * 7, dtype=np.uint64)
+    ps, ns, kz = synth.workload("plain")
+    P = synth.make_program(ps, kz)
     with g.Context(ARCH, dict(max_fixpoint_sweeps=1)) as c:
-        ps, ns, kz = synth.workload("plain")
-        P = synth.make_program(ps, kz)
+        assert gpu_run(c, odd, dev(s_odd))["status"] == -4
         r = gpu_run(c, P, dev(P.samples(1000)))
-        assert r["status"] == -4
+        assert r["status"] == 0 and r["info"]["sweeps"] == 1
+    with g.Context(ARCH) as c:
+        r = gpu_run(c, odd, dev(s_odd))
+        assert r["status"] == 0 and r["info"]["sweeps"] == 2
+        assert_full_parity(r, oracle_run(odd, s_odd))
 
 
 def test_invalid_program_rejected(ctx):
