@@ -53,8 +53,8 @@ def parse():
     ap.add_argument("--cpu-samples", type=int, default=8_000_000, help="sample cap of the CPU-baseline sample")
     ap.add_argument("--hist-variant", type=int, default=None, help="aggregation kernel variant (gpa_options)")
     ap.add_argument("--options", default="", help="gpa_options fields as JSON, e.g. '{\"search_slots\": 1216}'")
-    ap.add_argument("--autotune", action="store_true",
-                    help="tune the launch schedule on the workload first and time the tuned one")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="time the library's default schedule without tuning it on the workload first")
     ap.add_argument("--serving", action="store_true", help="run the serving workload instead")
     ap.add_argument("--sessions", type=int, default=200, help="serving: sessions")
     ap.add_argument("--serving-sessions", type=int, default=100,
@@ -396,14 +396,15 @@ def main():
     if a.options:
         opts.update(json.loads(a.options))
     tuned = None
-    if a.autotune:
+    if not a.no_autotune and not a.options and a.hist_variant is None and not a.search_slots:
         from paper_2009_04061_gb300 import autotune
         stream0 = torch.cuda.current_stream(dev)
         with gpa.Context(synth.default_arch(), opts or None) as c0:
             fixed_ms = autotune.time_step(c0, arrays, d, stream0)
         best, table = autotune.tune(synth.default_arch(), arrays, d, stream0)
-        tuned = {"fixed_ms_per_step": fixed_ms, "tuned_ms_per_step": min(t for _, t in table),
-                 "options": best, "candidates_tried": len(table)}
+        tuned = {"fixed_ms_per_step": fixed_ms, "tuned_ms_per_step": next(t for o, t in table if o == best),
+                 "options": best, "candidates_tried": len(table),
+                 "searched": {name: list(values) for name, values in autotune.DIMENSIONS}}
         opts = best
     torch.cuda.synchronize(dev)
     t_load = time.perf_counter()

@@ -121,6 +121,11 @@ typedef struct {
   int32_t large_search_nodes;   /* a global-memory search that reached this many nodes is started
                                    before the others on later steps of its program; 0 = 1024 */
   int32_t hist_chunk;           /* aggregation variant 0: tiles per claimed chunk, 0 = 24 (max 4096) */
+  int32_t reach_schedule;       /* reaching-definitions fixpoint: 0 (default) = a warp per function staged
+                                   in shared memory (launches by size class; functions beyond 200 KB of
+                                   stage take the windowed kernel); 1 = the windowed kernel for every
+                                   function (a lane per basic block, windows of 32 blocks in global
+                                   memory) */
 } gpa_options;
 
 /* A program: n_functions functions laid out one after another. All arrays are
@@ -268,7 +273,9 @@ gpa_status gpa_destroy(gpa_ctx* ctx);
 gpa_status gpa_load_program(gpa_ctx* ctx, const gpa_program_desc* prog, gpa_pid* out);
 
 /* Device bytes gpa_load_program would request for prog under ctx (validated
- * like a load; nothing is allocated or copied), for admission control. */
+ * like a load; nothing is allocated or copied), for admission control. It reads
+ * only the context's architecture table and options, so unlike the other calls
+ * it may run on another host thread while the context is in use. */
 gpa_status gpa_program_footprint(gpa_ctx* ctx, const gpa_program_desc* prog, int64_t* bytes);
 
 /* Device bytes requested for a loaded program (equal to its footprint). */

@@ -296,7 +296,8 @@ void launch_build_preds(const Prog& P, int n_succ, int32_t* pred_off, int32_t* c
                         int sms, int64_t* launches);
 void launch_histogram(const Prog& P, const uint64_t* samples, size_t n, cudaStream_t st, int sms, int64_t* launches,
                       int variant, int hist_chunk);
-void launch_dataflow(const Prog& P, const Arch& A, int max_sweeps, cudaStream_t st, int sms, int64_t* launches);
+void launch_dataflow(const Prog& P, const Arch& A, int max_sweeps, int schedule, cudaStream_t st, int sms,
+                     int64_t* launches);
 
 // Lets kernel func take up to the device's opt-in shared memory per block.
 // Every launch and captured graph node of a kernel then sees the same limit

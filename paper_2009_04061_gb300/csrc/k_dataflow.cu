@@ -221,14 +221,15 @@ __global__ void __launch_bounds__(32) k_reaching_smem(Prog P, int max_sweeps, in
 // lanes iterate until __ballot_sync reports no change, then move on. A full
 // pass without change ends the fixpoint; max_sweeps passes without reaching it
 // set ST_NOT_CONVERGED. Monotone OR updates from 0 make the result the least
-// fixpoint regardless of the visiting order.
-__global__ void k_reaching(Prog P, int max_sweeps) {
+// fixpoint regardless of the visiting order. Takes the functions the staged
+// kernel does not (every function with `all`).
+__global__ void k_reaching(Prog P, int max_sweeps, int all) {
   const int lane = threadIdx.x & 31;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int n_warps = (gridDim.x * blockDim.x) >> 5;
   for (int f = warp; f < P.nf; f += n_warps) {
     const int b0 = P.func_block_off[f], b1 = P.func_block_off[f + 1];
-    if (b1 > b0 &&
+    if (!all && b1 > b0 &&
         reach_smem_need(b1 - b0, P.pred_off[b1] - P.pred_off[b0], P.func_loop_off[f + 1] - P.func_loop_off[f]) <=
             P.reach_smem)
       continue;
@@ -277,14 +278,15 @@ __global__ void k_reaching(Prog P, int max_sweeps) {
 
 }  // namespace
 
-void launch_dataflow(const Prog& P, const Arch& A, int max_sweeps, cudaStream_t st, int sms, int64_t* launches) {
+void launch_dataflow(const Prog& P, const Arch& A, int max_sweeps, int schedule, cudaStream_t st, int sms,
+                     int64_t* launches) {
   const int threads = 256;
   int64_t warps_needed = P.nb;
   int blocks = (int)((warps_needed * 32 + threads - 1) / threads);
   if (blocks > sms * 16) blocks = sms * 16;
   if (blocks < 1) blocks = 1;
   k_block_masks<<<blocks, threads, 0, st>>>(P);
-  if (P.reach_smem > 0) {
+  if (schedule == 0 && P.reach_smem > 0) {
     // One launch per size class: the larger the functions, the more shared
     // memory each warp stages and the fewer warps per SM.
     allow_max_smem(k_reaching_smem);
@@ -302,7 +304,7 @@ void launch_dataflow(const Prog& P, const Arch& A, int max_sweeps, cudaStream_t 
   int fblocks = (P.nf * 32 + 127) / 128;
   if (fblocks > sms * 16) fblocks = sms * 16;
   if (fblocks < 1) fblocks = 1;
-  k_reaching<<<fblocks, 128, 0, st>>>(P, max_sweeps);
+  k_reaching<<<fblocks, 128, 0, st>>>(P, max_sweeps, schedule == 1 ? 1 : 0);
   cudaMemsetAsync(P.res_maxlat, 0, sizeof(int32_t) * (size_t)P.nf * kNumRes, st);
   cudaMemsetAsync(P.res_guards, 0, sizeof(uint32_t) * (size_t)P.nf * kNumRes, st);
   k_res_maxlat<<<grid_for(P.ni, 256, sms), 256, 0, st>>>(P, A);

@@ -271,7 +271,7 @@ gpa_status gpa_create(const gpa_arch_desc* arch, const gpa_options* opts, gpa_ct
     if (o.max_fixpoint_sweeps < 0 || o.max_search_nodes < 0 || o.search_slots < 0 || o.max_sources_per_use < 0 ||
         o.max_sources_per_use > kBigSrc || o.small_search_nodes < 0 || o.mid_search_nodes < 0 ||
         o.hist_variant < 0 || o.hist_variant > 3 || o.large_search_nodes < 0 || o.hist_chunk < 0 ||
-        o.hist_chunk > 4096)
+        o.hist_chunk > 4096 || o.reach_schedule < 0 || o.reach_schedule > 1)
       return GPA_ERR_INVALID_ARG;
   }
   auto* c = new (std::nothrow) gpa_ctx();
@@ -772,7 +772,8 @@ static gpa_status blame_body(gpa_ctx* ctx, ProgramRec* R, cudaStream_t st, bool 
   // per-step counters: general searches, largest search, sweeps, raw edges, queues
   CK(cudaMemsetAsync(R->P.stats + SS_GENERAL, 0, sizeof(unsigned long long) * 3, st));
   CK(cudaMemsetAsync(R->P.stats + SS_RAW_N, 0, sizeof(unsigned long long) * (SS_N - SS_RAW_N), st));
-  launch_dataflow(R->P, ctx->arch, ctx->opts.max_fixpoint_sweeps, st, ctx->sms, &ctx->launches);
+  launch_dataflow(R->P, ctx->arch, ctx->opts.max_fixpoint_sweeps, ctx->opts.reach_schedule, st, ctx->sms,
+                  &ctx->launches);
   // The search scratch is shared by the context's programs: order its users.
   if (order_scratch) CK(cudaStreamWaitEvent(st, ctx->scratch_ev, 0));
   launch_blame(R->P, ctx->arch, ctx->tier, &ctx->fork, ctx->opts.max_sources_per_use, R->scan_tmp, st, ctx->sms,
@@ -798,7 +799,8 @@ static gpa_status coverage_run(gpa_ctx* ctx, ProgramRec* R, cudaStream_t st, int
   CK(cudaMemsetAsync(D.cov_cnt, 0, sizeof(uint32_t) * (size_t)std::max(R->n_use, 1), st));
   CK(cudaMemsetAsync(D.stats + SS_GENERAL, 0, sizeof(unsigned long long) * 3, st));
   CK(cudaMemsetAsync(D.stats + SS_RAW_N, 0, sizeof(unsigned long long) * (SS_N - SS_RAW_N), st));
-  launch_dataflow(D, ctx->arch, ctx->opts.max_fixpoint_sweeps, st, ctx->sms, &ctx->launches);
+  launch_dataflow(D, ctx->arch, ctx->opts.max_fixpoint_sweeps, ctx->opts.reach_schedule, st, ctx->sms,
+                  &ctx->launches);
   CK(cudaStreamWaitEvent(st, ctx->scratch_ev, 0));
   launch_coverage(D, ctx->arch, ctx->tier, &ctx->fork, st, ctx->sms, &ctx->launches);
   CK(cudaEventRecord(ctx->scratch_ev, st));

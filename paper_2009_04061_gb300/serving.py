@@ -3,11 +3,14 @@
 Profiling sessions (a program and its packed samples) arrive over time. A
 session is admitted as soon as a slot is free and the device-memory budget
 has room for its program: a slot is a context of its own (own search scratch,
-own sample staging) with its own CUDA stream, so admitted sessions run side
-by side on the device while later ones queue. For each admitted session the
-slot's stream carries ingest (from pinned host memory) -> blame -> advice;
-completion is polled through a CUDA event, the advice copied out, and the
-program freed in stream order, so no call waits for other slots' work.
+own sample staging) with its own CUDA stream and its own host thread, so
+admitted sessions run side by side on the device and their host work (the
+program's validation and upload, the advice copy-out) runs side by side on
+the host cores, while later sessions queue. For each admitted session the
+slot's thread loads the program and queues ingest (from pinned host memory)
+-> blame -> advice on the slot's stream, waits for it, copies the advice out
+and frees the program in stream order. A session's device footprint (for the
+budget) is computed when it is submitted, on a small pool of host threads.
 
 Latency is ingest-to-advice: from a session's arrival (its submission) to
 its advice being on the host.
@@ -15,7 +18,10 @@ its advice being on the host.
 from __future__ import annotations
 
 import collections
+import queue
+import threading
 import time
+from concurrent.futures import ThreadPoolExecutor
 from dataclasses import dataclass, field
 
 import numpy as np
@@ -29,6 +35,7 @@ class Session:
     program: dict                 # program arrays (the gpa_program_desc fields)
     samples: np.ndarray           # packed uint64 samples, host memory (pinned for overlap)
     t_arrival: float = 0.0        # seconds on the server's clock
+    need: object = field(default=None, repr=False)  # future of its device footprint (bytes)
 
 
 @dataclass
@@ -53,12 +60,9 @@ class Result:
 class _Slot:
     ctx: object
     stream: object
-    session: Session | None = None
-    prog: object = None
-    event: object = None
-    t_admit: float = 0.0
-    bytes: int = 0
-    keep: object = field(default=None, repr=False)
+    jobs: object = None            # queue of (session, t_admit, bytes) for the slot's thread
+    busy: bool = False
+    thread: object = field(default=None, repr=False)
 
 
 class Server:
@@ -71,10 +75,11 @@ class Server:
                  keep_results: bool = False):
         import torch
         self._torch = torch
+        self.device = torch.cuda.current_device()
         if options is None:
             # Slots run side by side: four global-memory search warps per SM each
             # (about 2.6 GB of search scratch per slot) instead of a whole GPU's worth.
-            sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+            sms = torch.cuda.get_device_properties(self.device).multi_processor_count
             options = {"search_slots": 4 * sms}
         self.slots = [_Slot(gpa.Context(arch, options), torch.cuda.Stream()) for _ in range(slots)]
         self.budget = int(budget_bytes)
@@ -82,73 +87,106 @@ class Server:
         self.pending: collections.deque[Session] = collections.deque()
         self.keep_results = keep_results
         self.t0 = time.perf_counter()
+        self._done: queue.Queue = queue.Queue()
+        self._sizer = ThreadPoolExecutor(4)
+        for k, sl in enumerate(self.slots):
+            sl.jobs = queue.Queue()
+            sl.thread = threading.Thread(target=self._work, args=(k,), daemon=True)
+            sl.thread.start()
 
     def now(self) -> float:
         return time.perf_counter() - self.t0
 
     def submit(self, s: Session, t_arrival: float | None = None):
         s.t_arrival = self.now() if t_arrival is None else t_arrival
+        if s.need is None:
+            s.need = self._sizer.submit(self.slots[0].ctx.footprint, s.program)
         self.pending.append(s)
 
     def busy(self) -> int:
-        return sum(1 for sl in self.slots if sl.session is not None)
+        return sum(1 for sl in self.slots if sl.busy)
 
-    def _admit(self, sl: _Slot, s: Session, need: int):
-        prog = sl.ctx.load_program(s.program)
+    def _work(self, k: int):
+        """The slot's thread: run the sessions handed to it one after another."""
+        self._torch.cuda.set_device(self.device)
+        sl = self.slots[k]
+        while True:
+            job = sl.jobs.get()
+            if job is None:
+                return
+            s, t_admit, nbytes = job
+            try:
+                r = self._run(sl, s, t_admit, nbytes)
+            except BaseException as e:  # handed to the polling thread, which raises it
+                r = e
+            self._done.put((k, r))
+
+    def _run(self, sl: _Slot, s: Session, t_admit: float, nbytes: int) -> Result:
         st = sl.stream
-        prog.reset(st)
-        if s.samples.size:
-            prog.ingest_host(s.samples, stream=st)
-        prog.blame(st)
-        prog.advise(fetch=False, stream=st)
-        ev = self._torch.cuda.Event()
-        ev.record(st)
-        sl.session, sl.prog, sl.event, sl.t_admit, sl.bytes = s, prog, ev, self.now(), need
-        self.used += need
-
-    def _finish(self, sl: _Slot) -> Result:
-        s, prog, st = sl.session, sl.prog, sl.stream
-        st_code, info = prog.status(st)
-        if st_code != 0:
-            raise RuntimeError(f"session {s.sid}: device status {st_code} ({info})")
-        adv = prog.get_advice(st)
-        counts = blame = edges = None
-        if self.keep_results:
-            counts, _ = prog.counts(st)
-            blame = prog.blame_counts(st)
-            edges = prog.edges(st)
-        r = Result(s.sid, adv, int(s.samples.size), s.t_arrival, sl.t_admit, self.now(), sl.bytes, counts, blame,
-                   edges)
-        prog.unload_async(st)
-        self.used -= sl.bytes
-        sl.session = sl.prog = sl.event = None
-        sl.bytes = 0
-        return r
+        prog = sl.ctx.load_program(s.program)  # raises (nothing loaded) on a malformed program
+        try:
+            prog.reset(st)
+            if s.samples.size:
+                prog.ingest_host(s.samples, stream=st)
+            prog.blame(st)
+            prog.advise(fetch=False, stream=st)
+            code, info = prog.status(st)  # waits for the slot's stream
+            if code != 0:
+                raise RuntimeError(f"session {s.sid}: device status {code} ({info})")
+            adv = prog.get_advice(st)
+            counts = blame = edges = None
+            if self.keep_results:
+                counts, _ = prog.counts(st)
+                blame = prog.blame_counts(st)
+                edges = prog.edges(st)
+            return Result(s.sid, adv, int(s.samples.size), s.t_arrival, t_admit, self.now(), nbytes, counts, blame,
+                          edges)
+        finally:
+            prog.unload_async(st)
 
     def poll(self) -> list[Result]:
         """Collect finished sessions, then admit waiting ones (in arrival order)
         while a slot is free and the budget allows."""
-        done = [self._finish(sl) for sl in self.slots if sl.session is not None and sl.event.query()]
+        done = []
+        while True:
+            try:
+                k, r = self._done.get_nowait()
+            except queue.Empty:
+                break
+            self.slots[k].busy = False
+            if isinstance(r, BaseException):
+                raise r
+            self.used -= r.device_bytes
+            done.append(r)
         while self.pending:
-            free = [sl for sl in self.slots if sl.session is None]
+            free = [sl for sl in self.slots if not sl.busy]
             if not free:
                 break
             s = self.pending[0]
-            need = free[0].ctx.footprint(s.program)
+            if not s.need.done():
+                break
+            need = s.need.result()
             if need > self.budget:
                 raise ValueError(f"session {s.sid} needs {need} bytes, more than the whole budget")
             if self.used + need > self.budget:
                 break
             self.pending.popleft()
-            self._admit(free[0], s, need)
+            self.used += need
+            free[0].busy = True
+            free[0].jobs.put((s, self.now(), need))
         return done
 
     def close(self):
+        while self.busy():
+            self.poll()
+            time.sleep(1e-4)
         for sl in self.slots:
-            if sl.session is not None:
-                sl.stream.synchronize()
-                self._finish(sl)
+            sl.jobs.put(None)
+        for sl in self.slots:
+            sl.thread.join()
+            sl.stream.synchronize()
             sl.ctx.close()
+        self._sizer.shutdown(wait=True)
 
 
 def serve(server: Server, sessions: list[Session], arrivals: list[float], idle_sleep: float = 1e-4) -> list[Result]:
@@ -166,7 +204,7 @@ def serve(server: Server, sessions: list[Session], arrivals: list[float], idle_s
             k += 1
         got = server.poll()
         out += got
-        if not got and (k == len(order) or server.busy() == len(server.slots)):
+        if not got:
             time.sleep(idle_sleep)
     return out
 

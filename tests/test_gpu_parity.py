@@ -534,10 +534,27 @@ def test_autotune_picks_a_timed_candidate():
     ps, ns, kz = synth.workload("plain")
     P = synth.make_program(ps, kz)
     d = dev(P.samples(ns))
-    cands = [dict(hist_variant=0, small_search_nodes=64, mid_search_nodes=256, search_slots=152),
-             dict(hist_variant=1, small_search_nodes=128, mid_search_nodes=512, search_slots=304)]
-    best, table = autotune.tune(ARCH, P.arrays, d, torch.cuda.current_stream(), cands=cands, reps=1)
+    dims = [("hist_variant", (0, 1)), ("hist_chunk", (24, 8)), ("reach_schedule", (0, 1)),
+            ("search_slots_per_sm", (0, 4))]
+    best, table = autotune.tune(ARCH, P.arrays, d, torch.cuda.current_stream(), dims=dims, reps=1)
     assert best in [t[0] for t in table] and all(ms > 0 for _, ms in table)
+    assert 4 <= len(table) <= 5                       # one pass: the start and each other value once
+
+
+def test_reach_schedules_agree(ctx):
+    """The fixpoint's two schedules (a warp per function staged in shared memory, and the
+    windowed kernel with a lane per basic block for every function) give the oracle's
+    RIN/ROUT and everything after them, on programs of every size class."""
+    import paper_2009_04061_gb300 as g
+    rng = np.random.default_rng(17)
+    P = synth.make_program(synth.batched_params(30, rng, 17), 1.0)
+    s = P.samples(1_000_000, seed=17)
+    R = oracle_run(P, s)
+    for sched in (0, 1):
+        with g.Context(ARCH, dict(reach_schedule=sched)) as c:
+            assert_full_parity(gpu_run(c, P, dev(s)), R)
+    with pytest.raises(g.GpaError):
+        g.Context(ARCH, dict(reach_schedule=2))
 
 
 @pytest.mark.parametrize("which", ["rodinia", "tiny", "batched_subset"])
