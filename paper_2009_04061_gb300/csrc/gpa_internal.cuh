@@ -28,9 +28,10 @@ enum {
   SS_INVALID = 0, SS_GENERAL = 1, SS_MAX_NODES = 2, SS_SWEEPS = 3, SS_STATUS = 4,
   SS_RAW_N = 5, SS_QUEUE_N = 6, SS_QUEUE_HEAD = 7, SS_OVF_N = 8, SS_OVF_HEAD = 9, SS_OVF2_N = 10,
   SS_OVF2_HEAD = 11, SS_MAX_TASK = 12,
-  // Per-tier search phase cycles (3 tiers x 6), filled only when built with
-  // -DGPA_PHASE_TIMING: graph, distances, sources, rule 2, longest paths,
-  // and the count of rule-2 reachability runs.
+  // Per-tier search phase cycles (3 tiers x 6; the fourth tier adds to the
+  // third's), filled only when built with -DGPA_PHASE_TIMING: graph,
+  // distances, sources, rule 2, longest paths, and the count of rule-2
+  // reachability runs.
   // With -DGPA_PHASE_TIMING also: searches by log2 of their node count (16
   // slots) and the searches that needed pass B (1 slot).
   // And the slowest search: (cycles << 20 | nodes), its rule-2 runs and the
@@ -87,10 +88,10 @@ struct Prog {
   const uint8_t* func_natural;    // nf: 1 when every loop body of the function is a natural loop
                                   // (functions needing more use the global-memory fixpoint)
   // Fourth search tier, sized for this program's largest function (0 nodes:
-  // none): searches that outgrow the context's third tier.
-  int32_t t4_nodes, t4_src, t4_warps;
-  int64_t t4_bytes;               // per warp
-  char* t4_arena;                 // t4_warps * t4_bytes, global memory
+  // none): searches that outgrow the context's third tier, a CTA each.
+  int32_t t4_nodes, t4_src, t4_ctas;
+  int64_t t4_bytes;               // per CTA
+  char* t4_arena;                 // t4_ctas * t4_bytes, global memory
   const int32_t* func_instr_off;
   const int32_t* func_block_off;
   const int32_t* func_loop_off;
@@ -177,8 +178,8 @@ struct Prog {
 
 // Per-warp arenas of the general (multi-block) search.
 struct SearchArena {
-  int32_t nodes, src, layers, warps;
-  int64_t bytes;   // per warp
+  int32_t nodes, src, layers, warps;  // warps: search groups (the fourth tier's are CTAs)
+  int64_t bytes;   // per group
   char* global;    // global-memory tiers: warps * bytes
 };
 
@@ -338,7 +339,7 @@ constexpr int kLargeNodes = 1024;  // default of large_nodes
 void launch_blame(const Prog& P, const Arch& A, const SearchArena* tiers, const SearchFork* fork, int max_src,
                   int32_t* scan_tmp, cudaStream_t st, int sms, int64_t* launches);
 void launch_search(const Prog& P, const Arch& A, const SearchArena* tiers, const SearchFork* fork, cudaStream_t st,
-                   int64_t* launches);
+                   int sms, int64_t* launches);
 void launch_coverage(const Prog& P, const Arch& A, const SearchArena* tiers, const SearchFork* fork, cudaStream_t st,
                      int sms, int64_t* launches);
 int64_t search_arena_bytes(int nodes, int src, int layers);

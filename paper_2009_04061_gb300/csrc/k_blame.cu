@@ -426,7 +426,7 @@ void launch_coverage(const Prog& P, const Arch& A, const SearchArena* tiers, con
   const int g_instr = grid_for(P.ni, threads, sms);
   k_search_local<<<g_instr, threads, 0, st>>>(P, A);
   ++*launches;
-  launch_search(P, A, tiers, fork, st, launches);
+  launch_search(P, A, tiers, fork, st, sms, launches);
   k_coverage<<<g_instr, threads, 0, st>>>(P);
   ++*launches;
 }
@@ -439,7 +439,7 @@ void launch_blame(const Prog& P, const Arch& A, const SearchArena* tiers, const 
   k_blame_init<<<grid_for((int64_t)P.ni * kCnt, 256, sms), 256, 0, st>>>(P);
   k_search_local<<<g_instr, threads, 0, st>>>(P, A);
   *launches += 2;
-  launch_search(P, A, tiers, fork, st, launches);
+  launch_search(P, A, tiers, fork, st, sms, launches);
   k_merge_count<<<g_instr, threads, 0, st>>>(P, max_src);
   k_merge_big<<<sms, 32, 0, st>>>(P, max_src);
   *launches += 2;

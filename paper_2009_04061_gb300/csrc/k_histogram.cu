@@ -190,10 +190,11 @@ __global__ void __launch_bounds__(THREADS) k_histogram(Prog P, const uint64_t* _
 // flush counts as invalid samples. A vector whose two samples do not both carry
 // the window kernel's upper id bits and zero reserved bits, and any other
 // sample (another kernel, a pc outside a partial window), takes the checked
-// path: the hash, and a key that finds no slot within four probes goes to its
-// global counter. The hash is flushed when half full, and window and hash at
-// least every 2^16 tiles (fewer than 2^30 increments: no 32-bit count wraps)
-// and at the end.
+// path: the hash, and a key that finds no slot within two probes goes to its
+// global counter (measured: 1.13 ms for 5e8 samples against 1.18 with four
+// probes). The hash is flushed when half full, and window and hash at least
+// every 2^16 tiles (fewer than 2^30 increments: no 32-bit count wraps) and at
+// the end.
 constexpr int kRunThreads = 1024;
 constexpr int kRunVec = 4;                            // segments per tile: vectors per thread per tile
 constexpr int kRunTile = kRunThreads * kRunVec;       // vectors per tile (8,192 samples)
@@ -201,6 +202,7 @@ constexpr int kWinStride = 32;                        // window words per instru
 constexpr uint32_t kWinInstr = 1558;                  // instructions in the window
 constexpr int kMainWords = (int)kWinInstr * kWinStride;  // 199,424 bytes of 32-bit counters
 constexpr int kSideLog2 = 12;                         // 4,096-entry hash
+constexpr int kSideProbes = 2;                        // hash probes before the global counter
 constexpr int kRunFlushTiles = 1 << 16;               // forced flush: keeps 32-bit counts below 2^30
 static_assert((long long)kRunFlushTiles * 2 * kRunTile < (1ll << 30), "32-bit counts could wrap between flushes");
 static_assert(kMainWords % 4 == 0, "the window is read and cleared as 16-byte vectors");
@@ -310,7 +312,7 @@ __global__ void __launch_bounds__(kRunThreads, 1) k_histogram_runs(Prog P, const
       key = sample_key(x, foff, P.nf);
     }
     if (key == kNoKey) ++bad;
-    else if (!table_add<kSideLog2, 4>(skey, sval, key, 1u, side_ins)) atomicAdd(P.cnt + key, 1ull);
+    else if (!table_add<kSideLog2, kSideProbes>(skey, sval, key, 1u, side_ins)) atomicAdd(P.cnt + key, 1ull);
   };
 
   // Whole tiles go through the window; what is left (an 8-byte-aligned first

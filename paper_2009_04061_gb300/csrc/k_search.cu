@@ -2,14 +2,16 @@
 // stalled use j through resource r whose value may come from outside j's
 // block, with the three pruning rules evaluated over the set of source paths.
 //
-// One warp per (use, resource) task. The graph of (block, literal set) nodes
-// lives in a per-warp arena: shared memory for the common small searches,
-// a large global-memory arena for the few that outgrow it (same code). Lanes
-// scan node blocks in parallel through per-block event lists (defs and
-// unguarded reads, bottom-up), relax shortest distances in parallel with
-// shared-memory atomics, and check sources in parallel; lane 0 does the
-// short sequential steps (hash inserts, sorts of large lists, reachability
-// re-runs, the layered longest path) in the arena.
+// One search group per (use, resource) task: a warp in the first three tiers,
+// a whole CTA in the fourth (searches of tens of thousands to millions of
+// nodes). The graph of (block, literal set) nodes lives in the group's arena:
+// shared memory for the common small searches, global memory for the few that
+// outgrow it (same code). The group's threads scan node blocks in parallel
+// through per-block event lists (defs and unguarded reads, bottom-up), insert
+// nodes and sources into open-addressing hashes together, relax distances and
+// propagate reachability bits over frontiers with atomics, and run the
+// layered longest paths as level-synchronous frontiers; rank 0 only resets
+// counters between steps.
 //
 // Node 0 is the part of j's block above j, already scanned by the local pass
 // (its sources are settled there). A node's d is the shortest distance from
@@ -18,6 +20,8 @@
 // source farther than that fails rule 3 whatever the rest of the graph holds.
 // Only if some source is within its latency does pass B complete the graph,
 // which rule 2 and the longest paths need.
+#include <algorithm>
+
 #include "gpa_internal.cuh"
 
 namespace gpa {
@@ -74,20 +78,128 @@ __device__ __forceinline__ uint32_t node_hash(int blk, int S) {
 __device__ __forceinline__ int dist_of(const Arena& a, int u) { return (int)(a.dpk[u] >> 32); }
 __device__ __forceinline__ int par_of(const Arena& a, int u) { return (int)(a.dpk[u] & 0xFFFFFFFFull); }
 
-// Warp-wide exclusive prefix count of `pred`; returns this lane's slot and sets *total.
-__device__ __forceinline__ int warp_slot(bool pred, int* total) {
-  const unsigned m = __ballot_sync(0xffffffffu, pred);
-  *total = __popc(m);
-  return __popc(m & ((1u << (threadIdx.x & 31)) - 1u));
-}
+// The threads that run one search together: a warp (tiers 1-3) or a whole
+// CTA (the fourth tier's very large searches). Both give the search the same
+// steps: a barrier, an any-vote, exclusive prefix counts, inclusive sums and
+// reductions over the group, a read of a shared flag that every thread takes
+// before any of them may change it, and a broadcast from rank 0.
+struct WarpGroup {
+  static constexpr int kSize = 32;
+  __device__ __forceinline__ int rank() const { return threadIdx.x & 31; }
+  __device__ __forceinline__ void sync() const { __syncwarp(); }
+  __device__ __forceinline__ bool any(bool p) const { return __any_sync(0xffffffffu, p); }
+  // exclusive prefix count of `pred`: this thread's slot; *total over the group
+  __device__ __forceinline__ int slot(bool pred, int* total) const {
+    const unsigned m = __ballot_sync(0xffffffffu, pred);
+    *total = __popc(m);
+    return __popc(m & ((1u << (threadIdx.x & 31)) - 1u));
+  }
+  __device__ __forceinline__ int inclusive_sum(int x, int* total) const {
+    const int lane = threadIdx.x & 31;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    *total = __shfl_sync(0xffffffffu, x, 31);
+    return x;
+  }
+  __device__ __forceinline__ int sum(int x) const {
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    return x;
+  }
+  __device__ __forceinline__ int max(int x) const {
+    for (int o = 16; o > 0; o >>= 1) x = ::max(x, __shfl_xor_sync(0xffffffffu, x, o));
+    return x;
+  }
+  __device__ __forceinline__ int min(int x) const {
+    for (int o = 16; o > 0; o >>= 1) x = ::min(x, __shfl_xor_sync(0xffffffffu, x, o));
+    return x;
+  }
+  __device__ __forceinline__ int read(const volatile int* p) const { return *p; }
+  __device__ __forceinline__ unsigned long long broadcast(unsigned long long v) const {
+    return __shfl_sync(0xffffffffu, v, 0);
+  }
+};
+
+constexpr int kCtaThreads = 512;  // threads of a fourth-tier search CTA
+
+// A CTA as one search group. `red` is shared scratch of kCtaThreads / 32
+// ints, `cast` a shared 64-bit slot for broadcasts. Every collective ends with
+// a barrier, so the scratch is free again when it returns.
+struct CtaGroup {
+  static constexpr int kSize = kCtaThreads;
+  static constexpr int kWarps = kCtaThreads / 32;
+  int* red;
+  unsigned long long* cast;
+  __device__ __forceinline__ int rank() const { return threadIdx.x; }
+  __device__ __forceinline__ void sync() const { __syncthreads(); }
+  __device__ __forceinline__ bool any(bool p) const { return __syncthreads_or(p) != 0; }
+  // a value per warp (its last lane's) -> the sum over the warps before this
+  // thread's; *total: the sum over all warps
+  __device__ __forceinline__ int warp_offsets(int v, int* total) const {
+    const int w = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 31) red[w] = v;
+    __syncthreads();
+    int before = 0, all = 0;
+#pragma unroll
+    for (int i = 0; i < kWarps; ++i) {
+      const int c = red[i];
+      before += i < w ? c : 0;
+      all += c;
+    }
+    __syncthreads();
+    *total = all;
+    return before;
+  }
+  __device__ __forceinline__ int slot(bool pred, int* total) const {
+    const unsigned m = __ballot_sync(0xffffffffu, pred);
+    const int lane = threadIdx.x & 31;
+    return warp_offsets(__popc(m), total) + __popc(m & ((1u << lane) - 1u));
+  }
+  __device__ __forceinline__ int inclusive_sum(int x, int* total) const {
+    const int lane = threadIdx.x & 31;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    return warp_offsets(x, total) + x;
+  }
+  template <class Op>
+  __device__ __forceinline__ int reduce(int x, Op op) const {
+    for (int o = 16; o > 0; o >>= 1) x = op(x, __shfl_xor_sync(0xffffffffu, x, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = x;
+    __syncthreads();
+    int v = red[0];
+#pragma unroll
+    for (int i = 1; i < kWarps; ++i) v = op(v, red[i]);
+    __syncthreads();
+    return v;
+  }
+  __device__ __forceinline__ int sum(int x) const { return reduce(x, [](int p, int q) { return p + q; }); }
+  __device__ __forceinline__ int max(int x) const { return reduce(x, [](int p, int q) { return ::max(p, q); }); }
+  __device__ __forceinline__ int min(int x) const { return reduce(x, [](int p, int q) { return ::min(p, q); }); }
+  __device__ __forceinline__ int read(const volatile int* p) const {
+    const int v = *p;
+    __syncthreads();
+    return v;
+  }
+  __device__ __forceinline__ unsigned long long broadcast(unsigned long long v) const {
+    if (threadIdx.x == 0) *cast = v;
+    __syncthreads();
+    v = *cast;
+    __syncthreads();
+    return v;
+  }
+};
 
 // Returns false when the search outgrew the arena (nothing emitted).
 // With P.diag, the search counts the sources of (j, r) before and after
 // pruning into use entry e (`blocked`: an unguarded reader above j in its
 // block prunes them all by rule 2) and emits nothing.
-__device__ bool warp_search(const Prog& P, const Arch& A, const Arena& a, int j, int r, uint16_t S0, int bound,
-                            uint16_t live, int tier, int e = 0, bool blocked = false) {
-  const int lane = threadIdx.x & 31;
+template <class G>
+__device__ bool group_search(const G& g, const Prog& P, const Arch& A, const Arena& a, int j, int r, uint16_t S0,
+                             int bound, uint16_t live, int tier, int e = 0, bool blocked = false) {
+  const int me = g.rank();
 #ifdef GPA_PHASE_TIMING
   long long t_prev = clock64();
   const long long t_begin = t_prev;
@@ -95,9 +207,9 @@ __device__ bool warp_search(const Prog& P, const Arch& A, const Arena& a, int j,
   unsigned long long ph[5] = {0, 0, 0, 0, 0};
   unsigned long long r2runs = 0;
   auto phase = [&](int i) {
-    if (lane == 0) {
+    if (me == 0) {
       const long long t = clock64();
-      atomicAdd(&P.stats[SS_PHASE + (tier - 1) * 6 + i], (unsigned long long)(t - t_prev));
+      atomicAdd(&P.stats[SS_PHASE + (min(tier, 3) - 1) * 6 + i], (unsigned long long)(t - t_prev));
       ph[i] = (unsigned long long)(t - t_prev);
       t_prev = t;
       if (i == 4 || i == 0) {
@@ -128,14 +240,14 @@ __device__ bool warp_search(const Prog& P, const Arch& A, const Arena& a, int j,
   // both free until rule 2): ubuf holds ctr[6] of them.
   int* ubuf = a.seen;
   int* ukeep = a.tmp;
-  if (lane == 0) {
+  if (me == 0) {
     ctr[0] = 1; ctr[1] = 0; ctr[2] = 0; ctr[3] = 0; ctr[4] = 0; ctr[6] = 1;
     ubuf[0] = 0;
     S0 = keep_literals(S0, live);
     a.blk[0] = b0; a.S[0] = (int)S0 | ((int)S0 << 16); a.cov[0] = first0; a.wall[0] = -1; a.fl[0] = 0;
     a.dpk[0] = 0ull; a.k[0] = 0; a.e0[0] = 0; a.e1[0] = 0;
   }
-  __syncwarp();
+  g.sync();
 
   // Self-checks of the arena invariants before indexed accesses: an edge
   // range inside [0, edges) here, each target inside [0, nodes) where it is
@@ -212,8 +324,8 @@ __device__ bool warp_search(const Prog& P, const Arch& A, const Arena& a, int j,
   // pm: the node's predecessor record (range, first two predecessors);
   // ro0 / ro1: the reach words of those two (loaded before the scan).
   auto link_chunk = [&](const int* lst, int cnt, int4 pm, uint32_t ro0, uint32_t ro1) {
-    const bool mine = lane < cnt;
-    const int u = mine ? lst[lane] : 0;
+    const bool mine = me < cnt;
+    const int u = mine ? lst[me] : 0;
     const int B = mine ? a.blk[u] : 0;
     const int Sout = mine ? ((a.S[u] >> 16) & 0xFFFF) : 0;
     const bool open = mine && !(a.fl[u] & 4);
@@ -231,17 +343,12 @@ __device__ bool warp_search(const Prog& P, const Arch& A, const Arena& a, int j,
     };
     int deg = 0;
     for (int q = pm.x; q < pm.y; ++q) deg += reaches(q) ? 1 : 0;
-    int incl = deg;
-    for (int o = 1; o < 32; o <<= 1) {
-      const int y = __shfl_up_sync(0xffffffffu, incl, o);
-      if (lane >= o) incl += y;
-    }
-    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    int total;
+    const int incl = g.inclusive_sum(deg, &total);
     const int ne = ctr[1];
-    if (ne + total > a.E) { if (lane == 0) ctr[4] = 2; __syncwarp(); return; }
+    if (ne + total > a.E) { if (me == 0) ctr[4] = 2; g.sync(); return; }
     if (mine) { a.e0[u] = ne + incl - deg; a.e1[u] = ne + incl; }
-    int maxdeg = deg;
-    for (int o = 16; o > 0; o >>= 1) maxdeg = max(maxdeg, __shfl_xor_sync(0xffffffffu, maxdeg, o));
+    const int maxdeg = g.max(deg);
     int qp = pm.x;
     for (int kk = 0; kk < maxdeg; ++kk) {
       bool pending = kk < deg;
@@ -253,14 +360,14 @@ __device__ bool warp_search(const Prog& P, const Arch& A, const Arena& a, int j,
       uint32_t h = pending ? (node_hash(p, Sout) & hmask) : 0;
       int v = -1;
       for (int round = 0; round < 4 * (int)hmask + 64; ++round) {
-        if (!__any_sync(0xffffffffu, pending)) break;
+        if (!g.any(pending)) break;
         if (pending) {
           const int c = a.ht[h];
           if (c >= 0) {
             if (a.blk[c] == p && (a.S[c] & 0xFFFF) == Sout) { v = c; pending = false; }
             else h = (h + 1) & hmask;
           } else if (c == -1) {
-            if (atomicCAS(&a.ht[h], -1, -2 - lane) == -1) {
+            if (atomicCAS(&a.ht[h], -1, -2 - me) == -1) {
               const int nv = atomicAdd((int*)&a.ctr[0], 1);
               if (nv >= a.N) {
                 a.ctr[4] = 1; a.ht[h] = -1; pending = false;
@@ -277,23 +384,23 @@ __device__ bool warp_search(const Prog& P, const Arch& A, const Arena& a, int j,
             }
           }  // c <= -2: another lane is publishing this slot; look again next round
         }
-        __syncwarp();
+        g.sync();
       }
       if (pending) a.ctr[4] = 6;  // the round limit is a bound, not expected to be reached
       if (kk < deg && v >= 0) a.eto[a.e0[u] + kk] = v | (p >= B ? (int)kBackBit : 0);
     }
-    __syncwarp();
-    if (lane == 0) ctr[1] = ne + total;
-    __syncwarp();
+    g.sync();
+    if (me == 0) ctr[1] = ne + total;
+    g.sync();
   };
 
   // Expand every listed node: parallel scans, then parallel linking.
   auto expand_list = [&](const int* list, int cnt) {
-    for (int c0 = 0; c0 < cnt; c0 += 32) {
+    for (int c0 = 0; c0 < cnt; c0 += G::kSize) {
       int4 pm = make_int4(0, 0, -1, -1);
       uint32_t ro0 = 0u, ro1 = 0u;
-      if (c0 + lane < cnt) {
-        const int u = list[c0 + lane];
+      if (c0 + me < cnt) {
+        const int u = list[c0 + me];
         // The predecessor record and the reach words of the first two
         // predecessors are loaded first: their latency overlaps the scan.
         pm = P.block_meta[2 * (size_t)a.blk[u] + 1];
@@ -301,10 +408,10 @@ __device__ bool warp_search(const Prog& P, const Arch& A, const Arena& a, int j,
         if (pm.w >= 0) ro1 = P.rout[(size_t)pm.w * kWords + w];
         scan(u);
       }
-      __syncwarp();
+      g.sync();
       if (ctr[4]) return;
-      link_chunk(list + c0, min(32, cnt - c0), pm, ro0, ro1);
-      if (ctr[4]) return;
+      link_chunk(list + c0, min(G::kSize, cnt - c0), pm, ro0, ro1);
+      if (g.read(&ctr[4])) return;  // the next chunk's scans may set it
     }
   };
 
@@ -315,14 +422,14 @@ __device__ bool warp_search(const Prog& P, const Arch& A, const Arena& a, int j,
   auto relax_from = [&](const int* start, int cnt, int mode) {
     int* cur = a.ord;
     int* nxt = a.grp;
-    for (int t = lane; t < cnt; t += 32) cur[t] = start[t];
-    if (lane == 0) ctr[5] = 0;
-    __syncwarp();
+    for (int t = me; t < cnt; t += G::kSize) cur[t] = start[t];
+    if (me == 0) ctr[5] = 0;
+    g.sync();
     int fsize = cnt;
     while (fsize > 0) {
-      for (int f0 = 0; f0 < fsize; f0 += 32) {
-        if (f0 + lane >= fsize) continue;
-        const int u = cur[f0 + lane];
+      for (int f0 = 0; f0 < fsize; f0 += G::kSize) {
+        if (f0 + me >= fsize) continue;
+        const int u = cur[f0 + me];
         atomicAnd(&a.fl[u], ~8);
         const int n_now = ctr[0];
         if (!edges_ok(u, n_now)) continue;
@@ -348,12 +455,12 @@ __device__ bool warp_search(const Prog& P, const Arch& A, const Arena& a, int j,
           }
         }
       }
-      __syncwarp();
+      g.sync();
       fsize = ctr[5];
-      __syncwarp();
-      if (lane == 0) ctr[5] = 0;
+      g.sync();
+      if (me == 0) ctr[5] = 0;
       int* sw = cur; cur = nxt; nxt = sw;
-      __syncwarp();
+      g.sync();
     }
   };
 
@@ -371,23 +478,23 @@ __device__ bool warp_search(const Prog& P, const Arch& A, const Arena& a, int j,
   auto take_wave = [&](int lim) {
     const int m = ctr[6];
     int cnt = 0, kept = 0;
-    for (int i0 = 0; i0 < m; i0 += 32) {
-      const int i = i0 + lane;
+    for (int i0 = 0; i0 < m; i0 += G::kSize) {
+      const int i = i0 + me;
       const int u = i < m ? ubuf[i] : 0;
       const bool now = i < m && (lim < 0 ? relevant(u) : dist_of(a, u) <= lim);
       const bool keep = i < m && !now && lim >= 0;
       int tot_now, tot_keep;
-      const int at_now = warp_slot(now, &tot_now);
-      const int at_keep = warp_slot(keep, &tot_keep);
+      const int at_now = g.slot(now, &tot_now);
+      const int at_keep = g.slot(keep, &tot_keep);
       if (now) list[cnt + at_now] = u;
       if (keep) ukeep[kept + at_keep] = u;
       cnt += tot_now;
       kept += tot_keep;
     }
-    __syncwarp();
+    g.sync();
     int* sw = ubuf; ubuf = ukeep; ukeep = sw;
-    if (lane == 0) ctr[6] = kept;
-    __syncwarp();
+    if (me == 0) ctr[6] = kept;
+    g.sync();
     return cnt;
   };
 
@@ -405,16 +512,15 @@ __device__ bool warp_search(const Prog& P, const Arch& A, const Arena& a, int j,
   if (!ctr[4]) {
     const int no = min(ctr[2], a.O);
     int low = 0x7FFFFFFF;
-    for (int o = lane; o < no; o += 32) {
+    for (int o = me; o < no; o += G::kSize) {
       const int u = a.on[o];
       if (dist_of(a, u) + (last_of(u) - a.ox[o]) <= A.lat[P.opclass[a.ox[o]]]) {
         cand = true;
         low = min(low, P.block_minreach[a.blk[u]]);
       }
     }
-    cand = __any_sync(0xffffffffu, cand);
-    for (int o = 16; o > 0; o >>= 1) low = min(low, __shfl_xor_sync(0xffffffffu, low, o));
-    cand_low = low;
+    cand = g.any(cand);
+    cand_low = g.min(low);
   }
   // Pass B: complete the graph.
   if (cand) {
@@ -426,10 +532,10 @@ __device__ bool warp_search(const Prog& P, const Arch& A, const Arena& a, int j,
   }
   // Clear the hash slots this search used.
   const int nh = ctr[3];
-  for (int t = lane; t < nh; t += 32) a.ht[a.hused[t]] = -1;
-  __syncwarp();
+  for (int t = me; t < nh; t += G::kSize) a.ht[a.hused[t]] = -1;
+  g.sync();
   const int n = ctr[0];
-  if (lane == 0) {
+  if (me == 0) {
     atomicAdd(&P.stats[SS_GENERAL], 1ull);
     atomicMax(&P.stats[SS_MAX_NODES], (unsigned long long)n);
     atomicMax(&P.stats[SS_MAX_TASK], ((unsigned long long)n << 40) | ((unsigned long long)r << 31) | (unsigned)j);
@@ -440,20 +546,20 @@ __device__ bool warp_search(const Prog& P, const Arch& A, const Arena& a, int j,
   }
   phase(0);
   if (ctr[4]) {
-    if (lane == 0) ctr[7] = ctr[4];
-    __syncwarp();
+    if (me == 0) ctr[7] = ctr[4];
+    g.sync();
     return false;
   }
   if (!cand && !P.diag) return true;
 
   // Shortest distance with parents, and fewest back edges, over the whole graph.
-  for (int u = lane; u < n; u += 32) {
+  for (int u = me; u < n; u += G::kSize) {
     a.dpk[u] = u == 0 ? 0ull : (((unsigned long long)kInf << 32) | 0xFFFFFFFFull);
     a.k[u] = u == 0 ? 0 : kInf;
     a.fl[u] &= ~8;
   }
-  if (lane == 0) a.q[0] = 0;
-  __syncwarp();
+  if (me == 0) a.q[0] = 0;
+  g.sync();
   relax_from(a.q, 1, 0);
   relax_from(a.q, 1, 1);
   phase(1);
@@ -463,23 +569,23 @@ __device__ bool warp_search(const Prog& P, const Arch& A, const Arena& a, int j,
   // occurrence), atomicMin the fewest back edges, and the occurrences are
   // chained into a list.
   const int no = ctr[2];
-  if (lane == 0) { ctr[3] = 0; ctr[5] = 0; }
-  __syncwarp();
+  if (me == 0) { ctr[3] = 0; ctr[5] = 0; }
+  g.sync();
   const uint32_t smask = (uint32_t)(2 * a.SRC - 1);
-  for (int o0 = 0; o0 < no; o0 += 32) {
-    const int o = o0 + lane;
+  for (int o0 = 0; o0 < no; o0 += G::kSize) {
+    const int o = o0 + me;
     bool pending = o < no;
     const int x = pending ? a.ox[o] : -1;
     uint32_t h = pending ? (((uint32_t)x * 0x9E3779B1u) >> 7) & smask : 0;
     int m = -1;
     for (int round = 0; round < 4 * (int)smask + 64; ++round) {
-      if (!__any_sync(0xffffffffu, pending)) break;
+      if (!g.any(pending)) break;
       if (pending) {
         const int c = a.ht[h];
         if (c >= 0) {
           if (a.si[c] == x) { m = c; pending = false; } else h = (h + 1) & smask;
         } else if (c == -1) {
-          if (atomicCAS(&a.ht[h], -1, -2 - lane) == -1) {
+          if (atomicCAS(&a.ht[h], -1, -2 - me) == -1) {
             const int nm = atomicAdd((int*)&a.ctr[5], 1);
             if (nm >= a.SRC) {
               a.ctr[4] = 4; a.ht[h] = -1; pending = false;
@@ -494,7 +600,7 @@ __device__ bool warp_search(const Prog& P, const Arch& A, const Arena& a, int j,
           }
         }
       }
-      __syncwarp();
+      g.sync();
     }
     if (pending) a.ctr[4] = 6;
     if (m >= 0) {
@@ -504,31 +610,30 @@ __device__ bool warp_search(const Prog& P, const Arch& A, const Arena& a, int j,
       atomicMin(&a.sk[m], a.k[u]);
       a.onext[o] = atomicExch(&a.shead[m], o);
     }
-    __syncwarp();
+    g.sync();
   }
   {
     const int nh2 = ctr[3];
-    for (int t = lane; t < nh2; t += 32) a.ht[a.hused[t]] = -1;
+    for (int t = me; t < nh2; t += G::kSize) a.ht[a.hused[t]] = -1;
   }
-  __syncwarp();
+  g.sync();
   if (ctr[4]) {
-    if (lane == 0) ctr[7] = ctr[4];
-    __syncwarp();
+    if (me == 0) ctr[7] = ctr[4];
+    g.sync();
     return false;
   }
   const int nsrc = ctr[5];
   int alive = 0;
-  for (int m = lane; m < nsrc; m += 32) {
+  for (int m = me; m < nsrc; m += G::kSize) {
     a.sp[m] = (int)(a.sdb[m] >> 32) > A.lat[P.opclass[a.si[m]]] ? 1 : 0;  // rule 3
     if (P.diag == 1 && (blocked || !keeps_any(P, A, j, P.opclass[a.si[m]]))) a.sp[m] = 1;  // rule 2 above j, rule 1
     if (P.diag == 2) a.sp[m] = 0;  // export: rule 2 for every source
     alive += a.sp[m] ? 0 : 1;
   }
-  for (int o = 16; o > 0; o >>= 1) alive += __shfl_xor_sync(0xffffffffu, alive, o);
-  __syncwarp();
+  alive = g.sum(alive);
   phase(2);
   if (alive == 0) {
-    if (P.diag == 1 && lane == 0) cov_add(P, e, nsrc, 0);
+    if (P.diag == 1 && me == 0) cov_add(P, e, nsrc, 0);
     return true;
   }
 
@@ -536,67 +641,68 @@ __device__ bool warp_search(const Prog& P, const Arch& A, const Arena& a, int j,
   // of the positions (the unguarded reader met first from the bottom truncates
   // at least as much as any other reader of that block). A wall can only block
   // source i if it lies on the parent chain of i's nearest occurrence.
-  if (lane == 0) { ctr[3] = 0; ctr[5] = 0; }
-  __syncwarp();
-  for (int u0 = 0; u0 < n; u0 += 32) {
-    const int u = u0 + lane;
+  if (me == 0) { ctr[3] = 0; ctr[5] = 0; }
+  g.sync();
+  for (int u0 = 0; u0 < n; u0 += G::kSize) {
+    const int u = u0 + me;
     bool pending = u < n && u != 0 && a.wall[u] >= 0;
     const int B = pending ? a.blk[u] : -1;
     uint32_t h = pending ? (((uint32_t)B * 0x9E3779B1u) >> 5) & hmask : 0;
-    int g = -1;
+    int wg = -1;
     for (int round = 0; round < 4 * (int)hmask + 64; ++round) {
-      if (!__any_sync(0xffffffffu, pending)) break;
+      if (!g.any(pending)) break;
       if (pending) {
         const int c = a.ht[h];
         if (c >= 0) {
-          if (a.wblk[c] == B) { g = c; pending = false; } else h = (h + 1) & hmask;
+          if (a.wblk[c] == B) { wg = c; pending = false; } else h = (h + 1) & hmask;
         } else if (c == -1) {
-          if (atomicCAS(&a.ht[h], -1, -2 - lane) == -1) {
+          if (atomicCAS(&a.ht[h], -1, -2 - me) == -1) {
             const int ng = atomicAdd((int*)&a.ctr[5], 1);
             a.wblk[ng] = B; a.wpos[ng] = -1; a.wneed[ng] = 0;
             a.hused[atomicAdd((int*)&a.ctr[3], 1)] = (int)h;
             __threadfence_block();
             a.ht[h] = ng;
-            g = ng; pending = false;
+            wg = ng; pending = false;
           }
         }
       }
-      __syncwarp();
+      g.sync();
     }
     if (pending) a.ctr[4] = 6;
-    if (u < n) a.grp[u] = g;
-    if (g >= 0) atomicMax(&a.wpos[g], a.wall[u]);
-    __syncwarp();
+    if (u < n) a.grp[u] = wg;
+    if (wg >= 0) atomicMax(&a.wpos[wg], a.wall[u]);
+    g.sync();
   }
   {
     const int nh2 = ctr[3];
-    for (int t = lane; t < nh2; t += 32) a.ht[a.hused[t]] = -1;
+    for (int t = me; t < nh2; t += G::kSize) a.ht[a.hused[t]] = -1;
   }
-  __syncwarp();
+  g.sync();
   if (ctr[4]) {
-    if (lane == 0) ctr[7] = ctr[4];
-    __syncwarp();
+    if (me == 0) ctr[7] = ctr[4];
+    g.sync();
     return false;
   }
   const int nw = ctr[5];
-  for (int m = lane; m < nsrc; m += 32) {
+  for (int m = me; m < nsrc; m += G::kSize) {
     if (a.sp[m]) continue;
     const int o = (int)(a.sdb[m] & 0xFFFFFFFFull), u = a.on[o];
     if (u != 0 && a.wall[u] > a.ox[o]) a.wneed[a.grp[u]] = 1;
     for (int v = par_of(a, u), hops = 0; v > 0 && hops < n; v = par_of(a, v), ++hops)
       if (a.wall[v] >= 0) a.wneed[a.grp[v]] = 1;
   }
+  g.sync();
   // The needed groups, compacted into ord (free until the longest paths).
   int nl = 0;
-  for (int t0 = 0; t0 < nw; t0 += 32) {
-    const bool need = t0 + lane < nw && a.wneed[t0 + lane];
+  for (int t0 = 0; t0 < nw; t0 += G::kSize) {
+    const bool need = t0 + me < nw && a.wneed[t0 + me];
     int tot;
-    const int at = warp_slot(need, &tot);
-    if (need) a.ord[nl + at] = t0 + lane;
+    const int at = g.slot(need, &tot);
+    if (need) a.ord[nl + at] = t0 + me;
     nl += tot;
   }
-  for (int t = lane; t < nw; t += 32) a.wneed[t] = 0;
-  __syncwarp();
+  for (int t = me; t < nw; t += G::kSize) a.wneed[t] = 0;
+  g.sync();
   // Bit-parallel reachability over up to 32 groups at a time: bit b of
   // reach[u] (kept in seen) says u is reachable from the root without passing
   // the wall of the batch's b-th group. A node truncated by a group (each node
@@ -607,30 +713,30 @@ __device__ bool warp_search(const Prog& P, const Arch& A, const Arena& a, int j,
     const int nbits = min(32, nl - b0);
     const unsigned full = nbits == 32 ? 0xFFFFFFFFu : ((1u << nbits) - 1u);
 #ifdef GPA_PHASE_TIMING
-    if (lane == 0) atomicAdd(&P.stats[SS_PHASE + (tier - 1) * 6 + 5], 1ull);
+    if (me == 0) atomicAdd(&P.stats[SS_PHASE + (min(tier, 3) - 1) * 6 + 5], 1ull);
     ++r2runs;
 #endif
-    if (lane < nbits) a.wneed[a.ord[b0 + lane]] = lane + 1;
-    for (int u = lane; u < n; u += 32) reach[u] = u == 0 ? (int)full : 0;
-    __syncwarp();
+    if (me < nbits) a.wneed[a.ord[b0 + me]] = me + 1;
+    for (int u = me; u < n; u += G::kSize) reach[u] = u == 0 ? (int)full : 0;
+    g.sync();
     auto pass_mask = [&](int u) {
-      const int g = u != 0 ? a.grp[u] : -1;
-      const int b = g >= 0 ? a.wneed[g] : 0;
+      const int wg = u != 0 ? a.grp[u] : -1;
+      const int b = wg >= 0 ? a.wneed[wg] : 0;
       return b ? ~(1u << (b - 1)) : 0xFFFFFFFFu;
     };
     int* cur = a.q;
     int* nxt = a.tmp;
-    if (lane == 0) { cur[0] = 0; ctr[5] = 0; }
+    if (me == 0) { cur[0] = 0; ctr[5] = 0; }
     int fsize = 1;
-    __syncwarp();
+    g.sync();
     while (fsize > 0) {
       // Clear the queued flags of the whole frontier first: bits that arrive
       // at a frontier node during this round queue it again.
-      for (int f = lane; f < fsize; f += 32) atomicAnd(&a.fl[cur[f]], ~8);
-      __syncwarp();
-      for (int f0 = 0; f0 < fsize; f0 += 32) {
-        if (f0 + lane >= fsize) continue;
-        const int u = cur[f0 + lane];
+      for (int f = me; f < fsize; f += G::kSize) atomicAnd(&a.fl[cur[f]], ~8);
+      g.sync();
+      for (int f0 = 0; f0 < fsize; f0 += G::kSize) {
+        if (f0 + me >= fsize) continue;
+        const int u = cur[f0 + me];
         if (!edges_ok(u, n)) continue;
         const unsigned m = (unsigned)atomicOr(&reach[u], 0) & pass_mask(u);
         if (!m) continue;
@@ -643,38 +749,37 @@ __device__ bool warp_search(const Prog& P, const Arch& A, const Arena& a, int j,
           if ((old | add) != old && !(atomicOr(&a.fl[v], 8) & 8)) nxt[atomicAdd((int*)&a.ctr[5], 1)] = v;
         }
       }
-      __syncwarp();
+      g.sync();
       fsize = ctr[5];
-      __syncwarp();
-      if (lane == 0) ctr[5] = 0;
+      g.sync();
+      if (me == 0) ctr[5] = 0;
       int* sw = cur; cur = nxt; nxt = sw;
-      __syncwarp();
+      g.sync();
     }
     // A source survives the batch if, for every group, one of its occurrences
     // is reached without passing that group's wall (an occurrence above the
     // wall inside a truncated node is cut too).
     int dropped = 0;
-    for (int m = lane; m < nsrc; m += 32) {
+    for (int m = me; m < nsrc; m += G::kSize) {
       if (a.sp[m]) continue;
       unsigned ok = 0;
       for (int o = a.shead[m]; o >= 0 && (ok & full) != full; o = a.onext[o]) {
         const int u = a.on[o];
         unsigned r = (unsigned)reach[u];
-        const int g = u != 0 ? a.grp[u] : -1;
-        if (g >= 0 && a.wneed[g] && a.ox[o] < a.wpos[g]) r &= ~(1u << (a.wneed[g] - 1));
+        const int wg = u != 0 ? a.grp[u] : -1;
+        if (wg >= 0 && a.wneed[wg] && a.ox[o] < a.wpos[wg]) r &= ~(1u << (a.wneed[wg] - 1));
         ok |= r;
       }
       if ((ok & full) != full) { a.sp[m] = 1; ++dropped; }
     }
-    for (int o = 16; o > 0; o >>= 1) dropped += __shfl_xor_sync(0xffffffffu, dropped, o);
-    alive -= dropped;
-    __syncwarp();
-    if (lane < nbits) a.wneed[a.ord[b0 + lane]] = 0;
-    __syncwarp();
+    alive -= g.sum(dropped);
+    g.sync();
+    if (me < nbits) a.wneed[a.ord[b0 + me]] = 0;
+    g.sync();
   }
   phase(3);
   if (P.diag == 1) {
-    if (lane == 0) cov_add(P, e, nsrc, alive);
+    if (me == 0) cov_add(P, e, nsrc, alive);
     return true;
   }
   // The export keeps every source: sp marks the rule-2 cuts (its dom flag).
@@ -685,40 +790,40 @@ __device__ bool warp_search(const Prog& P, const Arch& A, const Arena& a, int j,
   // layer is a DAG over the forward edges, processed in topological order by
   // level-synchronous Kahn frontiers; back edges feed the next layer.
   int maxK = 0;
-  for (int m = lane; m < nsrc; m += 32) if (!a.sp[m] || every) maxK = max(maxK, a.sk[m]);
-  for (int o = 16; o > 0; o >>= 1) maxK = max(maxK, __shfl_xor_sync(0xffffffffu, maxK, o));
+  for (int m = me; m < nsrc; m += G::kSize) if (!a.sp[m] || every) maxK = max(maxK, a.sk[m]);
+  maxK = g.max(maxK);
   if (maxK >= a.L) {
-    if (lane == 0) ctr[7] = 5;
-    __syncwarp();
+    if (me == 0) ctr[7] = 5;
+    g.sync();
     return false;
   }
-  for (int t = lane; t < (maxK + 1) * n; t += 32) a.dl[(t / n) * a.N + (t % n)] = -1;
-  for (int u = lane; u < n; u += 32) a.ord[u] = 0;
-  __syncwarp();
-  for (int u = lane; u < n; u += 32)
+  for (int t = me; t < (maxK + 1) * n; t += G::kSize) a.dl[(t / n) * a.N + (t % n)] = -1;
+  for (int u = me; u < n; u += G::kSize) a.ord[u] = 0;
+  g.sync();
+  for (int u = me; u < n; u += G::kSize)
     for (int e = a.e0[u]; e < a.e1[u]; ++e)
       if (!((uint32_t)a.eto[e] >> 31)) atomicAdd(&a.ord[a.eto[e] & 0x7FFFFFFF], 1);
-  if (lane == 0) a.dl[0] = 0;
-  __syncwarp();
+  if (me == 0) a.dl[0] = 0;
+  g.sync();
   for (int l = 0; l <= maxK; ++l) {
     int* dll = a.dl + (int64_t)l * a.N;
-    if (lane == 0) ctr[5] = 0;
-    __syncwarp();
-    for (int u = lane; u < n; u += 32) {
+    if (me == 0) ctr[5] = 0;
+    g.sync();
+    for (int u = me; u < n; u += G::kSize) {
       a.seen[u] = a.ord[u];  // remaining forward in-edges
       if (a.ord[u] == 0) a.q[atomicAdd((int*)&a.ctr[5], 1)] = u;
     }
-    __syncwarp();
+    g.sync();
     int fsize = ctr[5];
     int* cur = a.q;
     int* nxt = a.tmp;
-    __syncwarp();
-    if (lane == 0) ctr[5] = 0;
-    __syncwarp();
+    g.sync();
+    if (me == 0) ctr[5] = 0;
+    g.sync();
     while (fsize > 0) {
-      for (int f0 = 0; f0 < fsize; f0 += 32) {
-        if (f0 + lane < fsize) {
-          const int u = cur[f0 + lane];
+      for (int f0 = 0; f0 < fsize; f0 += G::kSize) {
+        if (f0 + me < fsize) {
+          const int u = cur[f0 + me];
           const int cv = dll[u];
           const int nd = cv + wout(u);
           for (int e = a.e0[u]; e < a.e1[u]; ++e) {
@@ -733,15 +838,15 @@ __device__ bool warp_search(const Prog& P, const Arch& A, const Arena& a, int j,
           }
         }
       }
-      __syncwarp();
+      g.sync();
       fsize = ctr[5];
-      __syncwarp();
-      if (lane == 0) ctr[5] = 0;
+      g.sync();
+      if (me == 0) ctr[5] = 0;
       int* sw = cur; cur = nxt; nxt = sw;
-      __syncwarp();
+      g.sync();
     }
   }
-  for (int m = lane; m < nsrc; m += 32) {
+  for (int m = me; m < nsrc; m += G::kSize) {
     if (a.sp[m] && !every) continue;
     const int K = a.sk[m];
     int best = -1;
@@ -754,43 +859,23 @@ __device__ bool warp_search(const Prog& P, const Arch& A, const Arena& a, int j,
     if (every) xemit(P, j, a.si[m], r, (int)(a.sdb[m] >> 32), K, best, a.sp[m] || blocked);
     else emit_raw(P, A, j, a.si[m], r, def_kind(P, a.si[m], r), (int)(a.sdb[m] >> 32), best);
   }
-  __syncwarp();
+  g.sync();
   phase(4);
   return true;
 }
 
-// Persistent work-stealing warps over one queue. Tiers 1 and 2 keep the arena
-// in shared memory (tier 1: several warps per CTA, small arenas; tier 2: one
-// warp per CTA, a large arena); tier 3 uses global-memory arenas. A search that
-// outgrows its tier is queued for the next one. Tier 3 runs in two parts:
-// part 1 takes the searches queued straight for it (the large list first)
-// and may run beside tiers 1 and 2; part 2 takes the second tier's overflow.
-// Registers: at least six 128-thread CTAs per SM, i.e. 80 registers a thread
-// (96 without the bound). The first tier and the third tier's hinted part run
-// side by side and together fill the SM's registers, so fewer registers a warp
-// keep more warps in flight (measured: 40.7 against 41.9 ms a step).
-#ifndef GPA_SEARCH_MIN_CTAS
-#define GPA_SEARCH_MIN_CTAS 6
-#endif
-__global__ void __launch_bounds__(kWarpsPerCta * 32, GPA_SEARCH_MIN_CTAS)
-    k_search_warp(Prog P, Arch A, SearchArena SA, int tier, int part) {
-  extern __shared__ __align__(16) char smem[];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const int gw = blockIdx.x * (blockDim.x >> 5) + wid;
-  char* base = tier < 3 ? smem + (int64_t)wid * SA.bytes : SA.global + (int64_t)gw * SA.bytes;
-  // The search counters live in shared memory in every tier (the arena of
-  // tier 3 is in global memory): frontier sizes are read after every round.
-  __shared__ int s_ctr[kWarpsPerCta][8];
-  const Arena a = carve(base, SA.nodes, SA.src, SA.layers, s_ctr[wid]);
-  for (int t = lane; t < 2 * SA.nodes; t += 32) a.ht[t] = -1;
-  __syncwarp();
+// The task loop of a search group: claim (use, resource) tasks from one
+// queue until it is empty. Tier 1 reads the local pass's queue; tier 2 the
+// first overflow queue; tier 3 part 1 the large list and the region at the top
+// of the first queue, part 2 the second overflow, which reuses the first
+// queue's storage; tier 4 the third overflow (bottom of the first overflow
+// queue's storage) and its top region. A search that outgrows its tier is
+// queued for the next one; the last tier records why it ran out.
+template <class G>
+__device__ void run_tasks(const G& g, const Prog& P, const Arch& A, const Arena& a, int tier, int part) {
+  const int me = g.rank();
   // The tasks of this launch, in order: nl of the large list, n0 read up
   // from the bottom of q0, n1 read down from the top of q1.
-  // Tier 1 reads the local pass's queue; tier 2 the first overflow queue;
-  // tier 3 part 1 the large list and the region at the top of the first
-  // queue, part 2 the second overflow, which reuses the first queue's
-  // storage; tier 4 the third overflow (bottom of the first overflow queue's
-  // storage) and its top region.
   const unsigned long long cap = (unsigned long long)P.queue_cap;
   const int4* q0 = P.queue;
   const int4* q1 = P.queue;
@@ -812,8 +897,8 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, GPA_SEARCH_MIN_CTAS)
   n1 = min(n1, cap - n0);
   while (true) {
     unsigned long long t = 0;
-    if (lane == 0) t = atomicAdd(&P.stats[h_slot], 1ull);
-    t = __shfl_sync(0xffffffffu, t, 0);
+    if (me == 0) t = atomicAdd(&P.stats[h_slot], 1ull);
+    t = g.broadcast(t);
     if (t >= nl + n0 + n1) break;
     const int4 task = t < nl        ? P.large_queue[t]
                       : t < nl + n0 ? q0[t - nl]
@@ -822,14 +907,14 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, GPA_SEARCH_MIN_CTAS)
     // The coverage count needs every source: no latency bound.
     const int bound = P.diag ? kInf - 1 : P.res_maxlat[(size_t)f * kNumRes + task.y];
     const uint16_t live = live_literals(P.res_guards[(size_t)f * kNumRes + task.y], P.guard[task.x]);
-    const bool ok = warp_search(P, A, a, task.x, task.y, (uint16_t)task.z, bound, live, tier, task.w,
-                                (task.z >> 20) & 1);
+    const bool ok = group_search(g, P, A, a, task.x, task.y, (uint16_t)task.z, bound, live, tier, task.w,
+                                 (task.z >> 20) & 1);
     if (ok) {
       // later steps start a large third-tier search before the others
-      if (lane == 0 && tier >= 3 && !P.diag && ((volatile int*)a.ctr)[0] >= P.large_nodes) P.large_hint[task.w] = 1;
+      if (me == 0 && tier == 3 && !P.diag && ((volatile int*)a.ctr)[0] >= P.large_nodes) P.large_hint[task.w] = 1;
       continue;
     }
-    if (lane != 0) continue;
+    if (me != 0) continue;
     if (!P.diag) atomicMax(&P.tier_hint[task.w], (unsigned)(tier + 1));  // later steps queue it for a bigger tier
     if (tier < 3 || (tier == 3 && P.t4_nodes > 0)) {
       // tier 1 -> bottom of ovf_queue; tier 2 -> bottom of queue; tier 3 part 2
@@ -841,9 +926,52 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, GPA_SEARCH_MIN_CTAS)
       const unsigned long long o = atomicAdd(&P.stats[o_slot], 1ull);
       if (o < cap) oq[top ? cap - 1 - o : o] = task; else capacity(P, 8);
     } else {
-      capacity(P, s_ctr[wid][7] > 0 ? s_ctr[wid][7] : 1);  // the last tier: why it ran out
+      capacity(P, a.ctr[7] > 0 ? a.ctr[7] : 1);  // the last tier: why it ran out
     }
   }
+}
+
+// Persistent work-stealing warps, one search each. Tiers 1 and 2 keep the
+// arena in shared memory (tier 1: several warps per CTA, small arenas; tier 2:
+// one warp per CTA, a large arena); tier 3 uses global-memory arenas. Tier 3
+// runs in two parts: part 1 takes the searches queued straight for it (the
+// large list first) and may run beside tiers 1 and 2; part 2 takes the second
+// tier's overflow.
+// Registers: at least six 128-thread CTAs per SM, i.e. 80 registers a thread
+// (96 without the bound). The first tier and the third tier's hinted part run
+// side by side and together fill the SM's registers, so fewer registers a warp
+// keep more warps in flight (measured: 40.7 against 41.9 ms a step).
+#ifndef GPA_SEARCH_MIN_CTAS
+#define GPA_SEARCH_MIN_CTAS 6
+#endif
+__global__ void __launch_bounds__(kWarpsPerCta * 32, GPA_SEARCH_MIN_CTAS)
+    k_search_warp(Prog P, Arch A, SearchArena SA, int tier, int part) {
+  extern __shared__ __align__(16) char smem[];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int gw = blockIdx.x * (blockDim.x >> 5) + wid;
+  char* base = tier < 3 ? smem + (int64_t)wid * SA.bytes : SA.global + (int64_t)gw * SA.bytes;
+  // The search counters live in shared memory in every tier (the arena of
+  // tier 3 is in global memory): frontier sizes are read after every round.
+  __shared__ int s_ctr[kWarpsPerCta][8];
+  const Arena a = carve(base, SA.nodes, SA.src, SA.layers, s_ctr[wid]);
+  for (int t = lane; t < 2 * SA.nodes; t += 32) a.ht[t] = -1;
+  __syncwarp();
+  run_tasks(WarpGroup{}, P, A, a, tier, part);
+}
+
+// The fourth tier: a CTA per search, over a global-memory arena of its own
+// (the searches that outgrow the third tier's arenas have tens of thousands to
+// millions of (block, literal set) nodes: their waves, frontiers and source
+// lists are wide enough for a CTA's threads).
+__global__ void __launch_bounds__(kCtaThreads, 1) k_search_cta(Prog P, Arch A, SearchArena SA) {
+  __shared__ int s_ctr[8];
+  __shared__ int s_red[CtaGroup::kWarps];
+  __shared__ unsigned long long s_cast;
+  const CtaGroup g{s_red, &s_cast};
+  const Arena a = carve(SA.global + (int64_t)blockIdx.x * SA.bytes, SA.nodes, SA.src, SA.layers, s_ctr);
+  for (int t = threadIdx.x; t < 2 * SA.nodes; t += kCtaThreads) a.ht[t] = -1;
+  __syncthreads();
+  run_tasks(g, P, A, a, 4, 0);
 }
 
 }  // namespace
@@ -857,7 +985,7 @@ int search_warps_per_sm() {
 }
 
 void launch_search(const Prog& P, const Arch& A, const SearchArena* tiers, const SearchFork* fork, cudaStream_t st,
-                   int64_t* launches) {
+                   int sms, int64_t* launches) {
   // Each launch requests its own tier's arena size.
   const size_t smem1 = (size_t)tiers[0].bytes * kWarpsPerCta;
   const size_t smem2 = (size_t)tiers[1].bytes;
@@ -882,8 +1010,16 @@ void launch_search(const Prog& P, const Arch& A, const SearchArena* tiers, const
   k_search_warp<<<tiers[2].warps, 32, 0, st>>>(P, A, tiers[2], 3, 2);
   *launches += 4;
   if (P.t4_nodes > 0) {
-    SearchArena t4{P.t4_nodes, P.t4_src, kMaxLayers, P.t4_warps, P.t4_bytes, P.t4_arena};
-    k_search_warp<<<P.t4_warps, 32, 0, st>>>(P, A, t4, 4, 0);
+    // The fourth tier runs after the third on this stream, so the third tier's
+    // arena pool is free by then: when it holds more fourth-tier arenas than the
+    // program's own, the CTAs carve theirs from it (at most one CTA per SM).
+    SearchArena t4{P.t4_nodes, P.t4_src, kMaxLayers, P.t4_ctas, P.t4_bytes, P.t4_arena};
+    const int64_t in_pool = (int64_t)tiers[2].warps * tiers[2].bytes / P.t4_bytes;
+    if (in_pool > t4.warps && tiers[2].global) {
+      t4.warps = (int)std::min<int64_t>(in_pool, std::max(sms, 1));
+      t4.global = tiers[2].global;
+    }
+    k_search_cta<<<t4.warps, kCtaThreads, 0, st>>>(P, A, t4);
     ++*launches;
   }
 }

@@ -561,19 +561,19 @@ static gpa_status alloc_program(const gpa_program_desc* d, ProgramRec* R, int ti
   P.sm = SmModel{};
   // Fourth search tier: room for 64 literal sets per block of the largest
   // function (at most 2^22 nodes), when that is more than the context's
-  // third tier holds; fewer warps for bigger arenas (about 2 GB at most).
+  // third tier holds; fewer CTAs for bigger arenas (about 2 GB at most).
   {
     int64_t mb = 1;
     for (int f = 0; f < d->n_functions; ++f) mb = std::max<int64_t>(mb, d->func_block_off[f + 1] - d->func_block_off[f]);
     int64_t n4 = 2;
     while (n4 < 64 * mb && n4 < ((int64_t)1 << 22)) n4 <<= 1;
-    P.t4_nodes = 0; P.t4_arena = nullptr; P.t4_bytes = 0; P.t4_warps = 0; P.t4_src = 0;
+    P.t4_nodes = 0; P.t4_arena = nullptr; P.t4_bytes = 0; P.t4_ctas = 0; P.t4_src = 0;
     if (n4 > tier3_nodes) {
       P.t4_nodes = (int32_t)n4;
       P.t4_src = (int32_t)std::min<int64_t>(n4, 4096);
-      P.t4_warps = n4 <= ((int64_t)1 << 18) ? 16 : n4 <= ((int64_t)1 << 20) ? 8 : 4;
+      P.t4_ctas = n4 <= ((int64_t)1 << 18) ? 16 : n4 <= ((int64_t)1 << 20) ? 8 : 4;
       P.t4_bytes = search_arena_bytes(P.t4_nodes, P.t4_src, kMaxLayers);
-      TRY(dev_alloc(R, &P.t4_arena, (size_t)P.t4_bytes * P.t4_warps));
+      TRY(dev_alloc(R, &P.t4_arena, (size_t)P.t4_bytes * P.t4_ctas));
     }
   }
 #undef TRY
@@ -629,7 +629,7 @@ gpa_status gpa_load_program(gpa_ctx* ctx, const gpa_program_desc* d, gpa_pid* ou
     free_program(R);
     return GPA_ERR_CUDA;
   }
-  if (P.t4_arena && cudaMemsetAsync(P.t4_arena, 0, (size_t)P.t4_bytes * P.t4_warps, st) != cudaSuccess) {
+  if (P.t4_arena && cudaMemsetAsync(P.t4_arena, 0, (size_t)P.t4_bytes * P.t4_ctas, st) != cudaSuccess) {
     free_program(R);
     return GPA_ERR_CUDA;
   }
