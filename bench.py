@@ -12,6 +12,9 @@ no L2 flush is needed between steps).
   value  blamed PC samples/s with samples and program resident in HBM
   e2e    the same through the C ABI from pinned host memory: host->device copy
          of the samples inside the timed region, advice copied back to the host
+The default run also records, at one GPU, the serving workload (p50/p99
+ingest-to-advice latency) and the large stress kernel (one function of 200,000
+instructions, 1e9 samples streamed from pinned host memory every step).
 Prints one JSON line on rank 0. Under torchrun every rank processes its own
 batch (seeded by rank) on its own GPU with no data-path collective (weak scaling).
 `--impl reference` times the CPU oracle on a bounded sample of the same workload.
@@ -59,6 +62,9 @@ def parse():
     ap.add_argument("--sessions", type=int, default=200, help="serving: sessions")
     ap.add_argument("--serving-sessions", type=int, default=100,
                     help="sessions of the serving record in the default run (0 to skip)")
+    ap.add_argument("--large-samples", type=int, default=1_000_000_000,
+                    help="samples of the large stress kernel's record in the default run, streamed from "
+                         "pinned host memory (0 to skip)")
     ap.add_argument("--rate", type=float, default=200.0, help="serving: mean arrivals per second")
     ap.add_argument("--slots", type=int, default=8, help="serving: concurrent sessions")
     ap.add_argument("--budget-gb", type=float, default=64.0, help="serving: device-memory admission budget")
@@ -305,6 +311,67 @@ def pinned_h2d_gbs(host, dev, nbytes: int = 1 << 31) -> float:
         best = max(best, 8 * m / (e0.elapsed_time(e1) / 1e3) / 1e9)
     del dst
     return best
+
+
+def large_measure(a, gpa, dev, steps: int = 3) -> dict:
+    """The large stress kernel (one function of 200,000 instructions) at its full
+    sample count, streamed from pinned host memory through the C ABI every step
+    (the aggregation kernel reads the pinned buffer over the host link): the
+    step time (ingest, blame, advice copied out), the cold first step, and the
+    ingest rate against a plain pinned host-to-device copy."""
+    import torch
+    P, arrays, n = make_workload("large", a.seed, a.large_samples)
+    t0 = time.perf_counter()
+    host = torch.empty(n, dtype=torch.int64).pin_memory()
+    P.samples(n, seed=a.seed, out=host.numpy().view(np.uint64))
+    gen_s = time.perf_counter() - t0
+    stream = torch.cuda.current_stream(dev)
+    with gpa.Context(synth.default_arch()) as ctx:
+        prog = ctx.load_program(arrays)
+        try:
+            def step():
+                prog.reset(stream)
+                prog.ingest_host(host, stream=stream)
+                prog.blame(stream)
+                return prog.advise(fetch=True, stream=stream)  # synchronizes the stream
+
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            step()
+            cold_ms = (time.perf_counter() - t0) * 1e3
+            step()
+            st, info = prog.status(stream)
+            if st != 0:
+                raise SystemExit(f"large workload: device status {st}: {info}")
+            cnt, bad = prog.counts(stream)
+            assert int(cnt.sum()) + bad == n, "large workload: counts do not add up"
+            times = []
+            for _ in range(steps):
+                t0 = time.perf_counter()
+                adv = step()
+                times.append((time.perf_counter() - t0) * 1e3)
+            d2h = sum(v.nbytes for v in adv.values())
+            e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            prog.reset(stream)
+            e[0].record(stream)
+            prog.ingest_host(host, stream=stream)
+            e[1].record(stream)
+            prog.blame(stream)
+            e[2].record(stream)
+            torch.cuda.synchronize(dev)
+            ingest_ms, blame_ms = e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2])
+        finally:
+            prog.unload()
+    h2d = pinned_h2d_gbs(host, dev)
+    ms = statistics.median(times)
+    ingest_gbs = 8 * n / (ingest_ms / 1e3) / 1e9
+    return {"workload": "large", "functions": P.n_functions, "instructions": P.n_instr, "blocks": P.n_blocks,
+            "samples": n, "sample_bytes": 8 * n, "source": "pinned host memory, read over the host link each step",
+            "ms_per_step": ms, "samples_per_s": n / (ms / 1e3), "cold_first_step_ms": cold_ms,
+            "ingest_ms": ingest_ms, "blame_ms": blame_ms, "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": d2h,
+            "host_link": {"ingest_gbs": ingest_gbs, "pinned_h2d_gbs": h2d, "frac": ingest_gbs / h2d},
+            "general_searches": info["general_searches"], "largest_search_nodes": info["max_nodes"],
+            "generate_s": gen_s}
 
 
 def run_oracle_once(P, sub, k_funcs, threads: int = 1):
@@ -579,6 +646,15 @@ def main():
         del d
         torch.cuda.empty_cache()
         serving = serving_measure(a, gpa, dev, a.serving_sessions)
+    large = None
+    if rank == 0 and world == 1 and a.large_samples > 0 and a.workload != "large":
+        if prog is not None:
+            prog.unload()
+            ctx.close()
+            prog = ctx = None
+            del d
+            torch.cuda.empty_cache()
+        large = large_measure(a, gpa, dev)
 
     if rank == 0:
         line = {
@@ -599,6 +675,7 @@ def main():
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
             "batched_vs_plain": bvp, "autotune": tuned, "options": opts, "dependency_coverage": coverage,
             "parallel_optimizers": parallel, "cold_first_step": cold_step, "serving": serving,
+            "large_stress_kernel": large,
         }
         print(json.dumps(line), flush=True)
     if prog is not None:
