@@ -158,7 +158,8 @@ typedef struct {
  *                                 the program (as in one shard of a larger one) has site -1
  *                                 (called from elsewhere) or callee -1 (calls elsewhere), not
  *                                 both. Sites ascend: -1 entries first, the others distinct.
- * Limits: n_functions < 65536, instructions per function < 2^24. */
+ * Limits: n_functions < 65536, instructions per function < 2^24, instructions per block
+ * < 65536, n_instr * 24 < 2^32, n_blocks * 16 < 2^31 - 1, n_def + n_use < 2^31 - 1. */
 typedef struct {
   int32_t n_functions, n_instr, n_blocks, n_loops, n_lines;
   int32_t n_succ, n_def, n_use;

@@ -12,6 +12,8 @@ constexpr int kNumRes = 268;     // R0..R254, P0..P6, B0..B5
 constexpr int kPredBase = 255;
 constexpr int kBarBase = 262;
 constexpr int kWords = 9;        // 268 bits in 32-bit words
+constexpr int kEvBuckets = 16;   // event segments per block: resources by r mod 16
+__host__ __device__ inline int ev_bucket(int r) { return r & (kEvBuckets - 1); }
 constexpr int kCnt = 24;         // counters per instruction: class * 2 + latency flag
 constexpr uint16_t kAllLits = 0xFFFF;
 constexpr int kMaxLayers = 8;    // back-edge layers for longest paths (K <= 7)
@@ -119,9 +121,10 @@ struct Prog {
   const int4* block_meta;         // 2 per block: {first instr, end instr, first event, end event},
                                   // {first pred, end pred, first two predecessors or -1} (one
                                   // 32-byte line for the searches)
-  const int32_t* ev_off;          // nb + 1: per-block event lists
-  const uint32_t* events;         // defs and unguarded reads, bottom-up: resource | def << 9 |
-                                  // kind << 10 | guard << 12 | position in block << 16
+  const int32_t* ev_off;          // nb * 16 + 1: event segments of (block, resource bucket)
+  const uint32_t* events;         // per segment, the defs and unguarded reads of the bucket's
+                                  // resources, bottom-up: resource | def << 9 | kind << 10 |
+                                  // guard << 12 | position in block << 16
   // step state
   unsigned long long* cnt;        // ni * 24
   unsigned long long* stats;      // SS_N

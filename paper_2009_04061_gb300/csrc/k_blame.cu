@@ -53,8 +53,9 @@ __device__ bool scan_pred(const Prog& P, const Arch& A, int j, int r, int gj, in
   const int first = P.block_instr_off[p], last = P.block_instr_off[p + 1] - 1;
   bool wall = false;
   int last_def_pos = -1;
-  const int ev1 = P.ev_off[p + 1];
-  for (int t = P.ev_off[p]; t < ev1; ++t) {
+  const size_t seg = (size_t)p * kEvBuckets + ev_bucket(r);  // p's events of r's bucket
+  const int ev1 = P.ev_off[seg + 1];
+  for (int t = P.ev_off[seg]; t < ev1; ++t) {
     const uint32_t ev = P.events[t];
     if ((int)(ev & 0x1FFu) != r) continue;
     const int pos = (int)(ev >> 16), x = first + pos;
@@ -86,9 +87,10 @@ __global__ void k_search_local(Prog P, Arch A) {
     const int b0 = P.instr_block[j];
     const int first = P.block_instr_off[b0];
     const int pj = j - first;
-    const int ev0 = P.ev_off[b0], ev1 = P.ev_off[b0 + 1];
     for (int e = P.use_off[j]; e < P.use_off[j + 1]; ++e) {
       const int r = P.use_res[e] & 0x1FF;
+      const size_t seg = (size_t)b0 * kEvBuckets + ev_bucket(r);  // b0's events of r's bucket
+      const int ev0 = P.ev_off[seg], ev1 = P.ev_off[seg + 1];
       uint16_t S = 0;
       bool blocked = false, covered = false;
       int last_def_pos = -1;

@@ -35,7 +35,7 @@ constexpr int kWarpsPerCta = 4;
 
 struct Arena {
   int N, E, O, SRC, L;
-  int *blk, *S, *cov, *wall, *k, *e0, *e1, *fl, *seen, *ord, *tmp, *grp, *q;  // per node
+  int *blk, *S, *wall, *k, *e0, *e1, *fl, *seen, *ord, *tmp, *grp, *q;  // per node
   unsigned long long* dpk;  // (shortest distance << 32) | parent node
   unsigned long long* sdb;  // per source: (shortest distance << 32) | nearest occurrence
   int *dl, *ht, *hused, *eto, *on, *ox, *onext;
@@ -46,7 +46,7 @@ struct Arena {
 
 __host__ __device__ inline int64_t arena_bytes(int N, int SRC, int L) {
   const int64_t E = 2 * (int64_t)N, O = N;
-  int64_t ints = 13 * (int64_t)N + (int64_t)L * N + 2 * (int64_t)N + N + E + 3 * O + 3 * (int64_t)N + 4 * (int64_t)SRC + 8;
+  int64_t ints = 12 * (int64_t)N + (int64_t)L * N + 2 * (int64_t)N + N + E + 3 * O + 3 * (int64_t)N + 4 * (int64_t)SRC + 8;
   return 8 * (int64_t)N + 8 * (int64_t)SRC + ((ints * 4 + 15) & ~(int64_t)15);
 }
 
@@ -56,8 +56,8 @@ __device__ Arena carve(char* base, int N, int SRC, int L, int* ctr) {
   a.dpk = reinterpret_cast<unsigned long long*>(base);
   a.sdb = a.dpk + N;
   int* p = reinterpret_cast<int*>(base + 8 * (int64_t)N + 8 * (int64_t)SRC);
-  int** node_arrays[13] = {&a.blk, &a.S, &a.cov, &a.wall, &a.k, &a.e0, &a.e1, &a.fl, &a.seen, &a.ord, &a.tmp, &a.grp, &a.q};
-  for (int t = 0; t < 13; ++t) { *node_arrays[t] = p; p += N; }
+  int** node_arrays[12] = {&a.blk, &a.S, &a.wall, &a.k, &a.e0, &a.e1, &a.fl, &a.seen, &a.ord, &a.tmp, &a.grp, &a.q};
+  for (int t = 0; t < 12; ++t) { *node_arrays[t] = p; p += N; }
   a.dl = p; p += (int64_t)L * N;
   a.ht = p; p += 2 * N;
   a.hused = p; p += N;
@@ -244,7 +244,7 @@ __device__ bool group_search(const G& g, const Prog& P, const Arch& A, const Are
     ctr[0] = 1; ctr[1] = 0; ctr[2] = 0; ctr[3] = 0; ctr[4] = 0; ctr[6] = 1;
     ubuf[0] = 0;
     S0 = keep_literals(S0, live);
-    a.blk[0] = b0; a.S[0] = (int)S0 | ((int)S0 << 16); a.cov[0] = first0; a.wall[0] = -1; a.fl[0] = 0;
+    a.blk[0] = b0; a.S[0] = (int)S0 | ((int)S0 << 16); a.wall[0] = -1; a.fl[0] = 0;
     a.dpk[0] = 0ull; a.k[0] = 0; a.e0[0] = 0; a.e1[0] = 0;
   }
   g.sync();
@@ -270,26 +270,28 @@ __device__ bool group_search(const G& g, const Prog& P, const Arch& A, const Are
   };
   auto last_of = [&](int u) { return P.block_meta[2 * (size_t)a.blk[u]].y - 1; };
 
-  // Scan node u's block bottom-up through its event list (one lane). Records
-  // occurrences, the literal set leaving the top, the covering position and
-  // the first unguarded reader of r met (the wall). Sets a.fl[u] bit 2 if the
-  // scan stopped (covered).
+  // Scan node u's block bottom-up through its events of r's bucket (one
+  // thread). Records occurrences, the literal set leaving the top and the first
+  // unguarded reader of r met (the wall). Sets a.fl[u] bit 2 if the scan
+  // stopped (covered).
   auto scan = [&](int u) {
     uint16_t S = (uint16_t)(a.S[u] & 0xFFFF);
     bool stop = false;
     if (u != 0) {
       const int B = a.blk[u];
-      const int4 m = P.block_meta[2 * (size_t)B];
-      const int first = m.x;
-      int cov = first, wall = -1;
-      if (P.touch_mask[(size_t)B * kWords + w] & bit) {
+      const int first = __ldg(&P.block_meta[2 * (size_t)B].x);
+      int wall = -1;
+      if (__ldg(&P.touch_mask[(size_t)B * kWords + w]) & bit) {
+        // only the events of r's bucket
+        const size_t seg = (size_t)B * kEvBuckets + ev_bucket(r);
+        const int ev_beg = __ldg(&P.ev_off[seg]), ev_end = __ldg(&P.ev_off[seg + 1]);
         int last_def_pos = -1;
         // Events four at a time: independent read-only loads in flight together
         // (a sentinel resource 511 pads the last group).
-        for (int e0 = m.z; e0 < m.w && !stop; e0 += 4) {
+        for (int e0 = ev_beg; e0 < ev_end && !stop; e0 += 4) {
           uint32_t evs[4];
 #pragma unroll
-          for (int q = 0; q < 4; ++q) evs[q] = e0 + q < m.w ? __ldg(&P.events[e0 + q]) : 0x1FFu;
+          for (int q = 0; q < 4; ++q) evs[q] = e0 + q < ev_end ? __ldg(&P.events[e0 + q]) : 0x1FFu;
 #pragma unroll
           for (int q = 0; q < 4; ++q) {
             const uint32_t ev = evs[q];
@@ -302,14 +304,13 @@ __device__ bool group_search(const G& g, const Prog& P, const Arch& A, const Are
                 if (o < a.O) { a.on[o] = u; a.ox[o] = x; } else { a.ctr[4] = 3; }
               }
               S = add_literal(S, (int)((ev >> 12) & 0xFu));
-              if (contains(S, gj)) { stop = true; cov = x; }
+              if (contains(S, gj)) stop = true;
             } else if (wall < 0 && pos != last_def_pos && x != j) {  // unguarded reader of r
               wall = x;
             }
           }
         }
       }
-      a.cov[u] = cov;
       a.wall[u] = wall;
     }
     a.S[u] = (a.S[u] & 0xFFFF) | ((int)keep_literals(S, live) << 16);
@@ -372,7 +373,7 @@ __device__ bool group_search(const G& g, const Prog& P, const Arch& A, const Are
               if (nv >= a.N) {
                 a.ctr[4] = 1; a.ht[h] = -1; pending = false;
               } else {
-                a.blk[nv] = p; a.S[nv] = Sout; a.wall[nv] = -1; a.cov[nv] = 0; a.fl[nv] = 0; a.k[nv] = kInf;
+                a.blk[nv] = p; a.S[nv] = Sout; a.wall[nv] = -1; a.fl[nv] = 0; a.k[nv] = kInf;
                 a.e0[nv] = 0; a.e1[nv] = 0;  // no out-edges until the node is expanded
                 a.dpk[nv] = ((unsigned long long)kInf << 32) | 0xFFFFFFFFull;
                 a.hused[atomicAdd((int*)&a.ctr[3], 1)] = (int)h;

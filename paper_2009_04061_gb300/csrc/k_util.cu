@@ -103,32 +103,43 @@ __global__ void k_loop_depth(Prog P) {
   }
 }
 
-// Per-block event lists for the backward scans: for each instruction from the
-// last to the first, its defs (with kind and guard) and, if unguarded, its reads.
+// Event lists for the backward scans, one segment per (block, resource bucket
+// k = ev_bucket(r)): for each instruction of the block from the last to the
+// first, its defs of the bucket's resources (with kind and guard) and, if
+// unguarded, its reads of them. A scan for resource r reads only its bucket's
+// segment (about 2.6 events on the batched workload, against 21.5 for the
+// whole block); the events of r appear in it in the order of a bottom-up walk
+// of the block (an instruction's defs before its reads). ev_off is the CSR over
+// (block, bucket) pairs: segment (b, k) is [ev_off[b * 16 + k], ev_off[b * 16 + k + 1]).
 __global__ void k_ev_count(Prog P, int32_t* cnt) {
   for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < P.nb; b += gridDim.x * blockDim.x) {
-    int c = 0;
+    int c[kEvBuckets] = {};
     for (int x = P.block_instr_off[b]; x < P.block_instr_off[b + 1]; ++x) {
-      c += P.def_off[x + 1] - P.def_off[x];
-      if (P.guard[x] == 0) c += P.use_off[x + 1] - P.use_off[x];
+      for (int e = P.def_off[x]; e < P.def_off[x + 1]; ++e) ++c[ev_bucket(P.def_res[e] & 0x1FF)];
+      if (P.guard[x] == 0)
+        for (int e = P.use_off[x]; e < P.use_off[x + 1]; ++e) ++c[ev_bucket(P.use_res[e] & 0x1FF)];
     }
-    cnt[b] = c;
+    for (int k = 0; k < kEvBuckets; ++k) cnt[(size_t)b * kEvBuckets + k] = c[k];
   }
 }
 
 __global__ void k_ev_fill(Prog P, const int32_t* ev_off, uint32_t* events) {
   for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < P.nb; b += gridDim.x * blockDim.x) {
     const int first = P.block_instr_off[b];
-    int o = ev_off[b];
-    for (int x = P.block_instr_off[b + 1] - 1; x >= first; --x) {
-      const uint32_t pos = (uint32_t)(x - first) << 16;
-      const uint32_t g = P.guard[x];
-      for (int e = P.def_off[x]; e < P.def_off[x + 1]; ++e) {
-        const uint32_t v = P.def_res[e];
-        events[o++] = (v & 0x1FFu) | 0x200u | (((v >> 12) & 3u) << 10) | (g << 12) | pos;
+    for (int k = 0; k < kEvBuckets; ++k) {
+      int o = ev_off[(size_t)b * kEvBuckets + k];
+      const int o_end = ev_off[(size_t)b * kEvBuckets + k + 1];
+      for (int x = P.block_instr_off[b + 1] - 1; x >= first && o < o_end; --x) {
+        const uint32_t pos = (uint32_t)(x - first) << 16;
+        const uint32_t g = P.guard[x];
+        for (int e = P.def_off[x]; e < P.def_off[x + 1]; ++e) {
+          const uint32_t v = P.def_res[e];
+          if (ev_bucket(v & 0x1FFu) == k) events[o++] = (v & 0x1FFu) | 0x200u | (((v >> 12) & 3u) << 10) | (g << 12) | pos;
+        }
+        if (g == 0)
+          for (int e = P.use_off[x]; e < P.use_off[x + 1]; ++e)
+            if (ev_bucket(P.use_res[e] & 0x1FFu) == k) events[o++] = (P.use_res[e] & 0x1FFu) | pos;
       }
-      if (g == 0)
-        for (int e = P.use_off[x]; e < P.use_off[x + 1]; ++e) events[o++] = (P.use_res[e] & 0x1FFu) | pos;
     }
   }
 }
@@ -139,14 +150,15 @@ void launch_build_events(const Prog& P, int32_t* ev_off, uint32_t* events, int32
                          int64_t* launches) {
   k_ev_count<<<grid_for(P.nb, 256, sms), 256, 0, st>>>(P, ev_off);
   ++*launches;
-  scan_exclusive_inplace(ev_off, P.nb, tmp, st, launches);
+  scan_exclusive_inplace(ev_off, P.nb * kEvBuckets, tmp, st, launches);
   k_ev_fill<<<grid_for(P.nb, 256, sms), 256, 0, st>>>(P, ev_off, events);
   ++*launches;
 }
 
 __global__ void k_block_meta(Prog P, int4* meta) {
   for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < P.nb; b += gridDim.x * blockDim.x) {
-    meta[2 * (size_t)b] = make_int4(P.block_instr_off[b], P.block_instr_off[b + 1], P.ev_off[b], P.ev_off[b + 1]);
+    meta[2 * (size_t)b] = make_int4(P.block_instr_off[b], P.block_instr_off[b + 1], P.ev_off[(size_t)b * kEvBuckets],
+                                    P.ev_off[(size_t)(b + 1) * kEvBuckets]);
     const int q0 = P.pred_off[b], q1 = P.pred_off[b + 1];
     meta[2 * (size_t)b + 1] = make_int4(q0, q1, q1 > q0 ? P.pred[q0] : -1, q1 > q0 + 1 ? P.pred[q0 + 1] : -1);
   }

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <climits>
 #include <cstddef>
 #include <cstdio>
 #include <cstring>
@@ -114,6 +115,9 @@ gpa_status validate(const gpa_program_desc* d, const Arch& A) {
       d->n_use < 0)
     return GPA_ERR_INVALID_PROGRAM;
   if ((int64_t)ni * kCnt >= ((int64_t)1 << 32)) return GPA_ERR_INVALID_PROGRAM;
+  // event lists: int32 offsets over (block, resource bucket) segments and events
+  if ((int64_t)nb * kEvBuckets >= INT32_MAX || (int64_t)d->n_def + d->n_use >= INT32_MAX)
+    return GPA_ERR_INVALID_PROGRAM;
   if (!d->func_instr_off || !d->func_block_off || !d->func_loop_off || !d->block_instr_off || !d->succ_off ||
       !d->opclass || !d->guard || !d->iflags || !d->line || !d->def_off || !d->use_off || !d->block_loop)
     return GPA_ERR_INVALID_ARG;
@@ -504,13 +508,13 @@ static gpa_status alloc_program(const gpa_program_desc* d, ProgramRec* R, int ti
   TRY(dev_alloc(R, &bfunc, nb));
   int32_t* ev_off = nullptr;
   uint32_t* events = nullptr;
-  TRY(dev_alloc(R, &ev_off, nb + 1));
+  TRY(dev_alloc(R, &ev_off, nb * kEvBuckets + 1));
   TRY(dev_alloc(R, &events, (size_t)d->n_def + (size_t)d->n_use));
   P.ev_off = ev_off; P.events = events;
   TRY(dev_alloc(R, &P.res_maxlat, nf * kNumRes));
   TRY(dev_alloc(R, &P.res_guards, nf * kNumRes));
   P.pred_off = pred_off; P.pred = pred; P.loop_depth = ldepth; P.instr_block = iblock; P.block_func = bfunc;
-  TRY(dev_alloc(R, &R->scan_tmp, scan_tmp_ints((int)std::max(ni, nb) + 1)));
+  TRY(dev_alloc(R, &R->scan_tmp, scan_tmp_ints((int)std::max(ni, nb * kEvBuckets) + 1)));
   TRY(dev_alloc(R, &P.cnt, ni * kCnt));
   TRY(dev_alloc(R, &P.stats, (size_t)SS_N));
   TRY(dev_alloc(R, &P.def_mask, nb * kWords));
