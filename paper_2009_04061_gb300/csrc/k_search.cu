@@ -241,7 +241,7 @@ __device__ bool group_search(const G& g, const Prog& P, const Arch& A, const Are
   int* ubuf = a.seen;
   int* ukeep = a.tmp;
   if (me == 0) {
-    ctr[0] = 1; ctr[1] = 0; ctr[2] = 0; ctr[3] = 0; ctr[4] = 0; ctr[6] = 1;
+    ctr[0] = 1; ctr[1] = 0; ctr[2] = 0; ctr[3] = 0; ctr[4] = 0; ctr[5] = 0; ctr[6] = 1;
     ubuf[0] = 0;
     S0 = keep_literals(S0, live);
     a.blk[0] = b0; a.S[0] = (int)S0 | ((int)S0 << 16); a.wall[0] = -1; a.fl[0] = 0;
@@ -324,7 +324,7 @@ __device__ bool group_search(const G& g, const Prog& P, const Arch& A, const Are
   // that met a claim in progress retry the slot in the next round.
   // pm: the node's predecessor record (range, first two predecessors);
   // ro0 / ro1: the reach words of those two (loaded before the scan).
-  auto link_chunk = [&](const int* lst, int cnt, int4 pm, uint32_t ro0, uint32_t ro1) {
+  auto link_chunk = [&](const int* lst, int cnt, int4 pm, uint32_t ro0, uint32_t ro1, bool relax) {
     const bool mine = me < cnt;
     const int u = mine ? lst[me] : 0;
     const int B = mine ? a.blk[u] : 0;
@@ -350,6 +350,16 @@ __device__ bool group_search(const G& g, const Prog& P, const Arch& A, const Are
     if (ne + total > a.E) { if (me == 0) ctr[4] = 2; g.sync(); return; }
     if (mine) { a.e0[u] = ne + incl - deg; a.e1[u] = ne + incl; }
     const int maxdeg = g.max(deg);
+    // Pass A relaxes each new edge as it is linked, from u's distance now
+    // (packed with u as the parent); an expanded target that improves is
+    // queued in ord for relax_from, which carries the change on. A node whose
+    // own distance improves meanwhile is such a target, so its edges are
+    // relaxed again from the better distance.
+    unsigned long long nd_u = ~0ull;
+    if (relax && mine) {
+      const int du = dist_of(a, u);
+      if (du < kInf) nd_u = ((unsigned long long)(du + wout(u)) << 32) | (unsigned)u;
+    }
     int qp = pm.x;
     for (int kk = 0; kk < maxdeg; ++kk) {
       bool pending = kk < deg;
@@ -389,6 +399,9 @@ __device__ bool group_search(const G& g, const Prog& P, const Arch& A, const Are
       }
       if (pending) a.ctr[4] = 6;  // the round limit is a bound, not expected to be reached
       if (kk < deg && v >= 0) a.eto[a.e0[u] + kk] = v | (p >= B ? (int)kBackBit : 0);
+      if (relax && kk < deg && v >= 0 && nd_u < a.dpk[v] && atomicMin(&a.dpk[v], nd_u) > nd_u &&
+          (a.fl[v] & kExpanded) && !(atomicOr(&a.fl[v], 8) & 8))
+        a.ord[atomicAdd((int*)&a.ctr[5], 1)] = v;
     }
     g.sync();
     if (me == 0) ctr[1] = ne + total;
@@ -396,7 +409,7 @@ __device__ bool group_search(const G& g, const Prog& P, const Arch& A, const Are
   };
 
   // Expand every listed node: parallel scans, then parallel linking.
-  auto expand_list = [&](const int* list, int cnt) {
+  auto expand_list = [&](const int* list, int cnt, bool relax) {
     for (int c0 = 0; c0 < cnt; c0 += G::kSize) {
       int4 pm = make_int4(0, 0, -1, -1);
       uint32_t ro0 = 0u, ro1 = 0u;
@@ -411,7 +424,7 @@ __device__ bool group_search(const G& g, const Prog& P, const Arch& A, const Are
       }
       g.sync();
       if (ctr[4]) return;
-      link_chunk(list + c0, min(G::kSize, cnt - c0), pm, ro0, ro1);
+      link_chunk(list + c0, min(G::kSize, cnt - c0), pm, ro0, ro1, relax);
       if (g.read(&ctr[4])) return;  // the next chunk's scans may set it
     }
   };
@@ -499,13 +512,16 @@ __device__ bool group_search(const G& g, const Prog& P, const Arch& A, const Are
     return cnt;
   };
 
-  // Pass A: expand in waves the nodes within the bound, relaxing from each wave.
+  // Pass A: expand in waves the nodes within the bound, relaxing as they link.
   while (!ctr[4]) {
     const int cnt = take_wave(bound);
     if (cnt == 0) break;
-    expand_list(list, cnt);
+    expand_list(list, cnt, true);
     if (ctr[4]) break;
-    relax_from(list, cnt, 0);
+    // the wave's edges were relaxed as they were linked; carry on from the
+    // expanded nodes that improved (queued in ord, counted in ctr[5])
+    const int n_dirty = ctr[5];
+    if (n_dirty > 0) relax_from(a.ord, n_dirty, 0);
   }
   // A source within its latency? (Every candidate is found by pass A: a
   // source farther than the bound fails rule 3.)
@@ -528,7 +544,7 @@ __device__ bool group_search(const G& g, const Prog& P, const Arch& A, const Are
     while (!ctr[4]) {
       const int cnt = take_wave(-1);
       if (cnt == 0) break;
-      expand_list(list, cnt);
+      expand_list(list, cnt, false);
     }
   }
   // Clear the hash slots this search used.
