@@ -102,10 +102,10 @@ typedef struct {
   int32_t max_fixpoint_sweeps;  /* reaching-definitions sweep limit; 0 = 64 */
   int32_t max_search_nodes;     /* (block, predicate-set) nodes of the largest general search; 0 = 32768 */
   int32_t search_slots;         /* warps with a max_search_nodes global-memory arena; 0 = as many as the
-                                   search kernel keeps resident (21 per SM on GB300, about 14 GB of arenas
+                                   search kernel keeps resident (24 per SM on GB300, about 16 GB of arenas
                                    at the default max_search_nodes) */
   int32_t max_sources_per_use;  /* distinct sources merged per stalled use; 0 = 2048 (max 2048) */
-  int32_t small_search_nodes;   /* nodes of the shared-memory arena of a first-tier search warp; 0 = 128
+  int32_t small_search_nodes;   /* nodes of the shared-memory arena of a first-tier search warp; 0 = 64
                                    (max 1024). A search that outgrows it is redone in the next tier */
   int32_t mid_search_nodes;     /* nodes of the second tier's shared-memory arenas (three warps per SM
                                    up to 512 nodes, one up to 1024); 0 = small_search_nodes (searches that
@@ -126,6 +126,9 @@ typedef struct {
                                    stage take the windowed kernel); 1 = the windowed kernel for every
                                    function (a lane per basic block, windows of 32 blocks in global
                                    memory) */
+  int32_t small_search_warps;   /* first-tier search warps per SM (a multiple of 4, at most 32); 0 = 24.
+                                   The first tier shares the SMs with the third tier's searches known
+                                   from earlier steps, which take the registers it leaves */
 } gpa_options;
 
 /* A program: n_functions functions laid out one after another. All arrays are

@@ -12,8 +12,8 @@ tried with the best values found so far for the others):
 - reaching-definitions schedule: a warp per function staged in shared memory
   (launched by size class) against the windowed kernel, a lane per basic block
   in windows of 32 blocks, for every function;
-- search tiers: the node capacity of the first tier's shared-memory arenas and
-  the number of global-memory search warps per SM.
+- search tiers: the node capacity of the first tier's shared-memory arenas, the
+  first tier's warps per SM, and the number of global-memory search warps per SM.
 
 A dimension's values are compared by the time of the phase it schedules
 (ingest for the aggregation options, blame for the others). Every candidate
@@ -29,11 +29,12 @@ DIMENSIONS = [
     ("hist_variant", (0, 1, 2, 3)),
     ("hist_chunk", (24, 8, 16, 32, 48)),
     ("reach_schedule", (0, 1)),
-    ("small_search_nodes", (128, 64)),
+    ("small_search_nodes", (64, 128, 32)),
+    ("small_search_warps", (24, 16, 20)),
     ("search_slots_per_sm", (0, 12, 16)),
 ]
 PHASE = {"hist_variant": "ingest", "hist_chunk": "ingest", "reach_schedule": "blame", "small_search_nodes": "blame",
-         "search_slots_per_sm": "blame"}
+         "small_search_warps": "blame", "search_slots_per_sm": "blame"}
 
 
 def _options(point: dict, sms: int) -> dict:

@@ -75,6 +75,12 @@ __device__ __forceinline__ uint32_t node_hash(int blk, int S) {
   return h;
 }
 
+// A hint that brings the line holding p into this SM's L1 (no register is
+// written, so nothing waits for it).
+__device__ __forceinline__ void prefetch_l1(const void* p) {
+  asm volatile("prefetch.global.L1 [%0];" ::"l"(__cvta_generic_to_global(p)));
+}
+
 __device__ __forceinline__ int dist_of(const Arena& a, int u) { return (int)(a.dpk[u] >> 32); }
 __device__ __forceinline__ int par_of(const Arena& a, int u) { return (int)(a.dpk[u] & 0xFFFFFFFFull); }
 
@@ -273,18 +279,17 @@ __device__ bool group_search(const G& g, const Prog& P, const Arch& A, const Are
   // Scan node u's block bottom-up through its events of r's bucket (one
   // thread). Records occurrences, the literal set leaving the top and the first
   // unguarded reader of r met (the wall). Sets a.fl[u] bit 2 if the scan
-  // stopped (covered).
-  auto scan = [&](int u) {
+  // stopped (covered). `first` is the block's first instruction and
+  // [ev_beg, ev_end) its segment of r's bucket, empty when no instruction of
+  // the block defines r or reads it unguarded (loaded by the caller together
+  // with the block's other records).
+  auto scan = [&](int u, int first, int ev_beg, int ev_end) {
     uint16_t S = (uint16_t)(a.S[u] & 0xFFFF);
     bool stop = false;
     if (u != 0) {
       const int B = a.blk[u];
-      const int first = __ldg(&P.block_meta[2 * (size_t)B].x);
       int wall = -1;
-      if (__ldg(&P.touch_mask[(size_t)B * kWords + w]) & bit) {
-        // only the events of r's bucket
-        const size_t seg = (size_t)B * kEvBuckets + ev_bucket(r);
-        const int ev_beg = __ldg(&P.ev_off[seg]), ev_end = __ldg(&P.ev_off[seg + 1]);
+      {
         int last_def_pos = -1;
         // Events four at a time: independent read-only loads in flight together
         // (a sentinel resource 511 pads the last group).
@@ -415,12 +420,32 @@ __device__ bool group_search(const G& g, const Prog& P, const Arch& A, const Are
       uint32_t ro0 = 0u, ro1 = 0u;
       if (c0 + me < cnt) {
         const int u = list[c0 + me];
-        // The predecessor record and the reach words of the first two
-        // predecessors are loaded first: their latency overlaps the scan.
-        pm = P.block_meta[2 * (size_t)a.blk[u] + 1];
-        if (pm.z >= 0) ro0 = P.rout[(size_t)pm.z * kWords + w];
-        if (pm.w >= 0) ro1 = P.rout[(size_t)pm.w * kWords + w];
-        scan(u);
+        const int B = a.blk[u];
+        // First round of loads, all independent: the block's two records, the
+        // touch word of r and the bounds of r's event segment.
+        pm = __ldg(&P.block_meta[2 * (size_t)B + 1]);
+        const int first = __ldg(&P.block_meta[2 * (size_t)B].x);
+        const uint32_t tw = __ldg(&P.touch_mask[(size_t)B * kWords + w]);
+        const size_t seg = (size_t)B * kEvBuckets + ev_bucket(r);
+        const int ev_beg = __ldg(&P.ev_off[seg]);
+        int ev_end = __ldg(&P.ev_off[seg + 1]);
+        ev_end = (tw & bit) ? ev_end : ev_beg;  // an untouched block has nothing to scan
+        // Second round: the reach words of the first two predecessors (read
+        // when linking), and the first two predecessors' records, fetched into
+        // L1 for the wave that expands them; the scan's event loads follow.
+        if (pm.z >= 0) {
+          ro0 = P.rout[(size_t)pm.z * kWords + w];
+          prefetch_l1(&P.block_meta[2 * (size_t)pm.z]);
+          prefetch_l1(&P.touch_mask[(size_t)pm.z * kWords + w]);
+          prefetch_l1(&P.ev_off[(size_t)pm.z * kEvBuckets + ev_bucket(r)]);
+        }
+        if (pm.w >= 0) {
+          ro1 = P.rout[(size_t)pm.w * kWords + w];
+          prefetch_l1(&P.block_meta[2 * (size_t)pm.w]);
+          prefetch_l1(&P.touch_mask[(size_t)pm.w * kWords + w]);
+          prefetch_l1(&P.ev_off[(size_t)pm.w * kEvBuckets + ev_bucket(r)]);
+        }
+        scan(u, first, ev_beg, ev_end);
       }
       g.sync();
       if (ctr[4]) return;
@@ -512,21 +537,127 @@ __device__ bool group_search(const G& g, const Prog& P, const Arch& A, const Are
     return cnt;
   };
 
-  // Pass A: expand in waves the nodes within the bound, relaxing as they link.
-  while (!ctr[4]) {
-    const int cnt = take_wave(bound);
-    if (cnt == 0) break;
-    expand_list(list, cnt, true);
-    if (ctr[4]) break;
-    // the wave's edges were relaxed as they were linked; carry on from the
-    // expanded nodes that improved (queued in ord, counted in ctr[5])
-    const int n_dirty = ctr[5];
-    if (n_dirty > 0) relax_from(a.ord, n_dirty, 0);
+  // Pass A by one thread, for the first tier's small searches: a
+  // label-correcting queue (a node is queued when its distance improves and it
+  // is expanded or within the bound; a node is expanded once, when first taken
+  // within the bound; an expanded node taken again relaxes its edges from its
+  // better distance). It reaches the fixpoint of the waves below (every node
+  // whose shortest distance over the expanded nodes' edges is within the bound
+  // is expanded), without a vote, a prefix count or a claim round per node: a
+  // small search's waves are two or three nodes wide, so the warp-wide
+  // protocol cost more than the work it spread. The queue is a ring over q
+  // (a node is in it at most once at a time).
+  auto serial_pass_a = [&]() {
+    int* ring = a.q;
+    int head = 0, tail = 0, inq = 0;
+    int nn = ctr[0], ne = ctr[1], nh = ctr[3];
+    auto push = [&](int v) {
+      if (a.fl[v] & 8) return;
+      a.fl[v] |= 8;
+      ring[tail] = v;
+      tail = tail + 1 == a.N ? 0 : tail + 1;
+      ++inq;
+    };
+    push(0);
+    while (inq > 0) {
+      const int u = ring[head];
+      head = head + 1 == a.N ? 0 : head + 1;
+      --inq;
+      a.fl[u] &= ~8;
+      const int du = dist_of(a, u);
+      if (!(a.fl[u] & kExpanded)) {
+        if (du > bound) continue;
+        const int B = a.blk[u];
+        const int4 pm = __ldg(&P.block_meta[2 * (size_t)B + 1]);
+        const int first = __ldg(&P.block_meta[2 * (size_t)B].x);
+        const uint32_t tw = __ldg(&P.touch_mask[(size_t)B * kWords + w]);
+        const size_t seg = (size_t)B * kEvBuckets + ev_bucket(r);
+        const int ev_beg = __ldg(&P.ev_off[seg]);
+        int ev_end = __ldg(&P.ev_off[seg + 1]);
+        ev_end = (tw & bit) ? ev_end : ev_beg;
+        scan(u, first, ev_beg, ev_end);
+        if (ctr[4]) break;
+        const int Sout = (a.S[u] >> 16) & 0xFFFF;
+        a.e0[u] = ne;
+        for (int q = (a.fl[u] & 4) ? pm.y : pm.x; q < pm.y; ++q) {
+          const int p = q == pm.x ? pm.z : q == pm.x + 1 ? pm.w : __ldg(&P.pred[q]);
+          if (!(P.rout[(size_t)p * kWords + w] & bit)) continue;
+          if (ne >= a.E) { ctr[4] = 2; break; }
+          uint32_t h = node_hash(p, Sout) & hmask;
+          int v = -1;
+          for (int probe = 0; probe <= (int)hmask; ++probe) {
+            const int c = a.ht[h];
+            if (c < 0) break;
+            if (a.blk[c] == p && (a.S[c] & 0xFFFF) == Sout) { v = c; break; }
+            h = (h + 1) & hmask;
+          }
+          if (v < 0) {
+            if (a.ht[h] >= 0) { ctr[4] = 6; break; }  // not reached: 2N slots for at most N nodes
+            if (nn >= a.N) { ctr[4] = 1; break; }
+            v = nn++;
+            a.blk[v] = p; a.S[v] = Sout; a.wall[v] = -1; a.fl[v] = 0; a.k[v] = kInf;
+            a.e0[v] = 0; a.e1[v] = 0;
+            a.dpk[v] = ((unsigned long long)kInf << 32) | 0xFFFFFFFFull;
+            a.hused[nh++] = (int)h;
+            a.ht[h] = v;
+          }
+          a.eto[ne++] = v | (p >= B ? (int)kBackBit : 0);
+        }
+        a.e1[u] = ne;
+        if (ctr[4]) break;
+      }
+      if (du >= kInf) continue;
+      const unsigned long long nd = ((unsigned long long)(du + wout(u)) << 32) | (unsigned)u;
+      for (int e = a.e0[u]; e < a.e1[u]; ++e) {
+        const int v = a.eto[e] & 0x7FFFFFFF;
+        if (nd < a.dpk[v]) {
+          a.dpk[v] = nd;
+          if ((a.fl[v] & kExpanded) || (int)(nd >> 32) <= bound) push(v);
+        }
+      }
+    }
+    ctr[0] = nn; ctr[1] = ne; ctr[3] = nh;
+  };
+
+  // Pass A expands in waves the nodes within the bound, relaxing as they
+  // link (or by one thread, above); pass B, only if some source is within its
+  // latency, completes the graph. Both run in this one loop, so the wave code
+  // exists once in the kernel (the search kernel is bound by instruction fetch
+  // when its warps spread over a larger body).
+  bool cand = false, pass_b = false;
+  const bool serial_a = G::kSize == 32 && tier == 1;
+  if (serial_a) {
+    if (me == 0) serial_pass_a();
+    g.sync();
+    // pass B starts from the nodes pass A left unexpanded
+    const int n_now = ctr[0];
+    int m = 0;
+    for (int i0 = 0; i0 < n_now; i0 += G::kSize) {
+      const int i = i0 + me;
+      const bool un = i < n_now && !(a.fl[i] & kExpanded);
+      int tot;
+      const int at = g.slot(un, &tot);
+      if (un) ubuf[m + at] = i;
+      m += tot;
+    }
+    g.sync();
+    if (me == 0) ctr[6] = m;
+    g.sync();
   }
-  // A source within its latency? (Every candidate is found by pass A: a
-  // source farther than the bound fails rule 3.)
-  bool cand = false;
-  if (!ctr[4]) {
+  while (!ctr[4]) {
+    const int cnt = serial_a && !pass_b ? 0 : take_wave(pass_b ? -1 : bound);
+    if (cnt > 0) {
+      expand_list(list, cnt, !pass_b);
+      if (ctr[4]) break;
+      // pass A relaxed the wave's edges as they were linked; carry on from the
+      // expanded nodes that improved (queued in ord, counted in ctr[5])
+      const int n_dirty = pass_b ? 0 : ctr[5];
+      if (n_dirty > 0) relax_from(a.ord, n_dirty, 0);
+      continue;
+    }
+    if (pass_b) break;
+    // End of pass A. A source within its latency? (Every candidate is found
+    // by pass A: a source farther than the bound fails rule 3.)
     const int no = min(ctr[2], a.O);
     int low = 0x7FFFFFFF;
     for (int o = me; o < no; o += G::kSize) {
@@ -538,14 +669,8 @@ __device__ bool group_search(const G& g, const Prog& P, const Arch& A, const Are
     }
     cand = g.any(cand);
     cand_low = g.min(low);
-  }
-  // Pass B: complete the graph.
-  if (cand) {
-    while (!ctr[4]) {
-      const int cnt = take_wave(-1);
-      if (cnt == 0) break;
-      expand_list(list, cnt, false);
-    }
+    if (!cand) break;
+    pass_b = true;
   }
   // Clear the hash slots this search used.
   const int nh = ctr[3];
@@ -577,8 +702,8 @@ __device__ bool group_search(const G& g, const Prog& P, const Arch& A, const Are
   }
   if (me == 0) a.q[0] = 0;
   g.sync();
-  relax_from(a.q, 1, 0);
-  relax_from(a.q, 1, 1);
+#pragma unroll 1
+  for (int mode = 0; mode < 2; ++mode) relax_from(a.q, 1, mode);
   phase(1);
 
   // Sources: a warp-synchronous hash keyed by instruction gives each source an

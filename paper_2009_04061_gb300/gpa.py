@@ -42,7 +42,8 @@ class gpa_options(ctypes.Structure):
                 ("search_slots", ctypes.c_int32), ("max_sources_per_use", ctypes.c_int32),
                 ("small_search_nodes", ctypes.c_int32), ("mid_search_nodes", ctypes.c_int32),
                 ("hist_variant", ctypes.c_int32), ("large_search_nodes", ctypes.c_int32),
-                ("hist_chunk", ctypes.c_int32), ("reach_schedule", ctypes.c_int32)]
+                ("hist_chunk", ctypes.c_int32), ("reach_schedule", ctypes.c_int32),
+                ("small_search_warps", ctypes.c_int32)]
 
 
 _PROG_ARRAYS = ["func_instr_off", "func_block_off", "func_loop_off", "block_instr_off", "succ_off", "succ",

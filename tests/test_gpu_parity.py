@@ -249,6 +249,26 @@ def test_small_search_slots_overflow_to_large_tier():
         assert_full_parity(r, oracle_run(P, s))
 
 
+def test_first_tier_warp_counts_agree():
+    """The first tier's warps per SM only change how many searches run at once:
+    12, 16 and 24 warps (and 128-node arenas at 12) give the oracle's results, and a
+    count that is not a multiple of 4 or above 32 is refused."""
+    import paper_2009_04061_gb300 as g
+    rng = np.random.default_rng(19)
+    P = synth.make_program(synth.batched_params(24, rng, 19), 1.0)
+    s = P.samples(1_000_000, seed=19)
+    R = oracle_run(P, s)
+    for opts in (dict(small_search_warps=12), dict(small_search_warps=16),
+                 dict(small_search_warps=24, small_search_nodes=32), dict(small_search_nodes=128, small_search_warps=12)):
+        with g.Context(ARCH, opts) as c:
+            r = gpu_run(c, P, dev(s))
+            assert r["info"]["general_searches"] > 0
+            assert_full_parity(r, R)
+    for bad in (6, 36, -4):
+        with pytest.raises(g.GpaError):
+            g.Context(ARCH, dict(small_search_warps=bad))
+
+
 def test_tier_hints_on_repeated_steps():
     """Searches that outgrew a tier are queued straight for the bigger one on later
     steps of the same program; every step gives the oracle's results."""
