@@ -317,8 +317,6 @@ inline void allow_max_smem(F func) {
   cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
 }
 
-// Shared memory the staged reaching-definitions fixpoint needs for a function
-// of nbf blocks and ne predecessor entries, and the most it may use.
 // Shared memory of the staged fixpoint for a function of nbf blocks, ne
 // predecessor entries and nlf loops: ROUT (9 words a block), a 16-byte record
 // per block (16-byte aligned: up to 12 bytes of padding), the predecessor CSR,

@@ -18,17 +18,17 @@ namespace gpa {
 
 namespace {
 
-// Warp per basic block: lanes over its instructions, one reduce-or per word.
+// Thread per basic block (blocks average 7 instructions, so a warp per block
+// left most lanes idle): the masks stay in registers, each resource's bit
+// added to its word by a compare per word (no indexed register array), then
+// the 9 words of each mask stored.
 __global__ void k_block_masks(Prog P) {
-  const int lane = threadIdx.x & 31;
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int n_warps = (gridDim.x * blockDim.x) >> 5;
-  for (int b = warp; b < P.nb; b += n_warps) {
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < P.nb; b += gridDim.x * blockDim.x) {
     uint32_t dm[kWords], um[kWords];
 #pragma unroll
     for (int w = 0; w < kWords; ++w) { dm[w] = 0; um[w] = 0; }
     const int x1 = P.block_instr_off[b + 1];
-    for (int x = P.block_instr_off[b] + lane; x < x1; x += 32) {
+    for (int x = P.block_instr_off[b]; x < x1; ++x) {
       for (int e = P.def_off[x]; e < P.def_off[x + 1]; ++e) {
         const int r = P.def_res[e] & 0x1FF;
 #pragma unroll
@@ -42,17 +42,14 @@ __global__ void k_block_masks(Prog P) {
         }
       }
     }
+    const size_t o = (size_t)b * kWords;
 #pragma unroll
     for (int w = 0; w < kWords; ++w) {
-      const uint32_t d = __reduce_or_sync(0xffffffffu, dm[w]);
-      const uint32_t u = __reduce_or_sync(0xffffffffu, um[w]);
-      if (lane == w) {
-        P.def_mask[(size_t)b * kWords + w] = d;
-        P.uuse_mask[(size_t)b * kWords + w] = u;
-        P.touch_mask[(size_t)b * kWords + w] = d | u;
-        P.rin[(size_t)b * kWords + w] = 0u;
-        P.rout[(size_t)b * kWords + w] = d;
-      }
+      P.def_mask[o + w] = dm[w];
+      P.uuse_mask[o + w] = um[w];
+      P.touch_mask[o + w] = dm[w] | um[w];
+      P.rin[o + w] = 0u;
+      P.rout[o + w] = dm[w];
     }
   }
 }
@@ -73,15 +70,19 @@ __global__ void k_res_maxlat(Prog P, Arch A) {
   }
 }
 
-// One warp per function, the function staged in shared memory: ROUT (9
-// words per block, starting at DEF), and per block a record of its first two
+// One CTA per function, the function staged in shared memory: ROUT (9 words
+// per block, starting at DEF), and per block a record of its first two
 // predecessors other than the block before it, its innermost loop, and flags
 // (the block before it is a predecessor; more predecessors in the CSR). ROUT
 // only grows, so ROUT[b] = ROUT[b] | OR of the predecessors' ROUT needs no
 // separate DEF. A sweep visits the blocks one after another in layout order (a
 // topological order of the forward edges, so one sweep carries a def along any
-// forward path), lanes 0-8 over the 9 words, with the previous block's ROUT in
-// a register and the next block's record and ROUT loaded a block ahead.
+// forward path), lanes 0-8 of the first warp over the 9 words, with the
+// previous block's ROUT in a register. A block's other predecessors are never
+// the block just before it, so their words for the next block are loaded
+// before this block's ROUT is stored: the sweep's chain per block is an OR and
+// a store. The rest (staging, records, loop masks, RIN and the copy-out) is
+// spread over the CTA's threads.
 // When every loop body of the function is a natural loop (or it has none),
 // each block also takes in, from the start, the defs of the bodies of the loops
 // around it: every block of a natural loop reaches every other one through the
@@ -99,20 +100,24 @@ __device__ __forceinline__ void cp_async4(void* smem_dst, const void* src) {
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
-__global__ void __launch_bounds__(32) k_reaching_smem(Prog P, int max_sweeps, int q_lo, int q_hi, int head, int cap) {
+__global__ void __launch_bounds__(256) k_reaching_smem(Prog P, int max_sweeps, int q_lo, int q_hi, int head, int cap) {
   extern __shared__ __align__(16) uint32_t sm[];
-  const int lane = threadIdx.x;
+  __shared__ int s_f;
+  const int tid = threadIdx.x, nt = blockDim.x;
   while (true) {
     // Functions are taken largest first, so the long ones start early.
-    unsigned long long q = 0;
-    if (lane == 0) q = atomicAdd(&P.stats[head], 1ull);
-    q = __shfl_sync(0xffffffffu, q, 0) + (unsigned long long)q_lo;
-    if (q >= (unsigned long long)q_hi) break;
-    const int f = P.reach_order[q];
+    __syncthreads();  // every thread has read s_f and left the previous function's stage
+    if (tid == 0) {
+      const unsigned long long q = atomicAdd(&P.stats[head], 1ull) + (unsigned long long)q_lo;
+      s_f = q < (unsigned long long)q_hi ? P.reach_order[q] : -1;
+    }
+    __syncthreads();
+    const int f = s_f;
+    if (f < 0) break;
     const int b0 = P.func_block_off[f], b1 = P.func_block_off[f + 1], nbf = b1 - b0;
     const int e0 = P.pred_off[b0], ne = P.pred_off[b1] - e0;
     const int l0 = P.func_loop_off[f], nlf = P.func_loop_off[f + 1] - l0;
-    if (nbf == 0 || reach_smem_need(nbf, ne, nlf) > cap) continue;
+    if (nbf == 0 || reach_smem_need(nbf, ne, nlf) > cap) continue;  // the same for every thread
     const bool exact = P.func_natural[f];  // one seeded sweep is the fixpoint
     const bool seed = exact && nlf > 0;
     uint32_t* so = sm;
@@ -125,24 +130,24 @@ __global__ void __launch_bounds__(32) k_reaching_smem(Prog P, int max_sweeps, in
     uint32_t* lin = ldef + (size_t)nlf * kWords;
     // Staging: asynchronous 4-byte copies, all in flight together, then the
     // global indices rebased to the function in place.
-    for (int t = lane; t < nbf * kWords; t += 32) cp_async4(so + t, P.def_mask + (size_t)b0 * kWords + t);
-    for (int t = lane; t <= nbf; t += 32) cp_async4(spo + t, P.pred_off + b0 + t);
-    for (int t = lane; t < ne; t += 32) cp_async4(sp + t, P.pred + e0 + t);
+    for (int t = tid; t < nbf * kWords; t += nt) cp_async4(so + t, P.def_mask + (size_t)b0 * kWords + t);
+    for (int t = tid; t <= nbf; t += nt) cp_async4(spo + t, P.pred_off + b0 + t);
+    for (int t = tid; t < ne; t += nt) cp_async4(sp + t, P.pred + e0 + t);
     if (seed) {
-      for (int t = lane; t < nbf; t += 32) cp_async4(sloop + t, P.block_loop + b0 + t);
-      for (int t = lane; t < nlf; t += 32) cp_async4(spar + t, P.loop_parent + l0 + t);
+      for (int t = tid; t < nbf; t += nt) cp_async4(sloop + t, P.block_loop + b0 + t);
+      for (int t = tid; t < nlf; t += nt) cp_async4(spar + t, P.loop_parent + l0 + t);
     }
     cp_async_wait_all();
-    __syncwarp();
-    for (int t = lane; t <= nbf; t += 32) spo[t] -= e0;
-    for (int t = lane; t < ne; t += 32) sp[t] -= b0;
+    __syncthreads();
+    for (int t = tid; t <= nbf; t += nt) spo[t] -= e0;
+    for (int t = tid; t < ne; t += nt) sp[t] -= b0;
     if (seed) {
-      for (int t = lane; t < nbf; t += 32) sloop[t] = sloop[t] >= 0 ? sloop[t] - l0 : -1;
-      for (int t = lane; t < nlf; t += 32) spar[t] = spar[t] >= 0 ? spar[t] - l0 : -1;
-      for (int t = lane; t < nlf * kWords; t += 32) ldef[t] = 0u;
+      for (int t = tid; t < nbf; t += nt) sloop[t] = sloop[t] >= 0 ? sloop[t] - l0 : -1;
+      for (int t = tid; t < nlf; t += nt) spar[t] = spar[t] >= 0 ? spar[t] - l0 : -1;
+      for (int t = tid; t < nlf * kWords; t += nt) ldef[t] = 0u;
     }
-    __syncwarp();
-    for (int b = lane; b < nbf; b += 32) {
+    __syncthreads();
+    for (int b = tid; b < nbf; b += nt) {
       int p1 = -1, p2 = -1, fl = 0;
       for (int e = spo[b]; e < spo[b + 1]; ++e) {
         const int p = sp[e];
@@ -155,64 +160,72 @@ __global__ void __launch_bounds__(32) k_reaching_smem(Prog P, int max_sweeps, in
     }
     if (seed) {
       // the defs of each loop's body, nested loops included
-      for (int t = lane; t < nbf * kWords; t += 32) {
+      for (int t = tid; t < nbf * kWords; t += nt) {
         const uint32_t v = so[t];
         if (!v) continue;
         const int w = t % kWords;
         for (int l = sloop[t / kWords]; l >= 0; l = spar[l]) atomicOr(&ldef[l * kWords + w], v);
       }
-      __syncwarp();
+      __syncthreads();
       // and of the enclosing loops' bodies
-      for (int t = lane; t < nlf * kWords; t += 32) {
+      for (int t = tid; t < nlf * kWords; t += nt) {
         const int w = t % kWords;
         uint32_t v = 0u;
         for (int l = t / kWords; l >= 0; l = spar[l]) v |= ldef[l * kWords + w];
         lin[t] = v;
       }
     }
-    __syncwarp();
-    bool converged = false;
-    int sweep = 0;
-    const int limit = exact ? 1 : max_sweeps;
-    for (; sweep < limit && !converged; ++sweep) {
-      bool ch = false;
-      if (lane < kWords) {
-        uint32_t prev = 0u;
-        int4 r = rec[0];
-        uint32_t old = so[lane];
-        for (int b = 0; b < nbf; ++b) {
-          const bool more = b + 1 < nbf;
-          const int4 rn = more ? rec[b + 1] : r;
-          const uint32_t oldn = more ? so[(b + 1) * kWords + lane] : 0u;
-          uint32_t in = r.z >= 0 ? lin[r.z * kWords + lane] : 0u;
-          if (r.w & 1) in |= prev;
-          if (r.x >= 0) in |= so[r.x * kWords + lane];
-          if (r.y >= 0) in |= so[r.y * kWords + lane];
-          if (r.w & 2)
-            for (int e = spo[b]; e < spo[b + 1]; ++e) in |= so[sp[e] * kWords + lane];
-          const uint32_t o = old | in;
-          ch |= o != old;
-          so[b * kWords + lane] = o;
-          prev = o;
-          r = rn;
-          old = oldn;
+    __syncthreads();
+    if (tid < 32) {
+      const int lane = tid;
+      bool converged = false;
+      int sweep = 0;
+      const int limit = exact ? 1 : max_sweeps;
+      for (; sweep < limit && !converged; ++sweep) {
+        bool ch = false;
+        if (lane < kWords) {
+          // words from the record's two predecessors and the enclosing loops
+          auto pre = [&](const int4& r) -> uint32_t {
+            return (r.z >= 0 ? lin[r.z * kWords + lane] : 0u) | (r.x >= 0 ? so[r.x * kWords + lane] : 0u) |
+                   (r.y >= 0 ? so[r.y * kWords + lane] : 0u);
+          };
+          uint32_t prev = 0u;
+          int4 r = rec[0];
+          uint32_t old = so[lane];
+          uint32_t in_r = pre(r);
+          for (int b = 0; b < nbf; ++b) {
+            const bool more = b + 1 < nbf;
+            const int4 rn = more ? rec[b + 1] : r;
+            const uint32_t oldn = more ? so[(b + 1) * kWords + lane] : 0u;
+            const uint32_t in_n = more ? pre(rn) : 0u;  // rn.x, rn.y != b: not written below
+            uint32_t in = in_r;
+            if (r.w & 1) in |= prev;
+            if (r.w & 2)
+              for (int e = spo[b]; e < spo[b + 1]; ++e) in |= so[sp[e] * kWords + lane];
+            const uint32_t o = old | in;
+            ch |= o != old;
+            so[b * kWords + lane] = o;
+            prev = o;
+            r = rn;
+            old = oldn;
+            in_r = in_n;
+          }
         }
+        converged = exact || !__any_sync(0xffffffffu, ch);
       }
-      converged = exact || !__any_sync(0xffffffffu, ch);
+      if (lane == 0) {
+        if (!converged) set_status(P, ST_NOT_CONVERGED);
+        atomicMax(&P.stats[SS_SWEEPS], (unsigned long long)sweep);
+      }
     }
-    __syncwarp();
-    for (int t = lane; t < nbf * kWords; t += 32) {
+    __syncthreads();
+    for (int t = tid; t < nbf * kWords; t += nt) {
       const int b = t / kWords, w = t - b * kWords;
       uint32_t in = 0u;
       for (int e = spo[b]; e < spo[b + 1]; ++e) in |= so[sp[e] * kWords + w];
       P.rin[(size_t)b0 * kWords + t] = in;
       P.rout[(size_t)b0 * kWords + t] = so[t];
     }
-    if (lane == 0) {
-      if (!converged) set_status(P, ST_NOT_CONVERGED);
-      atomicMax(&P.stats[SS_SWEEPS], (unsigned long long)sweep);
-    }
-    __syncwarp();
   }
 }
 
@@ -280,12 +293,7 @@ __global__ void k_reaching(Prog P, int max_sweeps, int all) {
 
 void launch_dataflow(const Prog& P, const Arch& A, int max_sweeps, int schedule, cudaStream_t st, int sms,
                      int64_t* launches) {
-  const int threads = 256;
-  int64_t warps_needed = P.nb;
-  int blocks = (int)((warps_needed * 32 + threads - 1) / threads);
-  if (blocks > sms * 16) blocks = sms * 16;
-  if (blocks < 1) blocks = 1;
-  k_block_masks<<<blocks, threads, 0, st>>>(P);
+  k_block_masks<<<grid_for(P.nb, 256, sms), 256, 0, st>>>(P);
   if (schedule == 0 && P.reach_smem > 0) {
     // One launch per size class: the larger the functions, the more shared
     // memory each warp stages and the fewer warps per SM.
@@ -297,7 +305,11 @@ void launch_dataflow(const Prog& P, const Arch& A, int max_sweeps, int schedule,
       const int smem = P.reach_cls_smem[c];
       const int per_sm = std::max(1, std::min(32, (int)((200 * 1024) / (smem + 1024))));
       const int g = std::min(n, sms * per_sm);
-      k_reaching_smem<<<g, 32, smem, st>>>(P, max_sweeps, P.reach_cls[c], P.reach_cls[c + 1], SS_REACH_CLS + c, smem);
+      // the larger the functions, the more threads share a function's
+      // staging, records and copy-out (its sweep is one warp's in any case)
+      const int threads = c == 0 ? 256 : c == 1 ? 128 : c == 2 ? 64 : 32;
+      k_reaching_smem<<<g, threads, smem, st>>>(P, max_sweeps, P.reach_cls[c], P.reach_cls[c + 1], SS_REACH_CLS + c,
+                                               smem);
       ++*launches;
     }
   }
