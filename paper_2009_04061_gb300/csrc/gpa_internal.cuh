@@ -56,7 +56,9 @@ enum {
   SS_OVF3H_N = 84,     // searches for the fourth tier stored from the top of `ovf_queue`
   SS_LARGE_N = 85,     // entries of large_queue
   SS_REACH_CLS = 86,   // next entry of reach_order for each of the staged fixpoint's 4 launches
-  SS_N = 90
+  SS_SUSE_N = 90,      // entries of suse (the stalled uses of this step)
+  SS_ADV_HEAD = 91,    // next entry of reach_order for the advice kernel's CTAs
+  SS_N = 92
 };
 
 struct Arch {
@@ -148,6 +150,7 @@ struct Prog {
   int64_t queue_cap;
   int32_t* edge_cnt;              // ni + 1 (exclusive scan in place -> offsets)
   int32_t* big_use;               // ni: uses with more than kMaxSrc sources (SS_BIG_N of them)
+  int32_t* suse;                  // ni: the stalled uses of this step, SS_SUSE_N of them (any order)
   int32_t* edge_off;              // ni + 1
   int32_t* e_use;
   int32_t* e_def;

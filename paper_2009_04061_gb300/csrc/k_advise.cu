@@ -7,14 +7,17 @@
 //
 // One CTA per function: threads stride over the function's instructions and
 // its merged edges (contiguous, since edges are ordered by use), reduce the
-// sums in shared memory, and thread 0 finishes the per-function results.
+// sums in shared memory, and thread 0 finishes the per-function results
+// (warp 0 merges the hotspot lists). The
+// CTAs take functions largest first from a counter, so the largest ones start
+// at once and the rest fill in behind them.
 #include "gpa_internal.cuh"
 
 namespace gpa {
 
 namespace {
 
-constexpr int kThreads = 256;
+constexpr int kThreads = 512;
 constexpr int kHot = 5;
 enum { O_RR = 0, O_SR, O_FS, O_FM, O_WB, O_MT, O_LU, O_CR, O_FI, N_O = 9 };
 constexpr int kAcc = 13;  // per-function sums, see k_advise
@@ -52,9 +55,12 @@ __device__ int lca_loop(const Prog& P, int a, int b) {
 }
 
 // Matched samples of an edge per edge-based optimizer. Shares are indexed
-// class slot (exec, memory, sync, constant memory) * 2 + latency flag.
+// class slot (exec, memory, sync, constant memory) * 2 + latency flag. The
+// def and use's innermost common loop (a walk up the loop nest) is found
+// only with `loops` (lu is 0 without it); `lca` receives it.
 struct EdgeMatch { unsigned long long rr, sr, lu, cr; };
-__device__ __forceinline__ EdgeMatch edge_match(const Prog& P, const Arch& A, int64_t e) {
+__device__ __forceinline__ EdgeMatch edge_match(const Prog& P, const Arch& A, int64_t e, bool loops = true,
+                                                int* lca = nullptr) {
   const unsigned long long* sh = P.e_share + e * 8;
   const uint32_t fl = A.flags[P.opclass[P.e_def[e]]];
   const bool local = fl & GPA_F_LOCAL;
@@ -63,7 +69,9 @@ __device__ __forceinline__ EdgeMatch edge_match(const Prog& P, const Arch& A, in
   m.rr = local ? (sh[2] + sh[3] + sh[6] + sh[7]) : 0ull;                       // Register Reuse
   m.sr = (fl & GPA_F_LONG_ARITH) ? (sh[0] + sh[1]) : 0ull;                    // Strength Reduction
   m.cr = sh[1] + (global_mem ? sh[3] : 0ull);                                 // latency samples
-  m.lu = lca_loop(P, innermost_loop(P, P.e_def[e]), innermost_loop(P, P.e_use[e])) >= 0 ? m.cr : 0ull;
+  const int q = loops && m.cr ? lca_loop(P, innermost_loop(P, P.e_def[e]), innermost_loop(P, P.e_use[e])) : -1;
+  m.lu = q >= 0 ? m.cr : 0ull;
+  if (lca) *lca = q;
   return m;
 }
 
@@ -150,9 +158,18 @@ __global__ void __launch_bounds__(kThreads) k_advise(Prog P, Arch A) {
   __shared__ unsigned long long red[kAcc][kThreads / 32];
   __shared__ unsigned long long tot[kAcc];
   __shared__ Cand wtop[kThreads / 32][kHot];  // each warp's top five (v == 0: none)
+  __shared__ int s_f;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
-  for (int f = blockIdx.x; f < P.nf; f += gridDim.x) {
+  while (true) {
+    __syncthreads();  // every thread has read s_f
+    if (tid == 0) {
+      const unsigned long long q = atomicAdd(&P.stats[SS_ADV_HEAD], 1ull);
+      s_f = q < (unsigned long long)P.nf ? P.reach_order[q] : -1;
+    }
+    __syncthreads();
+    const int f = s_f;
+    if (f < 0) break;
     const int i0 = P.func_instr_off[f], i1 = P.func_instr_off[f + 1];
     // Edge ranges are clamped to the edge capacity (overflow is reported in the status word).
     const int64_t e0 = min((int64_t)P.edge_off[i0], P.edge_cap), e1 = min((int64_t)P.edge_off[i1], P.edge_cap);
@@ -184,12 +201,11 @@ __global__ void __launch_bounds__(kThreads) k_advise(Prog P, Arch A) {
       if (bl) atomicAdd(&P.a_line_lat[P.line[x]], bl);
     }
     for (int64_t e = e0 + tid; e < e1; e += kThreads) {
-      const EdgeMatch m = edge_match(P, A, e);
+      int q;
+      const EdgeMatch m = edge_match(P, A, e, true, &q);
       acc[8] += m.rr; acc[9] += m.sr; acc[10] += m.lu; acc[11] += m.cr;
-      if (m.lu) {
-        const int q = lca_loop(P, innermost_loop(P, P.e_def[e]), innermost_loop(P, P.e_use[e]));
+      if (m.lu)
         for (int lp = q; lp >= 0; lp = P.loop_parent[lp]) atomicAdd(&P.a_loop_matched[lp], m.lu);
-      }
     }
 #pragma unroll
     for (int q = 0; q < kAcc; ++q) {
@@ -235,7 +251,7 @@ __global__ void __launch_bounds__(kThreads) k_advise(Prog P, Arch A) {
       const bool edge_based = (o == O_RR || o == O_SR || o == O_LU || o == O_CR);
       if (edge_based) {
         for (int64_t e = e0 + tid; e < e1; e += kThreads) {
-          const EdgeMatch m = edge_match(P, A, e);
+          const EdgeMatch m = edge_match(P, A, e, o == O_LU);
           const unsigned long long v = o == O_RR ? m.rr : o == O_SR ? m.sr : o == O_LU ? m.lu : m.cr;
           top_insert(top, nt, Cand{v, P.e_def[e] - i0, P.e_use[e] - i0, P.e_dmin[e]});
         }
@@ -271,22 +287,37 @@ __global__ void __launch_bounds__(kThreads) k_advise(Prog P, Arch A) {
         if (lane == 0) wtop[warp][h] = b;
       }
       __syncthreads();
-      if (tid == 0) {
-        Cand best[kHot];
-        int nb = 0;
-        for (int w = 0; w < kThreads / 32; ++w)
-          for (int h = 0; h < kHot; ++h) top_insert(best, nb, wtop[w][h]);
+      // The CTA's top five: warp 0 merges the warps' sorted lists the same way
+      // (lane w offers the next entry of warp w's list).
+      if (warp == 0) {
+        static_assert(kThreads / 32 <= 32, "one lane per warp's list");
         long long* out = P.a_hot + ((size_t)f * N_O + o) * kHot * 6;
+        int wp = 0, nb = 0;
         for (int h = 0; h < kHot; ++h) {
-          if (h < nb) {
-            out[h * 6 + 0] = best[h].def; out[h * 6 + 1] = best[h].use;
-            out[h * 6 + 2] = P.line[i0 + best[h].def]; out[h * 6 + 3] = P.line[i0 + best[h].use];
-            out[h * 6 + 4] = best[h].dist; out[h * 6 + 5] = (long long)best[h].v;
-          } else {
-            for (int q = 0; q < 6; ++q) out[h * 6 + q] = -1;
+          Cand b = lane < kThreads / 32 && wp < kHot ? wtop[lane][wp] : Cand{0ull, 0, 0, 0};
+          int owner = lane;
+          for (int o2 = 16; o2 > 0; o2 >>= 1) {
+            Cand y;
+            y.v = __shfl_xor_sync(0xffffffffu, b.v, o2);
+            y.def = __shfl_xor_sync(0xffffffffu, b.def, o2);
+            y.use = __shfl_xor_sync(0xffffffffu, b.use, o2);
+            y.dist = __shfl_xor_sync(0xffffffffu, b.dist, o2);
+            const int yo = __shfl_xor_sync(0xffffffffu, owner, o2);
+            if (better(y, b) || (!better(b, y) && yo < owner)) { b = y; owner = yo; }
+          }
+          if (lane == owner && b.v != 0ull) ++wp;
+          if (lane == 0) {
+            if (b.v != 0ull) {
+              out[h * 6 + 0] = b.def; out[h * 6 + 1] = b.use;
+              out[h * 6 + 2] = P.line[i0 + b.def]; out[h * 6 + 3] = P.line[i0 + b.use];
+              out[h * 6 + 4] = b.dist; out[h * 6 + 5] = (long long)b.v;
+              ++nb;
+            } else {
+              for (int q = 0; q < 6; ++q) out[h * 6 + q] = -1;
+            }
           }
         }
-        P.a_nhot[(size_t)f * N_O + o] = nb;
+        if (lane == 0) P.a_nhot[(size_t)f * N_O + o] = nb;
       }
       __syncthreads();
     }
@@ -311,7 +342,8 @@ void launch_advise(const Prog& P, const Arch& A, cudaStream_t st, int sms, int64
   }
   cudaMemsetAsync(P.a_line_stall, 0, sizeof(unsigned long long) * P.n_lines, st);
   cudaMemsetAsync(P.a_line_lat, 0, sizeof(unsigned long long) * P.n_lines, st);
-  int blocks = P.nf < sms * 4 ? P.nf : sms * 4;
+  cudaMemsetAsync(&P.stats[SS_ADV_HEAD], 0, sizeof(unsigned long long), st);
+  int blocks = P.nf < sms * 2 ? P.nf : sms * 2;
   k_advise<<<blocks > 0 ? blocks : 1, kThreads, 0, st>>>(P, A);
   ++*launches;
 }

@@ -80,9 +80,38 @@ __device__ bool scan_pred(const Prog& P, const Arch& A, int j, int r, int gj, in
   return false;
 }
 
+// The stalled uses (instructions with dependency-class samples), appended a
+// warp at a time: a tenth of the instructions on the batched workload, so the
+// kernels that work per stalled use take them from this list with every lane
+// busy instead of striding over all instructions. One instruction a thread
+// over a grid that covers them all (the loads of many CTAs in flight); the
+// dependency-class counters are words 4-7 and 10-13 of a row, read as four
+// 16-byte pairs.
+__global__ void k_stalled_list(Prog P) {
+  static_assert(2 * GPA_EXEC_DEPENDENCY == 4 && 2 * GPA_MEMORY_DEPENDENCY == 6 && 2 * GPA_SYNC == 10 &&
+                    2 * GPA_CONSTANT_MEMORY_DEPENDENCY == 12,
+                "dependency-class words 4-7 and 10-13");
+  const int lane = threadIdx.x & 31;
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  bool s = false;
+  if (j < P.ni) {
+    const ulonglong2* c = reinterpret_cast<const ulonglong2*>(P.cnt + (size_t)j * kCnt);
+    const ulonglong2 a = c[2], b = c[3], d = c[5], e = c[6];
+    s = (a.x | a.y | b.x | b.y | d.x | d.y | e.x | e.y) != 0ull;
+  }
+  const unsigned m = __ballot_sync(0xffffffffu, s);
+  if (!m) return;
+  unsigned long long base = 0;
+  if (lane == 0) base = atomicAdd(&P.stats[SS_SUSE_N], (unsigned long long)__popc(m));
+  base = __shfl_sync(0xffffffffu, base, 0);
+  if (s) P.suse[base + __popc(m & ((1u << lane) - 1u))] = j;
+}
+
+// Thread per stalled use (from the stalled-use list).
 __global__ void k_search_local(Prog P, Arch A) {
-  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < P.ni; j += gridDim.x * blockDim.x) {
-    if (!stalled(P, j)) continue;
+  const int n_suse = (int)P.stats[SS_SUSE_N];
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n_suse; k += gridDim.x * blockDim.x) {
+    const int j = P.suse[k];
     const int gj = P.guard[j];
     const int b0 = P.instr_block[j];
     const int first = P.block_instr_off[b0];
@@ -350,12 +379,15 @@ __device__ void apportion_use(const Prog& P, const Arch& A, int j, int off, int 
   }
 }
 
+// Thread per stalled use (a use with edges is stalled: searches run for
+// stalled uses only).
 __global__ void k_apportion(Prog P, Arch A, int max_src) {
-  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < P.ni; j += gridDim.x * blockDim.x) {
+  const int n_suse = (int)P.stats[SS_SUSE_N];
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n_suse; k += gridDim.x * blockDim.x) {
+    const int j = P.suse[k];
     const int off = P.edge_off[j];
     int c = P.edge_off[j + 1] - off;
     if (c > kMaxSrc) continue;  // k_apportion_big
-    if (c == 0 && !stalled(P, j)) continue;
     if (off + c > P.edge_cap) { capacity(P, 10); c = 0; }
     int mi[kMaxSrc], md[kMaxSrc], ml[kMaxSrc], sel[kMaxSrc];
     uint32_t mf[kMaxSrc];
@@ -426,8 +458,9 @@ void launch_coverage(const Prog& P, const Arch& A, const SearchArena* tiers, con
                      int sms, int64_t* launches) {
   const int threads = 128;
   const int g_instr = grid_for(P.ni, threads, sms);
+  k_stalled_list<<<std::max(1, (P.ni + 255) / 256), 256, 0, st>>>(P);
   k_search_local<<<g_instr, threads, 0, st>>>(P, A);
-  ++*launches;
+  *launches += 2;
   launch_search(P, A, tiers, fork, st, sms, launches);
   k_coverage<<<g_instr, threads, 0, st>>>(P);
   ++*launches;
@@ -439,8 +472,9 @@ void launch_blame(const Prog& P, const Arch& A, const SearchArena* tiers, const 
   const int g_instr = grid_for(P.ni, threads, sms);
   cudaMemsetAsync(P.head, 0xFF, sizeof(int32_t) * (size_t)P.ni, st);
   k_blame_init<<<grid_for((int64_t)P.ni * kCnt, 256, sms), 256, 0, st>>>(P);
+  k_stalled_list<<<std::max(1, (P.ni + 255) / 256), 256, 0, st>>>(P);
   k_search_local<<<g_instr, threads, 0, st>>>(P, A);
-  *launches += 2;
+  *launches += 3;
   launch_search(P, A, tiers, fork, st, sms, launches);
   k_merge_count<<<g_instr, threads, 0, st>>>(P, max_src);
   k_merge_big<<<sms, 32, 0, st>>>(P, max_src);

@@ -543,6 +543,7 @@ static gpa_status alloc_program(const gpa_program_desc* d, ProgramRec* R, int ti
   P.diag = 0;
   TRY(dev_alloc(R, &P.edge_off, ni + 1));
   TRY(dev_alloc(R, &P.big_use, ni));
+  TRY(dev_alloc(R, &P.suse, ni));
   P.edge_cnt = P.edge_off;
   P.edge_cap = P.raw_cap;
   TRY(dev_alloc(R, &P.e_use, (size_t)P.edge_cap));
