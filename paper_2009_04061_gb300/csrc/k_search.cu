@@ -624,7 +624,7 @@ __device__ bool group_search(const G& g, const Prog& P, const Arch& A, const Are
   // latency, completes the graph. Both run in this one loop, so the wave code
   // exists once in the kernel (the search kernel is bound by instruction fetch
   // when its warps spread over a larger body).
-  bool cand = false, pass_b = false;
+  bool cand = false, pass_b = false, grew_b = false;
   const bool serial_a = G::kSize == 32 && tier == 1;
   if (serial_a) {
     if (me == 0) serial_pass_a();
@@ -647,6 +647,7 @@ __device__ bool group_search(const G& g, const Prog& P, const Arch& A, const Are
   while (!ctr[4]) {
     const int cnt = serial_a && !pass_b ? 0 : take_wave(pass_b ? -1 : bound);
     if (cnt > 0) {
+      grew_b |= pass_b;
       expand_list(list, cnt, !pass_b);
       if (ctr[4]) break;
       // pass A relaxed the wave's edges as they were linked; carry on from the
@@ -694,16 +695,19 @@ __device__ bool group_search(const G& g, const Prog& P, const Arch& A, const Are
   }
   if (!cand && !P.diag) return true;
 
-  // Shortest distance with parents, and fewest back edges, over the whole graph.
+  // Shortest distance with parents, and fewest back edges, over the whole
+  // graph. When pass B expanded no node, every edge of the graph was relaxed
+  // to the fixpoint in pass A, whose (distance, parent) minimum over the same
+  // edges is this one: only the back edges are counted then.
   for (int u = me; u < n; u += G::kSize) {
-    a.dpk[u] = u == 0 ? 0ull : (((unsigned long long)kInf << 32) | 0xFFFFFFFFull);
+    if (grew_b) a.dpk[u] = u == 0 ? 0ull : (((unsigned long long)kInf << 32) | 0xFFFFFFFFull);
     a.k[u] = u == 0 ? 0 : kInf;
     a.fl[u] &= ~8;
   }
   if (me == 0) a.q[0] = 0;
   g.sync();
 #pragma unroll 1
-  for (int mode = 0; mode < 2; ++mode) relax_from(a.q, 1, mode);
+  for (int mode = grew_b ? 0 : 1; mode < 2; ++mode) relax_from(a.q, 1, mode);
   phase(1);
 
   // Sources: a warp-synchronous hash keyed by instruction gives each source an
