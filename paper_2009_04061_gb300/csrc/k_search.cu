@@ -607,13 +607,16 @@ __device__ bool group_search(const G& g, const Prog& P, const Arch& A, const Are
         if (ctr[4]) break;
       }
       if (du >= kInf) continue;
+      // distance with parent, and fewest back edges, relaxed together
       const unsigned long long nd = ((unsigned long long)(du + wout(u)) << 32) | (unsigned)u;
+      const int ku = a.k[u];
       for (int e = a.e0[u]; e < a.e1[u]; ++e) {
         const int v = a.eto[e] & 0x7FFFFFFF;
-        if (nd < a.dpk[v]) {
-          a.dpk[v] = nd;
-          if ((a.fl[v] & kExpanded) || (int)(nd >> 32) <= bound) push(v);
-        }
+        const int nk = ku + (int)((uint32_t)a.eto[e] >> 31);
+        bool better = false;
+        if (nd < a.dpk[v]) { a.dpk[v] = nd; better = true; }
+        if (nk < a.k[v]) { a.k[v] = nk; better = true; }
+        if (better && ((a.fl[v] & kExpanded) || dist_of(a, v) <= bound)) push(v);
       }
     }
     ctr[0] = nn; ctr[1] = ne; ctr[3] = nh;
@@ -698,16 +701,18 @@ __device__ bool group_search(const G& g, const Prog& P, const Arch& A, const Are
   // Shortest distance with parents, and fewest back edges, over the whole
   // graph. When pass B expanded no node, every edge of the graph was relaxed
   // to the fixpoint in pass A, whose (distance, parent) minimum over the same
-  // edges is this one: only the back edges are counted then.
+  // edges is this one; the one-thread pass A relaxes the back-edge counts
+  // along with the distances, so its searches then need neither.
+  const bool fresh_d = grew_b, fresh_k = grew_b || !serial_a;
   for (int u = me; u < n; u += G::kSize) {
-    if (grew_b) a.dpk[u] = u == 0 ? 0ull : (((unsigned long long)kInf << 32) | 0xFFFFFFFFull);
-    a.k[u] = u == 0 ? 0 : kInf;
+    if (fresh_d) a.dpk[u] = u == 0 ? 0ull : (((unsigned long long)kInf << 32) | 0xFFFFFFFFull);
+    if (fresh_k) a.k[u] = u == 0 ? 0 : kInf;
     a.fl[u] &= ~8;
   }
   if (me == 0) a.q[0] = 0;
   g.sync();
 #pragma unroll 1
-  for (int mode = grew_b ? 0 : 1; mode < 2; ++mode) relax_from(a.q, 1, mode);
+  for (int mode = fresh_d ? 0 : 1; mode < (fresh_k ? 2 : 1); ++mode) relax_from(a.q, 1, mode);
   phase(1);
 
   // Sources: a warp-synchronous hash keyed by instruction gives each source an
