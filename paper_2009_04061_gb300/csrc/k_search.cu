@@ -875,10 +875,40 @@ __device__ bool group_search(const G& g, const Prog& P, const Arch& A, const Are
       const int b = wg >= 0 ? a.wneed[wg] : 0;
       return b ? ~(1u << (b - 1)) : 0xFFFFFFFFu;
     };
+    // A first-tier search propagates by one thread with a worklist ring over
+    // q (a node is in it at most once at a time, flag 8): the same fixpoint
+    // as the frontier rounds below, without a round's barriers and counters.
+    if (serial_a && me == 0) {
+      int* ring = a.q;
+      int head = 0, tail = 1, inq = 1;
+      ring[0] = 0;
+      a.fl[0] |= 8;
+      while (inq > 0) {
+        const int u = ring[head];
+        head = head + 1 == a.N ? 0 : head + 1;
+        --inq;
+        a.fl[u] &= ~8;
+        const unsigned m = (unsigned)reach[u] & pass_mask(u);
+        if (!m || !edges_ok(u, n)) continue;
+        for (int e = a.e0[u]; e < a.e1[u]; ++e) {
+          const int v = a.eto[e] & 0x7FFFFFFF;
+          if (!target_ok(v, n)) break;
+          const unsigned add = m & ~(unsigned)reach[v];
+          if (!add) continue;
+          reach[v] |= (int)add;
+          if (!(a.fl[v] & 8)) {
+            a.fl[v] |= 8;
+            ring[tail] = v;
+            tail = tail + 1 == a.N ? 0 : tail + 1;
+            ++inq;
+          }
+        }
+      }
+    }
     int* cur = a.q;
     int* nxt = a.tmp;
     if (me == 0) { cur[0] = 0; ctr[5] = 0; }
-    int fsize = 1;
+    int fsize = serial_a ? 0 : 1;
     g.sync();
     while (fsize > 0) {
       // Clear the queued flags of the whole frontier first: bits that arrive
@@ -956,45 +986,80 @@ __device__ bool group_search(const G& g, const Prog& P, const Arch& A, const Are
       if (!((uint32_t)a.eto[e] >> 31)) atomicAdd(&a.ord[a.eto[e] & 0x7FFFFFFF], 1);
   if (me == 0) a.dl[0] = 0;
   g.sync();
-  for (int l = 0; l <= maxK; ++l) {
-    int* dll = a.dl + (int64_t)l * a.N;
-    if (me == 0) ctr[5] = 0;
+  if (serial_a) {
+    // A first-tier search runs the layers by one thread: Kahn's order with a
+    // queue over q (each node enters a layer's queue once, when its last
+    // forward in-edge is taken), the nodes' lengths read once into tmp.
+    for (int u = me; u < n; u += G::kSize) a.tmp[u] = wout(u);
     g.sync();
-    for (int u = me; u < n; u += G::kSize) {
-      a.seen[u] = a.ord[u];  // remaining forward in-edges
-      if (a.ord[u] == 0) a.q[atomicAdd((int*)&a.ctr[5], 1)] = u;
-    }
-    g.sync();
-    int fsize = ctr[5];
-    int* cur = a.q;
-    int* nxt = a.tmp;
-    g.sync();
-    if (me == 0) ctr[5] = 0;
-    g.sync();
-    while (fsize > 0) {
-      for (int f0 = 0; f0 < fsize; f0 += G::kSize) {
-        if (f0 + me < fsize) {
-          const int u = cur[f0 + me];
+    if (me == 0) {
+      int* ring = a.q;
+      for (int l = 0; l <= maxK; ++l) {
+        int* dll = a.dl + (int64_t)l * a.N;
+        int head = 0, tail = 0;
+        for (int u = 0; u < n; ++u) {
+          a.seen[u] = a.ord[u];  // remaining forward in-edges
+          if (a.ord[u] == 0) ring[tail++] = u;
+        }
+        while (head < tail) {
+          const int u = ring[head++];
           const int cv = dll[u];
-          const int nd = cv + wout(u);
+          const int nd = cv + a.tmp[u];
           for (int e = a.e0[u]; e < a.e1[u]; ++e) {
             const int v = a.eto[e] & 0x7FFFFFFF;
-            const bool back = (uint32_t)a.eto[e] >> 31;
-            if (back) {
-              if (cv >= 0 && l + 1 <= maxK) atomicMax(&a.dl[(int64_t)(l + 1) * a.N + v], nd);
+            if ((uint32_t)a.eto[e] >> 31) {
+              int* t = &a.dl[(int64_t)(l + 1) * a.N + v];
+              if (cv >= 0 && l + 1 <= maxK && nd > *t) *t = nd;
             } else {
-              if (cv >= 0) atomicMax(&dll[v], nd);
-              if (atomicSub(&a.seen[v], 1) == 1) nxt[atomicAdd((int*)&a.ctr[5], 1)] = v;
+              if (cv >= 0 && nd > dll[v]) dll[v] = nd;
+              if (--a.seen[v] == 0 && tail < a.N) ring[tail++] = v;
             }
           }
         }
       }
+    }
+    g.sync();
+  } else {
+    for (int l = 0; l <= maxK; ++l) {
+      int* dll = a.dl + (int64_t)l * a.N;
+      if (me == 0) ctr[5] = 0;
       g.sync();
-      fsize = ctr[5];
+      for (int u = me; u < n; u += G::kSize) {
+        a.seen[u] = a.ord[u];  // remaining forward in-edges
+        if (a.ord[u] == 0) a.q[atomicAdd((int*)&a.ctr[5], 1)] = u;
+      }
+      g.sync();
+      int fsize = ctr[5];
+      int* cur = a.q;
+      int* nxt = a.tmp;
       g.sync();
       if (me == 0) ctr[5] = 0;
-      int* sw = cur; cur = nxt; nxt = sw;
       g.sync();
+      while (fsize > 0) {
+        for (int f0 = 0; f0 < fsize; f0 += G::kSize) {
+          if (f0 + me < fsize) {
+            const int u = cur[f0 + me];
+            const int cv = dll[u];
+            const int nd = cv + wout(u);
+            for (int e = a.e0[u]; e < a.e1[u]; ++e) {
+              const int v = a.eto[e] & 0x7FFFFFFF;
+              const bool back = (uint32_t)a.eto[e] >> 31;
+              if (back) {
+                if (cv >= 0 && l + 1 <= maxK) atomicMax(&a.dl[(int64_t)(l + 1) * a.N + v], nd);
+              } else {
+                if (cv >= 0) atomicMax(&dll[v], nd);
+                if (atomicSub(&a.seen[v], 1) == 1) nxt[atomicAdd((int*)&a.ctr[5], 1)] = v;
+              }
+            }
+          }
+        }
+        g.sync();
+        fsize = ctr[5];
+        g.sync();
+        if (me == 0) ctr[5] = 0;
+        int* sw = cur; cur = nxt; nxt = sw;
+        g.sync();
+      }
     }
   }
   for (int m = me; m < nsrc; m += G::kSize) {
