@@ -278,6 +278,24 @@ def gpa_blame(ctx, pid, stream=None):
     _check(library().gpa_blame(ctx, pid, _stream(stream)), "gpa_blame")
 
 
+def advice_buffers(shape, pinned: bool = False) -> dict:
+    """Host arrays for one program's advice, shape = (n_functions, n_loops, n_lines),
+    to pass as `out` to gpa_advise / gpa_get_advice on every step instead of new
+    arrays each call. pinned: page-locked host memory (torch), which the device
+    writes at the host link's rate; fresh pageable arrays are paged in during the
+    copy."""
+    b = _advice_buffers(shape)
+    if not pinned:
+        return b
+    import torch
+    out = {}
+    for k, v in b.items():
+        t = torch.empty(v.nbytes, dtype=torch.uint8).pin_memory()
+        out[k] = t.numpy().view(v.dtype).reshape(v.shape)  # the array's base keeps the tensor alive
+        out[k][...] = 0
+    return out
+
+
 def _advice_buffers(shape):
     nf, nl, nlines = shape
     return dict(totals=np.zeros((nf, 4), np.uint64), matched=np.zeros((nf, NUM_OPT), np.uint64),
@@ -292,6 +310,7 @@ def _advice_buffers(shape):
 
 def _trim(b, shape):
     nf, nl, nlines = shape
+    b = dict(b)
     for k in ("loop_active", "loop_matched", "loop_speedup"):
         b[k] = b[k][:nl]
     for k in ("line_stall", "line_latency"):
@@ -299,12 +318,27 @@ def _trim(b, shape):
     return b
 
 
-def gpa_advise(ctx, pid, shape=None, stream=None):
-    """shape = (n_functions, n_loops, n_lines) to fetch results, or None to keep them on the device."""
+def _advice_out(shape, out):
+    """`out` (from advice_buffers) checked against shape, or new arrays."""
+    ref = _advice_buffers(shape)
+    if out is None:
+        return ref
+    for k in _ADV:
+        a = out.get(k)
+        if not isinstance(a, np.ndarray) or a.dtype != ref[k].dtype or a.shape != ref[k].shape or \
+                not a.flags.c_contiguous or not a.flags.writeable:
+            raise ValueError(f"advice buffer {k!r}: expected a writable contiguous {ref[k].dtype} array "
+                             f"of shape {ref[k].shape}")
+    return out
+
+
+def gpa_advise(ctx, pid, shape=None, stream=None, out=None):
+    """shape = (n_functions, n_loops, n_lines) to fetch results, or None to keep them on
+    the device; out: arrays from advice_buffers(shape) to fill (else new ones)."""
     if shape is None:
         _check(library().gpa_advise(ctx, pid, None, _stream(stream)), "gpa_advise")
         return None
-    b = _advice_buffers(shape)
+    b = _advice_out(shape, out)
     adv = gpa_advice(*[_p(b[k]) for k in _ADV])
     _check(library().gpa_advise(ctx, pid, ctypes.byref(adv), _stream(stream)), "gpa_advise")
     return _trim(b, shape)
@@ -332,8 +366,8 @@ def gpa_sm_model_of_device(device: int = 0) -> dict:
     return {k: int(getattr(m, k)) for k in _SM_FIELDS}
 
 
-def gpa_get_advice(ctx, pid, shape, stream=None):
-    b = _advice_buffers(shape)
+def gpa_get_advice(ctx, pid, shape, stream=None, out=None):
+    b = _advice_out(shape, out)
     adv = gpa_advice(*[_p(b[k]) for k in _ADV])
     _check(library().gpa_get_advice(ctx, pid, ctypes.byref(adv), _stream(stream)), "gpa_get_advice")
     return _trim(b, shape)
@@ -513,8 +547,11 @@ class Program:
     def blame(self, stream=None):
         gpa_blame(self.h, self.pid, stream)
 
-    def advise(self, fetch: bool = True, stream=None):
-        return gpa_advise(self.h, self.pid, self.shape if fetch else None, stream)
+    def advise(self, fetch: bool = True, stream=None, out=None):
+        return gpa_advise(self.h, self.pid, self.shape if fetch else None, stream, out)
+
+    def advice_buffers(self, pinned: bool = False) -> dict:
+        return advice_buffers(self.shape, pinned)
 
     def status(self, stream=None):
         return gpa_sync_status(self.h, self.pid, stream)
@@ -537,8 +574,8 @@ class Program:
     def launch_step(self, stream=None):
         gpa_step_launch(self.h, self.pid, stream)
 
-    def get_advice(self, stream=None):
-        return gpa_get_advice(self.h, self.pid, self.shape, stream)
+    def get_advice(self, stream=None, out=None):
+        return gpa_get_advice(self.h, self.pid, self.shape, stream, out)
 
     def search_profile(self, stream=None):
         return gpa_get_search_profile(self.h, self.pid, stream)

@@ -36,3 +36,20 @@ def test_invalid_arguments_are_rejected_without_a_device():
     assert lib.gpa_destroy(None) == -1
     assert lib.gpa_arch_default(None) == -1
     assert lib.gpa_launch_count(None) == -1
+
+
+def test_advice_buffers_are_checked_before_use():
+    """Reusable advice arrays must match the program's shapes and dtypes; a mismatch is
+    refused before the library sees a pointer."""
+    import numpy as np
+    import pytest
+    from paper_2009_04061_gb300 import gpa
+    shape = (3, 2, 5)
+    b = gpa.advice_buffers(shape)
+    assert gpa._advice_out(shape, b) is b
+    assert b["hot"].shape == (3, gpa.NUM_OPT, 5, 6) and b["line_stall"].shape == (5,)
+    bad = dict(b, speedup=np.zeros((3, gpa.NUM_OPT), np.float32))
+    with pytest.raises(ValueError):
+        gpa._advice_out(shape, bad)
+    with pytest.raises(ValueError):
+        gpa._advice_out((4, 2, 5), b)

@@ -269,6 +269,30 @@ def test_first_tier_warp_counts_agree():
             g.Context(ARCH, dict(small_search_warps=bad))
 
 
+def test_advice_into_reused_pinned_buffers(ctx):
+    """Advice copied into one set of pinned host arrays, step after step, equals advice
+    copied into fresh arrays."""
+    rng = np.random.default_rng(23)
+    P = synth.make_program(synth.batched_params(12, rng, 23), 1.0)
+    s = P.samples(500_000, seed=23)
+    d = dev(s)
+    prog = ctx.load_program(P)
+    try:
+        bufs = prog.advice_buffers(pinned=True)
+        for _ in range(2):
+            prog.reset()
+            prog.ingest(d)
+            prog.blame()
+            got = prog.advise(fetch=True, out=bufs)
+            ref = prog.get_advice()
+            assert set(got) == set(ref)
+            for k in ref:
+                assert np.array_equal(got[k], ref[k], equal_nan=True), k
+            bufs["speedup"][...] = 0.0  # the next step overwrites every entry
+    finally:
+        prog.unload()
+
+
 def test_tier_hints_on_repeated_steps():
     """Searches that outgrew a tier are queued straight for the bigger one on later
     steps of the same program; every step gives the oracle's results."""
