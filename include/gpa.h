@@ -121,7 +121,7 @@ typedef struct {
   int32_t large_search_nodes;   /* a global-memory search that reached this many nodes is started
                                    before the others on later steps of its program; 0 = 1024 */
   int32_t hist_chunk;           /* aggregation variant 0: tiles per claimed chunk, 0 = 24 (max 4096) */
-  int32_t reach_schedule;       /* reaching-definitions fixpoint: 0 (default) = a warp per function staged
+  int32_t reach_schedule;       /* reaching-definitions fixpoint: 0 (default) = a CTA per function staged
                                    in shared memory (launches by size class; functions beyond 200 KB of
                                    stage take the windowed kernel); 1 = the windowed kernel for every
                                    function (a lane per basic block, windows of 32 blocks in global

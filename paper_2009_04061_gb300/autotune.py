@@ -9,7 +9,7 @@ tried with the best values found so far for the others):
   grid-strided hash kernel of one of three CTA shapes and hash sizes);
 - aggregation tile chunk: tiles of 8,192 samples an SM claims at a time (the
   window kernel's scheduling grain);
-- reaching-definitions schedule: a warp per function staged in shared memory
+- reaching-definitions schedule: a CTA per function staged in shared memory
   (launched by size class) against the windowed kernel, a lane per basic block
   in windows of 32 blocks, for every function;
 - search tiers: the node capacity of the first tier's shared-memory arenas, the
