@@ -11,7 +11,10 @@
 // nodes and sources into open-addressing hashes together, relax distances and
 // propagate reachability bits over frontiers with atomics, and run the
 // layered longest paths as level-synchronous frontiers; rank 0 only resets
-// counters between steps.
+// counters between steps. The first tier's searches (at most 64 nodes, two or
+// three nodes a wave) run pass A, rule 2's reachability and the longest paths
+// on one thread instead (worklist queues reaching the same fixpoints): there
+// the warp-wide protocol of a wave cost more than the work it spread.
 //
 // Node 0 is the part of j's block above j, already scanned by the local pass
 // (its sources are settled there). A node's d is the shortest distance from
@@ -19,7 +22,8 @@
 // order up to `bound`, the largest latency of any def of r in the function: a
 // source farther than that fails rule 3 whatever the rest of the graph holds.
 // Only if some source is within its latency does pass B complete the graph,
-// which rule 2 and the longest paths need.
+// which rule 2 and the longest paths need; when pass B adds no node, pass A's
+// distances are already those of the whole graph.
 #include <algorithm>
 
 #include "gpa_internal.cuh"
