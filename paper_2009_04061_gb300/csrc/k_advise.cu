@@ -157,7 +157,9 @@ __device__ void parallel_advice(const Prog& P, int f, unsigned long long T, unsi
 __global__ void __launch_bounds__(kThreads) k_advise(Prog P, Arch A) {
   __shared__ unsigned long long red[kAcc][kThreads / 32];
   __shared__ unsigned long long tot[kAcc];
-  __shared__ Cand wtop[kThreads / 32][kHot];  // each warp's top five (v == 0: none)
+  // each warp's top five (v == 0: none), two sets: warp 0 merges one optimizer's
+  // while the other warps fill the other with the next optimizer's
+  __shared__ Cand wtop[2][kThreads / 32][kHot];
   __shared__ int s_f;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
@@ -274,17 +276,17 @@ __global__ void __launch_bounds__(kThreads) k_advise(Prog P, Arch A) {
       for (int h = 0; h < kHot; ++h) {
         Cand b = ptr < nt ? top[ptr] : Cand{0ull, 0, 0, 0};
         int owner = lane;
-        for (int o = 16; o > 0; o >>= 1) {
+        for (int sh = 16; sh > 0; sh >>= 1) {
           Cand y;
-          y.v = __shfl_xor_sync(0xffffffffu, b.v, o);
-          y.def = __shfl_xor_sync(0xffffffffu, b.def, o);
-          y.use = __shfl_xor_sync(0xffffffffu, b.use, o);
-          y.dist = __shfl_xor_sync(0xffffffffu, b.dist, o);
-          const int yo = __shfl_xor_sync(0xffffffffu, owner, o);
+          y.v = __shfl_xor_sync(0xffffffffu, b.v, sh);
+          y.def = __shfl_xor_sync(0xffffffffu, b.def, sh);
+          y.use = __shfl_xor_sync(0xffffffffu, b.use, sh);
+          y.dist = __shfl_xor_sync(0xffffffffu, b.dist, sh);
+          const int yo = __shfl_xor_sync(0xffffffffu, owner, sh);
           if (better(y, b) || (!better(b, y) && yo < owner)) { b = y; owner = yo; }
         }
         if (lane == owner && b.v != 0ull) ++ptr;
-        if (lane == 0) wtop[warp][h] = b;
+        if (lane == 0) wtop[o & 1][warp][h] = b;
       }
       __syncthreads();
       // The CTA's top five: warp 0 merges the warps' sorted lists the same way
@@ -294,15 +296,15 @@ __global__ void __launch_bounds__(kThreads) k_advise(Prog P, Arch A) {
         long long* out = P.a_hot + ((size_t)f * N_O + o) * kHot * 6;
         int wp = 0, nb = 0;
         for (int h = 0; h < kHot; ++h) {
-          Cand b = lane < kThreads / 32 && wp < kHot ? wtop[lane][wp] : Cand{0ull, 0, 0, 0};
+          Cand b = lane < kThreads / 32 && wp < kHot ? wtop[o & 1][lane][wp] : Cand{0ull, 0, 0, 0};
           int owner = lane;
-          for (int o2 = 16; o2 > 0; o2 >>= 1) {
+          for (int sh = 16; sh > 0; sh >>= 1) {
             Cand y;
-            y.v = __shfl_xor_sync(0xffffffffu, b.v, o2);
-            y.def = __shfl_xor_sync(0xffffffffu, b.def, o2);
-            y.use = __shfl_xor_sync(0xffffffffu, b.use, o2);
-            y.dist = __shfl_xor_sync(0xffffffffu, b.dist, o2);
-            const int yo = __shfl_xor_sync(0xffffffffu, owner, o2);
+            y.v = __shfl_xor_sync(0xffffffffu, b.v, sh);
+            y.def = __shfl_xor_sync(0xffffffffu, b.def, sh);
+            y.use = __shfl_xor_sync(0xffffffffu, b.use, sh);
+            y.dist = __shfl_xor_sync(0xffffffffu, b.dist, sh);
+            const int yo = __shfl_xor_sync(0xffffffffu, owner, sh);
             if (better(y, b) || (!better(b, y) && yo < owner)) { b = y; owner = yo; }
           }
           if (lane == owner && b.v != 0ull) ++wp;
@@ -319,7 +321,9 @@ __global__ void __launch_bounds__(kThreads) k_advise(Prog P, Arch A) {
         }
         if (lane == 0) P.a_nhot[(size_t)f * N_O + o] = nb;
       }
-      __syncthreads();
+      // No barrier here: the next pass fills the other set, and warp 0 reaches
+      // the barrier after that pass only once this merge is done, before the
+      // pass after next fills this set again.
     }
     // Eq. 5 per loop scope of this function (its loop counters were only touched by this CTA).
     __threadfence_block();
