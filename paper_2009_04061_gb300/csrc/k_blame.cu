@@ -458,8 +458,12 @@ void launch_coverage(const Prog& P, const Arch& A, const SearchArena* tiers, con
                      int sms, int64_t* launches) {
   const int threads = 128;
   const int g_instr = grid_for(P.ni, threads, sms);
+  // The per-use kernels take the stalled-use list (its length is known on the
+  // device only): enough CTAs for every SM to hold as many warps as their
+  // registers allow, each thread taking about one use on the batched workload.
+  const int g_use = std::max(1, std::min(grid_for(P.ni, threads, sms) * 4, (P.ni + threads - 1) / threads));
   k_stalled_list<<<std::max(1, (P.ni + 255) / 256), 256, 0, st>>>(P);
-  k_search_local<<<g_instr, threads, 0, st>>>(P, A);
+  k_search_local<<<g_use, threads, 0, st>>>(P, A);
   *launches += 2;
   launch_search(P, A, tiers, fork, st, sms, launches);
   k_coverage<<<g_instr, threads, 0, st>>>(P);
@@ -470,17 +474,21 @@ void launch_blame(const Prog& P, const Arch& A, const SearchArena* tiers, const 
                   int32_t* scan_tmp, cudaStream_t st, int sms, int64_t* launches) {
   const int threads = 128;
   const int g_instr = grid_for(P.ni, threads, sms);
+  // The per-use kernels take the stalled-use list (its length is known on the
+  // device only): enough CTAs for every SM to hold as many warps as their
+  // registers allow, each thread taking about one use on the batched workload.
+  const int g_use = std::max(1, std::min(grid_for(P.ni, threads, sms) * 4, (P.ni + threads - 1) / threads));
   cudaMemsetAsync(P.head, 0xFF, sizeof(int32_t) * (size_t)P.ni, st);
   k_blame_init<<<grid_for((int64_t)P.ni * kCnt, 256, sms), 256, 0, st>>>(P);
   k_stalled_list<<<std::max(1, (P.ni + 255) / 256), 256, 0, st>>>(P);
-  k_search_local<<<g_instr, threads, 0, st>>>(P, A);
+  k_search_local<<<g_use, threads, 0, st>>>(P, A);
   *launches += 3;
   launch_search(P, A, tiers, fork, st, sms, launches);
   k_merge_count<<<g_instr, threads, 0, st>>>(P, max_src);
   k_merge_big<<<sms, 32, 0, st>>>(P, max_src);
   *launches += 2;
   scan_exclusive_inplace(P.edge_off, P.ni, scan_tmp, st, launches);
-  k_apportion<<<g_instr, threads, 0, st>>>(P, A, max_src);
+  k_apportion<<<g_use, threads, 0, st>>>(P, A, max_src);
   const size_t big_smem = (size_t)kBigSrc * (16 + 8 + 8 + 4 * 5);
   allow_max_smem(k_apportion_big);
   k_apportion_big<<<sms, 32, big_smem, st>>>(P, A);
