@@ -263,16 +263,22 @@ const char* gpa_status_string(gpa_status s);
  * STG, LDS, STS, LDL, STL, LDC, ATOM, F2F, MUFU, DFMA, EXIT, CALL in that order. */
 gpa_status gpa_arch_default(gpa_arch_desc* arch);
 
-/* Creates a context on the current CUDA device. arch and opts are copied;
- * opts may be NULL. *out owns device memory until gpa_destroy. */
+/* Creates a context on the current CUDA device. arch (the architecture table of
+ * Sec. 3 "Architectural features", with the latencies the latency rule of Sec. 4
+ * uses) and opts are copied; opts may be NULL. *out owns device memory until
+ * gpa_destroy. */
 gpa_status gpa_create(const gpa_arch_desc* arch, const gpa_options* opts, gpa_ctx** out);
 
-/* Synchronizes the device, frees every program and the context. */
+/* Synchronizes the device, frees every program and the context (resource
+ * management; the paper has no counterpart). */
 gpa_status gpa_destroy(gpa_ctx* ctx);
 
 /* Validates and copies a program to the device and allocates its counters
  * and result buffers (stream-ordered allocations on the context's own build
  * stream; returns when they are done, without waiting for other streams).
+ * The program is what the paper's static analyzer provides to the dynamic one
+ * (Sec. 3: control flow graphs, loop nests, line maps; Sec. 2.2 and Sec. 4:
+ * per-instruction operands, virtual barrier registers, predicates).
  * *out receives the program id. */
 gpa_status gpa_load_program(gpa_ctx* ctx, const gpa_program_desc* prog, gpa_pid* out);
 
@@ -285,7 +291,8 @@ gpa_status gpa_program_footprint(gpa_ctx* ctx, const gpa_program_desc* prog, int
 /* Device bytes requested for a loaded program (equal to its footprint). */
 gpa_status gpa_program_bytes(gpa_ctx* ctx, gpa_pid pid, int64_t* bytes);
 
-/* Frees a program (synchronizes the device first). */
+/* Frees a program (synchronizes the device first; resource management, no
+ * counterpart in the paper). */
 gpa_status gpa_unload_program(gpa_ctx* ctx, gpa_pid pid);
 
 /* Frees a program in stream order: its device memory is released once the
@@ -414,14 +421,18 @@ gpa_status gpa_step_launch(gpa_ctx* ctx, gpa_pid pid, gpa_stream stream);
 gpa_status gpa_get_search_profile(gpa_ctx* ctx, gpa_pid pid, uint64_t* out, gpa_stream stream);
 
 /* Parity getters: synchronize stream and copy device results to host memory.
- * counts[n_instr*24]: counts[pc*24 + class*2 + latency]; *invalid may be NULL. */
+ * counts[n_instr*24]: the aggregated samples of Sec. 2.1 (Fig. 1), counts[pc*24 +
+ * class*2 + latency]; *invalid may be NULL. */
 gpa_status gpa_get_counts(gpa_ctx* ctx, gpa_pid pid, uint64_t* counts, uint64_t* invalid, gpa_stream stream);
-/* rin/rout[n_blocks*9]: bit r of block b's 9 words set iff some def of resource r
+/* rin/rout[n_blocks*9]: reaching definitions at resource granularity (Sec. 4,
+ * "Backward slicing"): bit r of block b's 9 words set iff some def of resource r
  * reaches the entry/exit of b. */
 gpa_status gpa_get_reaching(gpa_ctx* ctx, gpa_pid pid, uint32_t* rin, uint32_t* rout, gpa_stream stream);
-/* blame[n_instr*24], same layout as counts. */
+/* blame[n_instr*24], same layout as counts: each instruction's own samples outside
+ * the dependency classes plus what Eq. 1 apportions to it (Sec. 4). */
 gpa_status gpa_get_blame(gpa_ctx* ctx, gpa_pid pid, uint64_t* blame, gpa_stream stream);
-/* Surviving merged edges, sorted by (use, def). With all arrays NULL, only
+/* The dependency graph after pruning (Sec. 4, Fig. 4b-d): surviving merged edges,
+ * sorted by (use, def). With all arrays NULL, only
  * *n_edges is written. Otherwise each array has room for cap entries:
  * use[], def[] global instruction indices; dmin/dlong shortest and longest
  * source path; flags bit 0 write-after-read, 1 via barrier, 2 via register,
