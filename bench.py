@@ -375,6 +375,59 @@ def large_measure(a, gpa, dev, steps: int = 3) -> dict:
             "generate_s": gen_s}
 
 
+def e2e_overlapped(gpa, arrays, host, opts, stats, sm, dev, reps: int) -> float:
+    """Seconds per step end to end with consecutive steps overlapped, as a user feeding
+    a stream of batches would run them: two contexts, each with the program loaded, its
+    own stream, pinned advice arrays and host thread; step k runs on pair k % 2, so one
+    step's ingest over the host link runs beside the other's blame. Every step copies its
+    own samples from pinned host memory and reads its own advice back inside the timed
+    region, through the same calls as the sequential measurement."""
+    import threading
+    import torch
+    arch = synth.default_arch()
+    pairs, errors = [], []
+    try:
+        for _ in range(2):
+            c = gpa.Context(arch, opts or None)
+            p = c.load_program(arrays)
+            p.set_launch_stats(stats, sm)
+            pairs.append((c, p, torch.cuda.Stream(dev), p.advice_buffers(pinned=True)))
+
+        def run(i, k):
+            try:
+                torch.cuda.set_device(dev)  # the current device is per host thread
+                _, p, st, b = pairs[i]
+                for _ in range(k):
+                    p.reset(st)
+                    p.ingest_host(host, stream=st)
+                    p.blame(st)
+                    p.advise(fetch=True, stream=st, out=b)  # synchronizes st
+            except Exception as e:  # noqa: BLE001 (re-raised below)
+                errors.append(e)
+
+        for i in range(2):
+            run(i, 2)  # warm-up: kernels loaded, search tiers known
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        threads = [threading.Thread(target=run, args=(i, reps)) for i in range(2)]
+        for t in threads:
+            t.start()
+        for t in threads:
+            t.join()
+        te = (time.perf_counter() - t0) / (2 * reps)
+        if errors:
+            raise errors[0]
+        for _, p, st, _ in pairs:
+            code, info = p.status(st)
+            if code != 0:
+                raise SystemExit(f"overlapped end to end: device status {code}: {info}")
+        return te
+    finally:
+        for c, p, _, _ in pairs:
+            p.unload()
+            c.close()
+
+
 def run_oracle_once(P, sub, k_funcs, threads: int = 1):
     """Seconds the oracle takes for the bounded sample: the histogram of `sub` and
     the analysis of functions 0..k_funcs-1, on a program cut to those functions.
@@ -482,8 +535,9 @@ def main():
     load_ms = (time.perf_counter() - t_load) * 1e3
     # Seeded launch statistics of the workload's kernels on this GPU's SM model:
     # the advice step also runs the parallel optimizers (Table 2, Eqs. 6-10).
-    prog.set_launch_stats(synth.launch_stats(P.n_functions, a.seed),
-                          gpa.gpa_sm_model_of_device(torch.cuda.current_device()))
+    lstats = synth.launch_stats(P.n_functions, a.seed)
+    sm_model = gpa.gpa_sm_model_of_device(torch.cuda.current_device())
+    prog.set_launch_stats(lstats, sm_model)
     stream = torch.cuda.current_stream(dev)
 
     def step(ev=None):
@@ -603,8 +657,12 @@ def main():
         torch.cuda.synchronize(dev)
         ingest_gbs = 8 * n / (e0.elapsed_time(e1) / 1e3) / 1e9
         h2d = pinned_h2d_gbs(host, dev)
-        e2e = {"value": weak_value(n, te * 1e3, world), "unit": UNIT, "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": d2h,
-               "ms_per_step": te * 1e3,
+        to = reduce_max(e2e_overlapped(gpa, arrays, host, opts, lstats, sm_model, dev, reps), world)
+        e2e = {"value": weak_value(n, to * 1e3, world), "unit": UNIT, "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": d2h,
+               "ms_per_step": to * 1e3,
+               "schedule": "consecutive steps overlapped: two contexts, steps alternating on two streams and host "
+                           "threads; each step copies its samples in and its advice out inside the timed region",
+               "sequential": {"value": weak_value(n, te * 1e3, world), "ms_per_step": te * 1e3},
                "host_link": {"ingest_gbs": ingest_gbs, "pinned_h2d_gbs": h2d, "frac": ingest_gbs / h2d}}
 
     cpu = None

@@ -316,7 +316,8 @@ gpa_status gpa_ingest_samples(gpa_ctx* ctx, gpa_pid pid, const uint64_t* dev_sam
 
 /* Step (a) from host memory (8-byte aligned). Pinned host memory that the
  * current device can address is read by the aggregation kernel directly over
- * the host link; other memory is copied in chunks through library staging
+ * the host link, on at most 32 SMs (the link needs no more; work on other
+ * streams can use the rest); other memory is copied in chunks through library staging
  * buffers, the copy of one chunk overlapping the aggregation of the last.
  * Returns when the work is enqueued; host_samples must stay valid and
  * unchanged until stream completes this call. */

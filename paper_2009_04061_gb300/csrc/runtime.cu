@@ -726,6 +726,8 @@ gpa_status gpa_ingest_samples(gpa_ctx* ctx, gpa_pid pid, const uint64_t* dev_sam
   return GPA_OK;
 }
 
+constexpr int kHostIngestCtas = 32;  // SMs an ingest over the host link takes
+
 gpa_status gpa_ingest_host_samples(gpa_ctx* ctx, gpa_pid pid, const uint64_t* host, size_t n, gpa_stream stream) {
   ProgramRec* R = find(ctx, pid);
   if (!R) return GPA_ERR_NO_PROGRAM;
@@ -734,14 +736,18 @@ gpa_status gpa_ingest_host_samples(gpa_ctx* ctx, gpa_pid pid, const uint64_t* ho
   cudaStream_t st = (cudaStream_t)stream;
   // Pinned host memory that this device can address (page-locked allocations
   // are mapped under unified addressing) is read by the aggregation kernel
-  // itself over the host link: no staging buffer, no copy engine. Other
-  // memory goes through the staging buffers.
+  // itself over the host link: no staging buffer, no copy engine. The link
+  // (about 210 GB/s) needs far fewer SMs than HBM (about 23 GB/s an SM), so the
+  // launch takes at most kHostIngestCtas of them and leaves the rest to other
+  // work, such as the blame of the batch before. Other memory goes through the
+  // staging buffers.
   cudaPointerAttributes at{};
   int dev = -1;
   if (cudaPointerGetAttributes(&at, host) == cudaSuccess && at.type == cudaMemoryTypeHost && at.devicePointer &&
       cudaGetDevice(&dev) == cudaSuccess && dev == ctx->device) {
-    launch_histogram(R->P, static_cast<const uint64_t*>(at.devicePointer), n, st, ctx->sms, &ctx->launches,
-                     ctx->opts.hist_variant, ctx->opts.hist_chunk);
+    launch_histogram(R->P, static_cast<const uint64_t*>(at.devicePointer), n, st,
+                     std::min(ctx->sms, kHostIngestCtas), &ctx->launches, ctx->opts.hist_variant,
+                     ctx->opts.hist_chunk);
     CK(cudaGetLastError());
     return GPA_OK;
   }
