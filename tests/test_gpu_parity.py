@@ -460,8 +460,12 @@ def test_fourth_tier_program_arena():
 
 def test_full_batched_workload_sampled_functions(ctx):
     """The bench's workload at full size (2,000 functions, 5e8 samples): invariants over the
-    whole program, and five functions (smallest to largest) against the oracle element by element."""
+    whole program, and a stratified sample of functions (every 10th by size, plus the sizes
+    nearest 60, 400, 1,500, 5,000 and 20,000 instructions: about 205, so every search tier's
+    size range is met) against the oracle element by element: counts, RIN/ROUT, blame,
+    edges with shares, and advice."""
     import torch
+    from concurrent.futures import ThreadPoolExecutor
     ps, n, kz = synth.workload("batched")
     P = synth.make_program(ps, kz)
     host = torch.empty(n, dtype=torch.int64)
@@ -471,22 +475,33 @@ def test_full_batched_workload_sampled_functions(ctx):
     assert int(g["counts"].sum()) + g["invalid"] == n
     assert np.array_equal(g["blame"].sum(0), g["counts"].sum(0))          # conservation per class and flag
     sizes = np.diff(P.func_instr_off)
-    picks = sorted({int(np.argmin(np.abs(sizes - t))) for t in (60, 400, 1500, 5000, 20000)})
-    k = s >> np.uint64(48)
-    for f in picks:
-        sf = s[k == np.uint64(f)]
-        cnt, bad = oracle.histogram(P, sf)
-        R = oracle.analyze(P, ARCH, cnt, f, f + 1)
+    by_size = np.argsort(sizes, kind="stable")
+    picks = {int(np.argmin(np.abs(sizes - t))) for t in (60, 400, 1500, 5000, 20000)}
+    picks |= {int(f) for f in by_size[::10]}
+    picks = sorted(picks)
+    # The oracle's histogram of the picked functions' samples (every sample of a picked
+    # function is in the subset, so its counters are complete), in slices on host threads.
+    keep = np.zeros(P.n_functions + 1, bool)  # the last entry: kernel ids past the program
+    keep[picks] = True
+    kid = np.minimum(s >> np.uint64(48), np.uint64(P.n_functions)).astype(np.int64)
+    sub = s[keep[kid]]
+    del kid
+    with ThreadPoolExecutor(8) as ex:
+        parts = list(ex.map(lambda x: oracle.histogram(P, x)[0], np.array_split(sub, 4)))
+        cnt = parts[0]
+        for c in parts[1:]:
+            cnt += c
+        del parts
+        results = list(ex.map(lambda f: (oracle.analyze(P, ARCH, cnt, f, f + 1), oracle.reaching(P, f, f + 1)), picks))
+    for f, (R, (rin, rout)) in zip(picks, results):
         i0, i1 = int(P.func_instr_off[f]), int(P.func_instr_off[f + 1])
         b0, b1 = int(P.func_block_off[f]), int(P.func_block_off[f + 1])
         l0, l1 = int(P.func_loop_off[f]), int(P.func_loop_off[f + 1])
         assert np.array_equal(g["counts"][i0:i1], cnt[i0:i1]), f
-        rin, rout = oracle.reaching(P, f, f + 1)
         assert np.array_equal(g["rin"][b0:b1], rin) and np.array_equal(g["rout"][b0:b1], rout), f
         assert np.array_equal(g["blame"][i0:i1], R["blame"]), f
         assert_edges_equal(g["edges"], R["edges"], i0, i1)
-        ga = {key: v for key, v in g["advice"].items()}
-        assert_advice_equal(ga, R, f, f + 1, l0, l1)
+        assert_advice_equal(dict(g["advice"]), R, f, f + 1, l0, l1)
 
 
 def test_graph_step_matches_eager(ctx):
